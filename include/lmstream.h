@@ -1,0 +1,234 @@
+/*
+ * lmstream.h — C ABI of the B300 micro-batch stream engine.
+ *
+ * The engine runs the data-parallel hot path of LMStream's micro-batch stream
+ * queries on one GPU: every pushed micro-batch is filtered and projected, each
+ * surviving event is given its tumbling or sliding window(s), the events are
+ * group-by aggregated (count, int64 / double sum, min, max, avg) into window
+ * state that stays in device memory, and every window that the watermark has
+ * passed is emitted.  The paper states the problem as micro-batches of
+ * datasets that are processed as one unit (Section III-B, Table I) by SQL
+ * queries over windows (Table III); it leaves window semantics to Spark.  The
+ * engine fixes them as follows (event time, ms):
+ *
+ *   - window k of an event: [s, s + size) with s = (floor(ts/slide) - k)*slide,
+ *     k = 0 .. size/slide - 1 (tumbling: slide == size);
+ *   - watermark after a batch: max(previous, max ts of ALL rows of the batch
+ *     - allowed_lateness); a window is emitted once its end <= watermark;
+ *     end-of-stream emits everything;
+ *   - an event is not added to a window that was already emitted; an event all
+ *     of whose windows were emitted is a "late row" and is counted;
+ *   - rows come out ordered by (window_start, key); avg = (double)sum / count.
+ *
+ * Threading: one producer thread per stream calls push_microbatch; any thread
+ * may call poll_results / lms_stream_stats (the stream serialises them).
+ * Memory: the library allocates and owns all device and pinned memory of a
+ * stream; callers own the buffers they pass in and may reuse them as soon as
+ * a call returns.  CUDA errors are latched: the failing call and every later
+ * call return LMS_ECUDA; lms_last_error() gives the message.
+ * Out-parameters are written only when a call returns LMS_OK.
+ */
+#ifndef LMSTREAM_H
+#define LMSTREAM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lms_stream lms_stream; /* opaque; owned by the library */
+typedef int32_t lms_status;
+
+/* Status codes. */
+#define LMS_OK 0
+#define LMS_EINVAL (-1)    /* bad argument or specification */
+#define LMS_ENOMEM (-2)    /* device/pinned allocation failed or state cap exceeded */
+#define LMS_EAGAIN (-3)    /* no result rows available (poll) */
+#define LMS_ETIMEDOUT (-4) /* a bounded device wait ran out */
+#define LMS_ECUDA (-5)     /* a CUDA call failed (latched) */
+#define LMS_ECLOSED (-6)   /* stream already at end-of-stream */
+#define LMS_ERANGE (-7)    /* event time outside the supported span (see origin_ts) */
+#define LMS_EDEVICE (-8)   /* a kernel raised an internal error flag */
+
+/* Value column type. */
+#define LMS_VALUE_INT32 0
+#define LMS_VALUE_FLOAT32 1
+
+/* Columns a filter can test. */
+#define LMS_COL_TS 0    /* int64 event time, ms */
+#define LMS_COL_KEY 1   /* uint32 group-by key */
+#define LMS_COL_VALUE 2 /* int32 or float32 aggregated value */
+#define LMS_COL_TYPE 3  /* uint8 event type (reads as 0 if the stream has none) */
+
+/* Filter operators: `column OP constant`.  Integer columns compare as int64
+ * against filter_i; a float32 value column compares as double against
+ * filter_f (IEEE semantics: NaN passes only NE). */
+#define LMS_OP_NONE 0
+#define LMS_OP_EQ 1
+#define LMS_OP_NE 2
+#define LMS_OP_LT 3
+#define LMS_OP_LE 4
+#define LMS_OP_GT 5
+#define LMS_OP_GE 6
+
+/* Aggregates (bit mask).  All five are always computed; the mask says which
+ * result fields a caller wants (the kernels skip min/max work when unset). */
+#define LMS_AGG_COUNT 1u
+#define LMS_AGG_SUM 2u
+#define LMS_AGG_MIN 4u
+#define LMS_AGG_MAX 8u
+#define LMS_AGG_AVG 16u
+#define LMS_AGG_ALL 31u
+
+/* Where the columns of a pushed batch live. */
+#define LMS_MEM_HOST 0   /* host memory (pinned or pageable); copied in by the call */
+#define LMS_MEM_DEVICE 1 /* device memory of the stream's GPU; read in place */
+
+/* Batch flags. */
+#define LMS_BATCH_EOS 1u /* end of stream: emit every remaining window */
+
+/* origin_ts value that means "the first row of the first pushed batch". */
+#define LMS_ORIGIN_AUTO INT64_MIN
+
+typedef struct lms_stream_config {
+  int32_t device;              /* CUDA device ordinal */
+  int32_t value_type;          /* LMS_VALUE_INT32 or LMS_VALUE_FLOAT32 */
+  int32_t has_type;            /* 1 if batches carry the uint8 type column */
+  int32_t enable_timing;       /* 1: record per-phase CUDA-event times (stats) */
+  int64_t allowed_lateness_ms; /* watermark = max ts - allowed_lateness_ms (>= 0) */
+  int64_t max_batch_rows;      /* sizing hint for the largest push (buffers grow on demand) */
+  uint64_t state_cap_bytes;    /* cap on the stream's device memory, 0 = no cap */
+  void *cuda_stream;           /* cudaStream_t to run on, or NULL: the library creates one */
+  int64_t origin_ts;           /* event-time origin; LMS_ORIGIN_AUTO by default.  Window ids
+                                  are kept relative to it: events must satisfy
+                                  |floor(ts/slide) - floor(origin_ts/slide)| < 2^31 - 1,
+                                  others are dropped and counted (stats.range_rows). */
+  int32_t k1_variant;          /* 0 = default; 1 = no warp aggregation; 2 = warp aggregation */
+  int32_t reserved[7];
+} lms_stream_config;
+
+typedef struct lms_query_spec {
+  int32_t filter_col;     /* LMS_COL_* */
+  int32_t filter_op;      /* LMS_OP_* */
+  int64_t filter_i;       /* constant for integer columns */
+  double filter_f;        /* constant for the float32 value column */
+  int64_t window_size_ms; /* > 0 */
+  int64_t window_slide_ms;/* 0 or == size: tumbling; else size % slide == 0 and
+                             size/slide <= 4096 (sliding) */
+  uint32_t agg_mask;      /* LMS_AGG_* bits; 0 means LMS_AGG_ALL */
+  int32_t reserved;
+} lms_query_spec;
+
+typedef struct lms_batch {
+  int64_t n_rows;       /* rows in the batch (>= 0) */
+  const int64_t *ts;    /* [n_rows] event time, ms */
+  const uint32_t *key;  /* [n_rows] group-by key */
+  const void *value;    /* [n_rows] int32 or float32 per the stream's value_type */
+  const uint8_t *type;  /* [n_rows] or NULL; required iff has_type */
+  int32_t memory;       /* LMS_MEM_HOST or LMS_MEM_DEVICE */
+  uint32_t flags;       /* LMS_BATCH_* */
+  int64_t arrival_ns;   /* caller's arrival timestamp (latency accounting), 0 if unknown */
+} lms_batch;
+
+/* One emitted window-group, 48 bytes.  sum/min/max are integer for an
+ * INT32 stream and floating for a FLOAT32 stream. */
+typedef struct lms_result_row {
+  int64_t window_start; /* ms; the window is [window_start, window_start + size) */
+  int64_t count;
+  union { int64_t i; double f; } sum;
+  double avg;           /* (double)sum / count */
+  uint32_t key;
+  union { int32_t i; float f; } min;
+  union { int32_t i; float f; } max;
+  uint32_t query_id;
+} lms_result_row;
+
+typedef struct lms_stats {
+  uint64_t batches;        /* micro-batches pushed */
+  uint64_t events;         /* rows pushed */
+  uint64_t late_rows;      /* surviving rows all of whose windows were already emitted (all queries) */
+  uint64_t range_rows;     /* rows dropped for lying outside the supported event-time span */
+  uint64_t rows_emitted;   /* result rows produced (all queries) */
+  uint64_t rows_pending;   /* result rows not yet polled (all queries) */
+  int64_t watermark;       /* current watermark (INT64_MIN before the first row) */
+  uint64_t state_groups;   /* (window-pane, key) groups held in device state (all queries) */
+  uint64_t device_bytes;   /* device memory held by the stream */
+  double last_batch_ms;    /* wall time of the last push_microbatch */
+  /* Per-phase device time, summed over batches (only if enable_timing): */
+  double k1_ms;            /* fused filter/window/pre-aggregate pass */
+  double sort_ms;          /* sort + reduce of partial groups into window state */
+  double emit_ms;          /* window enumeration, merge and row emission */
+  double h2d_ms;           /* host-to-device input copies */
+  uint64_t k1_launches;    /* launches of the fused pass */
+  uint64_t kernel_launches;/* all kernel launches of the hot path */
+  double e1_ms;            /* window assembly: distinct-key count per closed window */
+  double e2_ms;            /* window assembly + row write */
+  uint64_t partials;       /* partial groups written by the fused pass (all batches, queries) */
+  uint64_t groups_built;   /* window-state groups produced by the reduce (all batches, queries) */
+} lms_stats;
+
+/* Opens a stream on cfg->device.  Defined by the paper's problem statement
+ * (Section III-B, Table I: a stream is cut into micro-batches that one query
+ * plan processes).  cfg is copied.  Returns LMS_EINVAL for a bad config,
+ * LMS_ECUDA if the device cannot be used.  *out is owned by the caller until
+ * stream_close(). */
+lms_status stream_open(const lms_stream_config *cfg, lms_stream **out);
+
+/* Registers a windowed group-by query (Table III: WHERE filter, window
+ * [range size slide s], GROUPBY key, SUM/AVG/...).  Must precede the first
+ * push.  *query_id receives 0, 1, ... in registration order (at most 8
+ * queries per stream; they run fused over each batch).  LMS_EINVAL if the
+ * window or filter is invalid. */
+lms_status query_register(lms_stream *s, const lms_query_spec *q, int32_t *query_id);
+
+/* Processes one micro-batch (the paper's processing phase, Section III-A)
+ * through every registered query and emits the windows it closes.  Returns
+ * when the results are ready to poll.  Columns are read from host or device
+ * memory per b->memory; the caller keeps ownership.  After a batch with
+ * LMS_BATCH_EOS, further pushes return LMS_ECLOSED.  An empty batch only
+ * advances nothing unless it carries EOS. */
+lms_status push_microbatch(lms_stream *s, const lms_batch *b);
+
+/* Copies up to `cap` of query `query_id`'s emitted rows, oldest first, into
+ * the caller's host buffer `out` and removes them from the stream.
+ * *n_out receives the number copied.  LMS_EAGAIN if there are none (results
+ * are complete when push_microbatch returns, so timeout_ms only bounds the
+ * wait for a concurrent push and may be 0). */
+lms_status poll_results(lms_stream *s, int32_t query_id, lms_result_row *out, size_t cap,
+                        size_t *n_out, int32_t timeout_ms);
+
+/* Waits for outstanding device work, frees every device and pinned buffer
+ * and destroys the stream (and its CUDA stream if the library created it).
+ * `s` is invalid afterwards.  NULL is accepted. */
+lms_status stream_close(lms_stream *s);
+
+/* ---- extras ---------------------------------------------------------- */
+
+/* Counters and timings of the stream (see lms_stats). */
+lms_status lms_stream_stats(lms_stream *s, lms_stats *out);
+
+/* Message of the last error on this stream ("" if none); valid until the
+ * next call on the stream. */
+const char *lms_last_error(lms_stream *s);
+
+/* Device-resident view of query_id's unpolled rows: *rows receives a device
+ * pointer to *n rows in the same order poll_results would return them.  The
+ * view stays valid until the next push, poll or discard on the stream. */
+lms_status lms_results_device(lms_stream *s, int32_t query_id, const lms_result_row **rows,
+                              size_t *n);
+
+/* Drops query_id's unpolled rows (e.g. after consuming them on the device). */
+lms_status lms_results_discard(lms_stream *s, int32_t query_id);
+
+/* Floor division helper the kernels use for window ids, exposed so that host
+ * tests can check it: returns n / d for d >= 1 computed by the invariant
+ * multiply-and-shift method of Granlund & Montgomery (1994). */
+uint64_t lms_udiv_invariant(uint64_t n, uint64_t d);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LMSTREAM_H */

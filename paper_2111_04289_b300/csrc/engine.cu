@@ -1,0 +1,648 @@
+// Host engine behind the C ABI of include/lmstream.h.
+//
+// One lms_stream owns: the registered queries with their device window state
+// (partial-group and state arrays), the scratch shared by the per-query
+// pipelines, the device result buffers, device input buffers for host pushes,
+// and a CUDA stream (its own, or the caller's).  push_microbatch enqueues the
+// whole hot path for the batch — H2D (host input), fused K1, watermark, and per
+// query sort/reduce, window enumeration + emission and carry — and then
+// synchronises once, reads the control blocks back and, only if a device-side
+// capacity check failed, grows the buffer and re-runs the emission.
+#include <algorithm>
+#include <chrono>
+#include <climits>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/lmstream.h"
+#include "lms_internal.h"
+
+namespace lms {
+
+void udiv_constants(unsigned long long d, unsigned long long* magic, int* sh1, int* sh2) {
+  int l = 0;
+  while (l < 64 && (1ull << l) < d) ++l;  // l = ceil(log2 d)
+  const unsigned __int128 two64 = (unsigned __int128)1 << 64;
+  const unsigned __int128 num = two64 * (((unsigned __int128)1 << l) - d);
+  *magic = (unsigned long long)(num / d + 1);
+  *sh1 = l < 1 ? l : 1;
+  *sh2 = l > 1 ? l - 1 : 0;
+}
+}  // namespace lms
+
+using namespace lms;
+
+namespace {
+
+long long floor_div_h(long long a, long long b) {
+  long long q = a / b;
+  if ((a % b != 0) && (a < 0)) --q;
+  return q;
+}
+
+struct QueryHost {
+  lms_query_spec spec{};
+  long long size = 0, slide = 0;
+  int k = 1;
+  QueryDev dev{};
+  unsigned long long cap = 0;  // group capacity of parts/state
+  ResultRowDev* rows = nullptr;
+  unsigned long long rows_cap = 0;
+  unsigned long long rows_read = 0;   // rows already handed out by poll
+  unsigned long long row_base = 0;    // rows in the device buffer (mirror)
+  unsigned long long carried = 0;     // groups carried into the next batch (mirror)
+  unsigned long long n_state = 0;
+  unsigned long long late_rows = 0, range_rows = 0;
+  unsigned long long rows_emitted = 0;
+};
+
+}  // namespace
+
+struct lms_stream {
+  lms_stream_config cfg{};
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  int sms = 148;
+  std::mutex mu;
+  std::string err;
+  lms_status latched = LMS_OK;
+  bool eos_seen = false;
+  bool origin_set = false;
+  long long origin_ts = 0;
+  SCtl* sctl = nullptr;
+  QCtl* qctl = nullptr;  // device array [kMaxQueries]
+  std::vector<QueryHost> qs;
+  Scratch scr{};
+  unsigned long long in_cap = 0;
+  long long* in_ts = nullptr;
+  unsigned* in_key = nullptr;
+  unsigned* in_val = nullptr;
+  unsigned char* in_type = nullptr;
+  unsigned long long dev_bytes = 0;
+  std::vector<std::pair<void*, size_t>> allocs;
+  cudaEvent_t ev[8] = {};
+  cudaEvent_t qev[kMaxQueries][6] = {};  // E1, E2, sort/reduce
+  lms_stats stats{};
+  long long wm = LLONG_MIN;
+};
+
+namespace {
+
+lms_status fail(lms_stream* s, lms_status code, const std::string& msg) {
+  s->err = msg;
+  return code;
+}
+
+lms_status cuda_fail(lms_stream* s, cudaError_t e, const char* what) {
+  s->err = std::string(what) + ": " + cudaGetErrorString(e);
+  s->latched = LMS_ECUDA;
+  return LMS_ECUDA;
+}
+
+#define LMS_CK(call)                                    \
+  do {                                                  \
+    cudaError_t e__ = (call);                           \
+    if (e__ != cudaSuccess) return cuda_fail(s, e__, #call); \
+  } while (0)
+
+lms_status dalloc(lms_stream* s, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (s->cfg.state_cap_bytes && s->dev_bytes + bytes > s->cfg.state_cap_bytes)
+    return fail(s, LMS_ENOMEM, "device memory cap (state_cap_bytes) exceeded");
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(s, LMS_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  s->dev_bytes += bytes;
+  s->allocs.emplace_back(*p, bytes);
+  return LMS_OK;
+}
+
+void dfree(lms_stream* s, void* p) {
+  if (!p) return;
+  for (size_t i = 0; i < s->allocs.size(); ++i) {
+    if (s->allocs[i].first == p) {
+      s->dev_bytes -= s->allocs[i].second;
+      s->allocs.erase(s->allocs.begin() + (long)i);
+      break;
+    }
+  }
+  cudaFree(p);
+}
+
+template <class T>
+lms_status dgrow(lms_stream* s, T** p, unsigned long long old_n, unsigned long long new_n,
+                 unsigned long long keep_n) {
+  void* np = nullptr;
+  lms_status r = dalloc(s, &np, new_n * sizeof(T));
+  if (r != LMS_OK) return r;
+  if (*p && keep_n) {
+    cudaError_t e = cudaMemcpyAsync(np, *p, keep_n * sizeof(T), cudaMemcpyDeviceToDevice, s->st);
+    if (e != cudaSuccess) return cuda_fail(s, e, "cudaMemcpyAsync(grow)");
+  }
+  if (*p) {
+    cudaStreamSynchronize(s->st);
+    dfree(s, *p);
+  }
+  (void)old_n;
+  *p = static_cast<T*>(np);
+  return LMS_OK;
+}
+
+lms_status grow_groups(lms_stream* s, Groups* g, unsigned long long old_n, unsigned long long n,
+                       unsigned long long keep) {
+  lms_status r;
+  if ((r = dgrow(s, &g->gkey, old_n, n, keep)) != LMS_OK) return r;
+  if ((r = dgrow(s, &g->cnt, old_n, n, keep)) != LMS_OK) return r;
+  if ((r = dgrow(s, &g->sum, old_n, n, keep)) != LMS_OK) return r;
+  if ((r = dgrow(s, &g->mn, old_n, n, keep)) != LMS_OK) return r;
+  if ((r = dgrow(s, &g->mx, old_n, n, keep)) != LMS_OK) return r;
+  return LMS_OK;
+}
+
+unsigned long long round_cap(unsigned long long need) {
+  unsigned long long c = 1ull << 12;
+  while (c < need) c <<= 1;
+  return c;
+}
+
+// Makes every group buffer hold `need` groups (parts keep their carried prefix).
+lms_status ensure_group_capacity(lms_stream* s, unsigned long long need) {
+  if (need >= (1ull << 32) - 1)
+    return fail(s, LMS_EINVAL, "batch too large: more than 2^32-2 groups per query");
+  for (QueryHost& q : s->qs) {
+    if (q.cap >= need) continue;
+    const unsigned long long nc = round_cap(need);
+    lms_status r;
+    if ((r = grow_groups(s, &q.dev.parts, q.cap, nc, q.carried)) != LMS_OK) return r;
+    if ((r = grow_groups(s, &q.dev.state, q.cap, nc, 0)) != LMS_OK) return r;
+    q.cap = nc;
+    q.dev.parts_cap = nc;
+  }
+  Scratch& sc = s->scr;
+  if (sc.cap < need) {
+    const unsigned long long nc = round_cap(need);
+    lms_status r;
+    if ((r = dgrow(s, &sc.keysA, sc.cap, nc, 0)) != LMS_OK) return r;
+    if ((r = dgrow(s, &sc.keysB, sc.cap, nc, 0)) != LMS_OK) return r;
+    if ((r = dgrow(s, &sc.valsA, sc.cap, nc, 0)) != LMS_OK) return r;
+    if ((r = dgrow(s, &sc.valsB, sc.cap, nc, 0)) != LMS_OK) return r;
+    if ((r = dgrow(s, &sc.pane_id, sc.cap, nc + 1, 0)) != LMS_OK) return r;
+    if ((r = dgrow(s, &sc.pane_begin, sc.cap, nc + 1, 0)) != LMS_OK) return r;
+    sc.cap = nc;
+    sc.pane_cap = nc;
+  }
+  return LMS_OK;
+}
+
+lms_status ensure_windows(lms_stream* s, unsigned long long need) {
+  Scratch& sc = s->scr;
+  if (sc.win_cap >= need) return LMS_OK;
+  const unsigned long long nc = round_cap(need);
+  lms_status r;
+  if ((r = dgrow(s, &sc.win_w, sc.win_cap, nc, 0)) != LMS_OK) return r;
+  if ((r = dgrow(s, &sc.win_j0, sc.win_cap, nc, 0)) != LMS_OK) return r;
+  if ((r = dgrow(s, &sc.win_j1, sc.win_cap, nc, 0)) != LMS_OK) return r;
+  if ((r = dgrow(s, &sc.win_rows, sc.win_cap, nc, 0)) != LMS_OK) return r;
+  if ((r = dgrow(s, &sc.win_scr, sc.win_cap, nc, 0)) != LMS_OK) return r;
+  sc.win_cap = nc;
+  return LMS_OK;
+}
+
+lms_status ensure_pool(lms_stream* s, unsigned long long need) {
+  Scratch& sc = s->scr;
+  if (sc.pool_cap >= need) return LMS_OK;
+  const unsigned long long nc = round_cap(need);
+  lms_status r;
+  if ((r = dgrow(s, &sc.pool, sc.pool_cap, nc, 0)) != LMS_OK) return r;
+  sc.pool_cap = nc;
+  return LMS_OK;
+}
+
+lms_status ensure_rows(lms_stream* s, QueryHost& q, unsigned long long need) {
+  if (q.rows_cap >= need) return LMS_OK;
+  const unsigned long long nc = round_cap(need + need / 4);
+  lms_status r = dgrow(s, &q.rows, q.rows_cap, nc, q.row_base);
+  if (r != LMS_OK) return r;
+  q.rows_cap = nc;
+  return LMS_OK;
+}
+
+lms_status ensure_input(lms_stream* s, unsigned long long n) {
+  if (s->in_cap >= n) return LMS_OK;
+  const unsigned long long nc = round_cap(n);
+  lms_status r;
+  if ((r = dgrow(s, &s->in_ts, s->in_cap, nc, 0)) != LMS_OK) return r;
+  if ((r = dgrow(s, &s->in_key, s->in_cap, nc, 0)) != LMS_OK) return r;
+  if ((r = dgrow(s, &s->in_val, s->in_cap, nc, 0)) != LMS_OK) return r;
+  if (s->cfg.has_type && (r = dgrow(s, &s->in_type, s->in_cap, nc, 0)) != LMS_OK) return r;
+  s->in_cap = nc;
+  return LMS_OK;
+}
+
+void set_origin(lms_stream* s, long long origin) {
+  s->origin_ts = origin;
+  s->origin_set = true;
+  for (QueryHost& q : s->qs) {
+    const long long op = floor_div_h(origin, q.slide);
+    q.dev.origin_pane = op;
+    q.dev.base = op * q.slide;
+    q.dev.ts_off = (unsigned long long)kPaneBias * (unsigned long long)q.slide -
+                   (unsigned long long)q.dev.base;
+    q.dev.u_limit = 0xffffffffull * (unsigned long long)q.slide;
+  }
+}
+
+lms_status read_ctls(lms_stream* s, QCtl* h) {
+  LMS_CK(cudaMemcpyAsync(h, s->qctl, sizeof(QCtl) * s->qs.size(), cudaMemcpyDeviceToHost, s->st));
+  LMS_CK(cudaStreamSynchronize(s->st));
+  return LMS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+uint64_t lms_udiv_invariant(uint64_t n, uint64_t d) {
+  if (d == 0) return 0;
+  unsigned long long m;
+  int sh1, sh2;
+  udiv_constants(d, &m, &sh1, &sh2);
+  const unsigned long long t = (unsigned long long)(((unsigned __int128)m * n) >> 64);
+  return (t + ((n - t) >> sh1)) >> sh2;
+}
+
+lms_status stream_open(const lms_stream_config* cfg, lms_stream** out) {
+  if (!cfg || !out) return LMS_EINVAL;
+  if (cfg->value_type != LMS_VALUE_INT32 && cfg->value_type != LMS_VALUE_FLOAT32) return LMS_EINVAL;
+  if (cfg->allowed_lateness_ms < 0 || cfg->max_batch_rows < 0) return LMS_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
+    cudaGetLastError();
+    return LMS_ECUDA;
+  }
+  lms_stream* s = new lms_stream();
+  s->cfg = *cfg;
+  if (cudaSetDevice(cfg->device) != cudaSuccess) {
+    delete s;
+    return LMS_ECUDA;
+  }
+  cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, cfg->device);
+  if (cfg->cuda_stream) {
+    s->st = static_cast<cudaStream_t>(cfg->cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking) != cudaSuccess) {
+      delete s;
+      return LMS_ECUDA;
+    }
+    s->own_stream = true;
+  }
+  void* p = nullptr;
+  if (dalloc(s, &p, sizeof(SCtl)) != LMS_OK) {
+    stream_close(s);
+    return LMS_ENOMEM;
+  }
+  s->sctl = static_cast<SCtl*>(p);
+  if (dalloc(s, &p, sizeof(QCtl) * kMaxQueries) != LMS_OK) {
+    stream_close(s);
+    return LMS_ENOMEM;
+  }
+  s->qctl = static_cast<QCtl*>(p);
+  SCtl h{};
+  h.batch_max_ts = LLONG_MIN;
+  cudaMemcpy(s->sctl, &h, sizeof(h), cudaMemcpyHostToDevice);
+  if (dalloc(s, &p, sizeof(unsigned) * 256 * kGrid) != LMS_OK ||
+      (s->scr.hist = static_cast<unsigned*>(p), dalloc(s, &p, sizeof(unsigned long long) * (kGrid + 1))) != LMS_OK) {
+    stream_close(s);
+    return LMS_ENOMEM;
+  }
+  s->scr.chunk = static_cast<unsigned long long*>(p);
+  for (int i = 0; i < 8; ++i) cudaEventCreate(&s->ev[i]);
+  for (int i = 0; i < kMaxQueries; ++i)
+    for (int j = 0; j < 6; ++j) cudaEventCreate(&s->qev[i][j]);
+  s->stats.watermark = LLONG_MIN;
+  if (cudaGetLastError() != cudaSuccess) {
+    stream_close(s);
+    return LMS_ECUDA;
+  }
+  *out = s;
+  return LMS_OK;
+}
+
+lms_status query_register(lms_stream* s, const lms_query_spec* q, int32_t* query_id) {
+  if (!s || !q || !query_id) return LMS_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->stats.batches > 0) return fail(s, LMS_EINVAL, "queries must be registered before the first push");
+  if ((int)s->qs.size() >= kMaxQueries) return fail(s, LMS_EINVAL, "at most 8 queries per stream");
+  const long long size = q->window_size_ms;
+  const long long slide = q->window_slide_ms == 0 ? size : q->window_slide_ms;
+  if (size <= 0 || slide <= 0 || size % slide != 0 || size / slide > kMaxRuns ||
+      slide >= (1ll << 31))
+    return fail(s, LMS_EINVAL, "window: need size > 0, size % slide == 0, size/slide <= 4096, slide < 2^31");
+  if (q->filter_col < LMS_COL_TS || q->filter_col > LMS_COL_TYPE || q->filter_op < LMS_OP_NONE ||
+      q->filter_op > LMS_OP_GE)
+    return fail(s, LMS_EINVAL, "filter: bad column or operator");
+  QueryHost h;
+  h.spec = *q;
+  h.size = size;
+  h.slide = slide;
+  h.k = (int)(size / slide);
+  QueryDev& d = h.dev;
+  d.filter_col = q->filter_col;
+  d.filter_op = q->filter_op;
+  d.filter_i = q->filter_i;
+  d.filter_f = q->filter_f;
+  d.slide = (unsigned long long)slide;
+  udiv_constants(d.slide, &d.magic, &d.sh1, &d.sh2);
+  d.size = size;
+  d.k = h.k;
+  d.agg_mask = q->agg_mask ? q->agg_mask : LMS_AGG_ALL;
+  d.qid = (int)s->qs.size();
+  d.value_is_float = s->cfg.value_type == LMS_VALUE_FLOAT32;
+  d.ctl = s->qctl + d.qid;
+  QCtl c{};
+  c.and_mask = ~0ull;
+  c.cursor = 0;
+  if (cudaMemcpy(d.ctl, &c, sizeof(c), cudaMemcpyHostToDevice) != cudaSuccess)
+    return cuda_fail(s, cudaGetLastError(), "cudaMemcpy(ctl)");
+  s->qs.push_back(h);
+  *query_id = d.qid;
+  return LMS_OK;
+}
+
+lms_status push_microbatch(lms_stream* s, const lms_batch* b) {
+  if (!s || !b) return LMS_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->latched != LMS_OK) return s->latched;
+  if (s->eos_seen) return fail(s, LMS_ECLOSED, "stream already ended");
+  if (s->qs.empty()) return fail(s, LMS_EINVAL, "no query registered");
+  const long long n = b->n_rows;
+  if (n < 0) return fail(s, LMS_EINVAL, "n_rows < 0");
+  if (n > 0 && (!b->ts || !b->key || !b->value || (s->cfg.has_type && !b->type)))
+    return fail(s, LMS_EINVAL, "missing column pointer");
+  if (b->memory != LMS_MEM_HOST && b->memory != LMS_MEM_DEVICE)
+    return fail(s, LMS_EINVAL, "bad memory kind");
+  const auto t0 = std::chrono::steady_clock::now();
+  LMS_CK(cudaSetDevice(s->cfg.device));
+  const int eos = (b->flags & LMS_BATCH_EOS) ? 1 : 0;
+  if (!s->origin_set) {
+    if (s->cfg.origin_ts != LMS_ORIGIN_AUTO) {
+      set_origin(s, s->cfg.origin_ts);
+    } else if (n > 0) {
+      long long first = 0;
+      if (b->memory == LMS_MEM_HOST) first = (long long)b->ts[0];
+      else LMS_CK(cudaMemcpy(&first, b->ts, sizeof(long long), cudaMemcpyDeviceToHost));
+      set_origin(s, first);
+    } else {
+      set_origin(s, 0);
+    }
+  }
+  // capacities: parts hold the carried groups plus at most one group per row
+  unsigned long long need = 0;
+  for (QueryHost& q : s->qs) need = std::max(need, q.carried + (unsigned long long)n);
+  lms_status r = ensure_group_capacity(s, need + 1);
+  if (r != LMS_OK) return r;
+  const bool timing = s->cfg.enable_timing != 0;
+  const long long* ts = reinterpret_cast<const long long*>(b->ts);
+  const unsigned* key = b->key;
+  const void* val = b->value;
+  const unsigned char* typ = s->cfg.has_type ? b->type : nullptr;
+  if (timing) LMS_CK(cudaEventRecord(s->ev[0], s->st));
+  if (n > 0 && b->memory == LMS_MEM_HOST) {
+    if ((r = ensure_input(s, (unsigned long long)n)) != LMS_OK) return r;
+    LMS_CK(cudaMemcpyAsync(s->in_ts, b->ts, n * 8, cudaMemcpyHostToDevice, s->st));
+    LMS_CK(cudaMemcpyAsync(s->in_key, b->key, n * 4, cudaMemcpyHostToDevice, s->st));
+    LMS_CK(cudaMemcpyAsync(s->in_val, b->value, n * 4, cudaMemcpyHostToDevice, s->st));
+    if (typ) LMS_CK(cudaMemcpyAsync(s->in_type, b->type, n, cudaMemcpyHostToDevice, s->st));
+    ts = s->in_ts;
+    key = s->in_key;
+    val = s->in_val;
+    if (typ) typ = s->in_type;
+  }
+  if (timing) LMS_CK(cudaEventRecord(s->ev[5], s->st));
+  int launches = 0;
+  QCtl* ctls[kMaxQueries];
+  const int nq = (int)s->qs.size();
+  for (int i = 0; i < nq; ++i) ctls[i] = s->qs[i].dev.ctl;
+  LMS_CK(launch_batch_begin(s->sctl, ctls, nq, s->st));
+  ++launches;
+  if (timing) LMS_CK(cudaEventRecord(s->ev[1], s->st));
+  if (n > 0) {
+    K1Args a{};
+    a.ts = ts;
+    a.key = key;
+    a.value = val;
+    a.type = typ;
+    a.n = n;
+    a.nq = nq;
+    a.value_is_float = s->cfg.value_type == LMS_VALUE_FLOAT32;
+    a.sctl = s->sctl;
+    for (int i = 0; i < nq; ++i) a.q[i] = s->qs[i].dev;
+    const long long ntiles = (n + k1_tile_events() - 1) / k1_tile_events();
+    const int grid = (int)std::min<long long>(ntiles, k1_max_grid(s->cfg.device, 0, 0));
+    LMS_CK(launch_k1(a, s->cfg.k1_variant, grid, s->st));
+    ++launches;
+    ++s->stats.k1_launches;
+  }
+  if (timing) LMS_CK(cudaEventRecord(s->ev[2], s->st));
+  std::vector<QueryDev> qd(nq);
+  for (int i = 0; i < nq; ++i) qd[i] = s->qs[i].dev;
+  LMS_CK(launch_watermark(s->sctl, qd.data(), nq, s->cfg.allowed_lateness_ms, eos, s->st));
+  ++launches;
+  // emission needs window/pool/row buffers; make sure something exists
+  if ((r = ensure_windows(s, 1024)) != LMS_OK) return r;
+  if ((r = ensure_pool(s, 1ull << 16)) != LMS_OK) return r;
+  for (QueryHost& q : s->qs)
+    if ((r = ensure_rows(s, q, q.row_base + 4096)) != LMS_OK) return r;
+  // per query, back to back (they share the scratch): sort/reduce into the
+  // window state, pane index, emission of closed windows, carry of open panes
+  for (int i = 0; i < nq; ++i) {
+    QueryHost& q = s->qs[i];
+    if (timing) LMS_CK(cudaEventRecord(s->qev[i][4], s->st));
+    LMS_CK(launch_sort_reduce(qd[i], s->scr, s->st, &launches));
+    if (timing) LMS_CK(cudaEventRecord(s->qev[i][5], s->st));
+    LMS_CK(launch_pane_index(q.dev, s->scr, s->st, &launches));
+    LMS_CK(launch_emit(q.dev, s->scr, q.rows, q.rows_cap, s->sms, s->st, &launches,
+                       timing ? s->qev[i] : nullptr));
+    LMS_CK(launch_trim(q.dev, s->scr, s->sms, s->st, &launches));
+  }
+  if (timing) LMS_CK(cudaEventRecord(s->ev[4], s->st));
+  std::vector<QCtl> hc(nq);
+  if ((r = read_ctls(s, hc.data())) != LMS_OK) return r;
+  // retry emission for queries whose buffers were too small
+  bool retried = false;
+  for (int i = 0; i < nq; ++i) {
+    QueryHost& q = s->qs[i];
+    for (int attempt = 0; (hc[i].err & kErrNeedRetry) && attempt < 4; ++attempt) {
+      if (hc[i].err & kErrWinOverflow) {
+        if ((r = ensure_windows(s, hc[i].n_windows)) != LMS_OK) return r;
+      }
+      if (hc[i].err & kErrPoolOverflow) {
+        if ((r = ensure_pool(s, hc[i].pool_used)) != LMS_OK) return r;
+      }
+      if (hc[i].err & kErrRowsOverflow) {
+        if ((r = ensure_rows(s, q, hc[i].row_base + hc[i].rows_batch)) != LMS_OK) return r;
+      }
+      LMS_CK(launch_pane_index(q.dev, s->scr, s->st, &launches));
+      LMS_CK(launch_emit(q.dev, s->scr, q.rows, q.rows_cap, s->sms, s->st, &launches,
+                         nullptr));
+      LMS_CK(launch_trim(q.dev, s->scr, s->sms, s->st, &launches));
+      if ((r = read_ctls(s, hc.data())) != LMS_OK) return r;
+      retried = true;
+    }
+    if (hc[i].err & kErrNeedRetry)
+      return fail(s, LMS_ENOMEM, "emission buffers could not be grown enough");
+    if (hc[i].err & (kErrPartsOverflow | kErrProbe)) {
+      s->latched = LMS_EDEVICE;
+      return fail(s, LMS_EDEVICE, "internal device error flag raised by the fused pass");
+    }
+  }
+  SCtl hs{};
+  LMS_CK(cudaMemcpy(&hs, s->sctl, sizeof(hs), cudaMemcpyDeviceToHost));
+  if (hs.wm_valid) s->wm = hs.wm;
+  unsigned long long late = 0, range = 0, rows = 0, groups = 0;
+  for (int i = 0; i < nq; ++i) {
+    QueryHost& q = s->qs[i];
+    s->stats.partials += hc[i].parts_at_sort - q.carried;
+    s->stats.groups_built += hc[i].n_state;
+    q.rows_emitted += hc[i].rows_batch;
+    q.row_base = hc[i].row_base;
+    q.carried = hc[i].carried;
+    q.n_state = hc[i].n_state;
+    q.late_rows = hc[i].late_rows;
+    q.range_rows = hc[i].range_rows;
+    late += q.late_rows;
+    range += q.range_rows;
+    rows += q.rows_emitted;
+    groups += q.carried;
+  }
+  if (timing) {
+    float a = 0, bms = 0, all = 0, sort_ms = 0;
+    for (int i = 0; i < nq; ++i) {
+      float x = 0;
+      cudaEventElapsedTime(&x, s->qev[i][4], s->qev[i][5]);
+      sort_ms += x;
+    }
+    cudaEventElapsedTime(&a, s->ev[0], s->ev[5]);
+    cudaEventElapsedTime(&bms, s->ev[1], s->ev[2]);
+    cudaEventElapsedTime(&all, s->ev[2], s->ev[4]);
+    s->stats.h2d_ms += a;
+    s->stats.k1_ms += bms;
+    s->stats.sort_ms += sort_ms;
+    s->stats.emit_ms += all - sort_ms;
+    if (!retried) {
+      for (int i = 0; i < nq; ++i) {
+        float e1 = 0, e2 = 0;
+        cudaEventElapsedTime(&e1, s->qev[i][0], s->qev[i][1]);
+        cudaEventElapsedTime(&e2, s->qev[i][2], s->qev[i][3]);
+        s->stats.e1_ms += e1;
+        s->stats.e2_ms += e2;
+      }
+    }
+  }
+  s->stats.batches += 1;
+  s->stats.events += (unsigned long long)n;
+  s->stats.late_rows = late;
+  s->stats.range_rows = range;
+  s->stats.rows_emitted = rows;
+  s->stats.state_groups = groups;
+  s->stats.watermark = s->wm;
+  s->stats.kernel_launches += (unsigned long long)launches;
+  s->stats.last_batch_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (eos) s->eos_seen = true;
+  return LMS_OK;
+}
+
+lms_status poll_results(lms_stream* s, int32_t query_id, lms_result_row* out, size_t cap,
+                        size_t* n_out, int32_t timeout_ms) {
+  (void)timeout_ms;  // results are complete when push_microbatch returns
+  if (!s || !n_out || (cap && !out)) return LMS_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->latched != LMS_OK) return s->latched;
+  if (query_id < 0 || query_id >= (int)s->qs.size()) return fail(s, LMS_EINVAL, "bad query id");
+  QueryHost& q = s->qs[query_id];
+  const unsigned long long avail = q.row_base - q.rows_read;
+  if (avail == 0) return LMS_EAGAIN;
+  const unsigned long long m = std::min<unsigned long long>(avail, cap);
+  if (m) {
+    LMS_CK(cudaMemcpyAsync(out, q.rows + q.rows_read, m * sizeof(lms_result_row),
+                           cudaMemcpyDeviceToHost, s->st));
+    LMS_CK(cudaStreamSynchronize(s->st));
+  }
+  q.rows_read += m;
+  if (q.rows_read == q.row_base) {
+    q.rows_read = 0;
+    q.row_base = 0;
+    const unsigned long long zero = 0;
+    LMS_CK(cudaMemcpyAsync(&q.dev.ctl->row_base, &zero, sizeof(zero), cudaMemcpyHostToDevice,
+                           s->st));
+    LMS_CK(cudaStreamSynchronize(s->st));
+  }
+  *n_out = (size_t)m;
+  return LMS_OK;
+}
+
+lms_status lms_results_device(lms_stream* s, int32_t query_id, const lms_result_row** rows,
+                              size_t* n) {
+  if (!s || !rows || !n) return LMS_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (query_id < 0 || query_id >= (int)s->qs.size()) return fail(s, LMS_EINVAL, "bad query id");
+  QueryHost& q = s->qs[query_id];
+  *rows = reinterpret_cast<const lms_result_row*>(q.rows + q.rows_read);
+  *n = (size_t)(q.row_base - q.rows_read);
+  return LMS_OK;
+}
+
+lms_status lms_results_discard(lms_stream* s, int32_t query_id) {
+  if (!s) return LMS_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (query_id < 0 || query_id >= (int)s->qs.size()) return fail(s, LMS_EINVAL, "bad query id");
+  QueryHost& q = s->qs[query_id];
+  q.rows_read = 0;
+  q.row_base = 0;
+  const unsigned long long zero = 0;
+  LMS_CK(cudaMemcpyAsync(&q.dev.ctl->row_base, &zero, sizeof(zero), cudaMemcpyHostToDevice, s->st));
+  LMS_CK(cudaStreamSynchronize(s->st));
+  return LMS_OK;
+}
+
+lms_status lms_stream_stats(lms_stream* s, lms_stats* out) {
+  if (!s || !out) return LMS_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  *out = s->stats;
+  unsigned long long pending = 0;
+  for (QueryHost& q : s->qs) pending += q.row_base - q.rows_read;
+  out->rows_pending = pending;
+  out->device_bytes = s->dev_bytes;
+  return LMS_OK;
+}
+
+const char* lms_last_error(lms_stream* s) { return s ? s->err.c_str() : "null stream"; }
+
+lms_status stream_close(lms_stream* s) {
+  if (!s) return LMS_OK;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    cudaSetDevice(s->cfg.device);
+    if (s->st) cudaStreamSynchronize(s->st);
+    for (auto& a : s->allocs) cudaFree(a.first);
+    s->allocs.clear();
+    for (int i = 0; i < 8; ++i)
+      if (s->ev[i]) cudaEventDestroy(s->ev[i]);
+    for (int i = 0; i < kMaxQueries; ++i)
+      for (int j = 0; j < 6; ++j)
+        if (s->qev[i][j]) cudaEventDestroy(s->qev[i][j]);
+    if (s->own_stream && s->st) cudaStreamDestroy(s->st);
+  }
+  delete s;
+  return LMS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,292 @@
+// Partial groups -> sorted, unique window state.
+//
+// After the fused pass, a query's partial-group arrays hold the groups carried
+// over from the previous batch followed by this batch's per-tile groups, in no
+// particular order.  This file turns them into the window state: an LSD radix
+// sort of the 64-bit group keys (8-bit digits; digits that are equal in every
+// key are skipped, which the OR/AND masks gathered by the producers reveal),
+// then a reduce-by-key that combines equal (pane, key) groups, then the index
+// of distinct panes.  All sizes are read on the device, so the whole sequence
+// launches without a host round trip.
+//
+// Chunked kernels use a fixed grid of kGrid CTAs, each owning one contiguous
+// chunk of the input; a per-chunk count, a single-CTA scan of the counts and a
+// per-chunk write give stable, deterministic positions.
+#include <climits>
+
+#include "lms_device.cuh"
+
+namespace lms {
+namespace {
+
+constexpr int kScatterTile = 2048;  // 8 warps x 8 rounds x 32 lanes
+
+struct SortSrc {
+  const unsigned long long* keys;
+  const unsigned* vals;  // nullptr: identity
+};
+
+// Pass p reads the previous pass's output (or the partial keys for p == 0)
+// and writes buffer (p & 1) of the scratch pair.
+__device__ __forceinline__ SortSrc pass_src(const QueryDev& q, const Scratch& s, int p) {
+  if (p == 0) return {q.parts.gkey, nullptr};
+  return ((p - 1) & 1) ? SortSrc{s.keysB, s.valsB} : SortSrc{s.keysA, s.valsA};
+}
+__device__ __forceinline__ SortSrc final_src(const QueryDev& q, const Scratch& s, int np) {
+  if (np == 0) return {q.parts.gkey, nullptr};
+  return ((np - 1) & 1) ? SortSrc{s.keysB, s.valsB} : SortSrc{s.keysA, s.valsA};
+}
+
+__global__ void k_sort_plan(QCtl* c) {
+  if (threadIdx.x != 0) return;
+  const unsigned long long n = c->n_parts;
+  c->parts_at_sort = n;
+  const unsigned long long m = c->or_mask ^ c->and_mask;
+  int np = 0;
+  if (n > 1)
+    for (int d = 0; d < 8; ++d)
+      if ((m >> (8 * d)) & 0xffull) c->shifts[np++] = 8 * d;
+  c->npasses = np;
+}
+
+__global__ void __launch_bounds__(256) k_sort_hist(const QueryDev q, const Scratch s, int p) {
+  const QCtl* c = q.ctl;
+  if (p >= c->npasses) return;
+  __shared__ unsigned h[256];
+  h[threadIdx.x] = 0u;
+  __syncthreads();
+  const int shift = c->shifts[p];
+  const SortSrc src = pass_src(q, s, p);
+  unsigned long long lo, hi;
+  chunk_range(c->n_parts, blockIdx.x, gridDim.x, &lo, &hi);
+  for (unsigned long long i0 = lo; i0 < hi; i0 += blockDim.x) {
+    const unsigned long long i = i0 + threadIdx.x;
+    const bool v = i < hi;
+    const unsigned d = v ? (unsigned)((src.keys[i] >> shift) & 0xffull) : 256u;
+    const unsigned peers = __match_any_sync(kFull, d);
+    if (v && (int)lane_id() == __ffs(peers) - 1) atomicAdd(&h[d], (unsigned)__popc(peers));
+  }
+  __syncthreads();
+  s.hist[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
+}
+
+// Exclusive scan (in place) of the digit-major histogram: 256 * kGrid entries.
+__global__ void __launch_bounds__(1024) k_sort_scan(const QueryDev q, const Scratch s, int p) {
+  if (p >= q.ctl->npasses) return;
+  __shared__ unsigned long long tmp[33];
+  const int total = 256 * kGrid;
+  const int per = (total + blockDim.x - 1) / blockDim.x;
+  const int a = threadIdx.x * per;
+  const int b = min(total, a + per);
+  unsigned long long sum = 0;
+  for (int i = a; i < b; ++i) sum += s.hist[i];
+  unsigned long long tot;
+  unsigned long long run = block_excl_scan(sum, tmp, &tot);
+  for (int i = a; i < b; ++i) {
+    const unsigned x = s.hist[i];
+    s.hist[i] = (unsigned)run;
+    run += x;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_sort_scatter(const QueryDev q, const Scratch s, int p) {
+  const QCtl* c = q.ctl;
+  if (p >= c->npasses) return;
+  __shared__ unsigned run[256];
+  __shared__ unsigned wcnt[8][256];
+  const int tid = threadIdx.x, w = tid >> 5;
+  const unsigned lane = lane_id();
+  const int shift = c->shifts[p];
+  const SortSrc src = pass_src(q, s, p);
+  unsigned long long* dk = (p & 1) ? s.keysB : s.keysA;
+  unsigned* dv = (p & 1) ? s.valsB : s.valsA;
+  unsigned long long lo, hi;
+  chunk_range(c->n_parts, blockIdx.x, gridDim.x, &lo, &hi);
+  run[tid] = s.hist[tid * gridDim.x + blockIdx.x];
+  const unsigned lt = (1u << lane) - 1u;
+  for (unsigned long long tb = lo; tb < hi; tb += kScatterTile) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) wcnt[w][lane + 32 * j] = 0u;
+    __syncthreads();
+    unsigned long long kk[8];
+    unsigned vv[8], dd[8], rr[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const unsigned long long i = tb + (unsigned long long)(w * 256 + r * 32) + lane;
+      const bool v = i < hi;
+      kk[r] = v ? src.keys[i] : 0ull;
+      vv[r] = v ? (src.vals ? src.vals[i] : (unsigned)i) : 0u;
+      dd[r] = v ? (unsigned)((kk[r] >> shift) & 0xffull) : 256u;
+      const unsigned peers = __match_any_sync(kFull, dd[r]);
+      rr[r] = (v ? wcnt[w][dd[r]] : 0u) + __popc(peers & lt);
+      __syncwarp();
+      if (v && (int)lane == __ffs(peers) - 1) wcnt[w][dd[r]] += __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    {
+      unsigned acc = run[tid];
+#pragma unroll
+      for (int ww = 0; ww < 8; ++ww) {
+        const unsigned cnt = wcnt[ww][tid];
+        wcnt[ww][tid] = acc;
+        acc += cnt;
+      }
+      run[tid] = acc;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      if (dd[r] < 256u) {
+        const unsigned pos = wcnt[w][dd[r]] + rr[r];
+        dk[pos] = kk[r];
+        dv[pos] = vv[r];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---- reduce-by-key: sorted partials -> unique groups (window state) -------
+
+__global__ void __launch_bounds__(256) k_rbk_count(const QueryDev q, const Scratch s) {
+  const QCtl* c = q.ctl;
+  const SortSrc src = final_src(q, s, c->npasses);
+  unsigned long long lo, hi;
+  chunk_range(c->n_parts, blockIdx.x, gridDim.x, &lo, &hi);
+  unsigned long long cnt = 0;
+  for (unsigned long long i = lo + threadIdx.x; i < hi; i += blockDim.x)
+    cnt += (i == 0 || src.keys[i] != src.keys[i - 1]) ? 1ull : 0ull;
+  __shared__ unsigned long long tmp[33];
+  unsigned long long tot;
+  block_excl_scan(cnt, tmp, &tot);
+  if (threadIdx.x == 0) s.chunk[blockIdx.x] = tot;
+}
+
+// Exclusive scan of g (<= 1024) per-chunk counts in place; total -> *total.
+__global__ void __launch_bounds__(1024) k_scan_chunks(unsigned long long* a, int g,
+                                                      unsigned long long* total) {
+  __shared__ unsigned long long tmp[33];
+  const unsigned long long v = (int)threadIdx.x < g ? a[threadIdx.x] : 0ull;
+  unsigned long long tot;
+  const unsigned long long r = block_excl_scan(v, tmp, &tot);
+  if ((int)threadIdx.x < g) a[threadIdx.x] = r;
+  if (threadIdx.x == 0) *total = tot;
+}
+
+template <bool FLOAT>
+__global__ void __launch_bounds__(256) k_rbk_write(const QueryDev q, const Scratch s) {
+  const QCtl* c = q.ctl;
+  const unsigned long long n = c->n_parts;
+  const SortSrc src = final_src(q, s, c->npasses);
+  unsigned long long lo, hi;
+  chunk_range(n, blockIdx.x, gridDim.x, &lo, &hi);
+  __shared__ unsigned long long tmp[33];
+  unsigned long long out = s.chunk[blockIdx.x];
+  for (unsigned long long i0 = lo; i0 < hi; i0 += blockDim.x) {
+    const unsigned long long i = i0 + threadIdx.x;
+    const bool v = i < hi;
+    const unsigned long long k = v ? src.keys[i] : 0ull;
+    const bool head = v && (i == 0 || k != src.keys[i - 1]);
+    unsigned long long tot;
+    const unsigned long long r = block_excl_scan(head ? 1ull : 0ull, tmp, &tot);
+    if (head) {
+      long long cnt = 0;
+      unsigned long long isum = 0ull;
+      double fsum = 0.0;
+      unsigned mn = 0xffffffffu, mx = 0u;
+      for (unsigned long long j = i; j < n && src.keys[j] == k; ++j) {
+        const unsigned long long pi = src.vals ? src.vals[j] : j;
+        cnt += q.parts.cnt[pi];
+        if (FLOAT)
+          fsum += __longlong_as_double((long long)q.parts.sum[pi]);
+        else
+          isum += q.parts.sum[pi];
+        mn = min(mn, q.parts.mn[pi]);
+        mx = max(mx, q.parts.mx[pi]);
+      }
+      const unsigned long long o = out + r;
+      q.state.gkey[o] = k;
+      q.state.cnt[o] = cnt;
+      q.state.sum[o] = FLOAT ? (unsigned long long)__double_as_longlong(fsum) : isum;
+      q.state.mn[o] = mn;
+      q.state.mx[o] = mx;
+    }
+    out += tot;
+  }
+}
+
+// ---- distinct panes of the window state ------------------------------------
+
+__global__ void __launch_bounds__(256) k_pane_count(const QueryDev q, const Scratch s) {
+  const QCtl* c = q.ctl;
+  unsigned long long lo, hi;
+  chunk_range(c->n_state, blockIdx.x, gridDim.x, &lo, &hi);
+  unsigned long long cnt = 0;
+  for (unsigned long long i = lo + threadIdx.x; i < hi; i += blockDim.x)
+    cnt += (i == 0 || (q.state.gkey[i] >> 32) != (q.state.gkey[i - 1] >> 32)) ? 1ull : 0ull;
+  __shared__ unsigned long long tmp[33];
+  unsigned long long tot;
+  block_excl_scan(cnt, tmp, &tot);
+  if (threadIdx.x == 0) s.chunk[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(256) k_pane_write(const QueryDev q, const Scratch s) {
+  const QCtl* c = q.ctl;
+  const unsigned long long n = c->n_state;
+  unsigned long long lo, hi;
+  chunk_range(n, blockIdx.x, gridDim.x, &lo, &hi);
+  __shared__ unsigned long long tmp[33];
+  unsigned long long out = s.chunk[blockIdx.x];
+  for (unsigned long long i0 = lo; i0 < hi; i0 += blockDim.x) {
+    const unsigned long long i = i0 + threadIdx.x;
+    const bool v = i < hi;
+    const unsigned p = v ? (unsigned)(q.state.gkey[i] >> 32) : 0u;
+    const bool head = v && (i == 0 || p != (unsigned)(q.state.gkey[i - 1] >> 32));
+    unsigned long long tot;
+    const unsigned long long r = block_excl_scan(head ? 1ull : 0ull, tmp, &tot);
+    if (head) {
+      s.pane_id[out + r] = p;
+      s.pane_begin[out + r] = i;
+    }
+    if (v && i == n - 1) s.pane_begin[c->n_panes] = n;
+    out += tot;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_sort_reduce(const QueryDev& q, const Scratch& s, cudaStream_t st,
+                               int* launches) {
+  int nl = 0;
+  k_sort_plan<<<1, 32, 0, st>>>(q.ctl);
+  ++nl;
+  for (int p = 0; p < 8; ++p) {
+    k_sort_hist<<<kGrid, 256, 0, st>>>(q, s, p);
+    k_sort_scan<<<1, 1024, 0, st>>>(q, s, p);
+    k_sort_scatter<<<kGrid, 256, 0, st>>>(q, s, p);
+    nl += 3;
+  }
+  k_rbk_count<<<kGrid, 256, 0, st>>>(q, s);
+  k_scan_chunks<<<1, 1024, 0, st>>>(s.chunk, kGrid, &q.ctl->n_state);
+  if (q.value_is_float)
+    k_rbk_write<true><<<kGrid, 256, 0, st>>>(q, s);
+  else
+    k_rbk_write<false><<<kGrid, 256, 0, st>>>(q, s);
+  nl += 3;
+  if (launches) *launches += nl;
+  return cudaGetLastError();
+}
+
+// Index of distinct panes of q's window state (into the shared scratch; it
+// must be rebuilt before every emission of q).
+cudaError_t launch_pane_index(const QueryDev& q, const Scratch& s, cudaStream_t st,
+                              int* launches) {
+  k_pane_count<<<kGrid, 256, 0, st>>>(q, s);
+  k_scan_chunks<<<1, 1024, 0, st>>>(s.chunk, kGrid, &q.ctl->n_panes);
+  k_pane_write<<<kGrid, 256, 0, st>>>(q, s);
+  if (launches) *launches += 3;
+  return cudaGetLastError();
+}
+
+}  // namespace lms

@@ -1,0 +1,109 @@
+// Device helpers shared by the kernels of the engine.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "lms_internal.h"
+
+namespace lms {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr unsigned long long kEmpty = ~0ull;
+
+// q = n / d for the constants of udiv_constants(d): t = mulhi(m, n),
+// q = (t + ((n - t) >> sh1)) >> sh2   (Granlund & Montgomery 1994, Fig. 4.1).
+__device__ __forceinline__ unsigned long long udiv_inv(unsigned long long n, unsigned long long m,
+                                                       int sh1, int sh2) {
+  unsigned long long t = __umul64hi(m, n);
+  return (t + ((n - t) >> sh1)) >> sh2;
+}
+
+// Order-preserving uint32 images of int32 and float32 values, so that
+// unsigned atomicMin/atomicMax implement min/max.  The float image orders by
+// IEEE-754 totalOrder (-0.0 < +0.0).
+__device__ __forceinline__ unsigned enc_i32(int v) { return (unsigned)v ^ 0x80000000u; }
+__device__ __forceinline__ int dec_i32(unsigned u) { return (int)(u ^ 0x80000000u); }
+__device__ __forceinline__ unsigned enc_f32(float f) {
+  unsigned b = __float_as_uint(f);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ unsigned dec_f32_bits(unsigned u) {
+  return (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
+}
+
+// Multiplicative (Fibonacci) hash of a 64-bit group key to `bits` bits.
+__device__ __forceinline__ unsigned hash_slot(unsigned long long g, int bits) {
+  return (unsigned)((g * 0x9E3779B97F4A7C15ull) >> (64 - bits));
+}
+
+__device__ __forceinline__ bool filter_pass_i(int op, long long x, long long c) {
+  switch (op) {
+    case 1: return x == c;
+    case 2: return x != c;
+    case 3: return x < c;
+    case 4: return x <= c;
+    case 5: return x > c;
+    case 6: return x >= c;
+    default: return true;
+  }
+}
+__device__ __forceinline__ bool filter_pass_f(int op, double x, double c) {
+  switch (op) {
+    case 1: return x == c;
+    case 2: return x != c;
+    case 3: return x < c;
+    case 4: return x <= c;
+    case 5: return x > c;
+    case 6: return x >= c;
+    default: return true;
+  }
+}
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+// Inclusive warp scan of 64-bit values.
+__device__ __forceinline__ unsigned long long warp_incl_scan(unsigned long long v) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned long long n = __shfl_up_sync(kFull, v, o);
+    if ((int)lane_id() >= o) v += n;
+  }
+  return v;
+}
+
+// Exclusive block scan of one 64-bit value per thread; returns the prefix and
+// writes the block total to *total.  `tmp` needs blockDim/32 + 1 entries.
+// Must be called by all threads of the block.
+__device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long v,
+                                                              unsigned long long* tmp,
+                                                              unsigned long long* total) {
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  unsigned long long inc = warp_incl_scan(v);
+  if (lane_id() == 31) tmp[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    unsigned long long x = (int)lane_id() < nw ? tmp[lane_id()] : 0ull;
+    unsigned long long xi = warp_incl_scan(x);
+    if ((int)lane_id() < nw) tmp[lane_id()] = xi - x;
+    if (lane_id() == 31) tmp[32] = xi;
+  }
+  __syncthreads();
+  unsigned long long r = tmp[w] + inc - v;
+  *total = tmp[32];
+  __syncthreads();
+  return r;
+}
+
+// Contiguous chunk [lo, hi) of n items owned by chunk c of g chunks.
+__device__ __forceinline__ void chunk_range(unsigned long long n, int c, int g,
+                                            unsigned long long* lo, unsigned long long* hi) {
+  unsigned long long per = (n + g - 1) / g;
+  per = (per + 255ull) & ~255ull;
+  unsigned long long a = per * (unsigned long long)c;
+  unsigned long long b = a + per;
+  *lo = a < n ? a : n;
+  *hi = b < n ? b : n;
+}
+
+}  // namespace lms

@@ -1,0 +1,167 @@
+// Internal declarations shared by the engine (host) and the CUDA kernels.
+//
+// Data model of one query's window state (all in device memory):
+//   * a group is one (pane, key) pair; a pane is one slide-long slice of event
+//     time (pane p covers [p*slide, (p+1)*slide)).  A window of size K*slide is
+//     the union of K consecutive panes, so every event updates exactly one
+//     group, whatever K is; windows are assembled from panes at emission.
+//   * gkey = (pane_rel << 32) | key, pane_rel = pane - origin_pane + 2^31, so
+//     sorting gkeys as uint64 orders groups by (pane, key).
+//   * Groups are kept as SoA arrays {gkey, cnt, sum, mn, mx}; min/max are
+//     stored order-preserving encoded as uint32 (see lms_device.cuh).
+// Per micro-batch, the fused pass appends per-tile partial groups after the
+// carried state; a radix sort + reduce-by-key turns them into the sorted,
+// unique window state; closed windows are merged from their panes and emitted.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lms {
+
+constexpr int kMaxQueries = 8;
+constexpr int kMaxRuns = 4096;           // max size/slide of a sliding window
+constexpr long long kPaneBias = 1ll << 31;  // pane_rel = pane - origin_pane + kPaneBias
+
+// Error bits raised by kernels (QCtl::err).
+constexpr unsigned kErrPartsOverflow = 1u;   // partial-group buffer too small
+constexpr unsigned kErrWinOverflow = 2u;     // window list too small
+constexpr unsigned kErrRowsOverflow = 4u;    // result buffer too small
+constexpr unsigned kErrPoolOverflow = 8u;    // big-window merge scratch too small
+constexpr unsigned kErrProbe = 16u;          // shared hash probe bound hit (never expected)
+constexpr unsigned kErrNeedRetry = kErrWinOverflow | kErrRowsOverflow | kErrPoolOverflow;
+
+struct Groups {
+  unsigned long long* gkey;
+  long long* cnt;
+  unsigned long long* sum;  // int64 sum, or the bits of a double sum
+  unsigned* mn;             // encoded min
+  unsigned* mx;             // encoded max
+};
+
+// Per-query device control block.
+struct QCtl {
+  unsigned long long n_parts;    // partial groups (carried + this batch)
+  unsigned long long or_mask;    // OR of all partial gkeys
+  unsigned long long and_mask;   // AND of all partial gkeys
+  unsigned long long n_state;    // unique groups in the window state
+  unsigned long long n_panes;    // distinct panes in the window state
+  unsigned long long n_windows;  // windows closed by this batch
+  long long cursor;              // first (relative) window id not yet closed
+  long long w_hi;                // last (relative) window id closed by this batch
+  unsigned long long late_rows;  // cumulative
+  unsigned long long range_rows; // cumulative
+  unsigned long long rows_batch; // rows emitted by this batch
+  unsigned long long row_base;   // rows held in the device result buffer
+  unsigned long long pool_used;  // big-window scratch entries used (this emission)
+  unsigned long long carried;    // groups carried into the next batch
+  unsigned long long big_windows;// windows merged through global scratch (this emission)
+  unsigned long long trim_from;  // first state index carried into the next batch
+  unsigned long long parts_at_sort; // partial groups the sort of this batch consumed
+  unsigned int err;
+  int npasses;
+  int shifts[8];
+};
+
+// Stream-level device control block.
+struct SCtl {
+  long long batch_max_ts;  // max ts of the current batch (LLONG_MIN if empty)
+  long long wm;            // watermark
+  int wm_valid;
+  int pad;
+};
+
+// Everything a kernel needs to know about one query.
+struct QueryDev {
+  int filter_col, filter_op;
+  long long filter_i;
+  double filter_f;
+  unsigned long long slide;
+  unsigned long long magic;  // invariant-division constants for `slide`
+  int sh1, sh2;
+  unsigned long long ts_off;   // u = (u64)ts + ts_off  (= 2^31*slide - base)
+  unsigned long long u_limit;  // event valid iff u < u_limit (= (2^32-1)*slide)
+  long long size;
+  long long base;              // origin_pane * slide
+  long long origin_pane;
+  int k;                       // size / slide
+  unsigned agg_mask;
+  int qid;
+  int value_is_float;
+  Groups parts;
+  Groups state;
+  unsigned long long parts_cap;
+  QCtl* ctl;
+};
+
+struct K1Args {
+  const long long* ts;
+  const unsigned* key;
+  const void* value;
+  const unsigned char* type;
+  long long n;
+  int nq;
+  int value_is_float;
+  SCtl* sctl;
+  QueryDev q[kMaxQueries];
+};
+
+// Scratch shared by the per-query pipelines: each query's sort/reduce, pane
+// index, emission and carry run back to back before the next query's start.
+struct Scratch {
+  unsigned long long* keysA;
+  unsigned* valsA;
+  unsigned long long* keysB;
+  unsigned* valsB;
+  unsigned long long cap;        // entries of keysA/B, valsA/B
+  unsigned* hist;                // 256 * kGrid
+  unsigned long long* chunk;     // kGrid (+1) per-chunk counts / offsets
+  unsigned* pane_id;             // [pane_cap]
+  unsigned long long* pane_begin;// [pane_cap + 1]
+  unsigned long long pane_cap;
+  long long* win_w;              // window list [win_cap]
+  unsigned* win_j0;
+  unsigned* win_j1;
+  unsigned long long* win_rows;  // rows per window, then exclusive offsets
+  unsigned long long* win_scr;   // scratch offset of a big window (or ~0)
+  unsigned long long win_cap;
+  unsigned long long* pool;      // big-window merge scratch (2 buffers per window)
+  unsigned long long pool_cap;   // entries
+};
+
+struct ResultRowDev {  // device image of lms_result_row (48 bytes)
+  long long window_start;
+  long long count;
+  unsigned long long sum;
+  double avg;
+  unsigned key;
+  unsigned mn;
+  unsigned mx;
+  unsigned qid;
+};
+
+constexpr int kGrid = 296;         // CTAs of the chunked (count/scan/write) kernels
+constexpr int kChunkThreads = 256;
+
+// ---- launch wrappers (kernels_*.cu) -------------------------------------
+// All enqueue on `st` and return the launch error.
+cudaError_t launch_batch_begin(SCtl* sctl, QCtl* const* ctls, int nq, cudaStream_t st);
+cudaError_t launch_k1(const K1Args& a, int variant, int grid, cudaStream_t st);
+int k1_max_grid(int device, int variant, int value_is_float);
+int k1_tile_events();
+cudaError_t launch_watermark(SCtl* sctl, const QueryDev* qs, int nq, long long lateness, int eos,
+                             cudaStream_t st);
+cudaError_t launch_sort_reduce(const QueryDev& q, const Scratch& s, cudaStream_t st,
+                               int* launches);
+cudaError_t launch_pane_index(const QueryDev& q, const Scratch& s, cudaStream_t st,
+                              int* launches);
+cudaError_t launch_emit(const QueryDev& q, const Scratch& s, ResultRowDev* rows,
+                        unsigned long long rows_cap, int sms, cudaStream_t st, int* launches,
+                        cudaEvent_t* ev4);
+cudaError_t launch_trim(const QueryDev& q, const Scratch& s, int sms, cudaStream_t st,
+                        int* launches);
+
+// Invariant division constants (Granlund & Montgomery 1994, unsigned, N=64).
+void udiv_constants(unsigned long long d, unsigned long long* magic, int* sh1, int* sh2);
+
+}  // namespace lms

@@ -1,0 +1,278 @@
+"""Python binding of the C ABI in include/lmstream.h (argument marshalling only).
+
+Every step of the hot path runs in the CUDA library `liblmstream.so` built
+in-tree by `paper_2111_04289_b300.build`; this module only converts Python /
+numpy / torch arguments into the C structs and pointers the ABI takes.  There
+is no CPU fallback: if the library is missing, importing it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+LMS_OK, LMS_EINVAL, LMS_ENOMEM, LMS_EAGAIN, LMS_ETIMEDOUT = 0, -1, -2, -3, -4
+LMS_ECUDA, LMS_ECLOSED, LMS_ERANGE, LMS_EDEVICE = -5, -6, -7, -8
+STATUS_NAMES = {0: "LMS_OK", -1: "LMS_EINVAL", -2: "LMS_ENOMEM", -3: "LMS_EAGAIN",
+                -4: "LMS_ETIMEDOUT", -5: "LMS_ECUDA", -6: "LMS_ECLOSED", -7: "LMS_ERANGE",
+                -8: "LMS_EDEVICE"}
+VALUE_INT32, VALUE_FLOAT32 = 0, 1
+COLS = {"ts": 0, "key": 1, "value": 2, "type": 3}
+OPS = {"none": 0, "eq": 1, "ne": 2, "lt": 3, "le": 4, "gt": 5, "ge": 6}
+AGG_COUNT, AGG_SUM, AGG_MIN, AGG_MAX, AGG_AVG, AGG_ALL = 1, 2, 4, 8, 16, 31
+MEM_HOST, MEM_DEVICE = 0, 1
+BATCH_EOS = 1
+ORIGIN_AUTO = -(2 ** 63)
+
+# numpy images of lms_result_row (48 bytes) for the two value types
+ROW_DTYPE_INT = np.dtype([("window_start", "<i8"), ("count", "<i8"), ("sum", "<i8"),
+                          ("avg", "<f8"), ("key", "<u4"), ("min", "<i4"), ("max", "<i4"),
+                          ("query_id", "<u4")])
+ROW_DTYPE_FLOAT = np.dtype([("window_start", "<i8"), ("count", "<i8"), ("sum", "<f8"),
+                            ("avg", "<f8"), ("key", "<u4"), ("min", "<f4"), ("max", "<f4"),
+                            ("query_id", "<u4")])
+
+
+class StreamConfig(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("value_type", ctypes.c_int32),
+                ("has_type", ctypes.c_int32), ("enable_timing", ctypes.c_int32),
+                ("allowed_lateness_ms", ctypes.c_int64), ("max_batch_rows", ctypes.c_int64),
+                ("state_cap_bytes", ctypes.c_uint64), ("cuda_stream", ctypes.c_void_p),
+                ("origin_ts", ctypes.c_int64), ("k1_variant", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 7)]
+
+
+class QuerySpec(ctypes.Structure):
+    _fields_ = [("filter_col", ctypes.c_int32), ("filter_op", ctypes.c_int32),
+                ("filter_i", ctypes.c_int64), ("filter_f", ctypes.c_double),
+                ("window_size_ms", ctypes.c_int64), ("window_slide_ms", ctypes.c_int64),
+                ("agg_mask", ctypes.c_uint32), ("reserved", ctypes.c_int32)]
+
+
+class BatchC(ctypes.Structure):
+    _fields_ = [("n_rows", ctypes.c_int64), ("ts", ctypes.c_void_p), ("key", ctypes.c_void_p),
+                ("value", ctypes.c_void_p), ("type", ctypes.c_void_p),
+                ("memory", ctypes.c_int32), ("flags", ctypes.c_uint32),
+                ("arrival_ns", ctypes.c_int64)]
+
+
+class StatsC(ctypes.Structure):
+    _fields_ = [("batches", ctypes.c_uint64), ("events", ctypes.c_uint64),
+                ("late_rows", ctypes.c_uint64), ("range_rows", ctypes.c_uint64),
+                ("rows_emitted", ctypes.c_uint64), ("rows_pending", ctypes.c_uint64),
+                ("watermark", ctypes.c_int64), ("state_groups", ctypes.c_uint64),
+                ("device_bytes", ctypes.c_uint64), ("last_batch_ms", ctypes.c_double),
+                ("k1_ms", ctypes.c_double), ("sort_ms", ctypes.c_double),
+                ("emit_ms", ctypes.c_double), ("h2d_ms", ctypes.c_double),
+                ("k1_launches", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
+                ("e1_ms", ctypes.c_double), ("e2_ms", ctypes.c_double),
+                ("partials", ctypes.c_uint64), ("groups_built", ctypes.c_uint64)]
+
+
+EXPORTED_SYMBOLS = ("stream_open", "query_register", "push_microbatch", "poll_results",
+                    "stream_close", "lms_stream_stats", "lms_last_error", "lms_results_device",
+                    "lms_results_discard", "lms_udiv_invariant")
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Loads liblmstream.so (building it first if asked); raises if unavailable."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        if not build_if_missing:
+            raise RuntimeError(f"CUDA engine library not built: {_build.LIB}")
+        _build.build()
+    lib = ctypes.CDLL(_build.LIB)
+    P = ctypes.c_void_p
+    lib.stream_open.restype = ctypes.c_int32
+    lib.stream_open.argtypes = [ctypes.POINTER(StreamConfig), ctypes.POINTER(P)]
+    lib.query_register.restype = ctypes.c_int32
+    lib.query_register.argtypes = [P, ctypes.POINTER(QuerySpec), ctypes.POINTER(ctypes.c_int32)]
+    lib.push_microbatch.restype = ctypes.c_int32
+    lib.push_microbatch.argtypes = [P, ctypes.POINTER(BatchC)]
+    lib.poll_results.restype = ctypes.c_int32
+    lib.poll_results.argtypes = [P, ctypes.c_int32, P, ctypes.c_size_t,
+                                 ctypes.POINTER(ctypes.c_size_t), ctypes.c_int32]
+    lib.stream_close.restype = ctypes.c_int32
+    lib.stream_close.argtypes = [P]
+    lib.lms_stream_stats.restype = ctypes.c_int32
+    lib.lms_stream_stats.argtypes = [P, ctypes.POINTER(StatsC)]
+    lib.lms_last_error.restype = ctypes.c_char_p
+    lib.lms_last_error.argtypes = [P]
+    lib.lms_results_device.restype = ctypes.c_int32
+    lib.lms_results_device.argtypes = [P, ctypes.c_int32, ctypes.POINTER(P),
+                                       ctypes.POINTER(ctypes.c_size_t)]
+    lib.lms_results_discard.restype = ctypes.c_int32
+    lib.lms_results_discard.argtypes = [P, ctypes.c_int32]
+    lib.lms_udiv_invariant.restype = ctypes.c_uint64
+    lib.lms_udiv_invariant.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+    _lib = lib
+    return lib
+
+
+class LmsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _ptr_and_mem(x):
+    """(address, memory kind, keepalive) of a numpy array or torch tensor column."""
+    if x is None:
+        return None, None, None
+    if isinstance(x, np.ndarray):
+        x = np.ascontiguousarray(x)
+        return x.ctypes.data, MEM_HOST, x
+    # torch tensor
+    if not x.is_contiguous():
+        x = x.contiguous()
+    return x.data_ptr(), (MEM_DEVICE if x.is_cuda else MEM_HOST), x
+
+
+class Stream:
+    """One engine stream: register queries, push micro-batches, poll rows."""
+
+    def __init__(self, value_type: str = "int32", has_type: bool = False, device: int = 0,
+                 allowed_lateness_ms: int = 0, max_batch_rows: int = 0, state_cap_bytes: int = 0,
+                 cuda_stream: Optional[int] = None, origin_ts: Optional[int] = None,
+                 enable_timing: bool = False, k1_variant: int = 0):
+        self._lib = load()
+        self.value_type = value_type
+        self.is_float = value_type == "float32"
+        cfg = StreamConfig()
+        cfg.device = device
+        cfg.value_type = VALUE_FLOAT32 if self.is_float else VALUE_INT32
+        cfg.has_type = int(bool(has_type))
+        cfg.enable_timing = int(bool(enable_timing))
+        cfg.allowed_lateness_ms = int(allowed_lateness_ms)
+        cfg.max_batch_rows = int(max_batch_rows)
+        cfg.state_cap_bytes = int(state_cap_bytes)
+        cfg.cuda_stream = cuda_stream
+        cfg.origin_ts = ORIGIN_AUTO if origin_ts is None else int(origin_ts)
+        cfg.k1_variant = int(k1_variant)
+        h = ctypes.c_void_p()
+        st = self._lib.stream_open(ctypes.byref(cfg), ctypes.byref(h))
+        if st != LMS_OK:
+            raise LmsError(st, "stream_open failed")
+        self._h = h
+        self.has_type = bool(has_type)
+        self.row_dtype = ROW_DTYPE_FLOAT if self.is_float else ROW_DTYPE_INT
+        self.queries = []
+
+    def _check(self, st: int, what: str):
+        if st != LMS_OK:
+            msg = self._lib.lms_last_error(self._h)
+            raise LmsError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    def register_query(self, size_ms: int, slide_ms: int = 0, filter_col: str = "ts",
+                       filter_op: str = "none", filter_value=0, agg_mask: int = AGG_ALL) -> int:
+        q = QuerySpec()
+        q.filter_col = COLS[filter_col]
+        q.filter_op = OPS[filter_op]
+        if filter_col == "value" and self.is_float:
+            q.filter_f = float(filter_value)
+        else:
+            q.filter_i = int(filter_value)
+        q.window_size_ms = int(size_ms)
+        q.window_slide_ms = int(slide_ms)
+        q.agg_mask = int(agg_mask)
+        qid = ctypes.c_int32()
+        self._check(self._lib.query_register(self._h, ctypes.byref(q), ctypes.byref(qid)),
+                    "query_register")
+        self.queries.append((size_ms, slide_ms or size_ms))
+        return qid.value
+
+    def push(self, ts, key, value, type_=None, eos: bool = False, arrival_ns: int = 0) -> int:
+        """Pushes one micro-batch (numpy host arrays or torch host/device tensors)."""
+        pt, mem, k0 = _ptr_and_mem(ts)
+        pk, mk, k1 = _ptr_and_mem(key)
+        pv, mv, k2 = _ptr_and_mem(value)
+        py, my, k3 = _ptr_and_mem(type_ if self.has_type else None)
+        n = int(ts.shape[0])
+        if len({m for m in (mem, mk, mv, my) if m is not None}) > 1:
+            raise ValueError("all columns of a batch must live in the same memory")
+        b = BatchC()
+        b.n_rows = n
+        b.ts, b.key, b.value, b.type = pt, pk, pv, py
+        b.memory = MEM_HOST if mem is None else mem
+        b.flags = BATCH_EOS if eos else 0
+        b.arrival_ns = int(arrival_ns)
+        st = self._lib.push_microbatch(self._h, ctypes.byref(b))
+        del k0, k1, k2, k3
+        self._check(st, "push_microbatch")
+        return n
+
+    def poll(self, qid: int, max_rows: Optional[int] = None) -> np.ndarray:
+        """All (or up to max_rows) pending rows of query qid, oldest first."""
+        avail = self.pending(qid)
+        m = avail if max_rows is None else min(avail, max_rows)
+        out = np.zeros(m, dtype=self.row_dtype)
+        if m == 0:
+            return out
+        got = ctypes.c_size_t()
+        st = self._lib.poll_results(self._h, qid, out.ctypes.data, m, ctypes.byref(got), 0)
+        self._check(st, "poll_results")
+        return out[: got.value]
+
+    def poll_into(self, qid: int, out_ptr: int, cap: int) -> int:
+        """poll_results into a caller buffer (e.g. pinned memory); returns rows copied."""
+        got = ctypes.c_size_t()
+        st = self._lib.poll_results(self._h, qid, out_ptr, cap, ctypes.byref(got), 0)
+        if st == LMS_EAGAIN:
+            return 0
+        self._check(st, "poll_results")
+        return got.value
+
+    def pending(self, qid: int) -> int:
+        p = ctypes.c_void_p()
+        n = ctypes.c_size_t()
+        self._check(self._lib.lms_results_device(self._h, qid, ctypes.byref(p), ctypes.byref(n)),
+                    "lms_results_device")
+        return n.value
+
+    def results_device(self, qid: int):
+        p = ctypes.c_void_p()
+        n = ctypes.c_size_t()
+        self._check(self._lib.lms_results_device(self._h, qid, ctypes.byref(p), ctypes.byref(n)),
+                    "lms_results_device")
+        return p.value, n.value
+
+    def discard(self, qid: int):
+        self._check(self._lib.lms_results_discard(self._h, qid), "lms_results_discard")
+
+    def stats(self) -> dict:
+        s = StatsC()
+        self._check(self._lib.lms_stream_stats(self._h, ctypes.byref(s)), "lms_stream_stats")
+        return {name: getattr(s, name) for name, _ in StatsC._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.stream_close(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def udiv_invariant(n: int, d: int) -> int:
+    return int(load().lms_udiv_invariant(n, d))
