@@ -222,6 +222,40 @@ lms_status lms_results_device(lms_stream *s, int32_t query_id, const lms_result_
 /* Drops query_id's unpolled rows (e.g. after consuming them on the device). */
 lms_status lms_results_discard(lms_stream *s, int32_t query_id);
 
+/* Largest n_rows lms_aggregate_batch_static accepts. */
+#define LMS_STATIC_MAX_ROWS 131072
+
+/* Allocation-free variant for callers that may not allocate device memory
+ * (plug-ins hosted in a process that owns the device memory budget, serving
+ * paths where allocation is forbidden).  The paper has no counterpart: it is
+ * the stream API's hot path run once, as a whole stream, over one batch.
+ *
+ * Aggregates the n_rows events in device memory (ts, key, value, optional type)
+ * for query q exactly as stream_open + query_register + one push_microbatch
+ * with LMS_BATCH_EOS + poll_results would (same kernels, same rows, same
+ * order), on the calling thread's current device and on cuda_stream (NULL:
+ * the legacy default stream).  Rows go to the caller's DEVICE buffer
+ * rows[0 .. rows_cap); *n_out receives their number.  The first row's ts is
+ * the event-time origin.  Returns when the rows are written.
+ *
+ * Every intermediate buffer lives in one fixed array of about 26 MiB that the
+ * library declares in device memory: it is present on every GPU that loads the
+ * library until the process exits, and this function calls no cudaMalloc,
+ * cudaFree or other allocating routine.  The first call on a device looks the
+ * array up (cudaGetSymbolAddress); make it before any stream capture.  All
+ * calls share the array and leave their data in it; each call first resets the
+ * parts that must start from zero.  Calls are serialised inside the library;
+ * other work touching the array concurrently would race.
+ *
+ * Errors: LMS_EINVAL for a bad argument or n_rows > LMS_STATIC_MAX_ROWS;
+ * LMS_ENOMEM if the closed windows (at most 131072), a window's merge scratch
+ * or the rows do not fit (rows_cap >= n_rows * size/slide always suffices);
+ * LMS_ECUDA for a CUDA failure; LMS_EDEVICE for an internal kernel flag. */
+lms_status lms_aggregate_batch_static(const lms_query_spec *q, int32_t value_type,
+                                      const int64_t *ts, const uint32_t *key, const void *value,
+                                      const uint8_t *type, int64_t n_rows, void *cuda_stream,
+                                      lms_result_row *rows, size_t rows_cap, size_t *n_out);
+
 /* Floor division helper the kernels use for window ids, exposed so that host
  * tests can check it: returns n / d for d >= 1 computed by the invariant
  * multiply-and-shift method of Granlund & Montgomery (1994). */

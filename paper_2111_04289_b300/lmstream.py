@@ -75,7 +75,8 @@ class StatsC(ctypes.Structure):
 
 EXPORTED_SYMBOLS = ("stream_open", "query_register", "push_microbatch", "poll_results",
                     "stream_close", "lms_stream_stats", "lms_last_error", "lms_results_device",
-                    "lms_results_discard", "lms_udiv_invariant")
+                    "lms_results_discard", "lms_udiv_invariant", "lms_aggregate_batch_static")
+STATIC_MAX_ROWS = 131072
 
 _lib = None
 
@@ -117,6 +118,10 @@ def load(build_if_missing: bool = True):
     lib.lms_results_discard.argtypes = [P, ctypes.c_int32]
     lib.lms_udiv_invariant.restype = ctypes.c_uint64
     lib.lms_udiv_invariant.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+    lib.lms_aggregate_batch_static.restype = ctypes.c_int32
+    lib.lms_aggregate_batch_static.argtypes = [
+        ctypes.POINTER(QuerySpec), ctypes.c_int32, P, P, P, P, ctypes.c_int64, P, P,
+        ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
     _lib = lib
     return lib
 
@@ -276,3 +281,33 @@ class Stream:
 
 def udiv_invariant(n: int, d: int) -> int:
     return int(load().lms_udiv_invariant(n, d))
+
+
+def aggregate_batch_static(ts, key, value, type_=None, *, value_type: str, size_ms: int,
+                           slide_ms: int = 0, filter_col: str = "ts", filter_op: str = "none",
+                           filter_value=0, agg_mask: int = AGG_ALL, rows_ptr: int, rows_cap: int,
+                           cuda_stream: Optional[int] = None) -> int:
+    """lms_aggregate_batch_static on device tensors; rows go to the device buffer
+    at rows_ptr (rows_cap rows of 48 bytes).  Returns the number of rows."""
+    lib = load()
+    q = QuerySpec()
+    q.filter_col = COLS[filter_col]
+    q.filter_op = OPS[filter_op]
+    if filter_col == "value" and value_type == "float32":
+        q.filter_f = float(filter_value)
+    else:
+        q.filter_i = int(filter_value)
+    q.window_size_ms = int(size_ms)
+    q.window_slide_ms = int(slide_ms)
+    q.agg_mask = int(agg_mask)
+    cols = [_ptr_and_mem(c) for c in (ts, key, value, type_)]
+    if any(m == MEM_HOST for _, m, _ in cols):
+        raise ValueError("lms_aggregate_batch_static reads device memory only")
+    n = ctypes.c_size_t()
+    st = lib.lms_aggregate_batch_static(
+        ctypes.byref(q), VALUE_FLOAT32 if value_type == "float32" else VALUE_INT32,
+        cols[0][0], cols[1][0], cols[2][0], cols[3][0], int(ts.shape[0]), cuda_stream,
+        rows_ptr, int(rows_cap), ctypes.byref(n))
+    if st != LMS_OK:
+        raise LmsError(st, "lms_aggregate_batch_static")
+    return n.value
