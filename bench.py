@@ -187,7 +187,8 @@ def run_ours(args):
     batches = synth.device_large_float_batches(torch, nb, n, synth.BASE_SEED + 100 + rank, dev)
     torch.cuda.synchronize()
     cur = torch.cuda.current_stream()
-    s = lm.Stream("float32", device=local, cuda_stream=cur.cuda_stream, enable_timing=True)
+    s = lm.Stream("float32", device=local, cuda_stream=cur.cuda_stream, enable_timing=True,
+                  k1_variant=args.k1_variant)
     qid = s.register_query(WINDOW_SIZE_MS, WINDOW_SLIDE_MS, "value", "gt", FILTER_GT)
     for i in range(args.warmup):
         b = batches[i]
@@ -326,6 +327,7 @@ def main():
     ap.add_argument("--ref-log2", type=int, default=20)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--k1-variant", type=int, default=0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: warmup < 3 is below the timing rules", file=sys.stderr)

@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <chrono>
 #include <climits>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -21,6 +22,17 @@
 #include "lms_internal.h"
 
 namespace lms {
+
+void set_float_filter(QueryDev* d) {
+  const double c = d->filter_f;
+  const float f = (float)c;
+  float lo = f, hi = f;
+  if ((double)f > c) lo = std::nextafter(f, -INFINITY);
+  else if ((double)f < c) hi = std::nextafter(f, INFINITY);
+  d->filter_lo = lo;
+  d->filter_hi = hi;
+  d->filter_exact = (lo == hi) ? 1 : 0;
+}
 
 void udiv_constants(unsigned long long d, unsigned long long* magic, int* sh1, int* sh2) {
   int l = 0;
@@ -155,16 +167,7 @@ lms_status dgrow(lms_stream* s, T** p, unsigned long long old_n, unsigned long l
   return LMS_OK;
 }
 
-lms_status grow_groups(lms_stream* s, Groups* g, unsigned long long old_n, unsigned long long n,
-                       unsigned long long keep) {
-  lms_status r;
-  if ((r = dgrow(s, &g->gkey, old_n, n, keep)) != LMS_OK) return r;
-  if ((r = dgrow(s, &g->cnt, old_n, n, keep)) != LMS_OK) return r;
-  if ((r = dgrow(s, &g->sum, old_n, n, keep)) != LMS_OK) return r;
-  if ((r = dgrow(s, &g->mn, old_n, n, keep)) != LMS_OK) return r;
-  if ((r = dgrow(s, &g->mx, old_n, n, keep)) != LMS_OK) return r;
-  return LMS_OK;
-}
+
 
 unsigned long long round_cap(unsigned long long need) {
   unsigned long long c = 1ull << 12;
@@ -180,8 +183,9 @@ lms_status ensure_group_capacity(lms_stream* s, unsigned long long need) {
     if (q.cap >= need) continue;
     const unsigned long long nc = round_cap(need);
     lms_status r;
-    if ((r = grow_groups(s, &q.dev.parts, q.cap, nc, q.carried)) != LMS_OK) return r;
-    if ((r = grow_groups(s, &q.dev.state, q.cap, nc, 0)) != LMS_OK) return r;
+    if ((r = dgrow(s, &q.dev.parts, q.cap, nc, q.carried)) != LMS_OK) return r;
+    if ((r = dgrow(s, &q.dev.pkeys, q.cap, nc, q.carried)) != LMS_OK) return r;
+    if ((r = dgrow(s, &q.dev.state, q.cap, nc, 0)) != LMS_OK) return r;
     q.cap = nc;
     q.dev.parts_cap = nc;
   }
@@ -317,7 +321,7 @@ lms_status stream_open(const lms_stream_config* cfg, lms_stream** out) {
   SCtl h{};
   h.batch_max_ts = LLONG_MIN;
   cudaMemcpy(s->sctl, &h, sizeof(h), cudaMemcpyHostToDevice);
-  if (dalloc(s, &p, sizeof(unsigned) * 256 * kGrid) != LMS_OK ||
+  if (dalloc(s, &p, sizeof(unsigned) * (256 * kGrid + 256)) != LMS_OK ||
       (s->scr.hist = static_cast<unsigned*>(p), dalloc(s, &p, sizeof(unsigned long long) * (kGrid + 1))) != LMS_OK) {
     stream_close(s);
     return LMS_ENOMEM;
@@ -358,6 +362,7 @@ lms_status query_register(lms_stream* s, const lms_query_spec* q, int32_t* query
   d.filter_op = q->filter_op;
   d.filter_i = q->filter_i;
   d.filter_f = q->filter_f;
+  set_float_filter(&d);
   d.slide = (unsigned long long)slide;
   udiv_constants(d.slide, &d.magic, &d.sh1, &d.sh2);
   d.size = size;

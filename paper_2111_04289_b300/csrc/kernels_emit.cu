@@ -18,9 +18,21 @@
 namespace lms {
 namespace {
 
-constexpr int kEmitThreads = 512;
-constexpr unsigned kEmitCap = 12288;  // entries per shared buffer (2 buffers, 192 KB)
-constexpr size_t kEmitSmem = 2ull * kEmitCap * sizeof(unsigned long long);
+constexpr int kEmitThreads = 1024;
+constexpr size_t kEmitSmemMax = 225 * 1024;  // dynamic shared memory of the emit kernel
+// Largest window (entries) merged in shared memory for windows of k panes:
+// two padded buffers (17 slots per 16 entries) plus two (k+1)-entry boundary
+// arrays must fit in kEmitSmemMax.
+inline unsigned emit_cap(int k) {
+  const size_t avail = kEmitSmemMax - 2ull * (k + 1) * sizeof(unsigned) - 64;
+  const size_t padded = avail / (2 * sizeof(unsigned long long));
+  return (unsigned)(((padded - 1) * 16 / 17) & ~size_t(15));
+}
+inline size_t emit_smem(int k) {
+  const unsigned cap = emit_cap(k);
+  return 2ull * (cap + (cap >> 4) + 1) * sizeof(unsigned long long) +
+         2ull * (k + 1) * sizeof(unsigned);
+}
 
 __device__ __forceinline__ long long floor_div_ll(long long a, long long b) {
   long long q = a / b;
@@ -156,16 +168,25 @@ __global__ void __launch_bounds__(256) k_win_write(const QueryDev q, const Scrat
   }
 }
 
+// Index of element i in a merge buffer.  Shared buffers are padded by one
+// slot per 16 elements so that threads writing consecutive chunks do not all
+// hit the same bank; global scratch is not padded.
+template <bool PAD>
+__device__ __forceinline__ unsigned pix(unsigned i) { return PAD ? i + (i >> 4) : i; }
+
 // Pairwise merge rounds of `nr` sorted runs of A (boundaries bc[0..nr],
 // bc[nr] = len), ping-ponging with B.  Values are distinct.  Returns the
-// buffer holding the fully merged sequence.  All threads must call.
+// buffer holding the fully merged sequence.  All threads must call.  Each
+// round gives every thread one chunk of about len / blockDim outputs.
+template <bool PAD>
 __device__ unsigned long long* merge_runs(unsigned long long* A, unsigned long long* B,
                                           unsigned* bc, unsigned* bn, int nr, unsigned len) {
+  const unsigned chunk = max(4u, (len + blockDim.x - 1) / blockDim.x);
   while (nr > 1) {
     const int np = (nr + 1) >> 1;
-    for (unsigned ch = threadIdx.x; ch * 8u < len; ch += blockDim.x) {
-      unsigned o = ch * 8u;
-      const unsigned oe = min(len, o + 8u);
+    for (unsigned ch = threadIdx.x; ch * chunk < len; ch += blockDim.x) {
+      unsigned o = ch * chunk;
+      const unsigned oe = min(len, o + chunk);
       // pair m holding output position o: largest m with bc[2m] <= o
       int lo = 0, hi = np - 1;
       while (lo < hi) {
@@ -181,13 +202,23 @@ __device__ unsigned long long* merge_runs(unsigned long long* A, unsigned long l
         unsigned a = diag > lb ? diag - lb : 0u, b = min(diag, la);
         while (a < b) {
           const unsigned mid = (a + b) >> 1;
-          if (A[s0 + mid] < A[s1 + diag - 1u - mid]) a = mid + 1u; else b = mid;
+          if (A[pix<PAD>(s0 + mid)] < A[pix<PAD>(s1 + diag - 1u - mid)]) a = mid + 1u;
+          else b = mid;
         }
         unsigned i = a, k = diag - a;
         const unsigned stop = min(oe, s2);
+        unsigned long long va = i < la ? A[pix<PAD>(s0 + i)] : ~0ull;
+        unsigned long long vb = k < lb ? A[pix<PAD>(s1 + k)] : ~0ull;
         while (o < stop) {
-          if (k >= lb || (i < la && A[s0 + i] < A[s1 + k])) B[o++] = A[s0 + i++];
-          else B[o++] = A[s1 + k++];
+          if (k >= lb || (i < la && va < vb)) {
+            B[pix<PAD>(o++)] = va;
+            ++i;
+            va = i < la ? A[pix<PAD>(s0 + i)] : ~0ull;
+          } else {
+            B[pix<PAD>(o++)] = vb;
+            ++k;
+            vb = k < lb ? A[pix<PAD>(s1 + k)] : ~0ull;
+          }
         }
         ++m;
       }
@@ -200,6 +231,31 @@ __device__ unsigned long long* merge_runs(unsigned long long* A, unsigned long l
     nr = np;
   }
   return A;
+}
+
+// Exclusive rank of `flag` among the block's threads and the block total, by
+// warp ballots.  wt holds 2 x 33 counters; alternate `parity` between calls.
+__device__ __forceinline__ unsigned block_rank(bool flag, unsigned* wt, int parity,
+                                               unsigned* total) {
+  unsigned* t = wt + parity * 33;
+  const unsigned lane = lane_id(), w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const unsigned b = __ballot_sync(kFull, flag);
+  if (lane == 0) t[w] = __popc(b);
+  __syncthreads();
+  if (w == 0) {
+    const unsigned x = lane < nw ? t[lane] : 0u;
+    unsigned inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(kFull, inc, o);
+      if ((int)lane >= o) inc += y;
+    }
+    if (lane < nw) t[lane] = inc - x;
+    if (lane == 31) t[32] = inc;
+  }
+  __syncthreads();
+  *total = t[32];
+  return t[w] + __popc(b & ((1u << lane) - 1u));
 }
 
 template <bool FLOAT>
@@ -220,19 +276,90 @@ __device__ __forceinline__ void write_row(const QueryDev& q, ResultRowDev* out, 
   o[2] = make_uint4(key, mnv, mxv, (unsigned)q.qid);
 }
 
+// Combines the state groups S[i..e) (one key, pane order) of a window.  Loads
+// are issued two records at a time so that their latencies overlap.
+template <bool FLOAT, bool PAD>
+__device__ __forceinline__ void combine_run(const QueryDev& q, const unsigned long long* S,
+                                            unsigned i, unsigned e, unsigned long long b0,
+                                            long long* cnt, unsigned long long* sbits,
+                                            unsigned* mn, unsigned* mx) {
+  long long c = 0;
+  unsigned long long isum = 0ull;
+  double fsum = 0.0;
+  unsigned lo = 0xffffffffu, hi = 0u;
+  for (unsigned t = i; t < e; t += 2) {
+    Grp g[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+      if (t + u < e) g[u] = load_grp(q.state + b0 + (S[pix<PAD>(t + u)] & 0xffffffffull));
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (t + u < e) {
+        c += g[u].cnt;
+        if (FLOAT) fsum += __longlong_as_double((long long)g[u].sum);
+        else isum += g[u].sum;
+        lo = min(lo, g[u].mn);
+        hi = max(hi, g[u].mx);
+      }
+    }
+  }
+  *cnt = c;
+  *sbits = FLOAT ? (unsigned long long)__double_as_longlong(fsum) : isum;
+  *mn = lo;
+  *mx = hi;
+}
+
+// Distinct keys of the merged window S[0..len): their count (E1) or their
+// rows (E2), in key order.
+template <bool FLOAT, bool WRITE, bool PAD>
+__device__ __forceinline__ unsigned long long emit_distinct(
+    const QueryDev& q, const unsigned long long* S, unsigned len, unsigned long long b0,
+    long long wstart, ResultRowDev* out, unsigned* wt, int* parity) {
+  unsigned long long run = 0;
+  for (unsigned i0 = 0; i0 < len; i0 += blockDim.x) {
+    const unsigned i = i0 + threadIdx.x;
+    const unsigned long long x = i < len ? S[pix<PAD>(i)] : 0ull;
+    const bool head = i < len && (i == 0 || (x >> 32) != (S[pix<PAD>(i - 1)] >> 32));
+    if (!WRITE) {
+      run += (unsigned)__syncthreads_count(head);
+      continue;
+    }
+    unsigned tot;
+    const unsigned r = block_rank(head, wt, *parity, &tot);
+    *parity ^= 1;
+    if (head) {
+      const unsigned key = (unsigned)(x >> 32);
+      unsigned e = i + 1;
+      while (e < len && (unsigned)(S[pix<PAD>(e)] >> 32) == key) ++e;
+      long long cnt;
+      unsigned long long sb;
+      unsigned mn, mx;
+      combine_run<FLOAT, PAD>(q, S, i, e, b0, &cnt, &sb, &mn, &mx);
+      write_row<FLOAT>(q, out + run + r, wstart, key, cnt, sb, mn, mx);
+    }
+    run += tot;
+  }
+  return run;
+}
+
 // E1 (WRITE=false): rows per closed window.  E2 (WRITE=true): the rows.
+// Dynamic shared memory: two padded merge buffers of `cap` entries, then two
+// run-boundary arrays of k + 1 entries.
 template <bool FLOAT, bool WRITE>
 __global__ void __launch_bounds__(kEmitThreads, 1)
     k_emit(const QueryDev q, const Scratch s, ResultRowDev* rows, unsigned cap) {
   extern __shared__ __align__(16) unsigned long long esm[];
-  __shared__ unsigned bnd0[kMaxRuns + 1], bnd1[kMaxRuns + 1];
-  __shared__ unsigned long long tmp[33];
+  const unsigned padded = cap + (cap >> 4) + 1;
+  unsigned* bnd0 = reinterpret_cast<unsigned*>(esm + 2ull * padded);
+  unsigned* bnd1 = bnd0 + (q.k + 1);
+  __shared__ unsigned wt[66];
   __shared__ unsigned long long s_off;
   QCtl* c = q.ctl;
   if (c->err & kErrNeedRetry) return;
   const unsigned long long W = c->n_windows;
   const int tid = threadIdx.x;
   const unsigned long long row_base = c->row_base;
+  int parity = 0;
   for (unsigned long long wi = blockIdx.x; wi < W; wi += gridDim.x) {
     const long long w = s.win_w[wi];
     const unsigned j0 = s.win_j0[wi], j1 = s.win_j1[wi];
@@ -240,24 +367,32 @@ __global__ void __launch_bounds__(kEmitThreads, 1)
     const unsigned len = (unsigned)(b1 - b0);
     const int nr = (int)(j1 - j0);
     const long long wstart = (w - kPaneBias) * (long long)q.slide + q.base;
+    ResultRowDev* out = WRITE ? rows + row_base + s.win_rows[wi] : nullptr;
     if (nr == 1) {  // one pane: the state run is already key-sorted and unique
       if (!WRITE) {
         if (tid == 0) s.win_rows[wi] = len;
       } else {
-        ResultRowDev* out = rows + row_base + s.win_rows[wi];
         for (unsigned i = tid; i < len; i += blockDim.x) {
-          const unsigned long long g = b0 + i;
-          write_row<FLOAT>(q, out + i, wstart, (unsigned)q.state.gkey[g], q.state.cnt[g],
-                           q.state.sum[g], q.state.mn[g], q.state.mx[g]);
+          const Grp g = load_grp(q.state + b0 + i);
+          write_row<FLOAT>(q, out + i, wstart, (unsigned)g.gkey, g.cnt, g.sum, g.mn, g.mx);
         }
       }
       continue;
     }
-    const bool big = len > cap;
-    unsigned long long* A;
-    unsigned long long* B;
-    unsigned long long* S;
-    if (big) {
+    if (len <= cap) {  // shared-memory merge
+      unsigned long long* A = esm;
+      unsigned long long* B = esm + padded;
+      for (unsigned i = tid; i < len; i += blockDim.x)
+        A[pix<true>(i)] = ((q.state[b0 + i].gkey & 0xffffffffull) << 32) | i;
+      for (int r = tid; r <= nr; r += blockDim.x)
+        bnd0[r] = (unsigned)(s.pane_begin[j0 + r] - b0);
+      __syncthreads();
+      const unsigned long long* S = merge_runs<true>(A, B, bnd0, bnd1, nr, len);
+      const unsigned long long n =
+          emit_distinct<FLOAT, WRITE, true>(q, S, len, b0, wstart, out, wt, &parity);
+      if (!WRITE && tid == 0) s.win_rows[wi] = n;
+    } else {  // global-scratch merge; E1 merges, E2 reuses the merged result
+      const unsigned long long* S;
       if (!WRITE) {
         if (tid == 0) {
           unsigned long long off = atomicAdd(&c->pool_used, 2ull * len);
@@ -276,55 +411,22 @@ __global__ void __launch_bounds__(kEmitThreads, 1)
           if (tid == 0) s.win_rows[wi] = 0ull;
           continue;
         }
-        A = s.pool + off;
-        B = A + len;
+        unsigned long long* A = s.pool + off;
+        unsigned long long* B = A + len;
+        for (unsigned i = tid; i < len; i += blockDim.x)
+          A[i] = ((q.state[b0 + i].gkey & 0xffffffffull) << 32) | i;
+        for (int r = tid; r <= nr; r += blockDim.x)
+          bnd0[r] = (unsigned)(s.pane_begin[j0 + r] - b0);
+        __syncthreads();
+        S = merge_runs<false>(A, B, bnd0, bnd1, nr, len);
+        if (tid == 0) s.win_scr[wi] = (unsigned long long)(S - s.pool);
       } else {
         S = s.pool + s.win_scr[wi];
       }
-    } else {
-      A = esm;
-      B = esm + cap;
+      const unsigned long long n =
+          emit_distinct<FLOAT, WRITE, false>(q, S, len, b0, wstart, out, wt, &parity);
+      if (!WRITE && tid == 0) s.win_rows[wi] = n;
     }
-    if (!(WRITE && big)) {
-      for (unsigned i = tid; i < len; i += blockDim.x)
-        A[i] = ((q.state.gkey[b0 + i] & 0xffffffffull) << 32) | i;
-      for (int r = tid; r <= nr; r += blockDim.x)
-        bnd0[r] = (unsigned)(s.pane_begin[j0 + r] - b0);
-      __syncthreads();
-      S = merge_runs(A, B, bnd0, bnd1, nr, len);
-      if (!WRITE && big && tid == 0) s.win_scr[wi] = (unsigned long long)(S - s.pool);
-    }
-    // distinct keys of the merged run
-    unsigned long long run = 0;
-    for (unsigned i0 = 0; i0 < len; i0 += blockDim.x) {
-      const unsigned i = i0 + tid;
-      const bool v = i < len;
-      const unsigned long long x = v ? S[i] : 0ull;
-      const bool head = v && (i == 0 || (x >> 32) != (S[i - 1] >> 32));
-      unsigned long long tot;
-      const unsigned long long r = block_excl_scan(head ? 1ull : 0ull, tmp, &tot);
-      if (WRITE && head) {
-        const unsigned key = (unsigned)(x >> 32);
-        long long cnt = 0;
-        unsigned long long isum = 0ull;
-        double fsum = 0.0;
-        unsigned mn = 0xffffffffu, mx = 0u;
-        for (unsigned t = i; t < len && (unsigned)(S[t] >> 32) == key; ++t) {
-          const unsigned long long g = b0 + (S[t] & 0xffffffffull);
-          cnt += q.state.cnt[g];
-          if (FLOAT) fsum += __longlong_as_double((long long)q.state.sum[g]);
-          else isum += q.state.sum[g];
-          mn = min(mn, q.state.mn[g]);
-          mx = max(mx, q.state.mx[g]);
-        }
-        const unsigned long long sb =
-            FLOAT ? (unsigned long long)__double_as_longlong(fsum) : isum;
-        write_row<FLOAT>(q, rows + row_base + s.win_rows[wi] + run + r, wstart, key, cnt, sb, mn,
-                         mx);
-      }
-      run += tot;
-    }
-    if (!WRITE && tid == 0) s.win_rows[wi] = run;
     __syncthreads();
   }
 }
@@ -403,14 +505,11 @@ __global__ void __launch_bounds__(256) k_trim_copy(const QueryDev q) {
   unsigned long long o_acc = 0ull, a_acc = ~0ull;
   for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
        i += (unsigned long long)gridDim.x * blockDim.x) {
-    const unsigned long long g = q.state.gkey[from + i];
-    q.parts.gkey[i] = g;
-    q.parts.cnt[i] = q.state.cnt[from + i];
-    q.parts.sum[i] = q.state.sum[from + i];
-    q.parts.mn[i] = q.state.mn[from + i];
-    q.parts.mx[i] = q.state.mx[from + i];
-    o_acc |= g;
-    a_acc &= g;
+    const Grp g = load_grp(q.state + from + i);
+    store_grp(q.parts + i, g.gkey, g.cnt, g.sum, g.mn, g.mx);
+    q.pkeys[i] = g.gkey;
+    o_acc |= g.gkey;
+    a_acc &= g.gkey;
   }
   const unsigned olo = __reduce_or_sync(kFull, (unsigned)o_acc);
   const unsigned ohi = __reduce_or_sync(kFull, (unsigned)(o_acc >> 32));
@@ -431,11 +530,11 @@ cudaError_t launch_emit_t(const QueryDev& q, const Scratch& s, ResultRowDev* row
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k_emit<FLOAT, WRITE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kEmitSmem);
+                                         (int)kEmitSmemMax);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  k_emit<FLOAT, WRITE><<<grid, kEmitThreads, smem, st>>>(q, s, rows, smem ? kEmitCap : 0u);
+  k_emit<FLOAT, WRITE><<<grid, kEmitThreads, smem, st>>>(q, s, rows, smem ? emit_cap(q.k) : 0u);
   return cudaGetLastError();
 }
 
@@ -473,7 +572,7 @@ cudaError_t launch_emit(const QueryDev& q, const Scratch& s, ResultRowDev* rows,
   k_win_scan<<<1, 1024, 0, st>>>(q, s);
   k_win_write<<<kGrid, 256, 0, st>>>(q, s);
   // Tumbling windows (one pane each) need no merge buffers.
-  const size_t smem = q.k > 1 ? kEmitSmem : 0;
+  const size_t smem = q.k > 1 ? emit_smem(q.k) : 0;
   const int grid = q.k > 1 ? sms : 4 * sms;
   if (ev4) cudaEventRecord(ev4[0], st);
   cudaError_t e = q.value_is_float ? launch_emit_t<true, false>(q, s, rows, grid, smem, st)

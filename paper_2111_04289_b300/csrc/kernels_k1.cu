@@ -146,7 +146,8 @@ __global__ void __launch_bounds__(kK1Threads, 1) k1_fused(const __grid_constant_
         bool ok = valid[i];
         if (ok && fop != 0) {
           if (fcol == 2 && FLOAT)
-            ok = filter_pass_f(fop, (double)__uint_as_float(val[i]), Q.filter_f);
+            ok = filter_pass_f32(fop, __uint_as_float(val[i]), Q.filter_lo, Q.filter_hi,
+                                 Q.filter_exact);
           else {
             long long x = fcol == 0 ? ts[i]
                           : fcol == 1 ? (long long)key[i]
@@ -236,11 +237,8 @@ __global__ void __launch_bounds__(kK1Threads, 1) k1_fused(const __grid_constant_
         if (occ & (1u << j)) {
           if (fits) {
             const unsigned long long g = hkey[s];
-            Q.parts.gkey[w] = g;
-            Q.parts.cnt[w] = (long long)hcnt[s];
-            Q.parts.sum[w] = hsum[s];
-            Q.parts.mn[w] = hmn[s];
-            Q.parts.mx[w] = hmx[s];
+            store_grp(Q.parts + w, g, (long long)hcnt[s], hsum[s], hmn[s], hmx[s]);
+            Q.pkeys[w] = g;
             o_acc |= g;
             a_acc &= g;
           }

@@ -29,11 +29,11 @@ struct SortSrc {
 // Pass p reads the previous pass's output (or the partial keys for p == 0)
 // and writes buffer (p & 1) of the scratch pair.
 __device__ __forceinline__ SortSrc pass_src(const QueryDev& q, const Scratch& s, int p) {
-  if (p == 0) return {q.parts.gkey, nullptr};
+  if (p == 0) return {q.pkeys, nullptr};
   return ((p - 1) & 1) ? SortSrc{s.keysB, s.valsB} : SortSrc{s.keysA, s.valsA};
 }
 __device__ __forceinline__ SortSrc final_src(const QueryDev& q, const Scratch& s, int np) {
-  if (np == 0) return {q.parts.gkey, nullptr};
+  if (np == 0) return {q.pkeys, nullptr};
   return ((np - 1) & 1) ? SortSrc{s.keysB, s.valsB} : SortSrc{s.keysA, s.valsA};
 }
 
@@ -70,23 +70,20 @@ __global__ void __launch_bounds__(256) k_sort_hist(const QueryDev q, const Scrat
   s.hist[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
 }
 
-// Exclusive scan (in place) of the digit-major histogram: 256 * kGrid entries.
-__global__ void __launch_bounds__(1024) k_sort_scan(const QueryDev q, const Scratch s, int p) {
+// Per digit (one CTA each): exclusive scan over the chunks of hist[d][*] in
+// place, digit total -> hist[256 * kGrid + d].
+__global__ void __launch_bounds__(256) k_sort_scan(const QueryDev q, const Scratch s, int p) {
   if (p >= q.ctl->npasses) return;
   __shared__ unsigned long long tmp[33];
-  const int total = 256 * kGrid;
-  const int per = (total + blockDim.x - 1) / blockDim.x;
-  const int a = threadIdx.x * per;
-  const int b = min(total, a + per);
-  unsigned long long sum = 0;
-  for (int i = a; i < b; ++i) sum += s.hist[i];
+  unsigned* h = s.hist + blockIdx.x * kGrid;
+  const int a = 2 * threadIdx.x;
+  const unsigned x0 = a < kGrid ? h[a] : 0u;
+  const unsigned x1 = a + 1 < kGrid ? h[a + 1] : 0u;
   unsigned long long tot;
-  unsigned long long run = block_excl_scan(sum, tmp, &tot);
-  for (int i = a; i < b; ++i) {
-    const unsigned x = s.hist[i];
-    s.hist[i] = (unsigned)run;
-    run += x;
-  }
+  const unsigned long long r = block_excl_scan((unsigned long long)(x0 + x1), tmp, &tot);
+  if (a < kGrid) h[a] = (unsigned)r;
+  if (a + 1 < kGrid) h[a + 1] = (unsigned)(r + x0);
+  if (threadIdx.x == 0) s.hist[256 * kGrid + blockIdx.x] = (unsigned)tot;
 }
 
 __global__ void __launch_bounds__(256) k_sort_scatter(const QueryDev q, const Scratch s, int p) {
@@ -102,7 +99,13 @@ __global__ void __launch_bounds__(256) k_sort_scatter(const QueryDev q, const Sc
   unsigned* dv = (p & 1) ? s.valsB : s.valsA;
   unsigned long long lo, hi;
   chunk_range(c->n_parts, blockIdx.x, gridDim.x, &lo, &hi);
-  run[tid] = s.hist[tid * gridDim.x + blockIdx.x];
+  {
+    __shared__ unsigned long long tmp[33];
+    unsigned long long tot;
+    const unsigned long long base =
+        block_excl_scan((unsigned long long)s.hist[256 * kGrid + tid], tmp, &tot);
+    run[tid] = (unsigned)base + s.hist[tid * gridDim.x + blockIdx.x];
+  }
   const unsigned lt = (1u << lane) - 1u;
   for (unsigned long long tb = lo; tb < hi; tb += kScatterTile) {
 #pragma unroll
@@ -197,20 +200,17 @@ __global__ void __launch_bounds__(256) k_rbk_write(const QueryDev q, const Scrat
       unsigned mn = 0xffffffffu, mx = 0u;
       for (unsigned long long j = i; j < n && src.keys[j] == k; ++j) {
         const unsigned long long pi = src.vals ? src.vals[j] : j;
-        cnt += q.parts.cnt[pi];
+        const Grp g = load_grp(q.parts + pi);
+        cnt += g.cnt;
         if (FLOAT)
-          fsum += __longlong_as_double((long long)q.parts.sum[pi]);
+          fsum += __longlong_as_double((long long)g.sum);
         else
-          isum += q.parts.sum[pi];
-        mn = min(mn, q.parts.mn[pi]);
-        mx = max(mx, q.parts.mx[pi]);
+          isum += g.sum;
+        mn = min(mn, g.mn);
+        mx = max(mx, g.mx);
       }
-      const unsigned long long o = out + r;
-      q.state.gkey[o] = k;
-      q.state.cnt[o] = cnt;
-      q.state.sum[o] = FLOAT ? (unsigned long long)__double_as_longlong(fsum) : isum;
-      q.state.mn[o] = mn;
-      q.state.mx[o] = mx;
+      store_grp(q.state + out + r, k, cnt,
+                FLOAT ? (unsigned long long)__double_as_longlong(fsum) : isum, mn, mx);
     }
     out += tot;
   }
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(256) k_pane_count(const QueryDev q, const Scra
   chunk_range(c->n_state, blockIdx.x, gridDim.x, &lo, &hi);
   unsigned long long cnt = 0;
   for (unsigned long long i = lo + threadIdx.x; i < hi; i += blockDim.x)
-    cnt += (i == 0 || (q.state.gkey[i] >> 32) != (q.state.gkey[i - 1] >> 32)) ? 1ull : 0ull;
+    cnt += (i == 0 || (q.state[i].gkey >> 32) != (q.state[i - 1].gkey >> 32)) ? 1ull : 0ull;
   __shared__ unsigned long long tmp[33];
   unsigned long long tot;
   block_excl_scan(cnt, tmp, &tot);
@@ -241,8 +241,8 @@ __global__ void __launch_bounds__(256) k_pane_write(const QueryDev q, const Scra
   for (unsigned long long i0 = lo; i0 < hi; i0 += blockDim.x) {
     const unsigned long long i = i0 + threadIdx.x;
     const bool v = i < hi;
-    const unsigned p = v ? (unsigned)(q.state.gkey[i] >> 32) : 0u;
-    const bool head = v && (i == 0 || p != (unsigned)(q.state.gkey[i - 1] >> 32));
+    const unsigned p = v ? (unsigned)(q.state[i].gkey >> 32) : 0u;
+    const bool head = v && (i == 0 || p != (unsigned)(q.state[i - 1].gkey >> 32));
     unsigned long long tot;
     const unsigned long long r = block_excl_scan(head ? 1ull : 0ull, tmp, &tot);
     if (head) {
@@ -263,7 +263,7 @@ cudaError_t launch_sort_reduce(const QueryDev& q, const Scratch& s, cudaStream_t
   ++nl;
   for (int p = 0; p < 8; ++p) {
     k_sort_hist<<<kGrid, 256, 0, st>>>(q, s, p);
-    k_sort_scan<<<1, 1024, 0, st>>>(q, s, p);
+    k_sort_scan<<<256, 256, 0, st>>>(q, s, p);
     k_sort_scatter<<<kGrid, 256, 0, st>>>(q, s, p);
     nl += 3;
   }

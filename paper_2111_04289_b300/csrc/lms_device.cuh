@@ -60,6 +60,38 @@ __device__ __forceinline__ bool filter_pass_f(int op, double x, double c) {
   }
 }
 
+// `(double)v OP c` for a float32 v, decided in float32 (see QueryDev).
+__device__ __forceinline__ bool filter_pass_f32(int op, float v, float lo, float hi, int exact) {
+  switch (op) {
+    case 1: return exact && v == lo;
+    case 2: return !(exact && v == lo);
+    case 3: return v < hi;
+    case 4: return v <= lo;
+    case 5: return v > lo;
+    case 6: return v >= hi;
+    default: return true;
+  }
+}
+
+__device__ __forceinline__ Grp load_grp(const Grp* p) {
+  const uint4 a = reinterpret_cast<const uint4*>(p)[0];
+  const uint4 b = reinterpret_cast<const uint4*>(p)[1];
+  Grp g;
+  g.gkey = ((unsigned long long)a.y << 32) | a.x;
+  g.cnt = (long long)(((unsigned long long)a.w << 32) | a.z);
+  g.sum = ((unsigned long long)b.y << 32) | b.x;
+  g.mn = b.z;
+  g.mx = b.w;
+  return g;
+}
+__device__ __forceinline__ void store_grp(Grp* p, unsigned long long gkey, long long cnt,
+                                          unsigned long long sum, unsigned mn, unsigned mx) {
+  uint4* q = reinterpret_cast<uint4*>(p);
+  q[0] = make_uint4((unsigned)gkey, (unsigned)(gkey >> 32), (unsigned)cnt,
+                    (unsigned)((unsigned long long)cnt >> 32));
+  q[1] = make_uint4((unsigned)sum, (unsigned)(sum >> 32), mn, mx);
+}
+
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
 // Inclusive warp scan of 64-bit values.

@@ -7,8 +7,9 @@
 //     group, whatever K is; windows are assembled from panes at emission.
 //   * gkey = (pane_rel << 32) | key, pane_rel = pane - origin_pane + 2^31, so
 //     sorting gkeys as uint64 orders groups by (pane, key).
-//   * Groups are kept as SoA arrays {gkey, cnt, sum, mn, mx}; min/max are
-//     stored order-preserving encoded as uint32 (see lms_device.cuh).
+//   * Groups are 32-byte records {gkey, cnt, sum, mn, mx} (Grp); min/max are
+//     stored order-preserving encoded as uint32 (see lms_device.cuh).  The
+//     partial groups' keys are also kept in a compact array for the sort.
 // Per micro-batch, the fused pass appends per-tile partial groups after the
 // carried state; a radix sort + reduce-by-key turns them into the sorted,
 // unique window state; closed windows are merged from their panes and emitted.
@@ -31,12 +32,14 @@ constexpr unsigned kErrPoolOverflow = 8u;    // big-window merge scratch too sma
 constexpr unsigned kErrProbe = 16u;          // shared hash probe bound hit (never expected)
 constexpr unsigned kErrNeedRetry = kErrWinOverflow | kErrRowsOverflow | kErrPoolOverflow;
 
-struct Groups {
-  unsigned long long* gkey;
-  long long* cnt;
-  unsigned long long* sum;  // int64 sum, or the bits of a double sum
-  unsigned* mn;             // encoded min
-  unsigned* mx;             // encoded max
+// One (pane, key) group: a 32-byte record, so that a random gather of a group
+// touches one DRAM sector.
+struct __align__(16) Grp {
+  unsigned long long gkey;
+  long long cnt;
+  unsigned long long sum;  // int64 sum, or the bits of a double sum
+  unsigned mn;             // encoded min
+  unsigned mx;             // encoded max
 };
 
 // Per-query device control block.
@@ -76,6 +79,13 @@ struct QueryDev {
   int filter_col, filter_op;
   long long filter_i;
   double filter_f;
+  // Float32 image of `(double)v OP filter_f` for float32 values v: with
+  // lo = largest float <= filter_f and hi = smallest float >= filter_f,
+  // v > c <=> v > lo, v >= c <=> v >= hi, v < c <=> v < hi, v <= c <=> v <= lo,
+  // v == c <=> (lo == hi) && v == lo.  Set by set_float_filter().
+  float filter_lo, filter_hi;
+  int filter_exact;
+  int pad0;
   unsigned long long slide;
   unsigned long long magic;  // invariant-division constants for `slide`
   int sh1, sh2;
@@ -88,8 +98,9 @@ struct QueryDev {
   unsigned agg_mask;
   int qid;
   int value_is_float;
-  Groups parts;
-  Groups state;
+  Grp* parts;                  // partial groups (carried + this batch)
+  unsigned long long* pkeys;   // their keys, compact (first radix pass reads these)
+  Grp* state;                  // sorted, unique window state
   unsigned long long parts_cap;
   QCtl* ctl;
 };
@@ -114,7 +125,7 @@ struct Scratch {
   unsigned long long* keysB;
   unsigned* valsB;
   unsigned long long cap;        // entries of keysA/B, valsA/B
-  unsigned* hist;                // 256 * kGrid
+  unsigned* hist;                // 256 * kGrid per-chunk digit counts, then 256 digit totals
   unsigned long long* chunk;     // kGrid (+1) per-chunk counts / offsets
   unsigned* pane_id;             // [pane_cap]
   unsigned long long* pane_begin;// [pane_cap + 1]
@@ -160,6 +171,9 @@ cudaError_t launch_emit(const QueryDev& q, const Scratch& s, ResultRowDev* rows,
                         cudaEvent_t* ev4);
 cudaError_t launch_trim(const QueryDev& q, const Scratch& s, int sms, cudaStream_t st,
                         int* launches);
+
+// Fills filter_lo / filter_hi / filter_exact from filter_f.
+void set_float_filter(QueryDev* d);
 
 // Invariant division constants (Granlund & Montgomery 1994, unsigned, N=64).
 void udiv_constants(unsigned long long d, unsigned long long* magic, int* sh1, int* sh2);

@@ -38,7 +38,7 @@ constexpr size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
   size_t sctl, qctl;
-  size_t parts[5], state[5];
+  size_t parts, pkeys, state;
   size_t keysA, keysB, valsA, valsB, hist, chunk, pane_id, pane_begin;
   size_t win_w, win_j0, win_j1, win_rows, win_scr, pool, total;
 };
@@ -48,14 +48,14 @@ constexpr Layout make_layout() {
   size_t o = 0;
   L.sctl = o; o += al(sizeof(SCtl));
   L.qctl = o; o += al(sizeof(QCtl));
-  const size_t gsz[5] = {8, 8, 8, 4, 4};  // gkey, cnt, sum, mn, mx
-  for (int i = 0; i < 5; ++i) { L.parts[i] = o; o += al(gsz[i] * kStaticGroups); }
-  for (int i = 0; i < 5; ++i) { L.state[i] = o; o += al(gsz[i] * kStaticGroups); }
+  L.parts = o; o += al(sizeof(Grp) * kStaticGroups);
+  L.pkeys = o; o += al(8 * kStaticGroups);
+  L.state = o; o += al(sizeof(Grp) * kStaticGroups);
   L.keysA = o; o += al(8 * kStaticGroups);
   L.keysB = o; o += al(8 * kStaticGroups);
   L.valsA = o; o += al(4 * kStaticGroups);
   L.valsB = o; o += al(4 * kStaticGroups);
-  L.hist = o; o += al(4ull * 256 * kGrid);
+  L.hist = o; o += al(4ull * (256 * kGrid + 256));
   L.chunk = o; o += al(8ull * (kGrid + 1));
   L.pane_id = o; o += al(4 * (kStaticGroups + 1));
   L.pane_begin = o; o += al(8 * (kStaticGroups + 1));
@@ -152,15 +152,9 @@ extern "C" lms_status lms_aggregate_batch_static(const lms_query_spec* q, int32_
   SCtl* sctl = reinterpret_cast<SCtl*>(base + kL.sctl);
   QueryDev d{};
   d.ctl = reinterpret_cast<QCtl*>(base + kL.qctl);
-  Groups* gs[2] = {&d.parts, &d.state};
-  const size_t* offs[2] = {kL.parts, kL.state};
-  for (int g = 0; g < 2; ++g) {
-    gs[g]->gkey = reinterpret_cast<unsigned long long*>(base + offs[g][0]);
-    gs[g]->cnt = reinterpret_cast<long long*>(base + offs[g][1]);
-    gs[g]->sum = reinterpret_cast<unsigned long long*>(base + offs[g][2]);
-    gs[g]->mn = reinterpret_cast<unsigned*>(base + offs[g][3]);
-    gs[g]->mx = reinterpret_cast<unsigned*>(base + offs[g][4]);
-  }
+  d.parts = reinterpret_cast<Grp*>(base + kL.parts);
+  d.pkeys = reinterpret_cast<unsigned long long*>(base + kL.pkeys);
+  d.state = reinterpret_cast<Grp*>(base + kL.state);
   d.parts_cap = kStaticGroups;
   Scratch s{};
   s.keysA = reinterpret_cast<unsigned long long*>(base + kL.keysA);
@@ -187,6 +181,7 @@ extern "C" lms_status lms_aggregate_batch_static(const lms_query_spec* q, int32_
   d.filter_op = q->filter_op;
   d.filter_i = q->filter_i;
   d.filter_f = q->filter_f;
+  set_float_filter(&d);
   d.slide = (unsigned long long)slide;
   udiv_constants(d.slide, &d.magic, &d.sh1, &d.sh2);
   d.size = size;
