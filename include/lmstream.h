@@ -105,7 +105,7 @@ typedef struct lms_stream_config {
                                   are kept relative to it: events must satisfy
                                   |floor(ts/slide) - floor(origin_ts/slide)| < 2^31 - 1,
                                   others are dropped and counted (stats.range_rows). */
-  int32_t k1_variant;          /* 0 = default; 1 = no warp aggregation; 2 = warp aggregation */
+  int32_t k1_variant;          /* 0 = default (= 1); 1 = no warp aggregation; 2 = warp match_any aggregation */
   int32_t reserved[7];
 } lms_stream_config;
 

@@ -213,8 +213,7 @@ lms_status ensure_windows(lms_stream* s, unsigned long long need) {
   if ((r = dgrow(s, &sc.win_w, sc.win_cap, nc, 0)) != LMS_OK) return r;
   if ((r = dgrow(s, &sc.win_j0, sc.win_cap, nc, 0)) != LMS_OK) return r;
   if ((r = dgrow(s, &sc.win_j1, sc.win_cap, nc, 0)) != LMS_OK) return r;
-  if ((r = dgrow(s, &sc.win_rows, sc.win_cap, nc, 0)) != LMS_OK) return r;
-  if ((r = dgrow(s, &sc.win_scr, sc.win_cap, nc, 0)) != LMS_OK) return r;
+  if ((r = dgrow(s, &sc.win_stat, sc.win_cap, nc, 0)) != LMS_OK) return r;
   sc.win_cap = nc;
   return LMS_OK;
 }
@@ -503,9 +502,9 @@ lms_status push_microbatch(lms_stream* s, const lms_batch* b) {
     }
     if (hc[i].err & kErrNeedRetry)
       return fail(s, LMS_ENOMEM, "emission buffers could not be grown enough");
-    if (hc[i].err & (kErrPartsOverflow | kErrProbe)) {
+    if (hc[i].err & (kErrPartsOverflow | kErrProbe | kErrLookback)) {
       s->latched = LMS_EDEVICE;
-      return fail(s, LMS_EDEVICE, "internal device error flag raised by the fused pass");
+      return fail(s, LMS_EDEVICE, "internal device error flag raised by a kernel");
     }
   }
   SCtl hs{};

@@ -93,6 +93,7 @@ __global__ void k_emit_begin(QCtl* c) {
   c->big_windows = 0ull;
   c->rows_batch = 0ull;
   c->n_windows = 0ull;
+  c->win_ticket = 0ull;
   c->err &= ~kErrNeedRetry;
 }
 
@@ -163,6 +164,7 @@ __global__ void __launch_bounds__(256) k_win_write(const QueryDev q, const Scrat
       s.win_w[o] = w;
       s.win_j0[o] = (unsigned)j;
       s.win_j1[o] = (unsigned)j1;
+      s.win_stat[o] = 0ull;
     }
     out += tot;
   }
@@ -262,9 +264,18 @@ template <bool FLOAT>
 __device__ __forceinline__ void write_row(const QueryDev& q, ResultRowDev* out, long long wstart,
                                           unsigned key, long long cnt, unsigned long long sbits,
                                           unsigned mn, unsigned mx) {
+  // avg = sum / count; counts of 1 and powers of two need no division (the
+  // product with an exact power of two is the correctly rounded quotient).
+  const double sd = FLOAT ? __longlong_as_double((long long)sbits) : (double)(long long)sbits;
   double avg;
-  if (FLOAT) avg = __longlong_as_double((long long)sbits) / (double)cnt;
-  else avg = (double)(long long)sbits / (double)cnt;
+  if (cnt == 1) {
+    avg = sd;
+  } else if ((cnt & (cnt - 1)) == 0) {
+    const int e = __ffsll(cnt) - 1;
+    avg = sd * __longlong_as_double((long long)(1023 - e) << 52);
+  } else {
+    avg = sd / (double)cnt;
+  }
   unsigned mnv = 0u, mxv = 0u;
   if (q.agg_mask & 4u) mnv = FLOAT ? dec_f32_bits(mn) : (unsigned)dec_i32(mn);
   if (q.agg_mask & 8u) mxv = FLOAT ? dec_f32_bits(mx) : (unsigned)dec_i32(mx);
@@ -309,21 +320,30 @@ __device__ __forceinline__ void combine_run(const QueryDev& q, const unsigned lo
   *mx = hi;
 }
 
-// Distinct keys of the merged window S[0..len): their count (E1) or their
-// rows (E2), in key order.
-template <bool FLOAT, bool WRITE, bool PAD>
-__device__ __forceinline__ unsigned long long emit_distinct(
-    const QueryDev& q, const unsigned long long* S, unsigned len, unsigned long long b0,
-    long long wstart, ResultRowDev* out, unsigned* wt, int* parity) {
+// Distinct keys of the merged window S[0..len), in key order: their number.
+template <bool PAD>
+__device__ __forceinline__ unsigned long long count_distinct(const unsigned long long* S,
+                                                             unsigned len) {
   unsigned long long run = 0;
+  for (unsigned i0 = 0; i0 < len; i0 += blockDim.x) {
+    const unsigned i = i0 + threadIdx.x;
+    const bool head = i < len && (i == 0 || (S[pix<PAD>(i)] >> 32) != (S[pix<PAD>(i - 1)] >> 32));
+    run += (unsigned)__syncthreads_count(head);
+  }
+  return run;
+}
+
+// One row per distinct key of the merged window, written from out[0].
+template <bool FLOAT, bool PAD>
+__device__ __forceinline__ void write_distinct(const QueryDev& q, const unsigned long long* S,
+                                               unsigned len, unsigned long long b0,
+                                               long long wstart, ResultRowDev* out, unsigned* wt,
+                                               int* parity) {
+  unsigned run = 0;
   for (unsigned i0 = 0; i0 < len; i0 += blockDim.x) {
     const unsigned i = i0 + threadIdx.x;
     const unsigned long long x = i < len ? S[pix<PAD>(i)] : 0ull;
     const bool head = i < len && (i == 0 || (x >> 32) != (S[pix<PAD>(i - 1)] >> 32));
-    if (!WRITE) {
-      run += (unsigned)__syncthreads_count(head);
-      continue;
-    }
     unsigned tot;
     const unsigned r = block_rank(head, wt, *parity, &tot);
     *parity ^= 1;
@@ -339,61 +359,99 @@ __device__ __forceinline__ unsigned long long emit_distinct(
     }
     run += tot;
   }
-  return run;
 }
 
-// E1 (WRITE=false): rows per closed window.  E2 (WRITE=true): the rows.
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Decoupled look-back over the windows before `wi` (windows are taken in
+// ticket order, so every predecessor is already running or done).  Publishes
+// this window's row count, waits (bounded, ~4 s) for the predecessors' counts
+// and returns the exclusive prefix, or ~0 after setting kErrLookback.
+__device__ unsigned long long window_lookback(unsigned long long* stat, unsigned long long wi,
+                                              unsigned long long n, QCtl* c) {
+  constexpr unsigned long long kAgg = 1ull << 62, kPre = 2ull << 62, kVal = kAgg - 1;
+  volatile unsigned long long* vs = stat;
+  if (wi == 0) {
+    vs[0] = kPre | n;
+    return 0ull;
+  }
+  vs[wi] = kAgg | n;
+  unsigned long long acc = 0;
+  long long p = (long long)wi - 1;
+  const unsigned long long t0 = global_ns();
+  unsigned spins = 0;
+  while (p >= 0) {
+    const unsigned long long v = vs[p];
+    if ((v >> 62) == 0) {
+      if ((++spins & 255u) == 0 && global_ns() - t0 > 4000000000ull) {
+        atomicOr(&c->err, kErrLookback);
+        return ~0ull;
+      }
+      __nanosleep(128);
+      continue;
+    }
+    acc += v & kVal;
+    if ((v >> 62) == 2) break;
+    --p;
+  }
+  __threadfence();
+  vs[wi] = kPre | (acc + n);
+  return acc;
+}
+
+// Assembles the closed windows, in window order, one CTA per window at a time:
+// merge the window's K pane runs (shared memory, or global scratch for windows
+// above `cap` entries), count its distinct keys, find its row offset by the
+// look-back, then write one row per distinct key in key order.
 // Dynamic shared memory: two padded merge buffers of `cap` entries, then two
 // run-boundary arrays of k + 1 entries.
-template <bool FLOAT, bool WRITE>
+template <bool FLOAT>
 __global__ void __launch_bounds__(kEmitThreads, 1)
-    k_emit(const QueryDev q, const Scratch s, ResultRowDev* rows, unsigned cap) {
+    k_emit(const QueryDev q, const Scratch s, ResultRowDev* rows, unsigned cap,
+           unsigned long long rows_cap) {
   extern __shared__ __align__(16) unsigned long long esm[];
   const unsigned padded = cap + (cap >> 4) + 1;
   unsigned* bnd0 = reinterpret_cast<unsigned*>(esm + 2ull * padded);
   unsigned* bnd1 = bnd0 + (q.k + 1);
   __shared__ unsigned wt[66];
-  __shared__ unsigned long long s_off;
+  __shared__ unsigned long long s_wi, s_off;
   QCtl* c = q.ctl;
   if (c->err & kErrNeedRetry) return;
   const unsigned long long W = c->n_windows;
   const int tid = threadIdx.x;
   const unsigned long long row_base = c->row_base;
   int parity = 0;
-  for (unsigned long long wi = blockIdx.x; wi < W; wi += gridDim.x) {
+  while (true) {
+    if (tid == 0) s_wi = atomicAdd(&c->win_ticket, 1ull);
+    __syncthreads();
+    const unsigned long long wi = s_wi;
+    if (wi >= W) break;
     const long long w = s.win_w[wi];
     const unsigned j0 = s.win_j0[wi], j1 = s.win_j1[wi];
     const unsigned long long b0 = s.pane_begin[j0], b1 = s.pane_begin[j1];
     const unsigned len = (unsigned)(b1 - b0);
     const int nr = (int)(j1 - j0);
     const long long wstart = (w - kPaneBias) * (long long)q.slide + q.base;
-    ResultRowDev* out = WRITE ? rows + row_base + s.win_rows[wi] : nullptr;
-    if (nr == 1) {  // one pane: the state run is already key-sorted and unique
-      if (!WRITE) {
-        if (tid == 0) s.win_rows[wi] = len;
+    const unsigned long long* S = nullptr;
+    bool in_smem = true;
+    unsigned long long n = len;  // one pane: its run is already unique and key-sorted
+    if (nr > 1) {
+      if (len <= cap) {
+        unsigned long long* A = esm;
+        unsigned long long* B = esm + padded;
+        for (unsigned i = tid; i < len; i += blockDim.x)
+          A[pix<true>(i)] = ((q.state[b0 + i].gkey & 0xffffffffull) << 32) | i;
+        for (int r = tid; r <= nr; r += blockDim.x)
+          bnd0[r] = (unsigned)(s.pane_begin[j0 + r] - b0);
+        __syncthreads();
+        S = merge_runs<true>(A, B, bnd0, bnd1, nr, len);
+        n = count_distinct<true>(S, len);
       } else {
-        for (unsigned i = tid; i < len; i += blockDim.x) {
-          const Grp g = load_grp(q.state + b0 + i);
-          write_row<FLOAT>(q, out + i, wstart, (unsigned)g.gkey, g.cnt, g.sum, g.mn, g.mx);
-        }
-      }
-      continue;
-    }
-    if (len <= cap) {  // shared-memory merge
-      unsigned long long* A = esm;
-      unsigned long long* B = esm + padded;
-      for (unsigned i = tid; i < len; i += blockDim.x)
-        A[pix<true>(i)] = ((q.state[b0 + i].gkey & 0xffffffffull) << 32) | i;
-      for (int r = tid; r <= nr; r += blockDim.x)
-        bnd0[r] = (unsigned)(s.pane_begin[j0 + r] - b0);
-      __syncthreads();
-      const unsigned long long* S = merge_runs<true>(A, B, bnd0, bnd1, nr, len);
-      const unsigned long long n =
-          emit_distinct<FLOAT, WRITE, true>(q, S, len, b0, wstart, out, wt, &parity);
-      if (!WRITE && tid == 0) s.win_rows[wi] = n;
-    } else {  // global-scratch merge; E1 merges, E2 reuses the merged result
-      const unsigned long long* S;
-      if (!WRITE) {
+        in_smem = false;
         if (tid == 0) {
           unsigned long long off = atomicAdd(&c->pool_used, 2ull * len);
           if (off + 2ull * len > s.pool_cap) {
@@ -406,72 +464,46 @@ __global__ void __launch_bounds__(kEmitThreads, 1)
         }
         __syncthreads();
         const unsigned long long off = s_off;
-        __syncthreads();
-        if (off == ~0ull) {
-          if (tid == 0) s.win_rows[wi] = 0ull;
-          continue;
+        if (off != ~0ull) {
+          unsigned long long* A = s.pool + off;
+          unsigned long long* B = A + len;
+          for (unsigned i = tid; i < len; i += blockDim.x)
+            A[i] = ((q.state[b0 + i].gkey & 0xffffffffull) << 32) | i;
+          for (int r = tid; r <= nr; r += blockDim.x)
+            bnd0[r] = (unsigned)(s.pane_begin[j0 + r] - b0);
+          __syncthreads();
+          S = merge_runs<false>(A, B, bnd0, bnd1, nr, len);
+          n = count_distinct<false>(S, len);
+        } else {
+          n = 0;  // the host grows the scratch and runs the emission again
         }
-        unsigned long long* A = s.pool + off;
-        unsigned long long* B = A + len;
-        for (unsigned i = tid; i < len; i += blockDim.x)
-          A[i] = ((q.state[b0 + i].gkey & 0xffffffffull) << 32) | i;
-        for (int r = tid; r <= nr; r += blockDim.x)
-          bnd0[r] = (unsigned)(s.pane_begin[j0 + r] - b0);
-        __syncthreads();
-        S = merge_runs<false>(A, B, bnd0, bnd1, nr, len);
-        if (tid == 0) s.win_scr[wi] = (unsigned long long)(S - s.pool);
-      } else {
-        S = s.pool + s.win_scr[wi];
       }
-      const unsigned long long n =
-          emit_distinct<FLOAT, WRITE, false>(q, S, len, b0, wstart, out, wt, &parity);
-      if (!WRITE && tid == 0) s.win_rows[wi] = n;
     }
     __syncthreads();
-  }
-}
-
-// Device-wide exclusive scan of win_rows[0..n_windows): per-chunk sums, chunk
-// scan (total -> rows_batch, capacity check), per-chunk apply.
-__global__ void __launch_bounds__(256) k_rows_sum(const QueryDev q, const Scratch s) {
-  const QCtl* c = q.ctl;
-  unsigned long long lo, hi;
-  chunk_range(c->err & kErrNeedRetry ? 0ull : c->n_windows, blockIdx.x, gridDim.x, &lo, &hi);
-  unsigned long long cnt = 0;
-  for (unsigned long long i = lo + threadIdx.x; i < hi; i += blockDim.x) cnt += s.win_rows[i];
-  __shared__ unsigned long long tmp[33];
-  unsigned long long tot;
-  block_excl_scan(cnt, tmp, &tot);
-  if (threadIdx.x == 0) s.chunk[blockIdx.x] = tot;
-}
-
-__global__ void __launch_bounds__(1024) k_rows_scan(const QueryDev q, const Scratch s,
-                                                    unsigned long long rows_cap) {
-  __shared__ unsigned long long tmp[33];
-  const unsigned long long v = (int)threadIdx.x < kGrid ? s.chunk[threadIdx.x] : 0ull;
-  unsigned long long tot;
-  const unsigned long long r = block_excl_scan(v, tmp, &tot);
-  if ((int)threadIdx.x < kGrid) s.chunk[threadIdx.x] = r;
-  if (threadIdx.x == 0) {
-    QCtl* c = q.ctl;
-    c->rows_batch = tot;
-    if (c->row_base + tot > rows_cap) atomicOr(&c->err, kErrRowsOverflow);
-  }
-}
-
-__global__ void __launch_bounds__(256) k_rows_apply(const QueryDev q, const Scratch s) {
-  const QCtl* c = q.ctl;
-  unsigned long long lo, hi;
-  chunk_range(c->err & kErrNeedRetry ? 0ull : c->n_windows, blockIdx.x, gridDim.x, &lo, &hi);
-  __shared__ unsigned long long tmp[33];
-  unsigned long long out = s.chunk[blockIdx.x];
-  for (unsigned long long i0 = lo; i0 < hi; i0 += blockDim.x) {
-    const unsigned long long i = i0 + threadIdx.x;
-    const unsigned long long v = i < hi ? s.win_rows[i] : 0ull;
-    unsigned long long tot;
-    const unsigned long long r = block_excl_scan(v, tmp, &tot);
-    if (i < hi) s.win_rows[i] = out + r;
-    out += tot;
+    if (tid == 0) {
+      const unsigned long long off = window_lookback(s.win_stat, wi, n, c);
+      s_off = off;
+      if (off != ~0ull) {
+        if (wi == W - 1) c->rows_batch = off + n;
+        if (row_base + off + n > rows_cap) atomicOr(&c->err, kErrRowsOverflow);
+      }
+    }
+    __syncthreads();
+    const unsigned long long off = s_off;
+    if (off != ~0ull && row_base + off + n <= rows_cap && !(c->err & kErrPoolOverflow)) {
+      ResultRowDev* out = rows + row_base + off;
+      if (nr == 1) {
+        for (unsigned i = tid; i < len; i += blockDim.x) {
+          const Grp g = load_grp(q.state + b0 + i);
+          write_row<FLOAT>(q, out + i, wstart, (unsigned)g.gkey, g.cnt, g.sum, g.mn, g.mx);
+        }
+      } else if (in_smem) {
+        write_distinct<FLOAT, true>(q, S, len, b0, wstart, out, wt, &parity);
+      } else {
+        write_distinct<FLOAT, false>(q, S, len, b0, wstart, out, wt, &parity);
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -523,18 +555,19 @@ __global__ void __launch_bounds__(256) k_trim_copy(const QueryDev q) {
   }
 }
 
-template <bool FLOAT, bool WRITE>
+template <bool FLOAT>
 cudaError_t launch_emit_t(const QueryDev& q, const Scratch& s, ResultRowDev* rows, int grid,
-                          size_t smem, cudaStream_t st) {
+                          size_t smem, unsigned long long rows_cap, cudaStream_t st) {
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_emit<FLOAT, WRITE>,
+    cudaError_t e = cudaFuncSetAttribute(k_emit<FLOAT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kEmitSmemMax);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  k_emit<FLOAT, WRITE><<<grid, kEmitThreads, smem, st>>>(q, s, rows, smem ? emit_cap(q.k) : 0u);
+  k_emit<FLOAT><<<grid, kEmitThreads, smem, st>>>(q, s, rows, smem ? emit_cap(q.k) : 0u,
+                                                 rows_cap);
   return cudaGetLastError();
 }
 
@@ -574,19 +607,15 @@ cudaError_t launch_emit(const QueryDev& q, const Scratch& s, ResultRowDev* rows,
   // Tumbling windows (one pane each) need no merge buffers.
   const size_t smem = q.k > 1 ? emit_smem(q.k) : 0;
   const int grid = q.k > 1 ? sms : 4 * sms;
-  if (ev4) cudaEventRecord(ev4[0], st);
-  cudaError_t e = q.value_is_float ? launch_emit_t<true, false>(q, s, rows, grid, smem, st)
-                                   : launch_emit_t<false, false>(q, s, rows, grid, smem, st);
-  if (ev4) cudaEventRecord(ev4[1], st);
-  if (e != cudaSuccess) return e;
-  k_rows_sum<<<kGrid, 256, 0, st>>>(q, s);
-  k_rows_scan<<<1, 1024, 0, st>>>(q, s, rows_cap);
-  k_rows_apply<<<kGrid, 256, 0, st>>>(q, s);
-  if (ev4) cudaEventRecord(ev4[2], st);
-  e = q.value_is_float ? launch_emit_t<true, true>(q, s, rows, grid, smem, st)
-                       : launch_emit_t<false, true>(q, s, rows, grid, smem, st);
+  if (ev4) {
+    cudaEventRecord(ev4[0], st);
+    cudaEventRecord(ev4[1], st);
+    cudaEventRecord(ev4[2], st);
+  }
+  cudaError_t e = q.value_is_float ? launch_emit_t<true>(q, s, rows, grid, smem, rows_cap, st)
+                                   : launch_emit_t<false>(q, s, rows, grid, smem, rows_cap, st);
   if (ev4) cudaEventRecord(ev4[3], st);
-  if (launches) *launches += 9;
+  if (launches) *launches += 5;
   return e;
 }
 

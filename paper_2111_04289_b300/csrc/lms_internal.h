@@ -30,6 +30,7 @@ constexpr unsigned kErrWinOverflow = 2u;     // window list too small
 constexpr unsigned kErrRowsOverflow = 4u;    // result buffer too small
 constexpr unsigned kErrPoolOverflow = 8u;    // big-window merge scratch too small
 constexpr unsigned kErrProbe = 16u;          // shared hash probe bound hit (never expected)
+constexpr unsigned kErrLookback = 32u;       // a window's bounded look-back wait ran out
 constexpr unsigned kErrNeedRetry = kErrWinOverflow | kErrRowsOverflow | kErrPoolOverflow;
 
 // One (pane, key) group: a 32-byte record, so that a random gather of a group
@@ -60,6 +61,7 @@ struct QCtl {
   unsigned long long carried;    // groups carried into the next batch
   unsigned long long big_windows;// windows merged through global scratch (this emission)
   unsigned long long trim_from;  // first state index carried into the next batch
+  unsigned long long win_ticket; // next window to assemble (emission takes windows in order)
   unsigned long long parts_at_sort; // partial groups the sort of this batch consumed
   unsigned int err;
   int npasses;
@@ -133,8 +135,8 @@ struct Scratch {
   long long* win_w;              // window list [win_cap]
   unsigned* win_j0;
   unsigned* win_j1;
-  unsigned long long* win_rows;  // rows per window, then exclusive offsets
-  unsigned long long* win_scr;   // scratch offset of a big window (or ~0)
+  unsigned long long* win_stat;  // look-back word per window: 0 = not ready,
+                                 // 1<<62 | rows (own count), 2<<62 | rows (inclusive prefix)
   unsigned long long win_cap;
   unsigned long long* pool;      // big-window merge scratch (2 buffers per window)
   unsigned long long pool_cap;   // entries

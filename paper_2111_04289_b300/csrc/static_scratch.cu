@@ -40,7 +40,7 @@ struct Layout {
   size_t sctl, qctl;
   size_t parts, pkeys, state;
   size_t keysA, keysB, valsA, valsB, hist, chunk, pane_id, pane_begin;
-  size_t win_w, win_j0, win_j1, win_rows, win_scr, pool, total;
+  size_t win_w, win_j0, win_j1, win_stat, pool, total;
 };
 
 constexpr Layout make_layout() {
@@ -62,8 +62,7 @@ constexpr Layout make_layout() {
   L.win_w = o; o += al(8 * kStaticWindows);
   L.win_j0 = o; o += al(4 * kStaticWindows);
   L.win_j1 = o; o += al(4 * kStaticWindows);
-  L.win_rows = o; o += al(8 * kStaticWindows);
-  L.win_scr = o; o += al(8 * kStaticWindows);
+  L.win_stat = o; o += al(8 * kStaticWindows);
   L.pool = o; o += al(8 * kStaticPool);
   L.total = o;
   return L;
@@ -170,8 +169,7 @@ extern "C" lms_status lms_aggregate_batch_static(const lms_query_spec* q, int32_
   s.win_w = reinterpret_cast<long long*>(base + kL.win_w);
   s.win_j0 = reinterpret_cast<unsigned*>(base + kL.win_j0);
   s.win_j1 = reinterpret_cast<unsigned*>(base + kL.win_j1);
-  s.win_rows = reinterpret_cast<unsigned long long*>(base + kL.win_rows);
-  s.win_scr = reinterpret_cast<unsigned long long*>(base + kL.win_scr);
+  s.win_stat = reinterpret_cast<unsigned long long*>(base + kL.win_stat);
   s.win_cap = kStaticWindows;
   s.pool = reinterpret_cast<unsigned long long*>(base + kL.pool);
   s.pool_cap = kStaticPool;
@@ -229,7 +227,7 @@ extern "C" lms_status lms_aggregate_batch_static(const lms_query_spec* q, int32_
   if (cudaStreamSynchronize(st) != cudaSuccess ||
       cudaMemcpy(&h, d.ctl, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess)
     return LMS_ECUDA;
-  if (h.err & (kErrPartsOverflow | kErrProbe)) return LMS_EDEVICE;
+  if (h.err & (kErrPartsOverflow | kErrProbe | kErrLookback)) return LMS_EDEVICE;
   if (h.err & kErrNeedRetry) return LMS_ENOMEM;  // windows, merge scratch or rows_cap too small
   *n_out = (size_t)h.rows_batch;
   return LMS_OK;
