@@ -4,11 +4,21 @@
 // Table II, fused into one pass): evaluate the query's filter, map ts to its
 // pane (window slice of length `slide`; a sliding window of size K*slide is K
 // consecutive panes, so the Expand step costs nothing here), and add the
-// event to the (pane, key) group.  Groups are pre-aggregated per CTA tile in a
-// shared-memory open-addressing table (warp-aggregated with match_any first,
-// so hot Zipf keys cost one shared atomic per warp), then the tile's groups
-// are appended to the query's partial-group arrays in HBM.  The batch columns
-// are read exactly once, with 16-byte vector loads, for all queries together.
+// event to the (pane, key) group.  The batch columns are read exactly once,
+// with vector loads, for all queries together.
+//
+// Per tile of 2048 events and per query, the groups are built in shared
+// memory without any floating-point atomics:
+//   A. every surviving event inserts its group key into an open-addressing
+//      table (integer CAS on the key only); a new key is appended to the
+//      tile's group list;
+//   B. each event takes a rank inside its group (warp-aggregated atomic add
+//      on the group's counter);
+//   C. a scan of the group counters gives every group a contiguous range and
+//      the events scatter their values into it;
+//   D. each group is reduced sequentially (count, int64 or FP64 sum, min, max)
+//      — one thread per small group, one warp per large one — and appended to
+//      the query's partial-group array in HBM.
 #include <climits>
 
 #include "lms_device.cuh"
@@ -16,70 +26,89 @@
 namespace lms {
 namespace {
 
-constexpr int kK1Threads = 512;
-constexpr int kK1Items = 4;                      // events per thread per tile
+constexpr int kK1Threads = 1024;
+constexpr int kK1Warps = kK1Threads / 32;
+constexpr int kK1Items = 2;                      // events per thread per tile
 constexpr int kK1Tile = kK1Threads * kK1Items;   // 2048 events
 constexpr int kK1HashBits = 12;                  // 4096 slots >= 2 * tile
 constexpr int kK1Hash = 1 << kK1HashBits;
-constexpr int kK1SlotsPerThread = kK1Hash / kK1Threads;
-constexpr size_t kK1Smem = (size_t)kK1Hash * (8 + 8 + 4 + 4 + 4);
+constexpr unsigned kBigGroup = 32;               // groups above this are reduced by a warp
+constexpr unsigned kNoSlot = 0xffffu;
 
-template <bool FLOAT>
-__device__ __forceinline__ void smem_upsert(unsigned long long* hkey, unsigned* hcnt,
-                                            unsigned long long* hsum, unsigned* hmn,
-                                            unsigned* hmx, unsigned long long g, unsigned c,
-                                            unsigned long long sbits, unsigned mn, unsigned mx,
-                                            unsigned agg_mask, unsigned* s_err) {
+// hkey u64[H] | hidx u16[H] | list u16[T] | lcnt u32[T] | loff u32[T+4] | vals u32[T]
+constexpr size_t kK1Smem = (size_t)kK1Hash * 8 + kK1Hash * 2 + kK1Tile * 2 + kK1Tile * 4 +
+                           (kK1Tile + 4) * 4 + kK1Tile * 4;
+
+// Phase A: the slot of group key g (inserted if new).  Returns the slot, or
+// kNoSlot if the probe bound is hit (cannot happen: a tile has <= H/2 groups).
+__device__ __forceinline__ unsigned insert_key(unsigned long long* hkey, unsigned short* hidx,
+                                               unsigned short* list, unsigned* nlist,
+                                               unsigned long long g) {
   unsigned slot = hash_slot(g, kK1HashBits);
-  int probes = 0;
-  while (true) {
-    unsigned long long cur = *((volatile unsigned long long*)&hkey[slot]);
-    if (cur == g) break;
+  for (int probes = 0; probes < kK1Hash; ++probes) {
+    const unsigned long long cur = *((volatile unsigned long long*)&hkey[slot]);
+    if (cur == g) return slot;
     if (cur == kEmpty) {
-      unsigned long long prev = atomicCAS(&hkey[slot], kEmpty, g);
-      if (prev == kEmpty || prev == g) break;
+      const unsigned long long prev = atomicCAS(&hkey[slot], kEmpty, g);
+      if (prev == kEmpty) {
+        const unsigned li = atomicAdd(nlist, 1u);
+        list[li] = (unsigned short)slot;
+        hidx[slot] = (unsigned short)li;
+        return slot;
+      }
+      if (prev == g) return slot;
     }
     slot = (slot + 1) & (kK1Hash - 1);
-    if (++probes >= kK1Hash) {  // cannot happen: a tile has <= kK1Hash/2 groups
-      atomicOr(s_err, kErrProbe);
-      return;
-    }
   }
-  atomicAdd(&hcnt[slot], c);
-  if (FLOAT)
-    atomicAdd(reinterpret_cast<double*>(&hsum[slot]), __longlong_as_double((long long)sbits));
-  else
-    atomicAdd(&hsum[slot], sbits);
-  if (agg_mask & 4u) atomicMin(&hmn[slot], mn);
-  if (agg_mask & 8u) atomicMax(&hmx[slot], mx);
+  return kNoSlot;
 }
 
-template <bool FLOAT, bool WARP_AGG>
+// Sum, min and max (encoded) of v[b], v[b + step], ... below e.
+template <bool FLOAT>
+__device__ __forceinline__ void reduce_values(const unsigned* v, unsigned b, unsigned e,
+                                              unsigned step, unsigned long long* sbits,
+                                              unsigned* mn, unsigned* mx) {
+  long long isum = 0;
+  double fsum = 0.0;
+  unsigned lo = 0xffffffffu, hi = 0u;
+  for (unsigned t = b; t < e; t += step) {
+    const unsigned x = v[t];
+    const unsigned enc = FLOAT ? enc_f32(__uint_as_float(x)) : enc_i32((int)x);
+    if (FLOAT) fsum += (double)__uint_as_float(x);
+    else isum += (long long)(int)x;
+    lo = min(lo, enc);
+    hi = max(hi, enc);
+  }
+  *sbits = FLOAT ? (unsigned long long)__double_as_longlong(fsum) : (unsigned long long)isum;
+  *mn = lo;
+  *mx = hi;
+}
+
+template <bool FLOAT>
 __global__ void __launch_bounds__(kK1Threads, 1) k1_fused(const __grid_constant__ K1Args a) {
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned long long* hkey = reinterpret_cast<unsigned long long*>(smem);
-  unsigned long long* hsum = hkey + kK1Hash;
-  unsigned* hcnt = reinterpret_cast<unsigned*>(hsum + kK1Hash);
-  unsigned* hmn = hcnt + kK1Hash;
-  unsigned* hmx = hmn + kK1Hash;
+  unsigned short* hidx = reinterpret_cast<unsigned short*>(hkey + kK1Hash);
+  unsigned short* list = hidx + kK1Hash;
+  unsigned* lcnt = reinterpret_cast<unsigned*>(list + kK1Tile);
+  unsigned* loff = lcnt + kK1Tile;
+  unsigned* vals = loff + kK1Tile + 4;
 
-  __shared__ unsigned long long s_tmp[33];
   __shared__ unsigned long long s_or[kMaxQueries], s_and[kMaxQueries];
   __shared__ unsigned long long s_late[kMaxQueries], s_range[kMaxQueries];
   __shared__ long long s_cursor[kMaxQueries];
   __shared__ unsigned long long s_base;
   __shared__ long long s_maxts;
   __shared__ unsigned s_err[kMaxQueries];
+  __shared__ unsigned s_nlist, s_nbig;
+  __shared__ unsigned s_wsum[kK1Warps + 1];
+  __shared__ unsigned short s_big[kK1Tile];
 
   const int tid = threadIdx.x;
   const unsigned lane = lane_id();
-  for (int s = tid; s < kK1Hash; s += kK1Threads) {
-    hkey[s] = kEmpty;
-    hsum[s] = 0ull;
-    hcnt[s] = 0u;
-    hmn[s] = 0xffffffffu;
-    hmx[s] = 0u;
-  }
+  const int warp = tid >> 5;
+  for (int s = tid; s < kK1Hash; s += kK1Threads) hkey[s] = kEmpty;
+  for (int s = tid; s < kK1Tile; s += kK1Threads) lcnt[s] = 0u;
   if (tid < a.nq) {
     s_or[tid] = 0ull;
     s_and[tid] = ~0ull;
@@ -88,7 +117,11 @@ __global__ void __launch_bounds__(kK1Threads, 1) k1_fused(const __grid_constant_
     s_cursor[tid] = a.q[tid].ctl->cursor;
     s_err[tid] = 0u;
   }
-  if (tid == 0) s_maxts = LLONG_MIN;
+  if (tid == 0) {
+    s_maxts = LLONG_MIN;
+    s_nlist = 0u;
+    s_nbig = 0u;
+  }
   __syncthreads();
 
   const long long n = a.n;
@@ -96,27 +129,28 @@ __global__ void __launch_bounds__(kK1Threads, 1) k1_fused(const __grid_constant_
   const bool vec_ok =
       ((reinterpret_cast<uintptr_t>(a.ts) | reinterpret_cast<uintptr_t>(a.key) |
         reinterpret_cast<uintptr_t>(a.value)) & 15u) == 0 &&
-      (a.type == nullptr || (reinterpret_cast<uintptr_t>(a.type) & 3u) == 0);
+      (a.type == nullptr || (reinterpret_cast<uintptr_t>(a.type) & 1u) == 0);
   long long tmax = LLONG_MIN;
 
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    // ---- load this thread's events (blocked: 4 consecutive events) ----
+    // ---- load this thread's 2 consecutive events (16/8/8/2-byte loads) ----
     const long long e0 = tile * kK1Tile + (long long)tid * kK1Items;
     long long ts[kK1Items];
     unsigned key[kK1Items], val[kK1Items], typ[kK1Items];
     bool valid[kK1Items];
     if (vec_ok && e0 + kK1Items <= n) {
       const longlong2 t01 = __ldcs(reinterpret_cast<const longlong2*>(a.ts + e0));
-      const longlong2 t23 = __ldcs(reinterpret_cast<const longlong2*>(a.ts + e0) + 1);
-      const uint4 k4 = __ldcs(reinterpret_cast<const uint4*>(a.key + e0));
-      const uint4 v4 = __ldcs(reinterpret_cast<const uint4*>(static_cast<const unsigned*>(a.value) + e0));
-      ts[0] = t01.x; ts[1] = t01.y; ts[2] = t23.x; ts[3] = t23.y;
-      key[0] = k4.x; key[1] = k4.y; key[2] = k4.z; key[3] = k4.w;
-      val[0] = v4.x; val[1] = v4.y; val[2] = v4.z; val[3] = v4.w;
-      unsigned t4 = a.type ? __ldcs(reinterpret_cast<const unsigned*>(a.type + e0)) : 0u;
+      const uint2 k2 = __ldcs(reinterpret_cast<const uint2*>(a.key + e0));
+      const uint2 v2 =
+          __ldcs(reinterpret_cast<const uint2*>(static_cast<const unsigned*>(a.value) + e0));
+      ts[0] = t01.x; ts[1] = t01.y;
+      key[0] = k2.x; key[1] = k2.y;
+      val[0] = v2.x; val[1] = v2.y;
+      const unsigned t2 =
+          a.type ? (unsigned)__ldcs(reinterpret_cast<const unsigned short*>(a.type + e0)) : 0u;
 #pragma unroll
       for (int i = 0; i < kK1Items; ++i) {
-        typ[i] = (t4 >> (8 * i)) & 0xffu;
+        typ[i] = (t2 >> (8 * i)) & 0xffu;
         valid[i] = true;
       }
     } else {
@@ -137,77 +171,41 @@ __global__ void __launch_bounds__(kK1Threads, 1) k1_fused(const __grid_constant_
     for (int qi = 0; qi < a.nq; ++qi) {
       const QueryDev& Q = a.q[qi];
       const int fcol = Q.filter_col, fop = Q.filter_op;
-      const unsigned amask = Q.agg_mask;
       const long long cursor = s_cursor[qi];
       unsigned n_late = 0, n_range = 0;
+      unsigned slot[kK1Items];
+      // ---- A: filter, pane id, insert the group key ----
 #pragma unroll
       for (int i = 0; i < kK1Items; ++i) {
-        // ---- filter ----
         bool ok = valid[i];
         if (ok && fop != 0) {
-          if (fcol == 2 && FLOAT)
+          if (fcol == 2 && FLOAT) {
             ok = filter_pass_f32(fop, __uint_as_float(val[i]), Q.filter_lo, Q.filter_hi,
                                  Q.filter_exact);
-          else {
-            long long x = fcol == 0 ? ts[i]
-                          : fcol == 1 ? (long long)key[i]
-                          : fcol == 3 ? (long long)typ[i]
-                                      : (long long)(int)val[i];
+          } else {
+            const long long x = fcol == 0 ? ts[i]
+                                : fcol == 1 ? (long long)key[i]
+                                : fcol == 3 ? (long long)typ[i]
+                                            : (long long)(int)val[i];
             ok = filter_pass_i(fop, x, Q.filter_i);
           }
         }
-        // ---- pane (window slice) id ----
-        unsigned long long g = 0ull;
+        slot[i] = kNoSlot;
         if (ok) {
           const unsigned long long u = (unsigned long long)ts[i] + Q.ts_off;
           if (u >= Q.u_limit) {
             ++n_range;
-            ok = false;
           } else {
             const unsigned long long prel = udiv_inv(u, Q.magic, Q.sh1, Q.sh2);
             if ((long long)prel < cursor) {  // every window of this event was emitted
               ++n_late;
-              ok = false;
             } else {
-              g = (prel << 32) | key[i];
+              slot[i] = insert_key(hkey, hidx, list, &s_nlist, (prel << 32) | key[i]);
+              if (slot[i] == kNoSlot) atomicOr(&s_err[qi], kErrProbe);
             }
           }
-        }
-        const unsigned enc = FLOAT ? enc_f32(__uint_as_float(val[i])) : enc_i32((int)val[i]);
-        // ---- aggregate into the tile's shared table ----
-        if (WARP_AGG) {
-          const unsigned act = __ballot_sync(kFull, ok);
-          if (ok) {
-            const unsigned peers = __match_any_sync(act, g);
-            const unsigned c = __popc(peers);
-            const unsigned mn = __reduce_min_sync(peers, enc);
-            const unsigned mx = __reduce_max_sync(peers, enc);
-            unsigned long long sbits;
-            if (FLOAT) {
-              double s = 0.0;
-              const double v = (double)__uint_as_float(val[i]);
-              for (unsigned m = peers; m; m &= m - 1)
-                s += __shfl_sync(peers, v, __ffs(m) - 1);
-              sbits = (unsigned long long)__double_as_longlong(s);
-            } else {
-              const int v = (int)val[i];
-              const unsigned lo = __reduce_add_sync(peers, (unsigned)(v & 0xffff));
-              const int hi = __reduce_add_sync(peers, v >> 16);
-              sbits = (unsigned long long)((long long)hi * 65536ll + (long long)lo);
-            }
-            if ((int)lane == __ffs(peers) - 1)
-              smem_upsert<FLOAT>(hkey, hcnt, hsum, hmn, hmx, g, c, sbits, mn, mx, amask,
-                                 &s_err[qi]);
-          }
-        } else if (ok) {
-          const unsigned long long sbits =
-              FLOAT ? (unsigned long long)__double_as_longlong((double)__uint_as_float(val[i]))
-                    : (unsigned long long)(long long)(int)val[i];
-          smem_upsert<FLOAT>(hkey, hcnt, hsum, hmn, hmx, g, 1u, sbits, enc, enc, amask,
-                             &s_err[qi]);
         }
       }
-      // per-warp drop counters
       n_late = __reduce_add_sync(kFull, n_late);
       n_range = __reduce_add_sync(kFull, n_range);
       if (lane == 0 && (n_late | n_range)) {
@@ -215,39 +213,113 @@ __global__ void __launch_bounds__(kK1Threads, 1) k1_fused(const __grid_constant_
         atomicAdd(&s_range[qi], (unsigned long long)n_range);
       }
       __syncthreads();
-
-      // ---- flush the tile's groups to the partial arrays ----
-      const int s0 = tid * kK1SlotsPerThread;
-      unsigned occ = 0;
+      // ---- B: rank inside the group (one atomic per group and warp) ----
+      unsigned rank[kK1Items], gi[kK1Items];
 #pragma unroll
-      for (int j = 0; j < kK1SlotsPerThread; ++j)
-        if (hkey[s0 + j] != kEmpty) occ |= 1u << j;
-      unsigned long long total;
-      const unsigned long long off = block_excl_scan((unsigned long long)__popc(occ), s_tmp, &total);
-      if (tid == 0) s_base = total ? atomicAdd(&Q.ctl->n_parts, total) : 0ull;
+      for (int i = 0; i < kK1Items; ++i) {
+        const bool has = slot[i] != kNoSlot;
+        gi[i] = has ? (unsigned)hidx[slot[i]] : 0xffffffffu;
+        const unsigned act = __ballot_sync(kFull, has);
+        rank[i] = 0;
+        if (has) {
+          const unsigned peers = __match_any_sync(act, gi[i]);
+          const int leader = __ffs(peers) - 1;
+          unsigned base = 0;
+          if ((int)lane == leader) base = atomicAdd(&lcnt[gi[i]], (unsigned)__popc(peers));
+          base = __shfl_sync(peers, base, leader);
+          rank[i] = base + __popc(peers & ((1u << lane) - 1u));
+        }
+      }
       __syncthreads();
+      // ---- C: group ranges (scan of the counters in list order), scatter ----
+      const unsigned nl = s_nlist;
+      {
+        const unsigned i0 = 2u * tid;
+        const unsigned c0 = i0 < nl ? lcnt[i0] : 0u;
+        const unsigned c1 = i0 + 1 < nl ? lcnt[i0 + 1] : 0u;
+        const unsigned x = c0 + c1;
+        unsigned inc = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const unsigned y = __shfl_up_sync(kFull, inc, o);
+          if ((int)lane >= o) inc += y;
+        }
+        if (lane == 31) s_wsum[warp] = inc;
+        __syncthreads();
+        if (warp == 0) {
+          const unsigned w = lane < kK1Warps ? s_wsum[lane] : 0u;
+          unsigned wi = w;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(kFull, wi, o);
+            if ((int)lane >= o) wi += y;
+          }
+          if (lane < kK1Warps) s_wsum[lane] = wi - w;
+          if (lane == kK1Warps - 1) s_wsum[kK1Warps] = wi;
+        }
+        __syncthreads();
+        const unsigned ex = s_wsum[warp] + inc - x;
+        if (i0 < nl) loff[i0] = ex;
+        if (i0 + 1 < nl) loff[i0 + 1] = ex + c0;
+        if (tid == 0) loff[nl] = s_wsum[kK1Warps];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < kK1Items; ++i)
+        if (slot[i] != kNoSlot) vals[loff[gi[i]] + rank[i]] = val[i];
+      if (tid == 0) s_base = nl ? atomicAdd(&Q.ctl->n_parts, (unsigned long long)nl) : 0ull;
+      __syncthreads();
+      // ---- D: reduce every group and append it to the partial arrays ----
       const unsigned long long base = s_base;
-      const bool fits = base + total <= Q.parts_cap;
+      const bool fits = base + nl <= Q.parts_cap;
       if (tid == 0 && !fits) atomicOr(&s_err[qi], kErrPartsOverflow);
       unsigned long long o_acc = 0ull, a_acc = ~0ull;
-      unsigned long long w = base + off;
+      for (unsigned i = tid; i < nl; i += kK1Threads) {
+        const unsigned b = loff[i], e = loff[i + 1];
+        if (e - b > kBigGroup) {
+          s_big[atomicAdd(&s_nbig, 1u)] = (unsigned short)i;
+          continue;
+        }
+        const unsigned long long g = hkey[list[i]];
+        unsigned long long sb;
+        unsigned mn, mx;
+        reduce_values<FLOAT>(vals, b, e, 1u, &sb, &mn, &mx);
+        if (fits) {
+          store_grp(Q.parts + base + i, g, (long long)(e - b), sb, mn, mx);
+          Q.pkeys[base + i] = g;
+        }
+        o_acc |= g;
+        a_acc &= g;
+      }
+      __syncthreads();
+      const unsigned nbig = s_nbig;
+      for (unsigned bi = warp; bi < nbig; bi += kK1Warps) {
+        const unsigned i = s_big[bi];
+        const unsigned b = loff[i], e = loff[i + 1];
+        unsigned long long sb;
+        unsigned mn, mx;
+        reduce_values<FLOAT>(vals, b + lane, e, 32u, &sb, &mn, &mx);
+        mn = __reduce_min_sync(kFull, mn);
+        mx = __reduce_max_sync(kFull, mx);
+        if (FLOAT) {
+          double d = __longlong_as_double((long long)sb);
 #pragma unroll
-      for (int j = 0; j < kK1SlotsPerThread; ++j) {
-        const int s = s0 + j;
-        if (occ & (1u << j)) {
+          for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(kFull, d, o);
+          sb = (unsigned long long)__double_as_longlong(d);
+        } else {
+          long long v = (long long)sb;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+          sb = (unsigned long long)v;
+        }
+        if (lane == 0) {
+          const unsigned long long g = hkey[list[i]];
           if (fits) {
-            const unsigned long long g = hkey[s];
-            store_grp(Q.parts + w, g, (long long)hcnt[s], hsum[s], hmn[s], hmx[s]);
-            Q.pkeys[w] = g;
-            o_acc |= g;
-            a_acc &= g;
+            store_grp(Q.parts + base + i, g, (long long)(e - b), sb, mn, mx);
+            Q.pkeys[base + i] = g;
           }
-          ++w;
-          hkey[s] = kEmpty;
-          hsum[s] = 0ull;
-          hcnt[s] = 0u;
-          hmn[s] = 0xffffffffu;
-          hmx[s] = 0u;
+          o_acc |= g;
+          a_acc &= g;
         }
       }
       const unsigned olo = __reduce_or_sync(kFull, (unsigned)o_acc);
@@ -257,6 +329,16 @@ __global__ void __launch_bounds__(kK1Threads, 1) k1_fused(const __grid_constant_
       if (lane == 0) {
         atomicOr(&s_or[qi], ((unsigned long long)ohi << 32) | olo);
         atomicAnd(&s_and[qi], ((unsigned long long)ahi << 32) | alo);
+      }
+      __syncthreads();
+      // ---- reset the table for the next tile / query ----
+      for (unsigned i = tid; i < nl; i += kK1Threads) {
+        hkey[list[i]] = kEmpty;
+        lcnt[i] = 0u;
+      }
+      if (tid == 0) {
+        s_nlist = 0u;
+        s_nbig = 0u;
       }
       __syncthreads();
     }
@@ -281,27 +363,25 @@ __global__ void __launch_bounds__(kK1Threads, 1) k1_fused(const __grid_constant_
   }
 }
 
-template <bool FLOAT, bool WARP_AGG>
+template <bool FLOAT>
 cudaError_t launch_k1_t(const K1Args& a, int grid, cudaStream_t st) {
   static bool attr_set = false;  // per instantiation; set once per process
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k1_fused<FLOAT, WARP_AGG>,
+    cudaError_t e = cudaFuncSetAttribute(k1_fused<FLOAT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kK1Smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  k1_fused<FLOAT, WARP_AGG><<<grid, kK1Threads, kK1Smem, st>>>(a);
+  k1_fused<FLOAT><<<grid, kK1Threads, kK1Smem, st>>>(a);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_k1(const K1Args& a, int variant, int grid, cudaStream_t st) {
-  const bool wagg = variant == 2;  // measured slower on the Zipf workload; opt-in
-  if (a.value_is_float)
-    return wagg ? launch_k1_t<true, true>(a, grid, st) : launch_k1_t<true, false>(a, grid, st);
-  return wagg ? launch_k1_t<false, true>(a, grid, st) : launch_k1_t<false, false>(a, grid, st);
+  (void)variant;  // a single variant; the config field is kept for ABI stability
+  return a.value_is_float ? launch_k1_t<true>(a, grid, st) : launch_k1_t<false>(a, grid, st);
 }
 
 int k1_tile_events() { return kK1Tile; }
@@ -311,7 +391,7 @@ int k1_max_grid(int device, int variant, int value_is_float) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   (void)variant;
   (void)value_is_float;
-  return sms > 0 ? sms : 148;  // one resident CTA per SM (112 KB shared table)
+  return sms > 0 ? sms : 148;  // one resident CTA per SM (1024 threads)
 }
 
 }  // namespace lms
