@@ -7,7 +7,7 @@
 // event to the (pane, key) group.  The batch columns are read exactly once,
 // with vector loads, for all queries together.
 //
-// Per tile of 2048 events and per query, the groups are built in shared
+// Per tile of 1024 events and per query, the groups are built in shared
 // memory without any floating-point atomics:
 //   A. every surviving event inserts its group key into an open-addressing
 //      table (integer CAS on the key only); a new key is appended to the
@@ -16,9 +16,15 @@
 //      on the group's counter);
 //   C. a scan of the group counters gives every group a contiguous range and
 //      the events scatter their values into it;
-//   D. each group is reduced sequentially (count, int64 or FP64 sum, min, max)
-//      — one thread per small group, one warp per large one — and appended to
-//      the query's partial-group array in HBM.
+//   D. each group is reduced (count, sum, min, max) — one thread per small
+//      group, one warp per large one — and appended to the query's
+//      partial-group array in HBM.  Float32 values are summed on the integer
+//      pipe: every value is aligned to the group's largest exponent B as a
+//      64-bit fixed-point number whose unit is 2^(B-178) (the largest value
+//      occupies bits 28..51, so 2048 of them could not overflow), then the sum is
+//      converted to double once.  The error is at most 2^-41 of the group's
+//      largest |value| (FP64 is slow on this part; groups holding Inf or NaN
+//      are summed in FP64 instead).
 #include <climits>
 
 #include "lms_device.cuh"
@@ -26,11 +32,11 @@
 namespace lms {
 namespace {
 
-constexpr int kK1Threads = 1024;
+constexpr int kK1Threads = 512;                  // two CTAs per SM
 constexpr int kK1Warps = kK1Threads / 32;
 constexpr int kK1Items = 2;                      // events per thread per tile
-constexpr int kK1Tile = kK1Threads * kK1Items;   // 2048 events
-constexpr int kK1HashBits = 12;                  // 4096 slots >= 2 * tile
+constexpr int kK1Tile = kK1Threads * kK1Items;   // 1024 events
+constexpr int kK1HashBits = 11;                  // 2048 slots >= 2 * tile
 constexpr int kK1Hash = 1 << kK1HashBits;
 constexpr unsigned kBigGroup = 32;               // groups above this are reduced by a warp
 constexpr unsigned kNoSlot = 0xffffu;
@@ -63,29 +69,69 @@ __device__ __forceinline__ unsigned insert_key(unsigned long long* hkey, unsigne
   return kNoSlot;
 }
 
-// Sum, min and max (encoded) of v[b], v[b + step], ... below e.
+// Biased exponent used for alignment (denormals count as exponent 1) and the
+// 24-bit significand of a float32 given by its bits.
+__device__ __forceinline__ unsigned f32_exp(unsigned x) {
+  const unsigned be = (x >> 23) & 0xffu;
+  return be ? be : 1u;
+}
+__device__ __forceinline__ long long f32_fixed(unsigned x, unsigned B) {
+  const unsigned be = (x >> 23) & 0xffu;
+  const long long m = be ? (long long)((x & 0x7fffffu) | 0x800000u) : (long long)(x & 0x7fffffu);
+  const int sh = (int)(be ? be : 1u) - (int)B + 28;  // <= 28
+  long long t;
+  if (sh >= 0) t = m << sh;
+  else if (sh > -40) t = (m + (1ll << (-sh - 1))) >> (-sh);  // round half up
+  else t = 0;
+  return (x & 0x80000000u) ? -t : t;
+}
+// double value of a fixed-point sum with unit 2^(B - 178)
+__device__ __forceinline__ double fixed_to_double(long long t, unsigned B) {
+  return (double)t * __longlong_as_double((long long)(1023 + (int)B - 178) << 52);
+}
+
+// Count of values, sum (int64, or double bits) and encoded min/max of
+// v[b], v[b + step], ... below e.  With step = 32 every lane of a warp calls it
+// and the caller combines the lanes with warp reductions.
 template <bool FLOAT>
 __device__ __forceinline__ void reduce_values(const unsigned* v, unsigned b, unsigned e,
-                                              unsigned step, unsigned long long* sbits,
-                                              unsigned* mn, unsigned* mx) {
-  long long isum = 0;
-  double fsum = 0.0;
-  unsigned lo = 0xffffffffu, hi = 0u;
+                                              unsigned step, unsigned* bmax, long long* fixed,
+                                              double* fsum, unsigned* mn, unsigned* mx) {
+  unsigned lo = 0xffffffffu, hi = 0u, B = 1u;
   for (unsigned t = b; t < e; t += step) {
     const unsigned x = v[t];
     const unsigned enc = FLOAT ? enc_f32(__uint_as_float(x)) : enc_i32((int)x);
-    if (FLOAT) fsum += (double)__uint_as_float(x);
-    else isum += (long long)(int)x;
     lo = min(lo, enc);
     hi = max(hi, enc);
+    if (FLOAT) B = max(B, f32_exp(x));
   }
-  *sbits = FLOAT ? (unsigned long long)__double_as_longlong(fsum) : (unsigned long long)isum;
   *mn = lo;
   *mx = hi;
+  *bmax = B;
+  *fsum = 0.0;
+  long long acc = 0;
+  if (!FLOAT) {
+    for (unsigned t = b; t < e; t += step) acc += (long long)(int)v[t];
+  }
+  *fixed = acc;
 }
 
 template <bool FLOAT>
-__global__ void __launch_bounds__(kK1Threads, 1) k1_fused(const __grid_constant__ K1Args a) {
+__device__ __forceinline__ long long fixed_sum(const unsigned* v, unsigned b, unsigned e,
+                                               unsigned step, unsigned B, double* fsum) {
+  long long acc = 0;
+  if (B == 255u) {  // Inf or NaN present: plain FP64 sum
+    double d = 0.0;
+    for (unsigned t = b; t < e; t += step) d += (double)__uint_as_float(v[t]);
+    *fsum = d;
+    return 0;
+  }
+  for (unsigned t = b; t < e; t += step) acc += f32_fixed(v[t], B);
+  return acc;
+}
+
+template <bool FLOAT>
+__global__ void __launch_bounds__(kK1Threads, 2) k1_fused(const __grid_constant__ K1Args a) {
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned long long* hkey = reinterpret_cast<unsigned long long*>(smem);
   unsigned short* hidx = reinterpret_cast<unsigned short*>(hkey + kK1Hash);
@@ -281,9 +327,15 @@ __global__ void __launch_bounds__(kK1Threads, 1) k1_fused(const __grid_constant_
           continue;
         }
         const unsigned long long g = hkey[list[i]];
-        unsigned long long sb;
-        unsigned mn, mx;
-        reduce_values<FLOAT>(vals, b, e, 1u, &sb, &mn, &mx);
+        unsigned B, mn, mx;
+        long long acc;
+        double fs;
+        reduce_values<FLOAT>(vals, b, e, 1u, &B, &acc, &fs, &mn, &mx);
+        unsigned long long sb = (unsigned long long)acc;
+        if (FLOAT) {
+          acc = fixed_sum<FLOAT>(vals, b, e, 1u, B, &fs);
+          sb = (unsigned long long)__double_as_longlong(B == 255u ? fs : fixed_to_double(acc, B));
+        }
         if (fits) {
           store_grp(Q.parts + base + i, g, (long long)(e - b), sb, mn, mx);
           Q.pkeys[base + i] = g;
@@ -296,21 +348,29 @@ __global__ void __launch_bounds__(kK1Threads, 1) k1_fused(const __grid_constant_
       for (unsigned bi = warp; bi < nbig; bi += kK1Warps) {
         const unsigned i = s_big[bi];
         const unsigned b = loff[i], e = loff[i + 1];
-        unsigned long long sb;
-        unsigned mn, mx;
-        reduce_values<FLOAT>(vals, b + lane, e, 32u, &sb, &mn, &mx);
+        unsigned B, mn, mx;
+        long long acc;
+        double fs;
+        reduce_values<FLOAT>(vals, b + lane, e, 32u, &B, &acc, &fs, &mn, &mx);
         mn = __reduce_min_sync(kFull, mn);
         mx = __reduce_max_sync(kFull, mx);
+        unsigned long long sb;
         if (FLOAT) {
-          double d = __longlong_as_double((long long)sb);
+          B = __reduce_max_sync(kFull, B);
+          acc = fixed_sum<FLOAT>(vals, b + lane, e, 32u, B, &fs);
+          if (B == 255u) {
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(kFull, d, o);
-          sb = (unsigned long long)__double_as_longlong(d);
+            for (int o = 16; o > 0; o >>= 1) fs += __shfl_xor_sync(kFull, fs, o);
+            sb = (unsigned long long)__double_as_longlong(fs);
+          } else {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+            sb = (unsigned long long)__double_as_longlong(fixed_to_double(acc, B));
+          }
         } else {
-          long long v = (long long)sb;
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-          sb = (unsigned long long)v;
+          for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+          sb = (unsigned long long)acc;
         }
         if (lane == 0) {
           const unsigned long long g = hkey[list[i]];
@@ -391,7 +451,7 @@ int k1_max_grid(int device, int variant, int value_is_float) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   (void)variant;
   (void)value_is_float;
-  return sms > 0 ? sms : 148;  // one resident CTA per SM (1024 threads)
+  return 2 * (sms > 0 ? sms : 148);  // two resident CTAs per SM
 }
 
 }  // namespace lms
