@@ -6,11 +6,13 @@
 // paper's per-micro-batch output step, Section III-A; window semantics as in
 // the public header).  A window of K panes is assembled from the sorted
 // window state: its panes are K contiguous, key-sorted runs of the state, so
-// the CTA that owns the window merges the runs (merge path, pairwise rounds)
-// in shared memory — or, for windows larger than shared memory, in global
-// scratch — and emits one row per distinct key, in key order.  Rows of all
-// closed windows are written in (window_start, key) order at offsets from a
-// device-wide scan of the per-window row counts.
+// a CTA merges the runs (merge path) into the window's key-sorted list in
+// shared memory and emits one row per distinct key, in key order.  A CTA
+// handles a range of consecutive windows and carries the list from window to
+// window (drop the pane that left, merge in the pane that entered).  Windows
+// larger than shared memory are merged in global scratch.  Rows of all closed
+// windows are written in (window_start, key) order; each range finds its row
+// offset by a decoupled look-back over the ranges before it.
 #include <climits>
 
 #include "lms_device.cuh"
@@ -18,20 +20,20 @@
 namespace lms {
 namespace {
 
-constexpr int kEmitThreads = 1024;
+constexpr int kEmitThreads = 512;
 constexpr size_t kEmitSmemMax = 225 * 1024;  // dynamic shared memory of the emit kernel
 // Largest window (entries) merged in shared memory for windows of k panes:
 // two padded buffers (17 slots per 16 entries) plus two (k+1)-entry boundary
 // arrays must fit in kEmitSmemMax.
 inline unsigned emit_cap(int k) {
-  const size_t avail = kEmitSmemMax - 2ull * (k + 1) * sizeof(unsigned) - 64;
+  const size_t avail = kEmitSmemMax - 2ull * (k + 2) * sizeof(unsigned) - 64;
   const size_t padded = avail / (2 * sizeof(unsigned long long));
   return (unsigned)(((padded - 1) * 16 / 17) & ~size_t(15));
 }
 inline size_t emit_smem(int k) {
   const unsigned cap = emit_cap(k);
   return 2ull * (cap + (cap >> 4) + 1) * sizeof(unsigned long long) +
-         2ull * (k + 1) * sizeof(unsigned);
+         2ull * (k + 2) * sizeof(unsigned);
 }
 
 __device__ __forceinline__ long long floor_div_ll(long long a, long long b) {
@@ -235,31 +237,6 @@ __device__ unsigned long long* merge_runs(unsigned long long* A, unsigned long l
   return A;
 }
 
-// Exclusive rank of `flag` among the block's threads and the block total, by
-// warp ballots.  wt holds 2 x 33 counters; alternate `parity` between calls.
-__device__ __forceinline__ unsigned block_rank(bool flag, unsigned* wt, int parity,
-                                               unsigned* total) {
-  unsigned* t = wt + parity * 33;
-  const unsigned lane = lane_id(), w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const unsigned b = __ballot_sync(kFull, flag);
-  if (lane == 0) t[w] = __popc(b);
-  __syncthreads();
-  if (w == 0) {
-    const unsigned x = lane < nw ? t[lane] : 0u;
-    unsigned inc = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned y = __shfl_up_sync(kFull, inc, o);
-      if ((int)lane >= o) inc += y;
-    }
-    if (lane < nw) t[lane] = inc - x;
-    if (lane == 31) t[32] = inc;
-  }
-  __syncthreads();
-  *total = t[32];
-  return t[w] + __popc(b & ((1u << lane) - 1u));
-}
-
 template <bool FLOAT>
 __device__ __forceinline__ void write_row(const QueryDev& q, ResultRowDev* out, long long wstart,
                                           unsigned key, long long cnt, unsigned long long sbits,
@@ -287,13 +264,14 @@ __device__ __forceinline__ void write_row(const QueryDev& q, ResultRowDev* out, 
   o[2] = make_uint4(key, mnv, mxv, (unsigned)q.qid);
 }
 
-// Combines the state groups S[i..e) (one key, pane order) of a window.  Loads
-// are issued two records at a time so that their latencies overlap.
+// Combines the state groups S[i..e) (one key, pane order) of a window; the low
+// 32 bits of an entry are the group's index in the window state.  Loads are
+// issued two records at a time so that their latencies overlap.
 template <bool FLOAT, bool PAD>
 __device__ __forceinline__ void combine_run(const QueryDev& q, const unsigned long long* S,
-                                            unsigned i, unsigned e, unsigned long long b0,
-                                            long long* cnt, unsigned long long* sbits,
-                                            unsigned* mn, unsigned* mx) {
+                                            unsigned i, unsigned e, long long* cnt,
+                                            unsigned long long* sbits, unsigned* mn,
+                                            unsigned* mx) {
   long long c = 0;
   unsigned long long isum = 0ull;
   double fsum = 0.0;
@@ -302,7 +280,7 @@ __device__ __forceinline__ void combine_run(const QueryDev& q, const unsigned lo
     Grp g[2];
 #pragma unroll
     for (int u = 0; u < 2; ++u)
-      if (t + u < e) g[u] = load_grp(q.state + b0 + (S[pix<PAD>(t + u)] & 0xffffffffull));
+      if (t + u < e) g[u] = load_grp(q.state + (S[pix<PAD>(t + u)] & 0xffffffffull));
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       if (t + u < e) {
@@ -320,45 +298,88 @@ __device__ __forceinline__ void combine_run(const QueryDev& q, const unsigned lo
   *mx = hi;
 }
 
+// Exclusive scan of one count per thread over the block; returns the prefix
+// and writes the block total to *total.  wt holds 33 counters.
+__device__ __forceinline__ unsigned block_scan_u32(unsigned v, unsigned* wt, unsigned* total) {
+  const unsigned lane = lane_id(), w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  unsigned inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(kFull, inc, o);
+    if ((int)lane >= o) inc += y;
+  }
+  if (lane == 31) wt[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    const unsigned x = lane < nw ? wt[lane] : 0u;
+    unsigned wi = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(kFull, wi, o);
+      if ((int)lane >= o) wi += y;
+    }
+    if (lane < nw) wt[lane] = wi - x;
+    if (lane == 31) wt[32] = wi;
+  }
+  __syncthreads();
+  const unsigned r = wt[w] + inc - v;
+  *total = wt[32];
+  __syncthreads();
+  return r;
+}
+
+// Heads (first entries of a key) in this thread's contiguous chunk of S[0..len).
+template <bool PAD>
+__device__ __forceinline__ unsigned chunk_heads(const unsigned long long* S, unsigned len,
+                                                unsigned a, unsigned b) {
+  unsigned h = 0;
+  unsigned prev = a > 0 ? (unsigned)(S[pix<PAD>(a - 1)] >> 32) : 0u;
+  for (unsigned i = a; i < b; ++i) {
+    const unsigned k = (unsigned)(S[pix<PAD>(i)] >> 32);
+    h += (i == 0 || k != prev) ? 1u : 0u;
+    prev = k;
+  }
+  return h;
+}
+
 // Distinct keys of the merged window S[0..len), in key order: their number.
 template <bool PAD>
 __device__ __forceinline__ unsigned long long count_distinct(const unsigned long long* S,
-                                                             unsigned len) {
-  unsigned long long run = 0;
-  for (unsigned i0 = 0; i0 < len; i0 += blockDim.x) {
-    const unsigned i = i0 + threadIdx.x;
-    const bool head = i < len && (i == 0 || (S[pix<PAD>(i)] >> 32) != (S[pix<PAD>(i - 1)] >> 32));
-    run += (unsigned)__syncthreads_count(head);
-  }
-  return run;
+                                                             unsigned len, unsigned* wt) {
+  const unsigned per = (len + blockDim.x - 1) / blockDim.x;
+  const unsigned a = min(len, threadIdx.x * per), b = min(len, a + per);
+  unsigned tot;
+  block_scan_u32(chunk_heads<PAD>(S, len, a, b), wt, &tot);
+  return tot;
 }
 
-// One row per distinct key of the merged window, written from out[0].
+// One row per distinct key of the merged window, written from out[0]; returns
+// the number of rows.  Each thread owns a contiguous chunk of the list and
+// writes the rows of the keys that start in it.
 template <bool FLOAT, bool PAD>
-__device__ __forceinline__ void write_distinct(const QueryDev& q, const unsigned long long* S,
-                                               unsigned len, unsigned long long b0,
-                                               long long wstart, ResultRowDev* out, unsigned* wt,
-                                               int* parity) {
-  unsigned run = 0;
-  for (unsigned i0 = 0; i0 < len; i0 += blockDim.x) {
-    const unsigned i = i0 + threadIdx.x;
-    const unsigned long long x = i < len ? S[pix<PAD>(i)] : 0ull;
-    const bool head = i < len && (i == 0 || (x >> 32) != (S[pix<PAD>(i - 1)] >> 32));
-    unsigned tot;
-    const unsigned r = block_rank(head, wt, *parity, &tot);
-    *parity ^= 1;
-    if (head) {
-      const unsigned key = (unsigned)(x >> 32);
+__device__ __forceinline__ unsigned write_distinct(const QueryDev& q, const unsigned long long* S,
+                                                   unsigned len, long long wstart,
+                                                   ResultRowDev* out, unsigned* wt) {
+  const unsigned per = (len + blockDim.x - 1) / blockDim.x;
+  const unsigned a = min(len, threadIdx.x * per), b = min(len, a + per);
+  unsigned tot;
+  unsigned r = block_scan_u32(chunk_heads<PAD>(S, len, a, b), wt, &tot);
+  unsigned prev = a > 0 ? (unsigned)(S[pix<PAD>(a - 1)] >> 32) : 0u;
+  for (unsigned i = a; i < b; ++i) {
+    const unsigned key = (unsigned)(S[pix<PAD>(i)] >> 32);
+    if (i == 0 || key != prev) {
       unsigned e = i + 1;
       while (e < len && (unsigned)(S[pix<PAD>(e)] >> 32) == key) ++e;
       long long cnt;
       unsigned long long sb;
       unsigned mn, mx;
-      combine_run<FLOAT, PAD>(q, S, i, e, b0, &cnt, &sb, &mn, &mx);
-      write_row<FLOAT>(q, out + run + r, wstart, key, cnt, sb, mn, mx);
+      combine_run<FLOAT, PAD>(q, S, i, e, &cnt, &sb, &mn, &mx);
+      write_row<FLOAT>(q, out + r, wstart, key, cnt, sb, mn, mx);
+      ++r;
     }
-    run += tot;
+    prev = key;
   }
+  return tot;
 }
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -367,21 +388,21 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Decoupled look-back over the windows before `wi` (windows are taken in
+// Decoupled look-back over the window ranges before `ri` (ranges are taken in
 // ticket order, so every predecessor is already running or done).  Publishes
-// this window's row count, waits (bounded, ~4 s) for the predecessors' counts
+// this range's row count, waits (bounded, ~4 s) for the predecessors' counts
 // and returns the exclusive prefix, or ~0 after setting kErrLookback.
-__device__ unsigned long long window_lookback(unsigned long long* stat, unsigned long long wi,
-                                              unsigned long long n, QCtl* c) {
+__device__ unsigned long long range_lookback(unsigned long long* stat, unsigned long long ri,
+                                             unsigned long long n, QCtl* c) {
   constexpr unsigned long long kAgg = 1ull << 62, kPre = 2ull << 62, kVal = kAgg - 1;
   volatile unsigned long long* vs = stat;
-  if (wi == 0) {
+  if (ri == 0) {
     vs[0] = kPre | n;
     return 0ull;
   }
-  vs[wi] = kAgg | n;
+  vs[ri] = kAgg | n;
   unsigned long long acc = 0;
-  long long p = (long long)wi - 1;
+  long long p = (long long)ri - 1;
   const unsigned long long t0 = global_ns();
   unsigned spins = 0;
   while (p >= 0) {
@@ -399,111 +420,214 @@ __device__ unsigned long long window_lookback(unsigned long long* stat, unsigned
     --p;
   }
   __threadfence();
-  vs[wi] = kPre | (acc + n);
+  vs[ri] = kPre | (acc + n);
   return acc;
 }
 
-// Assembles the closed windows, in window order, one CTA per window at a time:
-// merge the window's K pane runs (shared memory, or global scratch for windows
-// above `cap` entries), count its distinct keys, find its row offset by the
-// look-back, then write one row per distinct key in key order.
-// Dynamic shared memory: two padded merge buffers of `cap` entries, then two
-// run-boundary arrays of k + 1 entries.
-template <bool FLOAT>
-__global__ void __launch_bounds__(kEmitThreads, 1)
-    k_emit(const QueryDev q, const Scratch s, ResultRowDev* rows, unsigned cap,
-           unsigned long long rows_cap) {
-  extern __shared__ __align__(16) unsigned long long esm[];
-  const unsigned padded = cap + (cap >> 4) + 1;
-  unsigned* bnd0 = reinterpret_cast<unsigned*>(esm + 2ull * padded);
-  unsigned* bnd1 = bnd0 + (q.k + 1);
-  __shared__ unsigned wt[66];
-  __shared__ unsigned long long s_wi, s_off;
-  QCtl* c = q.ctl;
-  if (c->err & kErrNeedRetry) return;
-  const unsigned long long W = c->n_windows;
+// Copies state entries [g0, g1) as (key << 32 | state index) to T[base ..].
+__device__ __forceinline__ void load_runs(const QueryDev& q, unsigned long long* T, unsigned base,
+                                          unsigned long long g0, unsigned long long g1) {
+  for (unsigned long long g = g0 + threadIdx.x; g < g1; g += blockDim.x)
+    T[pix<true>(base + (unsigned)(g - g0))] = ((q.state[g].gkey & 0xffffffffull) << 32) | g;
+}
+
+// Keeps the entries of L[0..n) whose state index is >= lo, in order, in T.
+// Returns their number.  All threads must call.
+__device__ unsigned compact_list(const unsigned long long* L, unsigned n, unsigned long long lo,
+                                 unsigned long long* T, unsigned* wt) {
+  const unsigned per = (n + blockDim.x - 1) / blockDim.x;
+  const unsigned a = min(n, threadIdx.x * per), b = min(n, a + per);
+  unsigned keep = 0;
+  for (unsigned i = a; i < b; ++i) keep += (L[pix<true>(i)] & 0xffffffffull) >= lo ? 1u : 0u;
+  // exclusive scan of `keep` over the block
+  const unsigned lane = lane_id(), w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  unsigned inc = keep;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(kFull, inc, o);
+    if ((int)lane >= o) inc += y;
+  }
+  if (lane == 31) wt[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    const unsigned x = lane < nw ? wt[lane] : 0u;
+    unsigned wi = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(kFull, wi, o);
+      if ((int)lane >= o) wi += y;
+    }
+    if (lane < nw) wt[lane] = wi - x;
+    if (lane == 31) wt[32] = wi;
+  }
+  __syncthreads();
+  unsigned o = wt[w] + inc - keep;
+  const unsigned total = wt[32];
+  for (unsigned i = a; i < b; ++i) {
+    const unsigned long long x = L[pix<true>(i)];
+    if ((x & 0xffffffffull) >= lo) T[pix<true>(o++)] = x;
+  }
+  __syncthreads();
+  return total;
+}
+
+struct EmitSmem {
+  unsigned long long* L;  // key-sorted list of the current window
+  unsigned long long* T;  // the other buffer
+  unsigned* bnd0;
+  unsigned* bnd1;
+  unsigned* wt;
+};
+
+// Rows of windows [wa, wb): counted (WRITE=false) or written from out[0]
+// (WRITE=true).  Consecutive windows share most of their panes, so the
+// window's key-sorted list is carried from one window to the next: entries of
+// panes that left are dropped and the runs of panes that entered are merged
+// in.  Windows of one pane need no list; windows above `cap` entries are
+// merged in global scratch on their own.
+template <bool FLOAT, bool WRITE>
+__device__ unsigned long long run_range(const QueryDev& q, const Scratch& s, QCtl* c,
+                                        unsigned long long wa, unsigned long long wb,
+                                        unsigned cap, EmitSmem& m, ResultRowDev* out,
+                                        unsigned long long* s_off) {
   const int tid = threadIdx.x;
-  const unsigned long long row_base = c->row_base;
-  int parity = 0;
-  while (true) {
-    if (tid == 0) s_wi = atomicAdd(&c->win_ticket, 1ull);
-    __syncthreads();
-    const unsigned long long wi = s_wi;
-    if (wi >= W) break;
+  unsigned long long acc = 0;
+  bool have = false;
+  unsigned cj0 = 0, cj1 = 0, n = 0;
+  for (unsigned long long wi = wa; wi < wb; ++wi) {
     const long long w = s.win_w[wi];
     const unsigned j0 = s.win_j0[wi], j1 = s.win_j1[wi];
     const unsigned long long b0 = s.pane_begin[j0], b1 = s.pane_begin[j1];
     const unsigned len = (unsigned)(b1 - b0);
     const int nr = (int)(j1 - j0);
     const long long wstart = (w - kPaneBias) * (long long)q.slide + q.base;
-    const unsigned long long* S = nullptr;
-    bool in_smem = true;
-    unsigned long long n = len;  // one pane: its run is already unique and key-sorted
-    if (nr > 1) {
-      if (len <= cap) {
-        unsigned long long* A = esm;
-        unsigned long long* B = esm + padded;
-        for (unsigned i = tid; i < len; i += blockDim.x)
-          A[pix<true>(i)] = ((q.state[b0 + i].gkey & 0xffffffffull) << 32) | i;
-        for (int r = tid; r <= nr; r += blockDim.x)
-          bnd0[r] = (unsigned)(s.pane_begin[j0 + r] - b0);
-        __syncthreads();
-        S = merge_runs<true>(A, B, bnd0, bnd1, nr, len);
-        n = count_distinct<true>(S, len);
-      } else {
-        in_smem = false;
-        if (tid == 0) {
-          unsigned long long off = atomicAdd(&c->pool_used, 2ull * len);
-          if (off + 2ull * len > s.pool_cap) {
-            atomicOr(&c->err, kErrPoolOverflow);
-            off = ~0ull;
-          } else {
-            atomicAdd(&c->big_windows, 1ull);
-          }
-          s_off = off;
-        }
-        __syncthreads();
-        const unsigned long long off = s_off;
-        if (off != ~0ull) {
-          unsigned long long* A = s.pool + off;
-          unsigned long long* B = A + len;
-          for (unsigned i = tid; i < len; i += blockDim.x)
-            A[i] = ((q.state[b0 + i].gkey & 0xffffffffull) << 32) | i;
-          for (int r = tid; r <= nr; r += blockDim.x)
-            bnd0[r] = (unsigned)(s.pane_begin[j0 + r] - b0);
-          __syncthreads();
-          S = merge_runs<false>(A, B, bnd0, bnd1, nr, len);
-          n = count_distinct<false>(S, len);
-        } else {
-          n = 0;  // the host grows the scratch and runs the emission again
+    if (nr == 1) {  // one pane: its run is already unique and key-sorted
+      if (WRITE) {
+        for (unsigned i = tid; i < len; i += blockDim.x) {
+          const Grp g = load_grp(q.state + b0 + i);
+          write_row<FLOAT>(q, out + acc + i, wstart, (unsigned)g.gkey, g.cnt, g.sum, g.mn, g.mx);
         }
       }
+      acc += len;
+      have = false;
+      continue;
     }
+    if (len > cap) {  // global-scratch merge of this window alone
+      have = false;
+      if (tid == 0) {
+        unsigned long long off = atomicAdd(&c->pool_used, 2ull * len);
+        if (off + 2ull * len > s.pool_cap) {
+          atomicOr(&c->err, kErrPoolOverflow);
+          off = ~0ull;
+        } else {
+          atomicAdd(&c->big_windows, 1ull);
+        }
+        *s_off = off;
+      }
+      __syncthreads();
+      const unsigned long long off = *s_off;
+      __syncthreads();
+      if (off == ~0ull) continue;  // the host grows the scratch and runs the emission again
+      unsigned long long* A = s.pool + off;
+      unsigned long long* B = A + len;
+      for (unsigned i = tid; i < len; i += blockDim.x)
+        A[i] = ((q.state[b0 + i].gkey & 0xffffffffull) << 32) | (b0 + i);
+      for (int r = tid; r <= nr; r += blockDim.x)
+        m.bnd0[r] = (unsigned)(s.pane_begin[j0 + r] - b0);
+      __syncthreads();
+      const unsigned long long* S = merge_runs<false>(A, B, m.bnd0, m.bnd1, nr, len);
+      if (WRITE) acc += write_distinct<FLOAT, false>(q, S, len, wstart, out + acc, m.wt);
+      else acc += count_distinct<false>(S, len, m.wt);
+      __syncthreads();
+      continue;
+    }
+    // shared-memory list of this window
+    if (have && j0 < cj1) {
+      // drop the panes that left (their state indices are below b0) ...
+      unsigned nk = n;
+      if (j0 > cj0) {
+        nk = compact_list(m.L, n, b0, m.T, m.wt);
+        unsigned long long* t = m.L; m.L = m.T; m.T = t;
+      }
+      // ... then merge in the runs of the panes that entered
+      if (j1 > cj1) {
+        const unsigned long long g0 = s.pane_begin[cj1];
+        load_runs(q, m.L, nk, g0, b1);  // behind the kept entries
+        const int add = (int)(j1 - cj1);
+        if (tid == 0) m.bnd0[0] = 0u;
+        for (int r = tid; r <= add; r += blockDim.x)
+          m.bnd0[1 + r] = nk + (unsigned)(s.pane_begin[cj1 + r] - g0);
+        __syncthreads();
+        unsigned long long* S = merge_runs<true>(m.L, m.T, m.bnd0, m.bnd1, add + 1, len);
+        if (S != m.L) { m.T = m.L; m.L = S; }
+      }
+    } else {  // full build: merge the window's runs
+      load_runs(q, m.T, 0u, b0, b1);
+      for (int r = tid; r <= nr; r += blockDim.x)
+        m.bnd0[r] = (unsigned)(s.pane_begin[j0 + r] - b0);
+      __syncthreads();
+      unsigned long long* S = merge_runs<true>(m.T, m.L, m.bnd0, m.bnd1, nr, len);
+      if (S != m.L) { m.T = m.L; m.L = S; }
+    }
+    have = true;
+    cj0 = j0;
+    cj1 = j1;
+    n = len;
     __syncthreads();
-    if (tid == 0) {
-      const unsigned long long off = window_lookback(s.win_stat, wi, n, c);
+    if (WRITE) acc += write_distinct<FLOAT, true>(q, m.L, len, wstart, out + acc, m.wt);
+    else acc += count_distinct<true>(m.L, len, m.wt);
+  }
+  __syncthreads();
+  return acc;
+}
+
+// Assembles the closed windows.  CTAs take ranges of consecutive windows in
+// ticket order; for each range: count its rows (pass 1), find the range's row
+// offset by the look-back, then write its rows (pass 2) in (window, key) order.
+// Dynamic shared memory: two padded list buffers of `cap` entries, then two
+// run-boundary arrays of k + 2 entries.
+template <bool FLOAT>
+__global__ void __launch_bounds__(kEmitThreads, 1)
+    k_emit(const QueryDev q, const Scratch s, ResultRowDev* rows, unsigned cap,
+           unsigned long long rows_cap) {
+  extern __shared__ __align__(16) unsigned long long esm[];
+  const unsigned padded = cap + (cap >> 4) + 1;
+  __shared__ unsigned wt[33];
+  __shared__ unsigned long long s_ri, s_off;
+  EmitSmem m;
+  m.L = esm;
+  m.T = esm + padded;
+  m.bnd0 = reinterpret_cast<unsigned*>(esm + 2ull * padded);
+  m.bnd1 = m.bnd0 + (q.k + 2);
+  m.wt = wt;
+  QCtl* c = q.ctl;
+  if (c->err & kErrNeedRetry) return;
+  const unsigned long long W = c->n_windows;
+  const unsigned long long per = (W + 4ull * gridDim.x - 1) / (4ull * gridDim.x);
+  const unsigned long long NR = per ? (W + per - 1) / per : 0;
+  const unsigned long long row_base = c->row_base;
+  while (true) {
+    if (threadIdx.x == 0) s_ri = atomicAdd(&c->win_ticket, 1ull);
+    __syncthreads();
+    const unsigned long long ri = s_ri;
+    __syncthreads();
+    if (ri >= NR) break;
+    const unsigned long long wa = ri * per, wb = min(W, wa + per);
+    const unsigned long long n =
+        run_range<FLOAT, false>(q, s, c, wa, wb, cap, m, nullptr, &s_off);
+    if (threadIdx.x == 0) {
+      const unsigned long long off = range_lookback(s.win_stat, ri, n, c);
       s_off = off;
       if (off != ~0ull) {
-        if (wi == W - 1) c->rows_batch = off + n;
+        if (ri == NR - 1) c->rows_batch = off + n;
         if (row_base + off + n > rows_cap) atomicOr(&c->err, kErrRowsOverflow);
       }
     }
     __syncthreads();
     const unsigned long long off = s_off;
-    if (off != ~0ull && row_base + off + n <= rows_cap && !(c->err & kErrPoolOverflow)) {
-      ResultRowDev* out = rows + row_base + off;
-      if (nr == 1) {
-        for (unsigned i = tid; i < len; i += blockDim.x) {
-          const Grp g = load_grp(q.state + b0 + i);
-          write_row<FLOAT>(q, out + i, wstart, (unsigned)g.gkey, g.cnt, g.sum, g.mn, g.mx);
-        }
-      } else if (in_smem) {
-        write_distinct<FLOAT, true>(q, S, len, b0, wstart, out, wt, &parity);
-      } else {
-        write_distinct<FLOAT, false>(q, S, len, b0, wstart, out, wt, &parity);
-      }
-    }
     __syncthreads();
+    if (off != ~0ull && row_base + off + n <= rows_cap && !(c->err & kErrPoolOverflow))
+      run_range<FLOAT, true>(q, s, c, wa, wb, cap, m, rows + row_base + off, &s_off);
   }
 }
 
