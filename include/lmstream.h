@@ -222,6 +222,76 @@ lms_status lms_results_device(lms_stream *s, int32_t query_id, const lms_result_
 /* Drops query_id's unpolled rows (e.g. after consuming them on the device). */
 lms_status lms_results_discard(lms_stream *s, int32_t query_id);
 
+/* ---- control plane: dynamic micro-batching and per-operation planning ---- */
+
+/* Alg. 1 policies.  PAPER: ConstructMicroBatch as printed (decides only when
+ * new data arrived; admits when EstMaxLat >= target).  GUARDED: also
+ * re-evaluates buffered data on every poll and admits when
+ * EstMaxLat + poll period >= target. */
+#define LMS_ADMIT_PAPER 0
+#define LMS_ADMIT_GUARDED 1
+
+/* Query operations of Table II, in this order (base costs 1.0 1.0 1.0 0.9 0.9
+ * 0.9 0.8 0.8). */
+#define LMS_QOP_AGGREGATION 0
+#define LMS_QOP_FILTER 1
+#define LMS_QOP_SHUFFLE 2
+#define LMS_QOP_PROJECT 3
+#define LMS_QOP_JOIN 4
+#define LMS_QOP_EXPAND 5
+#define LMS_QOP_SCAN 6
+#define LMS_QOP_SORT 7
+
+typedef struct lms_admission lms_admission; /* opaque, owned by the caller */
+
+/* Predictor of a micro-batch's processing time (ms) from its bytes and
+ * dataset count; replaces Eq. 5's bytes / AvgThPut term when installed. */
+typedef double (*lms_proc_predictor)(void *ctx, double batch_bytes, int32_t n_datasets);
+
+/* ConstructMicroBatch state (Section III-C, Alg. 1).  slide_ms > 0: sliding
+ * window, target = SlideTime (Eq. 1); slide_ms == 0: tumbling, target = mean
+ * of the past MaxLat (Eq. 2).  NULL for bad arguments. */
+lms_admission *lms_admission_create(double slide_ms, int32_t policy, double poll_ms);
+void lms_admission_destroy(lms_admission *a);
+void lms_admission_set_predictor(lms_admission *a, lms_proc_predictor fn, void *ctx);
+
+/* One poll of Alg. 1 at now_ms: n_new datasets (arrival time ms, bytes) arrived
+ * since the previous poll.  Returns 1 if the buffered plus new datasets are
+ * admitted as the next micro-batch (*n_admitted = their number), 0 if they
+ * stay buffered, LMS_EINVAL for bad arguments.  *est_ms (optional) receives
+ * EstMaxLat (Eq. 5) of the candidate batch. */
+int32_t lms_admission_poll(lms_admission *a, double now_ms, const double *arrival_ms,
+                           const double *bytes, int32_t n_new, double *est_ms,
+                           int32_t *n_admitted);
+
+/* The admitted micro-batch ran for proc_ms: records it in AvgThPut (Eq. 3) and
+ * returns its MaxLat (Eq. 4); -1 if no batch was admitted. */
+double lms_admission_complete(lms_admission *a, double proc_ms);
+double lms_admission_avg_thput(const lms_admission *a);   /* Eq. 3, bytes/ms (0 before any) */
+int32_t lms_admission_buffered(const lms_admission *a);   /* datasets still buffered */
+double lms_admission_last_estimate(const lms_admission *a);
+
+/* MapDevice (Alg. 2) over a chain of n_ops operations (ops[0] = leaf) with the
+ * costs of Eqs. 6-8: partition = batch_bytes / num_cores.  device[o] receives
+ * 0 (GPU) or 1 (CPU); cpu_cost / gpu_cost (optional) the costs after the
+ * transition term was added.  This engine runs every operation on the GPU;
+ * the plan is provided for callers that place operations themselves. */
+lms_status lms_map_device(const int32_t *ops, int32_t n_ops, double batch_bytes,
+                          int32_t num_cores, double infpt_bytes, double base_trans_cost,
+                          int32_t *device, double *cpu_cost, double *gpu_cost);
+
+/* Online regression of the inflection point (Section III-E, Eq. 9):
+ * InfPT = b0 + b1 * Throughput + b2 * Latency by least squares over the last
+ * history_len samples (0 = all).  fit() evaluates it at the targets and
+ * returns LMS_EAGAIN (with b = (mean, 0, 0)) while fewer than 3 samples exist;
+ * a singular system also gives b = (mean, 0, 0). */
+typedef struct lms_regressor lms_regressor;
+lms_regressor *lms_regressor_create(int32_t history_len);
+void lms_regressor_destroy(lms_regressor *r);
+void lms_regressor_add(lms_regressor *r, double thput, double lat, double infpt);
+lms_status lms_regressor_fit(lms_regressor *r, double target_thput, double target_lat,
+                             double *beta3, double *infpt);
+
 /* Largest n_rows lms_aggregate_batch_static accepts. */
 #define LMS_STATIC_MAX_ROWS 131072
 

@@ -25,6 +25,8 @@ Readings where the paper is ambiguous (same as the engine's):
   * Alg. 1 returns at once when no new data arrived (policy "paper"); policy
     "guarded" also re-evaluates buffered data on every poll and admits when
     EstMaxLat + poll period reaches the target.
+  * Eq. 9 with a singular normal matrix (fewer than 3 samples, or constant or
+    collinear inputs) falls back to b = (mean InfPT, 0, 0).
 """
 from __future__ import annotations
 
@@ -164,6 +166,9 @@ def regress_infpt(thput: Sequence[float], lat: Sequence[float], infpt: Sequence[
     Returns (beta, predicted InfPT at the targets)."""
     X = np.column_stack([np.ones(len(thput)), np.asarray(thput, float), np.asarray(lat, float)])
     y = np.asarray(infpt, float)
-    # least-squares solution via the pseudo-inverse of the normal equations
-    beta = np.linalg.pinv(X.T @ X) @ (X.T @ y)
+    A = X.T @ X
+    if len(y) < 3 or np.linalg.cond(A) > 1e14:
+        beta = np.array([float(np.mean(y)) if len(y) else INFPT0_BYTES, 0.0, 0.0])
+    else:
+        beta = np.linalg.solve(A, X.T @ y)  # normal equations of least squares
     return beta, float(beta[0] + beta[1] * target_thput + beta[2] * target_lat)

@@ -75,7 +75,16 @@ class StatsC(ctypes.Structure):
 
 EXPORTED_SYMBOLS = ("stream_open", "query_register", "push_microbatch", "poll_results",
                     "stream_close", "lms_stream_stats", "lms_last_error", "lms_results_device",
-                    "lms_results_discard", "lms_udiv_invariant", "lms_aggregate_batch_static")
+                    "lms_results_discard", "lms_udiv_invariant", "lms_aggregate_batch_static",
+                    "lms_admission_create", "lms_admission_destroy", "lms_admission_set_predictor",
+                    "lms_admission_poll", "lms_admission_complete", "lms_admission_avg_thput",
+                    "lms_admission_buffered", "lms_admission_last_estimate", "lms_map_device",
+                    "lms_regressor_create", "lms_regressor_destroy", "lms_regressor_add",
+                    "lms_regressor_fit")
+ADMIT_PAPER, ADMIT_GUARDED = 0, 1
+QOPS = {"aggregation": 0, "filter": 1, "shuffle": 2, "project": 3, "join": 4, "expand": 5,
+        "scan": 6, "sort": 7}
+PROC_PREDICTOR = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_void_p, ctypes.c_double, ctypes.c_int32)
 STATIC_MAX_ROWS = 131072
 
 _lib = None
@@ -122,6 +131,29 @@ def load(build_if_missing: bool = True):
     lib.lms_aggregate_batch_static.argtypes = [
         ctypes.POINTER(QuerySpec), ctypes.c_int32, P, P, P, P, ctypes.c_int64, P, P,
         ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
+    D, I = ctypes.c_double, ctypes.c_int32
+    lib.lms_admission_create.restype = P
+    lib.lms_admission_create.argtypes = [D, I, D]
+    lib.lms_admission_destroy.argtypes = [P]
+    lib.lms_admission_set_predictor.argtypes = [P, P, P]
+    lib.lms_admission_poll.restype = I
+    lib.lms_admission_poll.argtypes = [P, D, P, P, I, ctypes.POINTER(D), ctypes.POINTER(I)]
+    lib.lms_admission_complete.restype = D
+    lib.lms_admission_complete.argtypes = [P, D]
+    lib.lms_admission_avg_thput.restype = D
+    lib.lms_admission_avg_thput.argtypes = [P]
+    lib.lms_admission_buffered.restype = I
+    lib.lms_admission_buffered.argtypes = [P]
+    lib.lms_admission_last_estimate.restype = D
+    lib.lms_admission_last_estimate.argtypes = [P]
+    lib.lms_map_device.restype = I
+    lib.lms_map_device.argtypes = [P, I, D, I, D, D, P, P, P]
+    lib.lms_regressor_create.restype = P
+    lib.lms_regressor_create.argtypes = [I]
+    lib.lms_regressor_destroy.argtypes = [P]
+    lib.lms_regressor_add.argtypes = [P, D, D, D]
+    lib.lms_regressor_fit.restype = I
+    lib.lms_regressor_fit.argtypes = [P, D, D, P, ctypes.POINTER(D)]
     _lib = lib
     return lib
 
@@ -311,3 +343,84 @@ def aggregate_batch_static(ts, key, value, type_=None, *, value_type: str, size_
     if st != LMS_OK:
         raise LmsError(st, "lms_aggregate_batch_static")
     return n.value
+
+
+class Admission:
+    """ConstructMicroBatch (Alg. 1) state held by the engine library."""
+
+    def __init__(self, slide_ms: float, policy: int = ADMIT_PAPER, poll_ms: float = 10.0):
+        self._lib = load()
+        self._h = self._lib.lms_admission_create(float(slide_ms), int(policy), float(poll_ms))
+        if not self._h:
+            raise ValueError("bad admission arguments")
+        self._pred = None
+
+    def set_predictor(self, fn):
+        self._pred = None if fn is None else PROC_PREDICTOR(lambda ctx, b, n: float(fn(b, n)))
+        self._lib.lms_admission_set_predictor(self._h, self._pred, None)
+
+    def poll(self, now_ms: float, arrivals=(), nbytes=()):
+        a = np.ascontiguousarray(arrivals, dtype=np.float64)
+        b = np.ascontiguousarray(nbytes, dtype=np.float64)
+        est = ctypes.c_double()
+        nadm = ctypes.c_int32()
+        r = self._lib.lms_admission_poll(self._h, float(now_ms), a.ctypes.data, b.ctypes.data,
+                                         int(a.shape[0]), ctypes.byref(est), ctypes.byref(nadm))
+        if r < 0:
+            raise LmsError(r, "lms_admission_poll")
+        return bool(r), est.value, nadm.value
+
+    def complete(self, proc_ms: float) -> float:
+        return float(self._lib.lms_admission_complete(self._h, float(proc_ms)))
+
+    def avg_thput(self) -> float:
+        return float(self._lib.lms_admission_avg_thput(self._h))
+
+    def buffered(self) -> int:
+        return int(self._lib.lms_admission_buffered(self._h))
+
+    def __del__(self):
+        try:
+            if self._h:
+                self._lib.lms_admission_destroy(self._h)
+        except Exception:
+            pass
+
+
+def map_device(ops, batch_bytes: float, num_cores: int, infpt: float, base_trans_cost=0.1):
+    lib = load()
+    o = np.ascontiguousarray([QOPS[x] for x in ops], dtype=np.int32)
+    dev = np.zeros(len(ops), np.int32)
+    cpu = np.zeros(len(ops))
+    gpu = np.zeros(len(ops))
+    st = lib.lms_map_device(o.ctypes.data, len(ops), float(batch_bytes), int(num_cores),
+                            float(infpt), float(base_trans_cost), dev.ctypes.data,
+                            cpu.ctypes.data, gpu.ctypes.data)
+    if st != LMS_OK:
+        raise LmsError(st, "lms_map_device")
+    return [("CPU" if d else "GPU", c, g) for d, c, g in zip(dev, cpu, gpu)]
+
+
+class Regressor:
+    """Online least-squares model of the inflection point (Eq. 9)."""
+
+    def __init__(self, history_len: int = 0):
+        self._lib = load()
+        self._h = self._lib.lms_regressor_create(int(history_len))
+
+    def add(self, thput, lat, infpt):
+        self._lib.lms_regressor_add(self._h, float(thput), float(lat), float(infpt))
+
+    def fit(self, target_thput, target_lat):
+        beta = np.zeros(3)
+        out = ctypes.c_double()
+        st = self._lib.lms_regressor_fit(self._h, float(target_thput), float(target_lat),
+                                         beta.ctypes.data, ctypes.byref(out))
+        return st, beta, out.value
+
+    def __del__(self):
+        try:
+            if self._h:
+                self._lib.lms_regressor_destroy(self._h)
+        except Exception:
+            pass
