@@ -25,8 +25,9 @@ Readings where the paper is ambiguous (same as the engine's):
   * Alg. 1 returns at once when no new data arrived (policy "paper"); policy
     "guarded" also re-evaluates buffered data on every poll and admits when
     EstMaxLat + poll period reaches the target.
-  * Eq. 9 with a singular normal matrix (fewer than 3 samples, or constant or
-    collinear inputs) falls back to b = (mean InfPT, 0, 0).
+  * Eq. 9 is fitted on centred inputs (the same least-squares solution); with
+    fewer than 3 samples, a constant input or collinear inputs (1 - r^2 below
+    1e-12) it falls back to b = (mean InfPT, 0, 0).
 """
 from __future__ import annotations
 
@@ -162,13 +163,22 @@ def map_device(ops: Sequence[str], batch_bytes: float, num_cores: int, infpt: fl
 
 def regress_infpt(thput: Sequence[float], lat: Sequence[float], infpt: Sequence[float],
                   target_thput: float, target_lat: float) -> Tuple[np.ndarray, float]:
-    """Eq. 9 by ordinary least squares (normal equations solved in float64).
-    Returns (beta, predicted InfPT at the targets)."""
-    X = np.column_stack([np.ones(len(thput)), np.asarray(thput, float), np.asarray(lat, float)])
+    """Eq. 9 by ordinary least squares with an intercept, solved on centred
+    inputs.  Returns (beta, predicted InfPT at the targets)."""
+    t = np.asarray(thput, float)
+    l = np.asarray(lat, float)
     y = np.asarray(infpt, float)
-    A = X.T @ X
-    if len(y) < 3 or np.linalg.cond(A) > 1e14:
-        beta = np.array([float(np.mean(y)) if len(y) else INFPT0_BYTES, 0.0, 0.0])
+    if len(y) == 0:
+        beta = np.array([float(INFPT0_BYTES), 0.0, 0.0])
     else:
-        beta = np.linalg.solve(A, X.T @ y)  # normal equations of least squares
+        tc, lc, yc = t - t.mean(), l - l.mean(), y - y.mean()
+        stt, sll, stl = float(tc @ tc), float(lc @ lc), float(tc @ lc)
+        degenerate = len(y) < 3 or stt == 0.0 or sll == 0.0 or 1.0 - stl * stl / (stt * sll) < 1e-12
+        if degenerate:
+            beta = np.array([float(y.mean()), 0.0, 0.0])
+        else:
+            b12 = np.linalg.solve(np.array([[stt, stl], [stl, sll]]),
+                                  np.array([float(tc @ yc), float(lc @ yc)]))
+            beta = np.array([float(y.mean() - b12[0] * t.mean() - b12[1] * l.mean()),
+                             float(b12[0]), float(b12[1])])
     return beta, float(beta[0] + beta[1] * target_thput + beta[2] * target_lat)

@@ -7,8 +7,9 @@
 // MaxLat; Eq. 3 sums over all partitions; the first non-empty micro-batch is
 // admitted (AvgThPut_-1 is undefined); policy GUARDED re-evaluates buffered
 // data on every poll and admits when EstMaxLat + poll period reaches the
-// target (policy PAPER is Alg. 1 as printed); Eq. 9 falls back to
-// (mean InfPT, 0, 0) when its normal matrix is singular.
+// target (policy PAPER is Alg. 1 as printed); Eq. 9 is solved on centred
+// inputs and falls back to (mean InfPT, 0, 0) with fewer than 3 samples, a
+// constant input, or collinear inputs (1 - r^2 below 1e-12).
 #include <algorithm>
 #include <cmath>
 #include <deque>
@@ -184,82 +185,43 @@ void lms_regressor_add(lms_regressor* r, double thput, double lat, double infpt)
   }
 }
 
-namespace {
-// Eigenvalues of a symmetric 3x3 matrix (closed form, trigonometric method).
-void sym3_eigen(const double A[3][3], double ev[3]) {
-  const double p1 = A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2];
-  const double q = (A[0][0] + A[1][1] + A[2][2]) / 3.0;
-  if (p1 == 0.0) {
-    ev[0] = A[0][0];
-    ev[1] = A[1][1];
-    ev[2] = A[2][2];
-    return;
-  }
-  const double p2 = (A[0][0] - q) * (A[0][0] - q) + (A[1][1] - q) * (A[1][1] - q) +
-                    (A[2][2] - q) * (A[2][2] - q) + 2.0 * p1;
-  const double p = std::sqrt(p2 / 6.0);
-  double B[3][3];
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) B[i][j] = (A[i][j] - (i == j ? q : 0.0)) / p;
-  const double detB = B[0][0] * (B[1][1] * B[2][2] - B[1][2] * B[2][1]) -
-                      B[0][1] * (B[1][0] * B[2][2] - B[1][2] * B[2][0]) +
-                      B[0][2] * (B[1][0] * B[2][1] - B[1][1] * B[2][0]);
-  double r = detB / 2.0;
-  r = std::max(-1.0, std::min(1.0, r));
-  const double phi = std::acos(r) / 3.0;
-  const double kPi = 3.14159265358979323846;
-  ev[0] = q + 2.0 * p * std::cos(phi);
-  ev[2] = q + 2.0 * p * std::cos(phi + 2.0 * kPi / 3.0);
-  ev[1] = 3.0 * q - ev[0] - ev[2];
-}
-}  // namespace
-
 lms_status lms_regressor_fit(lms_regressor* r, double target_thput, double target_lat,
                              double* beta, double* infpt) {
   if (!r || !beta || !infpt) return LMS_EINVAL;
   const size_t n = r->thp.size();
-  double A[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, b[3] = {0, 0, 0}, mean = 0.0;
-  for (size_t k = 0; k < n; ++k) {
-    const double x[3] = {1.0, r->thp[k], r->lat[k]};
-    for (int i = 0; i < 3; ++i) {
-      for (int j = 0; j < 3; ++j) A[i][j] += x[i] * x[j];
-      b[i] += x[i] * r->inf[k];
-    }
-    mean += r->inf[k];
-  }
-  bool singular = n < 3;
-  if (!singular) {
-    double ev[3];
-    sym3_eigen(A, ev);
-    const double hi = std::max(std::fabs(ev[0]), std::max(std::fabs(ev[1]), std::fabs(ev[2])));
-    const double lo = std::min(std::fabs(ev[0]), std::min(std::fabs(ev[1]), std::fabs(ev[2])));
-    singular = !(lo > 0.0) || hi / lo > 1e14;
-  }
-  if (singular) {
-    beta[0] = n ? mean / (double)n : 150.0 * 1024.0;
-    beta[1] = 0.0;
-    beta[2] = 0.0;
+  if (n == 0) {
+    beta[0] = 150.0 * 1024.0;
+    beta[1] = beta[2] = 0.0;
   } else {
-    // Gaussian elimination with partial pivoting on the normal equations
-    double M[3][4];
-    for (int i = 0; i < 3; ++i) {
-      for (int j = 0; j < 3; ++j) M[i][j] = A[i][j];
-      M[i][3] = b[i];
+    // least squares with an intercept, on centred inputs
+    double mt = 0, ml = 0, my = 0;
+    for (size_t k = 0; k < n; ++k) {
+      mt += r->thp[k];
+      ml += r->lat[k];
+      my += r->inf[k];
     }
-    for (int c = 0; c < 3; ++c) {
-      int piv = c;
-      for (int i = c + 1; i < 3; ++i)
-        if (std::fabs(M[i][c]) > std::fabs(M[piv][c])) piv = i;
-      for (int j = 0; j < 4; ++j) std::swap(M[c][j], M[piv][j]);
-      for (int i = c + 1; i < 3; ++i) {
-        const double f = M[i][c] / M[c][c];
-        for (int j = c; j < 4; ++j) M[i][j] -= f * M[c][j];
-      }
+    mt /= (double)n;
+    ml /= (double)n;
+    my /= (double)n;
+    double stt = 0, sll = 0, stl = 0, sty = 0, sly = 0;
+    for (size_t k = 0; k < n; ++k) {
+      const double tc = r->thp[k] - mt, lc = r->lat[k] - ml, yc = r->inf[k] - my;
+      stt += tc * tc;
+      sll += lc * lc;
+      stl += tc * lc;
+      sty += tc * yc;
+      sly += lc * yc;
     }
-    for (int i = 2; i >= 0; --i) {
-      double s = M[i][3];
-      for (int j = i + 1; j < 3; ++j) s -= M[i][j] * beta[j];
-      beta[i] = s / M[i][i];
+    const bool degenerate =
+        n < 3 || stt == 0.0 || sll == 0.0 || 1.0 - stl * stl / (stt * sll) < 1e-12;
+    if (degenerate) {
+      beta[0] = my;
+      beta[1] = beta[2] = 0.0;
+    } else {
+      const double det = stt * sll - stl * stl;
+      beta[1] = (sty * sll - sly * stl) / det;
+      beta[2] = (sly * stt - sty * stl) / det;
+      beta[0] = my - beta[1] * mt - beta[2] * ml;
     }
   }
   *infpt = beta[0] + beta[1] * target_thput + beta[2] * target_lat;
