@@ -292,6 +292,109 @@ void lms_regressor_add(lms_regressor *r, double thput, double lat, double infpt)
 lms_status lms_regressor_fit(lms_regressor *r, double target_thput, double target_lat,
                              double *beta3, double *infpt);
 
+/* Keeps only the first n_keep datasets of the micro-batch Alg. 1 just admitted
+ * (the caller re-offers the others as new datasets at its next poll); when
+ * last_bytes > 0 it replaces the size of the last kept dataset (a dataset that
+ * was split).  This is the serving loop's admission by memory, which the
+ * paper does not have.  LMS_EINVAL if nothing is admitted or n_keep is out of
+ * [1, admitted]. */
+lms_status lms_admission_truncate(lms_admission *a, int32_t n_keep, double last_bytes);
+
+/* ---- serving loop: dynamic micro-batching over an arrival process --------
+ *
+ * A virtual-clock loop (Section III-C's setting: datasets arrive every poll
+ * period and ConstructMicroBatch decides when they form a micro-batch) whose
+ * processing step is real: the backend runs each admitted micro-batch and
+ * returns its measured processing time, which advances the clock.  Arrivals
+ * are given as events per poll tick: tick t covers [t*poll_ms, (t+1)*poll_ms)
+ * and becomes visible at its end; event j of a tick with n events arrives at
+ * t*poll_ms + (j + 0.5) * poll_ms / n.  An event's latency is the completion
+ * time of the micro-batch that processed it minus its arrival time (Eq. 4 per
+ * event).  Decisions are taken at completions and on the poll grid. */
+#define LMS_POLICY_FIXED_SIZE 0    /* admit exactly fixed_rows events once buffered */
+#define LMS_POLICY_FIXED_TRIGGER 1 /* admit everything buffered every trigger_ms */
+#define LMS_POLICY_ANALYTIC 2      /* Alg. 1 with Eq. 5 (target = latency bound) */
+#define LMS_POLICY_LEARNED 3       /* Alg. 1 with the installed processing-time predictor */
+
+/* One piece of a tick handed to the backend: events j_begin .. j_end-1 of a
+ * tick starting at t0_ms with n_total events over width_ms; first_event is the
+ * stream-wide index of the tick's event 0 (a counter for generators). */
+typedef struct lms_serve_chunk {
+  double t0_ms;
+  double width_ms;
+  int64_t n_total;
+  int64_t j_begin;
+  int64_t j_end;
+  int64_t first_event;
+} lms_serve_chunk;
+
+/* Per micro-batch record of a serving run. */
+typedef struct lms_serve_batch {
+  double admit_ms;      /* virtual time the batch was admitted */
+  double proc_ms;       /* processing time reported by the backend */
+  double maxlat_ms;     /* completion - earliest arrival in the batch (Eq. 4) */
+  double est_ms;        /* the policy's EstMaxLat at admission (0 for fixed policies) */
+  double decide_ms;     /* wall time of the admission decision */
+  int64_t n_events;
+  int32_t n_chunks;
+  int32_t forced;       /* 1: end-of-arrivals flush or memory cap forced the batch */
+  /* filled by the backend, if it measures them: */
+  double h2d_ms, k1_ms, sort_ms, emit_ms;
+  uint64_t state_groups_before; /* window-state groups carried into the batch */
+  uint64_t rows_out;            /* result rows the batch emitted */
+} lms_serve_batch;
+
+/* The processing side of a serving run.  process() runs one micro-batch made
+ * of chunks[0 .. n_chunks) (n_events in all), fills what it measures in *rec,
+ * and returns the processing time in ms (< 0: error, the run stops).
+ * admissible_rows() (optional) returns the largest batch the backend can take
+ * now (admission by memory), or < 0 for no limit. */
+typedef struct lms_serve_backend {
+  void *ctx;
+  double (*process)(void *ctx, const lms_serve_chunk *chunks, int32_t n_chunks, int64_t n_events,
+                    lms_serve_batch *rec);
+  int64_t (*admissible_rows)(void *ctx);
+} lms_serve_backend;
+
+typedef struct lms_serve_config {
+  int32_t policy;            /* LMS_POLICY_* */
+  int32_t admit_rule;        /* LMS_ADMIT_PAPER or LMS_ADMIT_GUARDED (Alg. 1 policies) */
+  int64_t fixed_rows;        /* FIXED_SIZE: events per micro-batch (> 0) */
+  double trigger_ms;         /* FIXED_TRIGGER: period (> 0) */
+  double latency_bound_ms;   /* p99 bound, and Alg. 1's target */
+  double poll_ms;            /* tick length = Alg. 1's polling period (> 0) */
+  double bytes_per_event;    /* dataset size = events * bytes_per_event (Alg. 1's Part) */
+  int32_t add_decide_time;   /* 1: the decision's wall time also advances the clock */
+  int32_t stop_when_missed;  /* 1: stop as soon as the p99 bound can no longer hold */
+  double quantile_hi;        /* the tail quantile reported as p_hi (0.99) */
+  int32_t reserved[8];
+} lms_serve_config;
+
+typedef struct lms_serve_result {
+  int64_t offered_events;    /* sum of the tick counts */
+  int64_t processed_events;
+  int64_t batches;
+  int32_t completed;         /* 1: every event was processed; 0: stopped early */
+  int32_t met_bound;         /* completed and p_hi <= latency_bound_ms */
+  double arrival_span_ms;    /* n_ticks * poll_ms */
+  double end_ms;             /* virtual time of the last completion */
+  double busy_ms;            /* sum of processing times */
+  double p50_ms, p_hi_ms, mean_ms, max_ms;  /* per-event latency */
+  double events_per_s;       /* processed_events / arrival span */
+  int64_t max_backlog_events;
+} lms_serve_result;
+
+/* Runs the loop over n_ticks ticks (tick_counts[t] events each) until every
+ * event is processed (or, with stop_when_missed, until the bound is missed).
+ * pred/pred_ctx: the predictor for LMS_POLICY_LEARNED (ignored otherwise).
+ * log (optional, log_cap entries) receives one record per micro-batch;
+ * *n_log their number.  LMS_EINVAL for a bad config; the backend's error
+ * stops the run with LMS_EDEVICE. */
+lms_status lms_serve_run(const lms_serve_config *cfg, const int64_t *tick_counts, int64_t n_ticks,
+                         const lms_serve_backend *backend, lms_proc_predictor pred,
+                         void *pred_ctx, lms_serve_result *out, lms_serve_batch *log,
+                         size_t log_cap, size_t *n_log);
+
 /* Largest n_rows lms_aggregate_batch_static accepts. */
 #define LMS_STATIC_MAX_ROWS 131072
 

@@ -127,6 +127,14 @@ class Admission:
         self.buffered = tmp
         return False
 
+    def truncate(self, n_keep: int, last_bytes: float = 0.0) -> None:
+        """Memory admission of the serving loop (not in the paper): keep the
+        first n_keep admitted datasets; the caller re-offers the rest."""
+        assert self.admitted and 1 <= n_keep <= len(self.admitted)
+        self.admitted = self.admitted[:n_keep]
+        if last_bytes > 0:
+            self.admitted[-1] = Dataset(self.admitted[-1].arrival_ms, float(last_bytes))
+
     def complete(self, proc_ms: float) -> float:
         """Records Proc_i of the last admitted batch; returns MaxLat_i (Eq. 4)."""
         buff = [self.admitted_at - d.arrival_ms for d in self.admitted]

@@ -113,6 +113,14 @@ int32_t lms_admission_poll(lms_admission* a, double now_ms, const double* arriva
   return 0;
 }
 
+lms_status lms_admission_truncate(lms_admission* a, int32_t n_keep, double last_bytes) {
+  if (!a || a->admitted.empty() || n_keep < 1 || n_keep > (int32_t)a->admitted.size())
+    return LMS_EINVAL;
+  a->admitted.resize((size_t)n_keep);
+  if (last_bytes > 0) a->admitted.back().bytes = last_bytes;
+  return LMS_OK;
+}
+
 double lms_admission_complete(lms_admission* a, double proc_ms) {
   if (!a || a->admitted.empty()) return -1.0;
   double max_buff = 0.0, total = 0.0;

@@ -80,11 +80,57 @@ EXPORTED_SYMBOLS = ("stream_open", "query_register", "push_microbatch", "poll_re
                     "lms_admission_poll", "lms_admission_complete", "lms_admission_avg_thput",
                     "lms_admission_buffered", "lms_admission_last_estimate", "lms_map_device",
                     "lms_regressor_create", "lms_regressor_destroy", "lms_regressor_add",
-                    "lms_regressor_fit")
+                    "lms_regressor_fit", "lms_admission_truncate", "lms_serve_run")
 ADMIT_PAPER, ADMIT_GUARDED = 0, 1
 QOPS = {"aggregation": 0, "filter": 1, "shuffle": 2, "project": 3, "join": 4, "expand": 5,
         "scan": 6, "sort": 7}
 PROC_PREDICTOR = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_void_p, ctypes.c_double, ctypes.c_int32)
+POLICY_FIXED_SIZE, POLICY_FIXED_TRIGGER, POLICY_ANALYTIC, POLICY_LEARNED = 0, 1, 2, 3
+
+
+class ServeChunk(ctypes.Structure):
+    _fields_ = [("t0_ms", ctypes.c_double), ("width_ms", ctypes.c_double),
+                ("n_total", ctypes.c_int64), ("j_begin", ctypes.c_int64),
+                ("j_end", ctypes.c_int64), ("first_event", ctypes.c_int64)]
+
+
+class ServeBatch(ctypes.Structure):
+    _fields_ = [("admit_ms", ctypes.c_double), ("proc_ms", ctypes.c_double),
+                ("maxlat_ms", ctypes.c_double), ("est_ms", ctypes.c_double),
+                ("decide_ms", ctypes.c_double), ("n_events", ctypes.c_int64),
+                ("n_chunks", ctypes.c_int32), ("forced", ctypes.c_int32),
+                ("h2d_ms", ctypes.c_double), ("k1_ms", ctypes.c_double),
+                ("sort_ms", ctypes.c_double), ("emit_ms", ctypes.c_double),
+                ("state_groups_before", ctypes.c_uint64), ("rows_out", ctypes.c_uint64)]
+
+
+SERVE_PROCESS = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_void_p, ctypes.POINTER(ServeChunk),
+                                 ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ServeBatch))
+SERVE_ADMISSIBLE = ctypes.CFUNCTYPE(ctypes.c_int64, ctypes.c_void_p)
+
+
+class ServeBackend(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("process", ctypes.c_void_p),
+                ("admissible_rows", ctypes.c_void_p)]
+
+
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("policy", ctypes.c_int32), ("admit_rule", ctypes.c_int32),
+                ("fixed_rows", ctypes.c_int64), ("trigger_ms", ctypes.c_double),
+                ("latency_bound_ms", ctypes.c_double), ("poll_ms", ctypes.c_double),
+                ("bytes_per_event", ctypes.c_double), ("add_decide_time", ctypes.c_int32),
+                ("stop_when_missed", ctypes.c_int32), ("quantile_hi", ctypes.c_double),
+                ("reserved", ctypes.c_int32 * 8)]
+
+
+class ServeResult(ctypes.Structure):
+    _fields_ = [("offered_events", ctypes.c_int64), ("processed_events", ctypes.c_int64),
+                ("batches", ctypes.c_int64), ("completed", ctypes.c_int32),
+                ("met_bound", ctypes.c_int32), ("arrival_span_ms", ctypes.c_double),
+                ("end_ms", ctypes.c_double), ("busy_ms", ctypes.c_double),
+                ("p50_ms", ctypes.c_double), ("p_hi_ms", ctypes.c_double),
+                ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("events_per_s", ctypes.c_double), ("max_backlog_events", ctypes.c_int64)]
 STATIC_MAX_ROWS = 131072
 
 _lib = None
@@ -154,6 +200,12 @@ def load(build_if_missing: bool = True):
     lib.lms_regressor_add.argtypes = [P, D, D, D]
     lib.lms_regressor_fit.restype = I
     lib.lms_regressor_fit.argtypes = [P, D, D, P, ctypes.POINTER(D)]
+    lib.lms_admission_truncate.restype = I
+    lib.lms_admission_truncate.argtypes = [P, I, D]
+    lib.lms_serve_run.restype = I
+    lib.lms_serve_run.argtypes = [ctypes.POINTER(ServeConfig), P, ctypes.c_int64,
+                                  ctypes.POINTER(ServeBackend), P, P, ctypes.POINTER(ServeResult),
+                                  P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
     _lib = lib
     return lib
 
@@ -424,3 +476,56 @@ class Regressor:
                 self._lib.lms_regressor_destroy(self._h)
         except Exception:
             pass
+
+
+def _struct_dict(x) -> dict:
+    return {f[0]: getattr(x, f[0]) for f in x._fields_ if f[0] != "reserved"}
+
+
+def serve_run(tick_counts, *, poll_ms: float, policy: int, bound_ms: float, backend=None,
+              process=None, admissible=None, predictor=None, fixed_rows: int = 0,
+              trigger_ms: float = 0.0, bytes_per_event: float = 16.0,
+              admit_rule: int = ADMIT_GUARDED, add_decide_time: bool = False,
+              stop_when_missed: bool = False, quantile_hi: float = 0.99, log_cap: int = 1 << 16):
+    """Runs the serving loop (lms_serve_run).  Either `backend` (a ServeBackend
+    from a native backend) or Python callables `process(chunks, n_events, rec)`
+    -> ms and optional `admissible()` -> rows.  `predictor` is a Python callable
+    (bytes, n_datasets) -> ms or a (PROC_PREDICTOR-compatible address, ctx) pair.
+    Returns (result dict, per-batch records as a list of dicts)."""
+    lib = load()
+    counts = np.ascontiguousarray(tick_counts, dtype=np.int64)
+    cfg = ServeConfig(policy=int(policy), admit_rule=int(admit_rule), fixed_rows=int(fixed_rows),
+                      trigger_ms=float(trigger_ms), latency_bound_ms=float(bound_ms),
+                      poll_ms=float(poll_ms), bytes_per_event=float(bytes_per_event),
+                      add_decide_time=int(bool(add_decide_time)),
+                      stop_when_missed=int(bool(stop_when_missed)), quantile_hi=float(quantile_hi))
+    keep = []
+    if backend is None:
+        def _proc(ctx, chunks, n_chunks, n_events, rec):
+            return float(process([chunks[i] for i in range(n_chunks)], int(n_events), rec[0]))
+        cb = SERVE_PROCESS(_proc)
+        keep.append(cb)
+        adm = None
+        if admissible is not None:
+            adm = SERVE_ADMISSIBLE(lambda ctx: int(admissible()))
+            keep.append(adm)
+        backend = ServeBackend(None, ctypes.cast(cb, ctypes.c_void_p).value,
+                               ctypes.cast(adm, ctypes.c_void_p).value if adm else None)
+    pred_fn, pred_ctx = None, None
+    if predictor is not None:
+        if callable(predictor):
+            f = PROC_PREDICTOR(lambda ctx, b, n: float(predictor(b, n)))
+            keep.append(f)
+            pred_fn = ctypes.cast(f, ctypes.c_void_p).value
+        else:
+            pred_fn, pred_ctx = predictor
+    log = (ServeBatch * int(log_cap))()
+    n_log = ctypes.c_size_t()
+    res = ServeResult()
+    st = lib.lms_serve_run(ctypes.byref(cfg), counts.ctypes.data, int(counts.shape[0]),
+                           ctypes.byref(backend), pred_fn, pred_ctx, ctypes.byref(res),
+                           ctypes.cast(log, ctypes.c_void_p), int(log_cap), ctypes.byref(n_log))
+    if st != LMS_OK:
+        raise LmsError(st, "lms_serve_run")
+    recs = [_struct_dict(log[i]) for i in range(min(n_log.value, log_cap))]
+    return _struct_dict(res), recs

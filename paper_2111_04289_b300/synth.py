@@ -157,3 +157,46 @@ def device_large_float_batches(torch, nbatches: int, n: int, seed: int, device,
         val = torch.exp(torch.randn(n, generator=g, device=device, dtype=torch.float32))
         out.append({"ts": ts.contiguous(), "key": key.contiguous(), "value": val.contiguous()})
     return out
+
+
+@dataclass
+class ServingLoad:
+    """Arrival process of the serving workload: Poisson arrivals whose rate
+    follows a sinusoid between rate_min and rate_max events/s (period
+    period_ms, starting at the minimum), times rate_scale, with one burst per
+    period of burst_factor times the rate lasting burst_ms at a seeded phase.
+    Produces events per poll tick (the serving loop's input)."""
+
+    rate_min: float = 1e6
+    rate_max: float = 200e6
+    period_ms: float = 20_000.0
+    burst_factor: float = 5.0
+    burst_ms: float = 500.0
+    rate_scale: float = 1.0
+
+    def rate(self, t_ms: np.ndarray, burst_starts: np.ndarray) -> np.ndarray:
+        phase = 2.0 * np.pi * t_ms / self.period_ms
+        r = self.rate_min + (self.rate_max - self.rate_min) * 0.5 * (1.0 - np.cos(phase))
+        k = np.floor(t_ms / self.period_ms).astype(np.int64)
+        b0 = burst_starts[np.clip(k, 0, len(burst_starts) - 1)]
+        in_burst = (t_ms >= b0) & (t_ms < b0 + self.burst_ms)
+        return self.rate_scale * r * np.where(in_burst, self.burst_factor, 1.0)
+
+    def mean_rate(self) -> float:
+        """Mean offered events/s over whole periods (bursts included)."""
+        base = 0.5 * (self.rate_min + self.rate_max)
+        # each burst adds (factor - 1) x the rate integrated over the burst; its
+        # phase is random, so on average that is the mean rate
+        extra = (self.burst_factor - 1.0) * base * self.burst_ms / self.period_ms
+        return self.rate_scale * (base + extra)
+
+    def ticks(self, seed: int, duration_ms: float, poll_ms: float = 10.0) -> np.ndarray:
+        rng = np.random.default_rng(seed)
+        n_periods = int(np.ceil(duration_ms / self.period_ms))
+        burst_starts = (np.arange(n_periods) * self.period_ms +
+                        rng.uniform(0.0, self.period_ms - self.burst_ms, n_periods))
+        n_ticks = int(round(duration_ms / poll_ms))
+        # expected events per tick by the midpoint rule on 8 sub-steps
+        sub = (np.arange(n_ticks)[:, None] + (np.arange(8)[None, :] + 0.5) / 8.0) * poll_ms
+        lam = self.rate(sub, burst_starts).mean(axis=1) * poll_ms * 1e-3
+        return rng.poisson(lam).astype(np.int64)

@@ -20,6 +20,7 @@ HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))
 def _declared_functions():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"\{[^{}]*\}", "{}", src)  # struct bodies (function-pointer members)
     src = "\n".join(l for l in src.splitlines() if not l.lstrip().startswith("typedef"))
     names = re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*([a-z_0-9]+)\s*\(", src, flags=re.M)
     return sorted(set(names))
@@ -46,6 +47,10 @@ int main(void) {
          sizeof(lms_batch), sizeof(lms_result_row), sizeof(lms_stats));
   printf("%zu %zu %zu %zu\n", offsetof(lms_result_row, avg), offsetof(lms_result_row, key),
          offsetof(lms_result_row, query_id), offsetof(lms_stream_config, cuda_stream));
+  printf("%zu %zu %zu %zu %zu\n", sizeof(lms_serve_chunk), sizeof(lms_serve_batch),
+         sizeof(lms_serve_backend), sizeof(lms_serve_config), sizeof(lms_serve_result));
+  printf("%zu %zu %zu\n", offsetof(lms_serve_batch, h2d_ms), offsetof(lms_serve_config, quantile_hi),
+         offsetof(lms_serve_result, max_backlog_events));
   return 0;
 }
 """
@@ -60,9 +65,14 @@ int main(void) {
                          ctypes.sizeof(lm.BatchC), lm.ROW_DTYPE_INT.itemsize,
                          ctypes.sizeof(lm.StatsC)]
     assert sizes[3] == 48
-    assert sizes[5:] == [lm.ROW_DTYPE_INT.fields["avg"][1], lm.ROW_DTYPE_INT.fields["key"][1],
-                         lm.ROW_DTYPE_INT.fields["query_id"][1],
-                         lm.StreamConfig.cuda_stream.offset]
+    assert sizes[5:9] == [lm.ROW_DTYPE_INT.fields["avg"][1], lm.ROW_DTYPE_INT.fields["key"][1],
+                          lm.ROW_DTYPE_INT.fields["query_id"][1],
+                          lm.StreamConfig.cuda_stream.offset]
+    assert sizes[9:14] == [ctypes.sizeof(x) for x in (lm.ServeChunk, lm.ServeBatch,
+                                                      lm.ServeBackend, lm.ServeConfig,
+                                                      lm.ServeResult)]
+    assert sizes[14:] == [lm.ServeBatch.h2d_ms.offset, lm.ServeConfig.quantile_hi.offset,
+                          lm.ServeResult.max_backlog_events.offset]
 
 
 def test_invariant_division_matches_integer_division():
