@@ -219,6 +219,20 @@ const char *lms_last_error(lms_stream *s);
 lms_status lms_results_device(lms_stream *s, int32_t query_id, const lms_result_row **rows,
                               size_t *n);
 
+/* Grows the stream's buffers now so that a push of n_rows rows (from host
+ * memory if host_input is 1) allocates nothing.  Queries must be registered.
+ * LMS_ENOMEM if that exceeds state_cap_bytes or the device. */
+lms_status lms_stream_reserve(lms_stream *s, int64_t n_rows, int32_t host_input);
+
+/* Admission by device memory (the serving loop's; the paper has none): the
+ * largest n_rows the next push can take without the stream's device memory
+ * exceeding cfg.state_cap_bytes, counting the growth of every buffer a push of
+ * that size may need (group arrays for the carried groups plus one group per
+ * row, sort scratch, the input copy when host_input is 1) and a reserve of
+ * max(cap/16, 64 MiB) for result rows and window lists.  *n_out = -1 when the
+ * stream has no cap; 0 when nothing fits. */
+lms_status lms_stream_admissible_rows(lms_stream *s, int32_t host_input, int64_t *n_out);
+
 /* Drops query_id's unpolled rows (e.g. after consuming them on the device). */
 lms_status lms_results_discard(lms_stream *s, int32_t query_id);
 
@@ -394,6 +408,32 @@ lms_status lms_serve_run(const lms_serve_config *cfg, const int64_t *tick_counts
                          const lms_serve_backend *backend, lms_proc_predictor pred,
                          void *pred_ctx, lms_serve_result *out, lms_serve_batch *log,
                          size_t log_cap, size_t *n_log);
+
+/* The engine as a serving backend (large float stream: value float32, no type
+ * column).  It owns a stream opened with *cfg and the nq queries; each
+ * micro-batch the loop admits is made by a synthetic load generator (key
+ * Zipf(zipf_s) over n_keys keys, value lognormal(0, 1), ts = floor(arrival
+ * ms); SplitMix64 on the event's stream-wide index under `seed`) directly in
+ * pinned host memory outside the measured time, then processed as a client
+ * would: push_microbatch from host memory, then poll_results of every row into
+ * pinned host memory; the wall time of push + polls is the processing time.
+ * admissible_rows is lms_stream_admissible_rows capped at max_batch_rows.
+ * keep_rows = 1 keeps every polled row (lms_serve_gpu_kept_rows) for checks. */
+typedef struct lms_serve_gpu lms_serve_gpu;
+lms_status lms_serve_gpu_create(const lms_stream_config *cfg, const lms_query_spec *qs,
+                                int32_t nq, uint64_t seed, uint32_t n_keys, double zipf_s,
+                                int64_t max_batch_rows, int32_t keep_rows, lms_serve_gpu **out);
+lms_status lms_serve_gpu_backend(lms_serve_gpu *g, lms_serve_backend *out);
+lms_stream *lms_serve_gpu_stream(lms_serve_gpu *g);
+/* Writes the events the backend would generate for these chunks into host
+ * arrays (for checks against the oracle). */
+lms_status lms_serve_gpu_generate(lms_serve_gpu *g, const lms_serve_chunk *chunks,
+                                  int32_t n_chunks, int64_t n_events, int64_t *ts, uint32_t *key,
+                                  float *value);
+/* Copies up to cap kept rows of query_id (out == NULL: *n_out = how many). */
+lms_status lms_serve_gpu_kept_rows(lms_serve_gpu *g, int32_t query_id, lms_result_row *out,
+                                   size_t cap, size_t *n_out);
+void lms_serve_gpu_destroy(lms_serve_gpu *g);
 
 /* Largest n_rows lms_aggregate_batch_static accepts. */
 #define LMS_STATIC_MAX_ROWS 131072

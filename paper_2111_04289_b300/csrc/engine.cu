@@ -628,6 +628,56 @@ lms_status lms_stream_stats(lms_stream* s, lms_stats* out) {
   return LMS_OK;
 }
 
+lms_status lms_stream_reserve(lms_stream* s, int64_t n_rows, int32_t host_input) {
+  if (!s || n_rows < 0) return LMS_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->latched != LMS_OK) return s->latched;
+  if (s->qs.empty()) return fail(s, LMS_EINVAL, "no query registered");
+  LMS_CK(cudaSetDevice(s->cfg.device));
+  unsigned long long need = 0;
+  for (QueryHost& q : s->qs) need = std::max(need, q.carried + (unsigned long long)n_rows);
+  lms_status r = ensure_group_capacity(s, need + 1);
+  if (r == LMS_OK && host_input) r = ensure_input(s, (unsigned long long)n_rows);
+  if (r == LMS_OK) LMS_CK(cudaStreamSynchronize(s->st));
+  return r;
+}
+
+lms_status lms_stream_admissible_rows(lms_stream* s, int32_t host_input, int64_t* n_out) {
+  if (!s || !n_out) return LMS_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  const unsigned long long cap = s->cfg.state_cap_bytes;
+  if (cap == 0) {
+    *n_out = -1;
+    return LMS_OK;
+  }
+  // bytes per group of capacity: parts + pkeys + state per query; the shared
+  // sort keys/values and pane index; the input copy of a host push
+  const unsigned long long nq = s->qs.size();
+  const unsigned long long per_q = sizeof(Grp) + 8 + sizeof(Grp);
+  const unsigned long long per_scr = 8 + 8 + 4 + 4 + 4 + 8;
+  const unsigned long long per_in = host_input ? (8 + 4 + 4 + (s->cfg.has_type ? 1 : 0)) : 0;
+  unsigned long long carried = 0, qcap = 0;
+  for (const QueryHost& q : s->qs) {
+    carried = std::max(carried, q.carried);
+    qcap = std::max(qcap, q.cap);
+  }
+  const unsigned long long grown = nq * qcap * per_q + s->scr.cap * per_scr + 16 +
+                                   s->in_cap * (8 + 4 + 4 + (s->cfg.has_type ? 1 : 0));
+  const unsigned long long other = s->dev_bytes > grown ? s->dev_bytes - grown : 0;
+  // keep room for result rows, window lists and merge scratch growing
+  const unsigned long long reserve = std::max<unsigned long long>(cap / 16, 64ull << 20);
+  long long best = 0;
+  for (unsigned long long c = 1ull << 12; c <= (1ull << 34); c <<= 1) {
+    const unsigned long long total = other + nq * c * per_q + c * per_scr + 16 + c * per_in;
+    // a buffer is grown by allocating the new one before freeing the old
+    const unsigned long long peak = total + c * sizeof(Grp);
+    if (peak + reserve > cap) break;
+    if (c > carried + 1) best = std::max<long long>(best, (long long)(c - carried - 1));
+  }
+  *n_out = best;
+  return LMS_OK;
+}
+
 const char* lms_last_error(lms_stream* s) { return s ? s->err.c_str() : "null stream"; }
 
 lms_status stream_close(lms_stream* s) {

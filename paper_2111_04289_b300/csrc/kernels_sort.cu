@@ -37,10 +37,19 @@ __device__ __forceinline__ SortSrc final_src(const QueryDev& q, const Scratch& s
   return ((np - 1) & 1) ? SortSrc{s.keysB, s.valsB} : SortSrc{s.keysA, s.valsA};
 }
 
+// The key/value pair the final sort pass did not write (free after the sort).
+__device__ __forceinline__ void free_pair(const Scratch& s, int np, unsigned long long** k,
+                                          unsigned** v) {
+  const bool final_b = np > 0 && ((np - 1) & 1);
+  *k = final_b ? s.keysA : s.keysB;
+  *v = final_b ? s.valsA : s.valsB;
+}
+
 __global__ void k_sort_plan(QCtl* c) {
   if (threadIdx.x != 0) return;
   const unsigned long long n = c->n_parts;
   c->parts_at_sort = n;
+  c->n_long = 0;
   const unsigned long long m = c->or_mask ^ c->and_mask;
   int np = 0;
   if (n > 1)
@@ -177,11 +186,19 @@ __global__ void __launch_bounds__(1024) k_scan_chunks(unsigned long long* a, int
   if (threadIdx.x == 0) *total = tot;
 }
 
+// Runs of equal keys up to this length are reduced by the thread at their head;
+// longer runs (a hot key's groups from many tiles of one pane) are listed and
+// reduced by whole CTAs in k_rbk_long.
+constexpr unsigned long long kSerialRun = 32;
+
 template <bool FLOAT>
 __global__ void __launch_bounds__(256) k_rbk_write(const QueryDev q, const Scratch s) {
-  const QCtl* c = q.ctl;
+  QCtl* c = q.ctl;
   const unsigned long long n = c->n_parts;
   const SortSrc src = final_src(q, s, c->npasses);
+  unsigned long long* lst;
+  unsigned* lpos;
+  free_pair(s, c->npasses, &lst, &lpos);
   unsigned long long lo, hi;
   chunk_range(n, blockIdx.x, gridDim.x, &lo, &hi);
   __shared__ unsigned long long tmp[33];
@@ -194,25 +211,120 @@ __global__ void __launch_bounds__(256) k_rbk_write(const QueryDev q, const Scrat
     unsigned long long tot;
     const unsigned long long r = block_excl_scan(head ? 1ull : 0ull, tmp, &tot);
     if (head) {
-      long long cnt = 0;
-      unsigned long long isum = 0ull;
-      double fsum = 0.0;
-      unsigned mn = 0xffffffffu, mx = 0u;
-      for (unsigned long long j = i; j < n && src.keys[j] == k; ++j) {
-        const unsigned long long pi = src.vals ? src.vals[j] : j;
-        const Grp g = load_grp(q.parts + pi);
-        cnt += g.cnt;
-        if (FLOAT)
-          fsum += __longlong_as_double((long long)g.sum);
-        else
-          isum += g.sum;
-        mn = min(mn, g.mn);
-        mx = max(mx, g.mx);
+      if (i + kSerialRun < n && src.keys[i + kSerialRun] == k) {
+        // long run: find its end (gallop, then bisect) and hand it over
+        unsigned long long a = i + kSerialRun, step = kSerialRun;
+        unsigned long long b = n;
+        while (true) {
+          const unsigned long long t = a + step;
+          if (t >= n || src.keys[t] != k) {
+            b = t < n ? t : n;
+            break;
+          }
+          a = t;
+          step <<= 1;
+        }
+        while (b - a > 1) {  // keys[a] == k, keys[b] != k (or b == n)
+          const unsigned long long m = a + ((b - a) >> 1);
+          if (src.keys[m] == k) a = m;
+          else b = m;
+        }
+        const unsigned long long slot = atomicAdd(&c->n_long, 1ull);
+        lst[2 * slot] = i;
+        lst[2 * slot + 1] = b;
+        lpos[slot] = (unsigned)(out + r);
+      } else {
+        long long cnt = 0;
+        unsigned long long isum = 0ull;
+        double fsum = 0.0;
+        unsigned mn = 0xffffffffu, mx = 0u;
+        for (unsigned long long j = i; j < n && src.keys[j] == k; ++j) {
+          const unsigned long long pi = src.vals ? src.vals[j] : j;
+          const Grp g = load_grp(q.parts + pi);
+          cnt += g.cnt;
+          if (FLOAT)
+            fsum += __longlong_as_double((long long)g.sum);
+          else
+            isum += g.sum;
+          mn = min(mn, g.mn);
+          mx = max(mx, g.mx);
+        }
+        store_grp(q.state + out + r, k, cnt,
+                  FLOAT ? (unsigned long long)__double_as_longlong(fsum) : isum, mn, mx);
       }
-      store_grp(q.state + out + r, k, cnt,
-                FLOAT ? (unsigned long long)__double_as_longlong(fsum) : isum, mn, mx);
     }
     out += tot;
+  }
+}
+
+// One CTA per listed long run: strided gather of the run's groups, then a
+// fixed-shape tree reduction (deterministic for a given run).
+template <bool FLOAT>
+__global__ void __launch_bounds__(256) k_rbk_long(const QueryDev q, const Scratch s) {
+  const QCtl* c = q.ctl;
+  const unsigned long long nl = c->n_long;
+  const SortSrc src = final_src(q, s, c->npasses);
+  unsigned long long* lst;
+  unsigned* lpos;
+  free_pair(s, c->npasses, &lst, &lpos);
+  __shared__ long long s_cnt[8];
+  __shared__ unsigned long long s_sum[8];
+  __shared__ unsigned s_mn[8], s_mx[8];
+  const unsigned lane = lane_id(), w = threadIdx.x >> 5;
+  for (unsigned long long m = blockIdx.x; m < nl; m += gridDim.x) {
+    const unsigned long long a = lst[2 * m], b = lst[2 * m + 1];
+    long long cnt = 0;
+    unsigned long long isum = 0ull;
+    double fsum = 0.0;
+    unsigned mn = 0xffffffffu, mx = 0u;
+    for (unsigned long long j = a + threadIdx.x; j < b; j += blockDim.x) {
+      const unsigned long long pi = src.vals ? src.vals[j] : j;
+      const Grp g = load_grp(q.parts + pi);
+      cnt += g.cnt;
+      if (FLOAT)
+        fsum += __longlong_as_double((long long)g.sum);
+      else
+        isum += g.sum;
+      mn = min(mn, g.mn);
+      mx = max(mx, g.mx);
+    }
+    unsigned long long sbits = FLOAT ? (unsigned long long)__double_as_longlong(fsum) : isum;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      cnt += __shfl_down_sync(kFull, cnt, o);
+      const unsigned long long os = __shfl_down_sync(kFull, sbits, o);
+      if (FLOAT)
+        sbits = (unsigned long long)__double_as_longlong(
+            __longlong_as_double((long long)sbits) + __longlong_as_double((long long)os));
+      else
+        sbits += os;
+      mn = min(mn, __shfl_down_sync(kFull, mn, o));
+      mx = max(mx, __shfl_down_sync(kFull, mx, o));
+    }
+    if (lane == 0) {
+      s_cnt[w] = cnt;
+      s_sum[w] = sbits;
+      s_mn[w] = mn;
+      s_mx[w] = mx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      long long tc = s_cnt[0];
+      unsigned long long ts = s_sum[0];
+      unsigned tmn = s_mn[0], tmx = s_mx[0];
+      for (int k = 1; k < 8; ++k) {
+        tc += s_cnt[k];
+        if (FLOAT)
+          ts = (unsigned long long)__double_as_longlong(__longlong_as_double((long long)ts) +
+                                                        __longlong_as_double((long long)s_sum[k]));
+        else
+          ts += s_sum[k];
+        tmn = min(tmn, s_mn[k]);
+        tmx = max(tmx, s_mx[k]);
+      }
+      store_grp(q.state + lpos[m], src.keys[a], tc, ts, tmn, tmx);
+    }
+    __syncthreads();
   }
 }
 
@@ -269,11 +381,14 @@ cudaError_t launch_sort_reduce(const QueryDev& q, const Scratch& s, cudaStream_t
   }
   k_rbk_count<<<kGrid, 256, 0, st>>>(q, s);
   k_scan_chunks<<<1, 1024, 0, st>>>(s.chunk, kGrid, &q.ctl->n_state);
-  if (q.value_is_float)
+  if (q.value_is_float) {
     k_rbk_write<true><<<kGrid, 256, 0, st>>>(q, s);
-  else
+    k_rbk_long<true><<<kGrid, 256, 0, st>>>(q, s);
+  } else {
     k_rbk_write<false><<<kGrid, 256, 0, st>>>(q, s);
-  nl += 3;
+    k_rbk_long<false><<<kGrid, 256, 0, st>>>(q, s);
+  }
+  nl += 4;
   if (launches) *launches += nl;
   return cudaGetLastError();
 }

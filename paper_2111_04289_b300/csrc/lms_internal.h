@@ -63,6 +63,7 @@ struct QCtl {
   unsigned long long trim_from;  // first state index carried into the next batch
   unsigned long long win_ticket; // next window to assemble (emission takes windows in order)
   unsigned long long parts_at_sort; // partial groups the sort of this batch consumed
+  unsigned long long n_long;     // long runs of equal keys left to the cooperative reduce
   unsigned int err;
   int npasses;
   int shifts[8];
@@ -173,6 +174,17 @@ cudaError_t launch_emit(const QueryDev& q, const Scratch& s, ResultRowDev* rows,
                         cudaEvent_t* ev4);
 cudaError_t launch_trim(const QueryDev& q, const Scratch& s, int sms, cudaStream_t st,
                         int* launches);
+
+// Synthetic load generator of the serving backend (kernels_gen.cu).
+struct GenChunk {
+  double t0_ms, width_ms;
+  long long n_total, j_begin, first_event;
+  long long offset;  // index of the chunk's first event in the batch
+};
+cudaError_t launch_gen_serving(const GenChunk* chunks, int n_chunks, long long n,
+                               unsigned long long seed, const double* cdf, unsigned n_keys,
+                               long long* ts, unsigned* key, float* value, int sms,
+                               cudaStream_t st);
 
 // Fills filter_lo / filter_hi / filter_exact from filter_f.
 void set_float_filter(QueryDev* d);

@@ -80,7 +80,10 @@ EXPORTED_SYMBOLS = ("stream_open", "query_register", "push_microbatch", "poll_re
                     "lms_admission_poll", "lms_admission_complete", "lms_admission_avg_thput",
                     "lms_admission_buffered", "lms_admission_last_estimate", "lms_map_device",
                     "lms_regressor_create", "lms_regressor_destroy", "lms_regressor_add",
-                    "lms_regressor_fit", "lms_admission_truncate", "lms_serve_run")
+                    "lms_regressor_fit", "lms_admission_truncate", "lms_serve_run",
+                    "lms_stream_admissible_rows", "lms_serve_gpu_create", "lms_serve_gpu_backend",
+                    "lms_serve_gpu_stream", "lms_serve_gpu_generate", "lms_serve_gpu_kept_rows",
+                    "lms_serve_gpu_destroy", "lms_stream_reserve")
 ADMIT_PAPER, ADMIT_GUARDED = 0, 1
 QOPS = {"aggregation": 0, "filter": 1, "shuffle": 2, "project": 3, "join": 4, "expand": 5,
         "scan": 6, "sort": 7}
@@ -206,6 +209,23 @@ def load(build_if_missing: bool = True):
     lib.lms_serve_run.argtypes = [ctypes.POINTER(ServeConfig), P, ctypes.c_int64,
                                   ctypes.POINTER(ServeBackend), P, P, ctypes.POINTER(ServeResult),
                                   P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
+    lib.lms_stream_reserve.restype = I
+    lib.lms_stream_reserve.argtypes = [P, ctypes.c_int64, I]
+    lib.lms_stream_admissible_rows.restype = I
+    lib.lms_stream_admissible_rows.argtypes = [P, I, ctypes.POINTER(ctypes.c_int64)]
+    lib.lms_serve_gpu_create.restype = I
+    lib.lms_serve_gpu_create.argtypes = [ctypes.POINTER(StreamConfig), P, I, ctypes.c_uint64,
+                                         ctypes.c_uint32, D, ctypes.c_int64, I, ctypes.POINTER(P)]
+    lib.lms_serve_gpu_backend.restype = I
+    lib.lms_serve_gpu_backend.argtypes = [P, ctypes.POINTER(ServeBackend)]
+    lib.lms_serve_gpu_stream.restype = P
+    lib.lms_serve_gpu_stream.argtypes = [P]
+    lib.lms_serve_gpu_generate.restype = I
+    lib.lms_serve_gpu_generate.argtypes = [P, P, I, ctypes.c_int64, P, P, P]
+    lib.lms_serve_gpu_kept_rows.restype = I
+    lib.lms_serve_gpu_kept_rows.argtypes = [P, I, P, ctypes.c_size_t,
+                                            ctypes.POINTER(ctypes.c_size_t)]
+    lib.lms_serve_gpu_destroy.argtypes = [P]
     _lib = lib
     return lib
 
@@ -529,3 +549,90 @@ def serve_run(tick_counts, *, poll_ms: float, policy: int, bound_ms: float, back
         raise LmsError(st, "lms_serve_run")
     recs = [_struct_dict(log[i]) for i in range(min(n_log.value, log_cap))]
     return _struct_dict(res), recs
+
+
+def _query_spec(q: dict) -> QuerySpec:
+    fv = q.get("value", 0)
+    return QuerySpec(filter_col=COLS[q.get("col", "ts")], filter_op=OPS[q.get("op", "none")],
+                     filter_i=0 if isinstance(fv, float) else int(fv), filter_f=float(fv),
+                     window_size_ms=int(q["size"]), window_slide_ms=int(q.get("slide", 0)),
+                     agg_mask=AGG_ALL)
+
+
+class ServeGpu:
+    """The engine as a serving backend (lms_serve_gpu_*): a float32 stream with
+    the given queries and a device load generator (Zipf keys, lognormal values,
+    ts = floor(arrival ms))."""
+
+    def __init__(self, queries, *, seed: int, n_keys: int = 1_000_000, zipf_s: float = 1.1,
+                 max_batch_rows: int = 1 << 24, state_cap_bytes: int = 0,
+                 enable_timing: bool = True, keep_rows: bool = False, device: int = 0):
+        self._lib = load()
+        cfg = StreamConfig(device=device, value_type=VALUE_FLOAT32, has_type=0,
+                           enable_timing=int(enable_timing), allowed_lateness_ms=0,
+                           max_batch_rows=int(max_batch_rows),
+                           state_cap_bytes=int(state_cap_bytes), cuda_stream=None,
+                           origin_ts=ORIGIN_AUTO, k1_variant=0)
+        specs = (QuerySpec * len(queries))(*[_query_spec(q) for q in queries])
+        h = ctypes.c_void_p()
+        st = self._lib.lms_serve_gpu_create(ctypes.byref(cfg), specs, len(queries), int(seed),
+                                            int(n_keys), float(zipf_s), int(max_batch_rows),
+                                            int(keep_rows), ctypes.byref(h))
+        if st != LMS_OK:
+            raise LmsError(st, "lms_serve_gpu_create")
+        self._h = h.value
+        self.nq = len(queries)
+        self.max_batch_rows = int(max_batch_rows)
+
+    def backend(self) -> ServeBackend:
+        b = ServeBackend()
+        st = self._lib.lms_serve_gpu_backend(self._h, ctypes.byref(b))
+        if st != LMS_OK:
+            raise LmsError(st, "lms_serve_gpu_backend")
+        return b
+
+    def stats(self) -> dict:
+        out = StatsC()
+        self._lib.lms_stream_stats(self._lib.lms_serve_gpu_stream(self._h), ctypes.byref(out))
+        return {f[0]: getattr(out, f[0]) for f in StatsC._fields_}
+
+    def admissible_rows(self) -> int:
+        n = ctypes.c_int64()
+        st = self._lib.lms_stream_admissible_rows(self._lib.lms_serve_gpu_stream(self._h), 1,
+                                                  ctypes.byref(n))
+        if st != LMS_OK:
+            raise LmsError(st, "lms_stream_admissible_rows")
+        return n.value
+
+    def generate(self, chunks):
+        """chunks: list of (t0_ms, width_ms, n_total, j_begin, j_end, first_event)."""
+        arr = (ServeChunk * len(chunks))(*[ServeChunk(*c) for c in chunks])
+        n = int(sum(c[4] - c[3] for c in chunks))
+        ts = np.empty(n, np.int64)
+        key = np.empty(n, np.uint32)
+        val = np.empty(n, np.float32)
+        st = self._lib.lms_serve_gpu_generate(self._h, arr, len(chunks), n, ts.ctypes.data,
+                                              key.ctypes.data, val.ctypes.data)
+        if st != LMS_OK:
+            raise LmsError(st, "lms_serve_gpu_generate")
+        return ts, key, val
+
+    def kept_rows(self, qid: int) -> np.ndarray:
+        n = ctypes.c_size_t()
+        self._lib.lms_serve_gpu_kept_rows(self._h, int(qid), None, 0, ctypes.byref(n))
+        out = np.zeros(n.value, ROW_DTYPE_FLOAT)
+        if n.value:
+            self._lib.lms_serve_gpu_kept_rows(self._h, int(qid), out.ctypes.data, n.value,
+                                              ctypes.byref(n))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lms_serve_gpu_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -207,3 +207,19 @@ def test_batching_invariance_on_gpu():
     got, _ = run_engine(cuts, q, False, torch=torch)
     for f in ("window_start", "key", "count", "sum", "min", "max", "avg"):
         np.testing.assert_array_equal(ref[0][f], got[0][f])
+
+
+@pytest.mark.parametrize("is_float", [False, True])
+def test_hot_key_runs_longer_than_a_tile(is_float):
+    """Event time barely moves (a serving-like stream): one key takes 60 % of
+    the events of a pane, so its partial groups from hundreds of K1 tiles form
+    one long run that the cooperative reduce combines."""
+    rng = np.random.default_rng(21)
+    n = 600_000
+    ts = np.sort(rng.integers(0, 900, n)).astype(np.int64)
+    key = np.where(rng.random(n) < 0.6, 7, rng.integers(0, 5000, n)).astype(np.uint32)
+    val = (rng.lognormal(0, 1, n).astype(np.float32) if is_float
+           else rng.integers(-1000, 1000, n).astype(np.int32))
+    batches = [synth.Batch(ts[a:a + 200_000], key[a:a + 200_000], val[a:a + 200_000])
+               for a in range(0, n, 200_000)]
+    _check(batches, [dict(size=1000, slide=250), dict(size=300, slide=300)], is_float)
