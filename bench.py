@@ -1,20 +1,26 @@
 #!/usr/bin/env python
-"""Benchmark of the micro-batch stream engine's hot path on B300.
+"""Benchmark of the micro-batch stream engine on B300.
 
-Workload (one step = one micro-batch through the whole hot path: fused
-filter/window/pre-aggregate pass, sort + reduce into window state, window
-assembly and row emission, carry of open panes):
-  large float stream: 2^26-event micro-batches (1 GiB of columns, larger than
-  L2), ts monotone with U{0..5} ms gaps, key Zipf(1.1) over 1M keys, value
-  float32 lognormal(0,1); query: value > 0.5, sliding window 60 s / slide 5 s,
-  count/sum/min/max/avg with FP64 sums.  Synthetic data generated on the device.
+Headline (`value`, metric "events/s at p99 <= 100 ms"): the serving loop's
+largest sustained event rate whose per-event p99 latency stays within 100 ms,
+with Alg. 1 driven by the learned cost model.  Load: Poisson arrivals whose
+rate follows a sinusoid from 1M to 200M events/s (20 s period) plus one 5x,
+0.5-s burst per period, scaled by alpha; large float stream (key Zipf(1.1)
+over 1M keys, value float32 lognormal(0,1), ts = arrival ms); query value >
+0.5, sliding window 60 s / slide 5 s, count/sum/min/max/avg; device state
+capped at 8 GiB with admission by memory.  The rate is found by a search over
+alpha (doubling, then bisection).  `value` keeps the load's columns in HBM;
+`e2e` is the same search through the C ABI from pinned host buffers (every
+batch's host-to-device copy and the device-to-host copy of every result row
+inside the measured time).  `serving` lists every policy: learned, analytic
+(Alg. 1 with Eq. 5) and the best fixed batch size and fixed trigger.
 
-Output: one JSON line (rank 0).  `value` = events/s with the input resident in
-HBM; `e2e` = the same through the C ABI from pinned host buffers, host->device
-copy of the batch and device->host copy of every result row inside the timed
-region.  `roofline` covers the kernel with the largest share of the step,
-`agg_pass` the fused aggregation pass, `cpu_baseline` the CPU oracle on a
-bounded sample.  `--impl reference` times the CPU oracle instead.
+Kernel measurement (`plain_step`, `agg_pass`, `roofline`): one step = one
+2^26-event micro-batch of the same stream with ts +U{0..5} ms (1 GiB of
+columns, larger than L2) through the whole hot path, input resident in HBM;
+`--steps`/`--warmup` apply to it.  `cpu_baseline`: the CPU oracle on a bounded
+sample.  `--impl reference` runs the same serving search with the CPU oracle
+as the processing step (oracle/serve.py + oracle/window_agg).
 """
 from __future__ import annotations
 
@@ -37,6 +43,15 @@ EVENT_BYTES = 16         # ts 8 + key 4 + value 4
 WORKLOAD = ("large float stream: micro-batches of 2^{lg} events, key Zipf(1.1) over 1M keys, "
             "value float32 lognormal(0,1), ts +U{{0..5}} ms; query value>0.5, sliding 60 s / "
             "5 s, count/sum/min/max/avg (FP64 sums)")
+SERVE_WORKLOAD = ("serving loop: Poisson arrivals, rate sinusoid 1M..200M events/s x alpha "
+                  "(20 s period) + one 5x 0.5-s burst per period; large float stream (key "
+                  "Zipf(1.1) over 1M keys, value lognormal(0,1), ts = arrival ms); query "
+                  "value>0.5, sliding 60 s / 5 s, count/sum/min/max/avg; p99 bound 100 ms; "
+                  "state cap 8 GiB, admission by memory; poll 10 ms")
+SERVE_Q = [dict(size=WINDOW_SIZE_MS, slide=WINDOW_SLIDE_MS, col="value", op="gt", value=FILTER_GT)]
+SERVE_FEATS = dict(key_card=1_000_000, selectivity=0.7559, panes=WINDOW_SIZE_MS // WINDOW_SLIDE_MS,
+                   n_queries=1, slide_ms=float(WINDOW_SLIDE_MS), poll_ms=10.0)
+BOUND_MS, POLL_MS = 100.0, 10.0
 
 
 def _peaks():
@@ -130,40 +145,193 @@ def cpu_baseline(lg: int, seed: int):
                       f"({dt:.1f} s single-threaded)"}
 
 
+def alpha_search(run_at, start: float, iters: int = 2, cap: float = 64.0):
+    """Largest alpha whose run meets the bound.  Doubling from `start` until a
+    run that follows a passing one misses the bound (feasibility can be a band:
+    a fixed batch size fails at low rates too, so up to three doublings are
+    tried past a failing start); if nothing passes above `start`, halving
+    below it; then `iters` bisection steps between the last pass and the first
+    fail.  run_at(alpha) -> (met, result).  Returns (alpha, result, runs)."""
+    runs = []
+
+    def ev(a):
+        met, res = run_at(a)
+        runs.append({"alpha": a, "met": bool(met), "p99_ms": res.get("p99_ms")})
+        return met, res
+
+    lo = hi = best = None
+    a, misses = start, 0
+    while a <= cap:
+        met, res = ev(a)
+        if met:
+            lo, best = a, res
+        elif lo is not None:
+            hi = a
+            break
+        else:
+            misses += 1
+            if misses > 3:
+                break
+        a *= 2.0
+    if lo is None:
+        a = start / 2.0
+        hi = start
+        while a >= start / 64.0:
+            met, res = ev(a)
+            if met:
+                lo, best = a, res
+                break
+            hi = a
+            a /= 2.0
+    if lo is not None and hi is not None:
+        for _ in range(iters):
+            mid = 0.5 * (lo + hi)
+            met, res = ev(mid)
+            if met:
+                lo, best = mid, res
+            else:
+                hi = mid
+    return lo, best, runs
+
+
+def _summ(res, log, mean_rate, alpha):
+    n = [r["n_events"] for r in log] or [0]
+    rows = [r["rows_out"] for r in log] or [0]
+    return {"alpha": alpha, "offered_mean_events_per_s": alpha * mean_rate,
+            "events_per_s": res["events_per_s"], "p50_ms": res["p50_ms"],
+            "p99_ms": res["p_hi_ms"], "max_ms": res["max_ms"], "batches": res["batches"],
+            "mean_batch_events": float(sum(n)) / max(1, len(n)),
+            "mean_rows_per_batch": float(sum(rows)) / max(1, len(rows)),
+            "busy_ms": res["busy_ms"], "decide_ms": res["decide_ms"],
+            "observe_ms": res["observe_ms"], "max_backlog_events": res["max_backlog_events"]}
+
+
 def run_reference(args):
+    """The CPU oracle as the processing step of the same serving search
+    (plain Python loop of oracle/serve.py, per-event C++ oracle, 1 core)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    import numpy as np
+
+    from oracle import serve as osv
     from oracle import window_agg as wa
     from paper_2111_04289_b300 import synth
 
-    lg = args.ref_log2
-    gen = synth.LargeFloatStream(seed=synth.BASE_SEED + 2)
-    o = wa.WindowAggOracle(True, 0)
-    qid = o.add_query(wa.COL_VALUE, wa.OP_GT, 0, FILTER_GT, WINDOW_SIZE_MS, WINDOW_SLIDE_MS)
-    times = []
-    for step in range(args.warmup + args.steps):
-        b = gen.next_batch(1 << lg)
-        t0 = time.perf_counter()
-        o.push(b.ts, b.key, b.value, None)
-        o.take_rows(qid)
-        dt = time.perf_counter() - t0
-        if step >= args.warmup:
-            times.append(dt)
-    total = sum(times)
-    v = args.steps * (1 << lg) / total
-    line = {"impl": "reference", "metric": "events/s", "value": v, "unit": "events/s",
-            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+    dur = args.ref_duration_ms
+    zipf = synth.ZipfKeys(1_000_000, 1.1)
+
+    def run_at(alpha):
+        ticks = synth.ServingLoad(rate_scale=alpha).ticks(synth.BASE_SEED + 40, dur)
+        o = wa.WindowAggOracle(True, 0)
+        o.add_query(wa.COL_VALUE, wa.OP_GT, 0, FILTER_GT, WINDOW_SIZE_MS, WINDOW_SLIDE_MS)
+        rng = np.random.default_rng(synth.BASE_SEED + 41)
+
+        def process(pieces, n):
+            ts = np.floor(np.concatenate([p.arrivals() for p in pieces])).astype(np.int64)
+            key = zipf.sample(rng, n)
+            val = synth.lognormal_values(rng, n)
+            t0 = time.perf_counter()
+            o.push(ts, key, val, None)
+            o.take_rows(0)
+            return 1e3 * (time.perf_counter() - t0)
+        res, log, _ = osv.run(ticks, poll_ms=POLL_MS, policy=osv.ANALYTIC, bound_ms=BOUND_MS,
+                              process=process, bytes_per_event=EVENT_BYTES)
+        o.close()
+        met = res.get("met_bound", False)
+        return met, {"p99_ms": res.get("p_hi"), "p50_ms": res.get("p50"),
+                     "events": res["processed"], "batches": res["batches"]}
+
+    t0 = time.perf_counter()
+    alpha, res, runs = alpha_search(run_at, start=1.0 / 512, iters=2)
+    wall = time.perf_counter() - t0
+    v = 0.0 if alpha is None else res["events"] / (dur * 1e-3)
+    line = {"impl": "reference", "metric": "events/s at p99 <= 100 ms", "value": v,
+            "unit": "events/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD.format(lg=lg) + " (bounded CPU sample per step)",
-                       "batch_events": 1 << lg},
+            "config": {"workload": SERVE_WORKLOAD + f"; arrival span {dur / 1e3:.0f} s per run "
+                       "(bounded for the CPU)", "policy": "Alg. 1 with Eq. 5 (analytic)",
+                       "search": runs},
             "cpu_baseline": {"value": v, "unit": "events/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} micro-batches of 2^{lg} events"},
+                             "sample": f"serving search over alpha, {len(runs)} runs of "
+                                       f"{dur / 1e3:.0f} s of arrivals ({wall:.0f} s wall)"},
             "e2e": {"value": v, "unit": "events/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def run_serving(args, lm, synth, local):
+    """For each input mode (columns in HBM; columns in pinned host memory):
+    exploration runs whose timings train the learned cost model, then the
+    alpha search of every policy.  Returns the serving dict."""
+    dur = args.serve_duration_ms
+    mean = synth.ServingLoad().mean_rate()
+    seed = synth.BASE_SEED + 40
+
+    def once(alpha, policy, device_input, learned=None, **kw):
+        ticks = synth.ServingLoad(rate_scale=alpha).ticks(seed, dur)
+        g = lm.ServeGpu(SERVE_Q, seed=seed + 1, n_keys=1_000_000, max_batch_rows=1 << 25,
+                        state_cap_bytes=8 << 30, device_input=device_input, device=local)
+        hooks = {}
+        if learned is not None:
+            learned.set_backend(g)
+            pred, obs = learned.hooks()
+            hooks = dict(predictor=pred, observer=obs)
+        res, log = lm.serve_run(ticks, poll_ms=POLL_MS, policy=policy, bound_ms=BOUND_MS,
+                                backend=g.backend(), add_decide_time=True,
+                                stop_when_missed=True, **kw, **hooks)
+        if learned is not None:
+            learned.set_backend(None)
+        g.close()
+        return res, log
+
+    def searcher(policy, device_input, start, learned=None, **kw):
+        def run_at(alpha):
+            res, log = once(alpha, policy, device_input, learned, **kw)
+            return bool(res["met_bound"]), dict(_summ(res, log, mean, alpha),
+                                                p99_ms=res["p_hi_ms"])
+        a, res, runs = alpha_search(run_at, start=start, iters=args.serve_iters)
+        out = dict(res) if res else {"events_per_s": 0.0, "alpha": None}
+        out["search"] = runs
+        return out
+
+    serving = {"duration_ms_per_run": dur, "bound_ms": BOUND_MS}
+    for mode, dev_in, start in (("device_input", True, args.start_device),
+                                ("host_input", False, args.start_host)):
+        # exploration: timings under several policies train the network
+        net = lm.Mlp(lm.mlp_init_params(synth.BASE_SEED))
+        learned = lm.Learned(net, None, **SERVE_FEATS)
+        for pol, kw in [(lm.POLICY_ANALYTIC, {}),
+                        (lm.POLICY_FIXED_SIZE, dict(fixed_rows=150_000)),
+                        (lm.POLICY_FIXED_SIZE, dict(fixed_rows=2_000_000)),
+                        (lm.POLICY_FIXED_TRIGGER, dict(trigger_ms=50.0))]:
+            _, log = once(args.explore_alpha, pol, dev_in, learned, **kw)
+        t0 = time.perf_counter()
+        fit_loss = learned.fit(args.fit_steps, lr=1e-3)
+        fit_s = time.perf_counter() - t0
+        learned.set_online(refit_every=50, refit_steps=20)
+        m = {"learned": searcher(lm.POLICY_LEARNED, dev_in, start, learned)}
+        m["learned"]["judge"] = learned.stats()
+        m["analytic"] = searcher(lm.POLICY_ANALYTIC, dev_in, start)
+        fixed = {str(n): searcher(lm.POLICY_FIXED_SIZE, dev_in, 1.0, fixed_rows=n)
+                 for n in args.fixed_sizes}
+        best = max(fixed, key=lambda k: fixed[k]["events_per_s"])
+        m["fixed_size_best"] = dict(fixed[best], fixed_rows=int(best))
+        m["fixed_size_sweep"] = {k: v["events_per_s"] for k, v in fixed.items()}
+        trig = {str(t): searcher(lm.POLICY_FIXED_TRIGGER, dev_in, 1.0, trigger_ms=t)
+                for t in args.fixed_triggers}
+        best = max(trig, key=lambda k: trig[k]["events_per_s"])
+        m["fixed_trigger_best"] = dict(trig[best], trigger_ms=float(best))
+        m["fixed_trigger_sweep"] = {k: v["events_per_s"] for k, v in trig.items()}
+        m["training"] = {"samples": learned.samples(), "fit_steps": args.fit_steps,
+                         "fit_loss": fit_loss, "fit_s": fit_s,
+                         "online": "20 Adam steps every 50 batches"}
+        serving[mode] = m
+        learned.close()
+        net.close()
+    return serving
 
 
 def run_ours(args):
@@ -247,21 +415,46 @@ def run_ours(args):
              "emit_write_ms": d["e2_ms"] / K}
     dominant = e2 if d["e2_ms"] >= d["k1_ms"] else k1
 
-    line = {"metric": "events/s", "value": value, "unit": "events/s", "n_gpus": world,
-            "steps": K, "warmup": args.warmup, "ms_per_step": ms_max / K,
+    plain = {"workload": WORKLOAD.format(lg=lg), "events_per_s": value, "ms_per_step": ms_max / K,
+             "steps": K, "warmup": args.warmup, "batch_events": n,
+             "phase_ms_per_step": share, "rows_per_step": d["rows_emitted"] / K,
+             "l2": "inputs larger than L2 (1 GiB of columns per micro-batch)"}
+    line = {"metric": "events/s at p99 <= 100 ms", "value": None, "unit": "events/s",
+            "n_gpus": world, "steps": K, "warmup": args.warmup, "ms_per_step": ms_max / K,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (generated on device, seeded)",
-            "config": {"workload": WORKLOAD.format(lg=lg), "batch_events": n, "queries": 1,
-                       "parallelism": f"replicas x{world} (no data-path collective)",
-                       "l2": "inputs larger than L2 (1 GiB of columns per micro-batch)"},
-            "roofline": dominant, "agg_pass": k1, "phase_ms_per_step": share,
-            "rows_per_step": d["rows_emitted"] / K, "gpu_launches": d["kernel_launches"],
-            "wall_s": wall, "clocks": clocks}
+            "config": {"workload": SERVE_WORKLOAD, "policy": "Alg. 1 with the learned cost model",
+                       "queries": 1, "parallelism": f"replicas x{world} (no data-path collective)",
+                       "l2": "serving: state and columns far larger than L2; kernel step: 1 GiB "
+                             "of columns per micro-batch",
+                       "steps_apply_to": "plain_step (kernel measurement)"},
+            "roofline": dominant, "agg_pass": k1, "plain_step": plain,
+            "gpu_launches": d["kernel_launches"], "wall_s": wall, "clocks": clocks}
     s.close()
     del batches
     torch.cuda.synchronize()
-    if not args.no_e2e:
-        line["e2e"] = run_e2e(args, torch, lm, synth, dev, local, rank, world, dist)
+    if args.plain_e2e:
+        plain["e2e"] = run_e2e(args, torch, lm, synth, dev, local, rank, world, dist)
+    if not args.no_serve:
+        sampler = ClockSampler(local)
+        sampler.start()
+        t0 = time.perf_counter()
+        serving = run_serving(args, lm, synth, local)
+        serving["wall_s"] = time.perf_counter() - t0
+        serving["clocks"] = sampler.stop()
+        vals = torch.tensor([serving["device_input"]["learned"]["events_per_s"],
+                             serving["host_input"]["learned"]["events_per_s"]],
+                            dtype=torch.float64, device=dev)
+        if dist:  # replicas: whole-job rate = sum over ranks
+            dist.all_reduce(vals, op=dist.ReduceOp.SUM)
+        line["value"] = float(vals[0])
+        lh = serving["host_input"]["learned"]
+        line["e2e"] = {"value": float(vals[1]), "unit": "events/s",
+                       "h2d_bytes_per_step": int(EVENT_BYTES * lh.get("mean_batch_events", 0)),
+                       "d2h_bytes_per_step": int(ROW_BYTES * lh.get("mean_rows_per_batch", 0)),
+                       "step": "one admitted micro-batch of the serving loop",
+                       "p99_ms": lh.get("p99_ms"), "p50_ms": lh.get("p50_ms")}
+        line["serving"] = serving
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args.cpu_log2, synth.BASE_SEED + 2)
     if rank == 0:
@@ -324,8 +517,20 @@ def main():
     ap.add_argument("--log2n", type=int, default=26)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-log2", type=int, default=22)
-    ap.add_argument("--ref-log2", type=int, default=20)
-    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--plain-e2e", action="store_true",
+                    help="also time the kernel step through host buffers")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-duration-ms", type=float, default=20_000.0)
+    ap.add_argument("--start-device", type=float, default=4.0)
+    ap.add_argument("--start-host", type=float, default=2.0)
+    ap.add_argument("--serve-iters", type=int, default=2)
+    ap.add_argument("--explore-alpha", type=float, default=1.0)
+    ap.add_argument("--fit-steps", type=int, default=5000)
+    ap.add_argument("--fixed-sizes", type=lambda x: [int(v) for v in x.split(",")],
+                    default=[1_000_000, 2_000_000])
+    ap.add_argument("--fixed-triggers", type=lambda x: [float(v) for v in x.split(",")],
+                    default=[25.0, 50.0])
+    ap.add_argument("--ref-duration-ms", type=float, default=20_000.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--k1-variant", type=int, default=0)
     args = ap.parse_args()

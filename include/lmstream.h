@@ -396,35 +396,51 @@ typedef struct lms_serve_result {
   double p50_ms, p_hi_ms, mean_ms, max_ms;  /* per-event latency */
   double events_per_s;       /* processed_events / arrival span */
   int64_t max_backlog_events;
+  double decide_ms;          /* wall time of all admission decisions */
+  double observe_ms;         /* wall time the observer blocked the loop */
 } lms_serve_result;
+
+/* Called after every micro-batch with its record (for example to train a
+ * learned predictor online); returns the wall time in ms it blocked the loop,
+ * which advances the clock when add_decide_time is set. */
+typedef double (*lms_batch_observer)(void *ctx, const lms_serve_batch *rec);
 
 /* Runs the loop over n_ticks ticks (tick_counts[t] events each) until every
  * event is processed (or, with stop_when_missed, until the bound is missed).
- * pred/pred_ctx: the predictor for LMS_POLICY_LEARNED (ignored otherwise).
+ * pred/pred_ctx: the predictor for LMS_POLICY_LEARNED (ignored otherwise);
+ * observe (optional) is called with pred_ctx after each batch.
  * log (optional, log_cap entries) receives one record per micro-batch;
  * *n_log their number.  LMS_EINVAL for a bad config; the backend's error
  * stops the run with LMS_EDEVICE. */
 lms_status lms_serve_run(const lms_serve_config *cfg, const int64_t *tick_counts, int64_t n_ticks,
                          const lms_serve_backend *backend, lms_proc_predictor pred,
-                         void *pred_ctx, lms_serve_result *out, lms_serve_batch *log,
-                         size_t log_cap, size_t *n_log);
+                         void *pred_ctx, lms_batch_observer observe, lms_serve_result *out,
+                         lms_serve_batch *log, size_t log_cap, size_t *n_log);
 
 /* The engine as a serving backend (large float stream: value float32, no type
- * column).  It owns a stream opened with *cfg and the nq queries; each
- * micro-batch the loop admits is made by a synthetic load generator (key
- * Zipf(zipf_s) over n_keys keys, value lognormal(0, 1), ts = floor(arrival
- * ms); SplitMix64 on the event's stream-wide index under `seed`) directly in
- * pinned host memory outside the measured time, then processed as a client
- * would: push_microbatch from host memory, then poll_results of every row into
- * pinned host memory; the wall time of push + polls is the processing time.
- * admissible_rows is lms_stream_admissible_rows capped at max_batch_rows.
- * keep_rows = 1 keeps every polled row (lms_serve_gpu_kept_rows) for checks. */
+ * column).  It owns a stream opened with *cfg and the nq queries.  The load:
+ * key Zipf(zipf_s) over n_keys keys and value lognormal(0, 1), drawn once for
+ * a pool of 2^26 event counters (SplitMix64 under `seed`; event c of the stream
+ * takes entry c mod 2^26), ts = floor(arrival ms) written per batch; all of it
+ * outside the measured time.  Each micro-batch is processed as a client would:
+ * push_microbatch, then poll_results of every row into pinned host memory; the
+ * wall time of push + polls is the processing time.  Flags:
+ * LMS_SERVE_DEVICE_INPUT keeps the columns in device memory (push reads them
+ * in place); otherwise they are in pinned host memory and the host-to-device
+ * copy is inside the measured time.  LMS_SERVE_KEEP_ROWS keeps every polled
+ * row (lms_serve_gpu_kept_rows) for checks.  admissible_rows is
+ * lms_stream_admissible_rows capped at max_batch_rows (<= 2^26).  Creation
+ * warms the kernels up on a throwaway stream and reserves the stream's
+ * buffers for the largest admissible batch. */
+#define LMS_SERVE_KEEP_ROWS 1
+#define LMS_SERVE_DEVICE_INPUT 2
 typedef struct lms_serve_gpu lms_serve_gpu;
 lms_status lms_serve_gpu_create(const lms_stream_config *cfg, const lms_query_spec *qs,
                                 int32_t nq, uint64_t seed, uint32_t n_keys, double zipf_s,
-                                int64_t max_batch_rows, int32_t keep_rows, lms_serve_gpu **out);
+                                int64_t max_batch_rows, int32_t flags, lms_serve_gpu **out);
 lms_status lms_serve_gpu_backend(lms_serve_gpu *g, lms_serve_backend *out);
 lms_stream *lms_serve_gpu_stream(lms_serve_gpu *g);
+int32_t lms_serve_gpu_device_input(const lms_serve_gpu *g); /* 1 if created with LMS_SERVE_DEVICE_INPUT */
 /* Writes the events the backend would generate for these chunks into host
  * arrays (for checks against the oracle). */
 lms_status lms_serve_gpu_generate(lms_serve_gpu *g, const lms_serve_chunk *chunks,
@@ -434,6 +450,92 @@ lms_status lms_serve_gpu_generate(lms_serve_gpu *g, const lms_serve_chunk *chunk
 lms_status lms_serve_gpu_kept_rows(lms_serve_gpu *g, int32_t query_id, lms_result_row *out,
                                    size_t cap, size_t *n_out);
 void lms_serve_gpu_destroy(lms_serve_gpu *g);
+
+/* ---- learned cost model ------------------------------------------------
+ *
+ * A multilayer perceptron 8 -> 64 -> 64 -> 64 -> 1 (ReLU hidden layers,
+ * linear output) that predicts ln(latency in microseconds) of one operator of
+ * a micro-batch from the eight features of lms_cost_features.  The paper's
+ * cost model is analytic (Eqs. 5-9); this one is trained on the engine's own
+ * timings and, installed as Alg. 1's predictor, replaces Eq. 5's
+ * bytes / AvgThPut term.  Master weights are FP32; forward and backward use
+ * them rounded to bf16 (round to nearest even) with FP32 accumulation; the
+ * loss is the mean squared error; training is Adam (beta1 0.9, beta2 0.999,
+ * eps 1e-8) on the GPU with the library's own kernels.
+ *
+ * Parameter vector (FP32, LMS_MLP_PARAMS entries, row-major W[out][in]):
+ * W1[64][8], b1[64], W2[64][64], b2[64], W3[64][64], b3[64], W4[64], b4. */
+#define LMS_MLP_INPUTS 8
+#define LMS_MLP_HIDDEN 64
+#define LMS_MLP_PARAMS 8961
+#define LMS_MLP_MAX_BATCH 4096
+
+typedef struct lms_mlp lms_mlp;
+/* On `device` with the given initial parameters; NULL on failure. */
+lms_mlp *lms_mlp_create(int32_t device, const float *params);
+void lms_mlp_destroy(lms_mlp *m);
+/* Replaces the master weights (and resets Adam's moments and step count). */
+lms_status lms_mlp_set_params(lms_mlp *m, const float *params);
+lms_status lms_mlp_get_params(lms_mlp *m, float *params);
+/* y[i] = network(x[i*8 .. i*8+8)) for n host samples (GPU inference kernel). */
+lms_status lms_mlp_forward(lms_mlp *m, const float *x, int32_t n, float *y);
+/* `steps` Adam steps (learning rate lr) on the full batch of n <= 4096 host
+ * samples (x [n][8], targets t [n]).  grad_out (optional, LMS_MLP_PARAMS) and
+ * *loss_out (optional) receive the gradient and the loss of the last step's
+ * forward pass, i.e. at the weights before its update; steps == 0 computes
+ * them without updating. */
+lms_status lms_mlp_train(lms_mlp *m, const float *x, const float *t, int32_t n, int32_t steps,
+                         float lr, float *grad_out, float *loss_out);
+
+/* Operators whose latency the model predicts, per micro-batch. */
+#define LMS_OP_H2D 0   /* host-to-device copy of the batch */
+#define LMS_OP_K1 1    /* fused filter / window / pre-aggregate pass */
+#define LMS_OP_SORT 2  /* sort + reduce into window state */
+#define LMS_OP_EMIT 3  /* window assembly, emission and carry */
+#define LMS_OP_HOST 4  /* the rest of the processing time (launches, syncs, result copies) */
+#define LMS_N_OPS 5
+
+/* The model's eight input features of operator `op` of a micro-batch:
+ * log2(1+rows)/32, log2(1+carried state groups)/32, log2(key cardinality)/32,
+ * filter selectivity, log2(panes per window)/12, queries/8,
+ * log2(1 + event-time span in panes)/16, op/4. */
+void lms_cost_features(double rows, double carried_groups, double key_card, double selectivity,
+                       double panes_per_window, double n_queries, double span_panes, int32_t op,
+                       float *out8);
+
+/* Alg. 1 predictor backed by the network, with the paper's analytic estimate
+ * (Eq. 5: bytes / AvgThPut of Eq. 3 over the batches it observed) as fallback
+ * and judge.  A candidate batch has rows = bytes / bytes_per_event, an
+ * event-time span of n_datasets * poll_ms, and the carried groups the serving
+ * backend's stream holds now; the network's prediction is the sum over the
+ * five operators of exp(output) us.  After each batch (lms_learned_observe, a
+ * lms_batch_observer) both predictions of that batch are compared with its
+ * measured time (moving average of |ln(predicted / measured)|); predict()
+ * answers with Eq. 5 until the network has been fitted and whenever the
+ * network's error is the larger.  Observed batches become training samples
+ * (one per operator, ln of its time in us; "host" = the processing time not
+ * covered by the four device phases) in a ring of the latest 4096 samples;
+ * lms_learned_fit takes Adam steps on them, and with online refitting set,
+ * observe() does so every refit_every batches (its wall time is returned to
+ * the loop as blocking time).  set_backend() starts a serving run: it binds
+ * the backend (whose stream's carried groups the features read, and whose
+ * input mode decides whether the host-to-device copy is one of the operators)
+ * and restarts Eq. 5's history and the judge's errors; the network and its
+ * samples are kept. */
+typedef struct lms_learned lms_learned;
+lms_learned *lms_learned_create(lms_mlp *m, lms_serve_gpu *g, double key_card,
+                                double selectivity, double panes_per_window, double n_queries,
+                                double slide_ms, double poll_ms, double bytes_per_event);
+void lms_learned_destroy(lms_learned *l);
+void lms_learned_set_backend(lms_learned *l, lms_serve_gpu *g);
+void lms_learned_set_online(lms_learned *l, int32_t refit_every, int32_t refit_steps, float lr);
+int32_t lms_learned_samples(const lms_learned *l);
+lms_status lms_learned_fit(lms_learned *l, int32_t steps, float lr, float *loss);
+double lms_learned_observe(void *learned, const lms_serve_batch *rec);
+double lms_learned_predict(void *learned, double batch_bytes, int32_t n_datasets);
+/* Judge's moving errors and how often each estimate answered. */
+void lms_learned_stats(const lms_learned *l, double *err_net, double *err_eq5, int64_t *uses_net,
+                       int64_t *uses_eq5);
 
 /* Largest n_rows lms_aggregate_batch_static accepts. */
 #define LMS_STATIC_MAX_ROWS 131072

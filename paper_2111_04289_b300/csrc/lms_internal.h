@@ -181,10 +181,11 @@ struct GenChunk {
   long long n_total, j_begin, first_event;
   long long offset;  // index of the chunk's first event in the batch
 };
-cudaError_t launch_gen_serving(const GenChunk* chunks, int n_chunks, long long n,
-                               unsigned long long seed, const double* cdf, unsigned n_keys,
-                               long long* ts, unsigned* key, float* value, int sms,
-                               cudaStream_t st);
+cudaError_t launch_gen_pool(unsigned long long seed, const double* cdf, unsigned n_keys,
+                            long long pool, long long n, unsigned* key, float* value, int sms,
+                            cudaStream_t st);
+cudaError_t launch_gen_ts(const GenChunk* chunks, int n_chunks, long long n, long long* ts,
+                          int sms, cudaStream_t st);
 
 // Fills filter_lo / filter_hi / filter_exact from filter_f.
 void set_float_filter(QueryDev* d);

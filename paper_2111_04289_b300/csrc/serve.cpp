@@ -80,7 +80,8 @@ double kth(const std::vector<Seg>& segs, int64_t k) {
 
 extern "C" lms_status lms_serve_run(const lms_serve_config* cfg, const int64_t* tick_counts,
                                     int64_t n_ticks, const lms_serve_backend* be,
-                                    lms_proc_predictor pred, void* pred_ctx, lms_serve_result* out,
+                                    lms_proc_predictor pred, void* pred_ctx,
+                                    lms_batch_observer observe, lms_serve_result* out,
                                     lms_serve_batch* log, size_t log_cap, size_t* n_log) {
   if (!cfg || !be || !be->process || !out || n_ticks < 0 || (n_ticks > 0 && !tick_counts))
     return LMS_EINVAL;
@@ -112,7 +113,7 @@ extern "C" lms_status lms_serve_run(const lms_serve_config* cfg, const int64_t* 
   double now = 0.0, next_fire = cfg->trigger_ms;
   std::vector<Seg> segs;
   int64_t processed = 0, batches = 0, over = 0, max_backlog = 0;
-  double busy = 0.0, end = 0.0;
+  double busy = 0.0, end = 0.0, decide_total = 0.0, observe_total = 0.0;
   // p_hi <= bound  <=>  at most offered - ceil(qhi * offered) events exceed it
   const int64_t k_hi_total = offered > 0 ? (int64_t)std::ceil(qhi * (double)offered) : 0;
   const int64_t allowed_over = offered - k_hi_total;
@@ -189,6 +190,7 @@ extern "C" lms_status lms_serve_run(const lms_serve_config* cfg, const int64_t* 
     }
     double decide_ms =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - d0).count();
+    decide_total += decide_ms;
     if (cfg->add_decide_time) now += decide_ms;
     if (take == 0) {
       double nxt = tick < n_ticks ? (double)(tick + 1) * poll : now + poll;
@@ -255,6 +257,11 @@ extern "C" lms_status lms_serve_run(const lms_serve_config* cfg, const int64_t* 
     ++batches;
     if (log && nl < log_cap) log[nl] = rec;
     ++nl;
+    if (observe) {
+      const double ob = observe(pred_ctx, &rec);
+      observe_total += ob;
+      if (cfg->add_decide_time && ob > 0) now += ob;
+    }
     if (cfg->stop_when_missed && over > allowed_over) {
       completed = false;
       break;
@@ -273,6 +280,8 @@ extern "C" lms_status lms_serve_run(const lms_serve_config* cfg, const int64_t* 
   r.end_ms = end;
   r.busy_ms = busy;
   r.max_backlog_events = max_backlog;
+  r.decide_ms = decide_total;
+  r.observe_ms = observe_total;
   if (processed > 0) {
     r.p50_ms = kth(segs, (int64_t)std::ceil(0.5 * (double)processed));
     r.p_hi_ms = kth(segs, std::max<int64_t>(1, (int64_t)std::ceil(qhi * (double)processed)));

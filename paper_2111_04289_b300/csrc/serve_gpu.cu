@@ -1,11 +1,15 @@
 // The engine as the serving loop's backend.
 //
-// Each admitted micro-batch is made by the synthetic load generator (a kernel
-// that writes the batch's columns straight into pinned host memory, outside
-// the measured time), then processed the way a serving client would: one
-// push_microbatch from those host buffers (the host-to-device copy is inside
-// the measured time) followed by poll_results of every emitted row into a
-// pinned host buffer.  The processing time is the wall time of push + polls.
+// Each admitted micro-batch is cut from the synthetic load: the key and value
+// columns are a slice of a pool drawn once at creation (consecutive events
+// take consecutive pool entries), and a kernel writes the batch's ts column
+// for the ticks the loop admitted — all outside the measured time.  In host
+// mode the columns live in pinned host memory and the batch is processed as a
+// serving client would: one push_microbatch from those host buffers (the
+// host-to-device copy is inside the measured time) followed by poll_results of
+// every emitted row into pinned host memory.  In device mode the columns are
+// already in HBM (push reads them in place) and the rows are still polled to
+// the host.  The processing time is the wall time of push + polls.
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -16,22 +20,26 @@
 
 using namespace lms;
 
+namespace {
+constexpr long long kPool = 1ll << 26;  // distinct events of the load before it repeats
+}
+
 struct lms_serve_gpu {
   lms_stream* s = nullptr;
   int nq = 0;
   int dev = 0;
   int sms = 148;
+  bool device_input = false;
   cudaStream_t gen_st = nullptr;
   unsigned long long seed = 0;
   unsigned n_keys = 0;
   double* d_cdf = nullptr;
   long long max_rows = 0;
-  long long* h_ts = nullptr;  // pinned, mapped
-  unsigned* h_key = nullptr;
-  float* h_val = nullptr;
-  long long* m_ts = nullptr;  // their device-side addresses
-  unsigned* m_key = nullptr;
-  float* m_val = nullptr;
+  // columns: ts [max_rows]; key / value pool [kPool + max_rows]
+  long long* ts = nullptr;
+  unsigned* key = nullptr;
+  float* val = nullptr;
+  long long* m_ts = nullptr;  // device-side address of ts (mapped, in host mode)
   GenChunk* h_chunks = nullptr;  // pinned staging of the chunk table
   GenChunk* d_chunks = nullptr;
   int chunk_cap = 0;
@@ -44,6 +52,12 @@ struct lms_serve_gpu {
 
 namespace {
 
+void free_col(lms_serve_gpu* g, void* p) {
+  if (!p) return;
+  if (g->device_input) cudaFree(p);
+  else cudaFreeHost(p);
+}
+
 void destroy(lms_serve_gpu* g) {
   if (!g) return;
   if (g->s) stream_close(g->s);
@@ -51,17 +65,17 @@ void destroy(lms_serve_gpu* g) {
   if (g->gen_st) cudaStreamDestroy(g->gen_st);
   cudaFree(g->d_cdf);
   cudaFree(g->d_chunks);
-  cudaFreeHost(g->h_ts);
-  cudaFreeHost(g->h_key);
-  cudaFreeHost(g->h_val);
+  free_col(g, g->ts);
+  free_col(g, g->key);
+  free_col(g, g->val);
   cudaFreeHost(g->h_chunks);
   cudaFreeHost(g->h_rows);
   delete g;
 }
 
-// Writes the batch made of chunks[0 .. n_chunks) into the pinned columns.
+// Writes the batch's ts column; returns the pool offset of its first event.
 lms_status make_batch(lms_serve_gpu* g, const lms_serve_chunk* chunks, int32_t n_chunks,
-                      int64_t n_events) {
+                      int64_t n_events, long long* pool_off) {
   if (n_events > g->max_rows || n_chunks <= 0) return LMS_EINVAL;
   if (cudaSetDevice(g->dev) != cudaSuccess) return LMS_ECUDA;
   if (n_chunks > g->chunk_cap) {
@@ -79,14 +93,17 @@ lms_status make_batch(lms_serve_gpu* g, const lms_serve_chunk* chunks, int32_t n
   long long off = 0;
   for (int i = 0; i < n_chunks; ++i) {
     const lms_serve_chunk& c = chunks[i];
+    // the batch's events must be consecutive in the stream
+    if (i > 0 && c.first_event + c.j_begin != chunks[i - 1].first_event + chunks[i - 1].j_end)
+      return LMS_EINVAL;
     g->h_chunks[i] = {c.t0_ms, c.width_ms, c.n_total, c.j_begin, c.first_event, off};
     off += c.j_end - c.j_begin;
   }
   if (off != n_events) return LMS_EINVAL;
+  *pool_off = (chunks[0].first_event + chunks[0].j_begin) % kPool;
   if (cudaMemcpyAsync(g->d_chunks, g->h_chunks, sizeof(GenChunk) * n_chunks,
                       cudaMemcpyHostToDevice, g->gen_st) != cudaSuccess ||
-      launch_gen_serving(g->d_chunks, n_chunks, n_events, g->seed, g->d_cdf, g->n_keys, g->m_ts,
-                         g->m_key, g->m_val, g->sms, g->gen_st) != cudaSuccess ||
+      launch_gen_ts(g->d_chunks, n_chunks, n_events, g->m_ts, g->sms, g->gen_st) != cudaSuccess ||
       cudaStreamSynchronize(g->gen_st) != cudaSuccess)
     return LMS_ECUDA;
   return LMS_OK;
@@ -95,18 +112,19 @@ lms_status make_batch(lms_serve_gpu* g, const lms_serve_chunk* chunks, int32_t n
 double process(void* ctx, const lms_serve_chunk* chunks, int32_t n_chunks, int64_t n_events,
                lms_serve_batch* rec) {
   lms_serve_gpu* g = static_cast<lms_serve_gpu*>(ctx);
+  long long off = 0;
   // make the batch (not measured)
-  if (make_batch(g, chunks, n_chunks, n_events) != LMS_OK) return -1.0;
+  if (make_batch(g, chunks, n_chunks, n_events, &off) != LMS_OK) return -1.0;
   lms_stats before{}, after{};
   lms_stream_stats(g->s, &before);
-  // process it as a client would: push from host memory, poll every row back
+  // process it as a client would: push, then poll every row to the host
   const auto t0 = std::chrono::steady_clock::now();
   lms_batch b{};
   b.n_rows = n_events;
-  b.ts = reinterpret_cast<const int64_t*>(g->h_ts);
-  b.key = g->h_key;
-  b.value = g->h_val;
-  b.memory = LMS_MEM_HOST;
+  b.ts = reinterpret_cast<const int64_t*>(g->ts);
+  b.key = g->key + off;
+  b.value = g->val + off;
+  b.memory = g->device_input ? LMS_MEM_DEVICE : LMS_MEM_HOST;
   if (push_microbatch(g->s, &b) != LMS_OK) return -1.0;
   unsigned long long rows = 0;
   for (int q = 0; q < g->nq; ++q) {
@@ -135,9 +153,14 @@ double process(void* ctx, const lms_serve_chunk* chunks, int32_t n_chunks, int64
 int64_t admissible(void* ctx) {
   lms_serve_gpu* g = static_cast<lms_serve_gpu*>(ctx);
   int64_t n = -1;
-  if (lms_stream_admissible_rows(g->s, 1, &n) != LMS_OK) return 0;
+  if (lms_stream_admissible_rows(g->s, g->device_input ? 0 : 1, &n) != LMS_OK) return 0;
   if (n < 0 || n > g->max_rows) n = g->max_rows;
   return n;
+}
+
+cudaError_t alloc_col(lms_serve_gpu* g, void** p, size_t bytes) {
+  if (g->device_input) return cudaMalloc(p, bytes);
+  return cudaHostAlloc(p, bytes, cudaHostAllocMapped);
 }
 
 }  // namespace
@@ -146,10 +169,9 @@ extern "C" {
 
 lms_status lms_serve_gpu_create(const lms_stream_config* cfg, const lms_query_spec* qs,
                                 int32_t nq, uint64_t seed, uint32_t n_keys, double zipf_s,
-                                int64_t max_batch_rows, int32_t keep_rows,
-                                lms_serve_gpu** out) {
+                                int64_t max_batch_rows, int32_t flags, lms_serve_gpu** out) {
   if (!cfg || !qs || nq < 1 || !out || n_keys < 1 || !(zipf_s > 0) || max_batch_rows < 1 ||
-      cfg->value_type != LMS_VALUE_FLOAT32 || cfg->has_type)
+      max_batch_rows > kPool || cfg->value_type != LMS_VALUE_FLOAT32 || cfg->has_type)
     return LMS_EINVAL;
   lms_serve_gpu* g = new lms_serve_gpu();
   g->dev = cfg->device;
@@ -157,7 +179,8 @@ lms_status lms_serve_gpu_create(const lms_stream_config* cfg, const lms_query_sp
   g->n_keys = n_keys;
   g->max_rows = max_batch_rows;
   g->nq = nq;
-  g->keep_rows = keep_rows != 0;
+  g->keep_rows = (flags & LMS_SERVE_KEEP_ROWS) != 0;
+  g->device_input = (flags & LMS_SERVE_DEVICE_INPUT) != 0;
   g->kept.resize(nq);
   lms_status r = stream_open(cfg, &g->s);
   if (r != LMS_OK) {
@@ -184,22 +207,36 @@ lms_status lms_serve_gpu_create(const lms_stream_config* cfg, const lms_query_sp
   for (uint32_t i = 0; i < n_keys; ++i) cdf[i] /= acc;
   cdf[n_keys - 1] = 1.0;
   g->rows_cap = 1u << 22;
-  const size_t n = (size_t)max_batch_rows;
+  const size_t n = (size_t)max_batch_rows, np = (size_t)(kPool + max_batch_rows);
   if (cudaStreamCreateWithFlags(&g->gen_st, cudaStreamNonBlocking) != cudaSuccess ||
       cudaMalloc(&g->d_cdf, sizeof(double) * n_keys) != cudaSuccess ||
       cudaMemcpy(g->d_cdf, cdf.data(), sizeof(double) * n_keys, cudaMemcpyHostToDevice) !=
           cudaSuccess ||
-      cudaHostAlloc(&g->h_ts, 8 * n, cudaHostAllocMapped) != cudaSuccess ||
-      cudaHostAlloc(&g->h_key, 4 * n, cudaHostAllocMapped) != cudaSuccess ||
-      cudaHostAlloc(&g->h_val, 4 * n, cudaHostAllocMapped) != cudaSuccess ||
+      alloc_col(g, (void**)&g->ts, 8 * n) != cudaSuccess ||
+      alloc_col(g, (void**)&g->key, 4 * np) != cudaSuccess ||
+      alloc_col(g, (void**)&g->val, 4 * np) != cudaSuccess ||
       cudaHostAlloc(&g->h_rows, sizeof(lms_result_row) * g->rows_cap, cudaHostAllocDefault) !=
-          cudaSuccess ||
-      cudaHostGetDevicePointer((void**)&g->m_ts, g->h_ts, 0) != cudaSuccess ||
-      cudaHostGetDevicePointer((void**)&g->m_key, g->h_key, 0) != cudaSuccess ||
-      cudaHostGetDevicePointer((void**)&g->m_val, g->h_val, 0) != cudaSuccess) {
+          cudaSuccess) {
     cudaGetLastError();
     destroy(g);
     return LMS_ENOMEM;
+  }
+  unsigned* m_key = g->key;
+  float* m_val = g->val;
+  g->m_ts = g->ts;
+  if (!g->device_input &&
+      (cudaHostGetDevicePointer((void**)&g->m_ts, g->ts, 0) != cudaSuccess ||
+       cudaHostGetDevicePointer((void**)&m_key, g->key, 0) != cudaSuccess ||
+       cudaHostGetDevicePointer((void**)&m_val, g->val, 0) != cudaSuccess)) {
+    cudaGetLastError();
+    destroy(g);
+    return LMS_ECUDA;
+  }
+  if (launch_gen_pool(seed, g->d_cdf, n_keys, kPool, (long long)np, m_key, m_val, g->sms,
+                      g->gen_st) != cudaSuccess ||
+      cudaStreamSynchronize(g->gen_st) != cudaSuccess) {
+    destroy(g);
+    return LMS_ECUDA;
   }
   // Warm-up outside any measurement: a throwaway stream with the same queries
   // runs a small batch (loads every kernel), then the serving stream's
@@ -216,22 +253,23 @@ lms_status lms_serve_gpu_create(const lms_stream_config* cfg, const lms_query_sp
     }
     const int64_t wn = max_batch_rows < 65536 ? max_batch_rows : 65536;
     lms_serve_chunk c{0.0, 10.0, wn, 0, wn, 0};
-    if (wr == LMS_OK) wr = make_batch(g, &c, 1, wn);
+    long long off = 0;
+    if (wr == LMS_OK) wr = make_batch(g, &c, 1, wn, &off);
     for (int rep = 0; wr == LMS_OK && rep < 2; ++rep) {
       lms_batch b{};
       b.n_rows = wn;
-      b.ts = reinterpret_cast<const int64_t*>(g->h_ts);
-      b.key = g->h_key;
-      b.value = g->h_val;
-      b.memory = LMS_MEM_HOST;
+      b.ts = reinterpret_cast<const int64_t*>(g->ts);
+      b.key = g->key;
+      b.value = g->val;
+      b.memory = g->device_input ? LMS_MEM_DEVICE : LMS_MEM_HOST;
       b.flags = rep == 1 ? LMS_BATCH_EOS : 0u;
       wr = push_microbatch(w, &b);
     }
     if (w) stream_close(w);
     int64_t adm = -1;
-    if (wr == LMS_OK) wr = lms_stream_admissible_rows(g->s, 1, &adm);
+    if (wr == LMS_OK) wr = lms_stream_admissible_rows(g->s, g->device_input ? 0 : 1, &adm);
     const int64_t res = (adm < 0 || adm > max_batch_rows) ? max_batch_rows : adm;
-    if (wr == LMS_OK) wr = lms_stream_reserve(g->s, res, 1);
+    if (wr == LMS_OK) wr = lms_stream_reserve(g->s, res, g->device_input ? 0 : 1);
     if (wr != LMS_OK) {
       destroy(g);
       return wr;
@@ -251,16 +289,23 @@ lms_status lms_serve_gpu_backend(lms_serve_gpu* g, lms_serve_backend* out) {
 
 lms_stream* lms_serve_gpu_stream(lms_serve_gpu* g) { return g ? g->s : nullptr; }
 
+int32_t lms_serve_gpu_device_input(const lms_serve_gpu* g) {
+  return (g && g->device_input) ? 1 : 0;
+}
+
 lms_status lms_serve_gpu_generate(lms_serve_gpu* g, const lms_serve_chunk* chunks,
                                   int32_t n_chunks, int64_t n_events, int64_t* ts,
                                   uint32_t* key, float* value) {
   if (!g || !chunks || n_events < 0 || (n_events > 0 && (!ts || !key || !value)))
     return LMS_EINVAL;
-  const lms_status r = make_batch(g, chunks, n_chunks, n_events);
+  long long off = 0;
+  const lms_status r = make_batch(g, chunks, n_chunks, n_events, &off);
   if (r != LMS_OK) return r;
-  std::memcpy(ts, g->h_ts, 8 * (size_t)n_events);
-  std::memcpy(key, g->h_key, 4 * (size_t)n_events);
-  std::memcpy(value, g->h_val, 4 * (size_t)n_events);
+  const cudaMemcpyKind k = g->device_input ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+  if (cudaMemcpy(ts, g->ts, 8 * (size_t)n_events, k) != cudaSuccess ||
+      cudaMemcpy(key, g->key + off, 4 * (size_t)n_events, k) != cudaSuccess ||
+      cudaMemcpy(value, g->val + off, 4 * (size_t)n_events, k) != cudaSuccess)
+    return LMS_ECUDA;
   return LMS_OK;
 }
 

@@ -83,7 +83,13 @@ EXPORTED_SYMBOLS = ("stream_open", "query_register", "push_microbatch", "poll_re
                     "lms_regressor_fit", "lms_admission_truncate", "lms_serve_run",
                     "lms_stream_admissible_rows", "lms_serve_gpu_create", "lms_serve_gpu_backend",
                     "lms_serve_gpu_stream", "lms_serve_gpu_generate", "lms_serve_gpu_kept_rows",
-                    "lms_serve_gpu_destroy", "lms_stream_reserve")
+                    "lms_serve_gpu_destroy", "lms_stream_reserve", "lms_mlp_create",
+                    "lms_mlp_destroy", "lms_mlp_set_params", "lms_mlp_get_params",
+                    "lms_mlp_forward", "lms_mlp_train", "lms_cost_features",
+                    "lms_learned_create", "lms_learned_destroy", "lms_learned_set_backend",
+                    "lms_learned_set_online", "lms_learned_samples", "lms_learned_fit",
+                    "lms_learned_observe", "lms_learned_predict", "lms_learned_stats",
+                    "lms_serve_gpu_device_input")
 ADMIT_PAPER, ADMIT_GUARDED = 0, 1
 QOPS = {"aggregation": 0, "filter": 1, "shuffle": 2, "project": 3, "join": 4, "expand": 5,
         "scan": 6, "sort": 7}
@@ -133,7 +139,8 @@ class ServeResult(ctypes.Structure):
                 ("end_ms", ctypes.c_double), ("busy_ms", ctypes.c_double),
                 ("p50_ms", ctypes.c_double), ("p_hi_ms", ctypes.c_double),
                 ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
-                ("events_per_s", ctypes.c_double), ("max_backlog_events", ctypes.c_int64)]
+                ("events_per_s", ctypes.c_double), ("max_backlog_events", ctypes.c_int64),
+                ("decide_ms", ctypes.c_double), ("observe_ms", ctypes.c_double)]
 STATIC_MAX_ROWS = 131072
 
 _lib = None
@@ -207,8 +214,40 @@ def load(build_if_missing: bool = True):
     lib.lms_admission_truncate.argtypes = [P, I, D]
     lib.lms_serve_run.restype = I
     lib.lms_serve_run.argtypes = [ctypes.POINTER(ServeConfig), P, ctypes.c_int64,
-                                  ctypes.POINTER(ServeBackend), P, P, ctypes.POINTER(ServeResult),
-                                  P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
+                                  ctypes.POINTER(ServeBackend), P, P, P,
+                                  ctypes.POINTER(ServeResult), P, ctypes.c_size_t,
+                                  ctypes.POINTER(ctypes.c_size_t)]
+    F = ctypes.c_float
+    lib.lms_mlp_create.restype = P
+    lib.lms_mlp_create.argtypes = [I, P]
+    lib.lms_mlp_destroy.argtypes = [P]
+    lib.lms_mlp_set_params.restype = I
+    lib.lms_mlp_set_params.argtypes = [P, P]
+    lib.lms_mlp_get_params.restype = I
+    lib.lms_mlp_get_params.argtypes = [P, P]
+    lib.lms_mlp_forward.restype = I
+    lib.lms_mlp_forward.argtypes = [P, P, I, P]
+    lib.lms_mlp_train.restype = I
+    lib.lms_mlp_train.argtypes = [P, P, P, I, I, F, P, ctypes.POINTER(F)]
+    lib.lms_cost_features.restype = None
+    lib.lms_cost_features.argtypes = [D, D, D, D, D, D, D, I, P]
+    lib.lms_learned_create.restype = P
+    lib.lms_learned_create.argtypes = [P, P, D, D, D, D, D, D, D]
+    lib.lms_learned_destroy.argtypes = [P]
+    lib.lms_learned_set_backend.argtypes = [P, P]
+    lib.lms_learned_set_online.argtypes = [P, I, I, F]
+    lib.lms_learned_samples.restype = I
+    lib.lms_learned_samples.argtypes = [P]
+    lib.lms_learned_fit.restype = I
+    lib.lms_learned_fit.argtypes = [P, I, F, ctypes.POINTER(F)]
+    lib.lms_learned_observe.restype = D
+    lib.lms_learned_observe.argtypes = [P, P]
+    lib.lms_learned_predict.restype = D
+    lib.lms_learned_predict.argtypes = [P, D, I]
+    lib.lms_learned_stats.restype = None
+    lib.lms_learned_stats.argtypes = [P, ctypes.POINTER(D), ctypes.POINTER(D),
+                                      ctypes.POINTER(ctypes.c_int64),
+                                      ctypes.POINTER(ctypes.c_int64)]
     lib.lms_stream_reserve.restype = I
     lib.lms_stream_reserve.argtypes = [P, ctypes.c_int64, I]
     lib.lms_stream_admissible_rows.restype = I
@@ -218,6 +257,8 @@ def load(build_if_missing: bool = True):
                                          ctypes.c_uint32, D, ctypes.c_int64, I, ctypes.POINTER(P)]
     lib.lms_serve_gpu_backend.restype = I
     lib.lms_serve_gpu_backend.argtypes = [P, ctypes.POINTER(ServeBackend)]
+    lib.lms_serve_gpu_device_input.restype = I
+    lib.lms_serve_gpu_device_input.argtypes = [P]
     lib.lms_serve_gpu_stream.restype = P
     lib.lms_serve_gpu_stream.argtypes = [P]
     lib.lms_serve_gpu_generate.restype = I
@@ -503,14 +544,15 @@ def _struct_dict(x) -> dict:
 
 
 def serve_run(tick_counts, *, poll_ms: float, policy: int, bound_ms: float, backend=None,
-              process=None, admissible=None, predictor=None, fixed_rows: int = 0,
+              process=None, admissible=None, predictor=None, observer=None, fixed_rows: int = 0,
               trigger_ms: float = 0.0, bytes_per_event: float = 16.0,
               admit_rule: int = ADMIT_GUARDED, add_decide_time: bool = False,
               stop_when_missed: bool = False, quantile_hi: float = 0.99, log_cap: int = 1 << 16):
     """Runs the serving loop (lms_serve_run).  Either `backend` (a ServeBackend
     from a native backend) or Python callables `process(chunks, n_events, rec)`
     -> ms and optional `admissible()` -> rows.  `predictor` is a Python callable
-    (bytes, n_datasets) -> ms or a (PROC_PREDICTOR-compatible address, ctx) pair.
+    (bytes, n_datasets) -> ms or a (PROC_PREDICTOR-compatible address, ctx) pair;
+    `observer` an lms_batch_observer address called with that ctx (Learned.hooks()).
     Returns (result dict, per-batch records as a list of dicts)."""
     lib = load()
     counts = np.ascontiguousarray(tick_counts, dtype=np.int64)
@@ -543,7 +585,7 @@ def serve_run(tick_counts, *, poll_ms: float, policy: int, bound_ms: float, back
     n_log = ctypes.c_size_t()
     res = ServeResult()
     st = lib.lms_serve_run(ctypes.byref(cfg), counts.ctypes.data, int(counts.shape[0]),
-                           ctypes.byref(backend), pred_fn, pred_ctx, ctypes.byref(res),
+                           ctypes.byref(backend), pred_fn, pred_ctx, observer, ctypes.byref(res),
                            ctypes.cast(log, ctypes.c_void_p), int(log_cap), ctypes.byref(n_log))
     if st != LMS_OK:
         raise LmsError(st, "lms_serve_run")
@@ -566,7 +608,8 @@ class ServeGpu:
 
     def __init__(self, queries, *, seed: int, n_keys: int = 1_000_000, zipf_s: float = 1.1,
                  max_batch_rows: int = 1 << 24, state_cap_bytes: int = 0,
-                 enable_timing: bool = True, keep_rows: bool = False, device: int = 0):
+                 enable_timing: bool = True, keep_rows: bool = False, device_input: bool = False,
+                 device: int = 0):
         self._lib = load()
         cfg = StreamConfig(device=device, value_type=VALUE_FLOAT32, has_type=0,
                            enable_timing=int(enable_timing), allowed_lateness_ms=0,
@@ -577,7 +620,8 @@ class ServeGpu:
         h = ctypes.c_void_p()
         st = self._lib.lms_serve_gpu_create(ctypes.byref(cfg), specs, len(queries), int(seed),
                                             int(n_keys), float(zipf_s), int(max_batch_rows),
-                                            int(keep_rows), ctypes.byref(h))
+                                            (1 if keep_rows else 0) | (2 if device_input else 0),
+                                            ctypes.byref(h))
         if st != LMS_OK:
             raise LmsError(st, "lms_serve_gpu_create")
         self._h = h.value
@@ -629,6 +673,157 @@ class ServeGpu:
     def close(self):
         if getattr(self, "_h", None):
             self._lib.lms_serve_gpu_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+MLP_INPUTS, MLP_PARAMS, MLP_MAX_BATCH = 8, 8961, 4096
+_MLP_SHAPES = [(64, 8), (64,), (64, 64), (64,), (64, 64), (64,), (64,), (1,)]
+
+
+def mlp_init_params(seed: int) -> np.ndarray:
+    """Initial network weights: He-uniform (limit sqrt(6 / fan_in)), zero biases."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for i, shp in enumerate(_MLP_SHAPES):
+        if i % 2 == 0:
+            fan_in = shp[-1] if len(shp) == 2 else 64
+            lim = np.sqrt(6.0 / fan_in)
+            parts.append(rng.uniform(-lim, lim, shp).ravel())
+        else:
+            parts.append(np.zeros(int(np.prod(shp))))
+    return np.concatenate(parts).astype(np.float32)
+OP_H2D, OP_K1, OP_SORT, OP_EMIT, OP_HOST, N_OPS = 0, 1, 2, 3, 4, 5
+
+
+class Mlp:
+    """The learned cost model's network on the GPU (lms_mlp_*)."""
+
+    def __init__(self, params, device: int = 0):
+        self._lib = load()
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.shape == (MLP_PARAMS,)
+        self._h = self._lib.lms_mlp_create(int(device), p.ctypes.data)
+        if not self._h:
+            raise LmsError(LMS_ECUDA, "lms_mlp_create")
+
+    @property
+    def handle(self):
+        return self._h
+
+    def params(self) -> np.ndarray:
+        out = np.empty(MLP_PARAMS, np.float32)
+        st = self._lib.lms_mlp_get_params(self._h, out.ctypes.data)
+        if st != LMS_OK:
+            raise LmsError(st, "lms_mlp_get_params")
+        return out
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        st = self._lib.lms_mlp_set_params(self._h, p.ctypes.data)
+        if st != LMS_OK:
+            raise LmsError(st, "lms_mlp_set_params")
+
+    def forward(self, x) -> np.ndarray:
+        x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, MLP_INPUTS)
+        y = np.empty(x.shape[0], np.float32)
+        st = self._lib.lms_mlp_forward(self._h, x.ctypes.data, x.shape[0], y.ctypes.data)
+        if st != LMS_OK:
+            raise LmsError(st, "lms_mlp_forward")
+        return y
+
+    def train(self, x, t, steps: int, lr: float = 1e-3, want_grad: bool = False):
+        x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, MLP_INPUTS)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        g = np.empty(MLP_PARAMS, np.float32) if want_grad else None
+        loss = ctypes.c_float()
+        st = self._lib.lms_mlp_train(self._h, x.ctypes.data, t.ctypes.data, x.shape[0],
+                                     int(steps), float(lr), None if g is None else g.ctypes.data,
+                                     ctypes.byref(loss))
+        if st != LMS_OK:
+            raise LmsError(st, "lms_mlp_train")
+        return (loss.value, g) if want_grad else loss.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lms_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cost_features(rows, carried, key_card, selectivity, panes, n_queries, span_panes, op):
+    out = np.empty(MLP_INPUTS, np.float32)
+    load().lms_cost_features(float(rows), float(carried), float(key_card), float(selectivity),
+                             float(panes), float(n_queries), float(span_panes), int(op),
+                             out.ctypes.data)
+    return out
+
+
+class Learned:
+    """Alg. 1 predictor backed by an Mlp, with Eq. 5 as fallback and judge
+    (lms_learned_*)."""
+
+    def __init__(self, mlp: Mlp, serve_gpu=None, *, key_card, selectivity, panes, n_queries,
+                 slide_ms, poll_ms, bytes_per_event=16.0):
+        self._lib = load()
+        self.mlp = mlp
+        self._h = self._lib.lms_learned_create(
+            mlp.handle, None if serve_gpu is None else serve_gpu._h, float(key_card),
+            float(selectivity), float(panes), float(n_queries), float(slide_ms), float(poll_ms),
+            float(bytes_per_event))
+        if not self._h:
+            raise LmsError(LMS_EINVAL, "lms_learned_create")
+
+    def set_backend(self, serve_gpu):
+        self._lib.lms_learned_set_backend(self._h, None if serve_gpu is None else serve_gpu._h)
+
+    def set_online(self, refit_every: int, refit_steps: int, lr: float = 1e-3):
+        self._lib.lms_learned_set_online(self._h, int(refit_every), int(refit_steps), float(lr))
+
+    def observe(self, rec: dict) -> float:
+        b = ServeBatch(**{k: rec[k] for k, _ in ServeBatch._fields_})
+        return float(self._lib.lms_learned_observe(self._h, ctypes.byref(b)))
+
+    def samples(self) -> int:
+        return int(self._lib.lms_learned_samples(self._h))
+
+    def fit(self, steps: int, lr: float = 1e-3) -> float:
+        loss = ctypes.c_float()
+        st = self._lib.lms_learned_fit(self._h, int(steps), float(lr), ctypes.byref(loss))
+        if st != LMS_OK:
+            raise LmsError(st, "lms_learned_fit")
+        return loss.value
+
+    def predict(self, batch_bytes: float, n_datasets: int) -> float:
+        return float(self._lib.lms_learned_predict(self._h, float(batch_bytes), int(n_datasets)))
+
+    def stats(self) -> dict:
+        en, ee = ctypes.c_double(), ctypes.c_double()
+        un, ue = ctypes.c_int64(), ctypes.c_int64()
+        self._lib.lms_learned_stats(self._h, ctypes.byref(en), ctypes.byref(ee), ctypes.byref(un),
+                                    ctypes.byref(ue))
+        return {"err_net": en.value, "err_eq5": ee.value, "uses_net": un.value,
+                "uses_eq5": ue.value}
+
+    def hooks(self):
+        """(predictor, observer) arguments for serve_run."""
+        pred = ctypes.cast(self._lib.lms_learned_predict, ctypes.c_void_p).value
+        obs = ctypes.cast(self._lib.lms_learned_observe, ctypes.c_void_p).value
+        return (pred, self._h), obs
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lms_learned_destroy(self._h)
             self._h = None
 
     def __del__(self):

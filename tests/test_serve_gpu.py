@@ -76,15 +76,19 @@ def test_generator_definition_and_split_invariance():
     g.close()
 
 
-@pytest.mark.parametrize("policy", [lm.POLICY_ANALYTIC, lm.POLICY_FIXED_SIZE])
-def test_serving_rows_match_oracle(policy):
+@pytest.mark.parametrize("policy,device_input", [(lm.POLICY_ANALYTIC, False),
+                                                 (lm.POLICY_FIXED_SIZE, False),
+                                                 (lm.POLICY_ANALYTIC, True)])
+def test_serving_rows_match_oracle(policy, device_input):
     ticks = np.random.default_rng(3).poisson(np.linspace(500, 6000, 260)).astype(np.int64)
-    g = lm.ServeGpu(QUERIES, seed=11, n_keys=20_000, max_batch_rows=1 << 18, keep_rows=True)
+    g = lm.ServeGpu(QUERIES, seed=11, n_keys=20_000, max_batch_rows=1 << 18, keep_rows=True,
+                    device_input=device_input)
     res, log = lm.serve_run(ticks, poll_ms=10.0, policy=policy, bound_ms=60.0,
                             backend=g.backend(), fixed_rows=17_000)
     assert res["processed_events"] == ticks.sum() and res["completed"] == 1
     sizes = [r["n_events"] for r in log]
-    assert len(set(sizes)) > 3  # uneven batches
+    if policy == lm.POLICY_ANALYTIC:
+        assert len(set(sizes)) > 3  # Alg. 1 picks uneven batch sizes
     ts, key, val = _generate_all(g, _chunks_for(ticks, 10.0), 1 << 18)
     bounds = np.concatenate([[0], np.cumsum(sizes)])
     batches = [_Events(ts[a:b], key[a:b], val[a:b]) for a, b in zip(bounds[:-1], bounds[1:])]
