@@ -109,12 +109,14 @@ void lms_learned_set_online(lms_learned* l, int32_t refit_every, int32_t refit_s
 
 void lms_learned_set_backend(lms_learned* l, lms_serve_gpu* g) {
   if (!l) return;
-  // a new serving run: Eq. 5's history and the judge's errors start afresh
   l->g = g;
-  if (g) l->host_input = lms_serve_gpu_device_input(g) == 0;
+  if (!g) return;  // unbinding keeps the last run's judge statistics
+  // a new serving run: Eq. 5's history and the judge's errors start afresh
+  l->host_input = lms_serve_gpu_device_input(g) == 0;
   l->sum_bytes = l->sum_proc = 0.0;
   l->err_net = l->err_eq5 = 0.0;
   l->judged = 0;
+  l->uses_net = l->uses_eq5 = 0;
 }
 
 int32_t lms_learned_samples(const lms_learned* l) { return l ? l->count : 0; }
