@@ -224,6 +224,15 @@ lms_status lms_results_device(lms_stream *s, int32_t query_id, const lms_result_
  * LMS_ENOMEM if that exceeds state_cap_bytes or the device. */
 lms_status lms_stream_reserve(lms_stream *s, int64_t n_rows, int32_t host_input);
 
+/* Device bytes a push of n_rows rows (from host memory if host_input is 1)
+ * would newly allocate for its group, sort and input buffers (and the first
+ * push's emission buffers; later growth of the result and window buffers
+ * follows the rows a batch emits and is not included), and the device bytes
+ * the stream holds now. */
+lms_status lms_stream_push_bytes(lms_stream *s, int64_t n_rows, int32_t host_input,
+                                 uint64_t *bytes);
+lms_status lms_stream_device_bytes(lms_stream *s, uint64_t *bytes);
+
 /* Admission by device memory (the serving loop's; the paper has none): the
  * largest n_rows the next push can take without the stream's device memory
  * exceeding cfg.state_cap_bytes, counting the growth of every buffer a push of
@@ -536,6 +545,66 @@ double lms_learned_predict(void *learned, double batch_bytes, int32_t n_datasets
 /* Judge's moving errors and how often each estimate answered. */
 void lms_learned_stats(const lms_learned *l, double *err_net, double *err_eq5, int64_t *uses_net,
                        int64_t *uses_eq5);
+
+/* ---- continuous batching across streams --------------------------------
+ *
+ * A server with `slots` worker threads runs pushes of many streams at once on
+ * one GPU: each worker takes the oldest queued request whose stream is not
+ * already running and whose memory fits, and runs push_microbatch on that
+ * stream's own CUDA stream, so micro-batches of different streams overlap on
+ * the device while each stream's batches run one at a time in submission
+ * order.  Admission by memory: a request starts only if the device bytes held
+ * by every stream the server has seen, plus what the running requests and this
+ * one may allocate (lms_stream_push_bytes), stay within memory_budget_bytes
+ * (0 = no budget); otherwise it waits for a running request to finish, and
+ * fails with LMS_ENOMEM if nothing is running.  Results are polled from each
+ * stream as usual once its ticket has completed.  The paper has no
+ * counterpart: it processes one query's micro-batches one after another.
+ * Streams used with a server must have their own CUDA streams
+ * (cfg.cuda_stream = NULL) and must not be pushed outside the server meanwhile;
+ * the caller keeps every submitted batch's columns valid until its ticket
+ * completes. */
+typedef struct lms_server lms_server;
+typedef struct lms_server_config {
+  int32_t slots;                /* concurrent micro-batches (1..64) */
+  int32_t reserved0;
+  uint64_t memory_budget_bytes; /* device memory all streams may hold together, 0 = none */
+  int32_t reserved[8];
+} lms_server_config;
+typedef struct lms_server_stats {
+  int64_t submitted, completed, queued;
+  int64_t max_concurrent;       /* most requests running at once */
+  int64_t memory_waits;         /* times a worker found only requests that did not fit */
+  uint64_t peak_bytes;          /* largest held + reserved device bytes at a completion */
+  uint64_t held_bytes;          /* device bytes the known streams hold now */
+  double busy_ms;               /* sum of request run times */
+} lms_server_stats;
+lms_status lms_server_create(const lms_server_config *cfg, lms_server **out);
+/* The operations a server applies to streams; lms_server_create uses the
+ * engine's (push_microbatch, lms_stream_push_bytes, lms_stream_device_bytes).
+ * Other implementations serve to test the scheduling on the host. */
+typedef struct lms_server_ops {
+  void *ctx;
+  lms_status (*push)(void *ctx, lms_stream *s, const lms_batch *b);
+  lms_status (*push_bytes)(void *ctx, lms_stream *s, int64_t n_rows, int32_t host_input,
+                           uint64_t *bytes);
+  lms_status (*device_bytes)(void *ctx, lms_stream *s, uint64_t *bytes);
+} lms_server_ops;
+lms_status lms_server_create_ops(const lms_server_config *cfg, const lms_server_ops *ops,
+                                 lms_server **out);
+/* Queues a push of *b on s; *ticket identifies it.  Returns at once. */
+lms_status lms_server_submit(lms_server *sv, lms_stream *s, const lms_batch *b, uint64_t *ticket);
+/* Waits (timeout_ms < 0: without limit) for a ticket: *result = the push's
+ * status; start_ms / end_ms (optional) = when it ran, ms since the server was
+ * created.  LMS_ETIMEDOUT if it is not done in time (it can be waited again). */
+lms_status lms_server_wait(lms_server *sv, uint64_t ticket, int32_t timeout_ms,
+                           lms_status *result, double *start_ms, double *end_ms);
+/* Stops counting a stream's memory (before closing it); LMS_EAGAIN while it
+ * has queued or running requests. */
+lms_status lms_server_forget(lms_server *sv, lms_stream *s);
+lms_status lms_server_get_stats(lms_server *sv, lms_server_stats *out);
+/* Runs every queued request, then stops the workers and frees the server. */
+lms_status lms_server_destroy(lms_server *sv);
 
 /* Largest n_rows lms_aggregate_batch_static accepts. */
 #define LMS_STATIC_MAX_ROWS 131072

@@ -401,7 +401,10 @@ lms_status push_microbatch(lms_stream* s, const lms_batch* b) {
     } else if (n > 0) {
       long long first = 0;
       if (b->memory == LMS_MEM_HOST) first = (long long)b->ts[0];
-      else LMS_CK(cudaMemcpy(&first, b->ts, sizeof(long long), cudaMemcpyDeviceToHost));
+      else {
+        LMS_CK(cudaMemcpyAsync(&first, b->ts, sizeof(long long), cudaMemcpyDeviceToHost, s->st));
+        LMS_CK(cudaStreamSynchronize(s->st));
+      }
       set_origin(s, first);
     } else {
       set_origin(s, 0);
@@ -508,7 +511,8 @@ lms_status push_microbatch(lms_stream* s, const lms_batch* b) {
     }
   }
   SCtl hs{};
-  LMS_CK(cudaMemcpy(&hs, s->sctl, sizeof(hs), cudaMemcpyDeviceToHost));
+  LMS_CK(cudaMemcpyAsync(&hs, s->sctl, sizeof(hs), cudaMemcpyDeviceToHost, s->st));
+  LMS_CK(cudaStreamSynchronize(s->st));
   if (hs.wm_valid) s->wm = hs.wm;
   unsigned long long late = 0, range = 0, rows = 0, groups = 0;
   for (int i = 0; i < nq; ++i) {
@@ -640,6 +644,37 @@ lms_status lms_stream_reserve(lms_stream* s, int64_t n_rows, int32_t host_input)
   if (r == LMS_OK && host_input) r = ensure_input(s, (unsigned long long)n_rows);
   if (r == LMS_OK) LMS_CK(cudaStreamSynchronize(s->st));
   return r;
+}
+
+lms_status lms_stream_push_bytes(lms_stream* s, int64_t n_rows, int32_t host_input,
+                                 uint64_t* bytes) {
+  if (!s || n_rows < 0 || !bytes) return LMS_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  unsigned long long need = 0, total = 0;
+  for (const QueryHost& q : s->qs) need = std::max(need, q.carried + (unsigned long long)n_rows);
+  need += 1;
+  const unsigned long long nc = round_cap(need);
+  for (const QueryHost& q : s->qs)
+    if (q.cap < need) total += nc * (2 * sizeof(Grp) + 8);
+  if (s->scr.cap < need) total += nc * (8 + 8 + 4 + 4) + (nc + 1) * (4 + 8);
+  if (host_input && s->in_cap < (unsigned long long)n_rows) {
+    const unsigned long long ic = round_cap((unsigned long long)n_rows);
+    total += ic * (8 + 4 + 4 + (s->cfg.has_type ? 1 : 0));
+  }
+  // emission buffers a first push allocates (later growth follows the rows
+  // a batch emits and is not predicted here)
+  if (s->scr.win_cap == 0) total += 1024ull * (8 + 4 + 4 + 8) + (1ull << 16) * 8;
+  for (const QueryHost& q : s->qs)
+    if (q.rows_cap == 0) total += round_cap(4096 + 4096 / 4) * sizeof(lms_result_row);
+  *bytes = total;
+  return LMS_OK;
+}
+
+lms_status lms_stream_device_bytes(lms_stream* s, uint64_t* bytes) {
+  if (!s || !bytes) return LMS_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  *bytes = s->dev_bytes;
+  return LMS_OK;
 }
 
 lms_status lms_stream_admissible_rows(lms_stream* s, int32_t host_input, int64_t* n_out) {

@@ -682,14 +682,10 @@ __global__ void __launch_bounds__(256) k_trim_copy(const QueryDev q) {
 template <bool FLOAT>
 cudaError_t launch_emit_t(const QueryDev& q, const Scratch& s, ResultRowDev* rows, int grid,
                           size_t smem, unsigned long long rows_cap, cudaStream_t st) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_emit<FLOAT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kEmitSmemMax);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  // once per process (thread-safe static initialisation)
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      k_emit<FLOAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEmitSmemMax);
+  if (attr != cudaSuccess) return attr;
   k_emit<FLOAT><<<grid, kEmitThreads, smem, st>>>(q, s, rows, smem ? emit_cap(q.k) : 0u,
                                                  rows_cap);
   return cudaGetLastError();

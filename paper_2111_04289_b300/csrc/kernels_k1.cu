@@ -425,14 +425,10 @@ __global__ void __launch_bounds__(kK1Threads, 2) k1_fused(const __grid_constant_
 
 template <bool FLOAT>
 cudaError_t launch_k1_t(const K1Args& a, int grid, cudaStream_t st) {
-  static bool attr_set = false;  // per instantiation; set once per process
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k1_fused<FLOAT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kK1Smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  // once per process and instantiation (thread-safe static initialisation)
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      k1_fused<FLOAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kK1Smem);
+  if (attr != cudaSuccess) return attr;
   k1_fused<FLOAT><<<grid, kK1Threads, kK1Smem, st>>>(a);
   return cudaGetLastError();
 }

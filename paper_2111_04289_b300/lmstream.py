@@ -89,12 +89,41 @@ EXPORTED_SYMBOLS = ("stream_open", "query_register", "push_microbatch", "poll_re
                     "lms_learned_create", "lms_learned_destroy", "lms_learned_set_backend",
                     "lms_learned_set_online", "lms_learned_samples", "lms_learned_fit",
                     "lms_learned_observe", "lms_learned_predict", "lms_learned_stats",
-                    "lms_serve_gpu_device_input")
+                    "lms_serve_gpu_device_input", "lms_stream_push_bytes",
+                    "lms_stream_device_bytes", "lms_server_create", "lms_server_submit",
+                    "lms_server_wait", "lms_server_forget", "lms_server_get_stats",
+                    "lms_server_destroy", "lms_server_create_ops")
 ADMIT_PAPER, ADMIT_GUARDED = 0, 1
 QOPS = {"aggregation": 0, "filter": 1, "shuffle": 2, "project": 3, "join": 4, "expand": 5,
         "scan": 6, "sort": 7}
 PROC_PREDICTOR = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_void_p, ctypes.c_double, ctypes.c_int32)
 POLICY_FIXED_SIZE, POLICY_FIXED_TRIGGER, POLICY_ANALYTIC, POLICY_LEARNED = 0, 1, 2, 3
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("memory_budget_bytes", ctypes.c_uint64), ("reserved", ctypes.c_int32 * 8)]
+
+
+SERVER_PUSH = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                               ctypes.POINTER(BatchC))
+SERVER_PUSH_BYTES = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_int64, ctypes.c_int32,
+                                     ctypes.POINTER(ctypes.c_uint64))
+SERVER_DEVICE_BYTES = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.POINTER(ctypes.c_uint64))
+
+
+class ServerOps(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("push", ctypes.c_void_p),
+                ("push_bytes", ctypes.c_void_p), ("device_bytes", ctypes.c_void_p)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("queued", ctypes.c_int64), ("max_concurrent", ctypes.c_int64),
+                ("memory_waits", ctypes.c_int64), ("peak_bytes", ctypes.c_uint64),
+                ("held_bytes", ctypes.c_uint64), ("busy_ms", ctypes.c_double)]
 
 
 class ServeChunk(ctypes.Structure):
@@ -257,6 +286,27 @@ def load(build_if_missing: bool = True):
                                          ctypes.c_uint32, D, ctypes.c_int64, I, ctypes.POINTER(P)]
     lib.lms_serve_gpu_backend.restype = I
     lib.lms_serve_gpu_backend.argtypes = [P, ctypes.POINTER(ServeBackend)]
+    lib.lms_stream_push_bytes.restype = I
+    lib.lms_stream_push_bytes.argtypes = [P, ctypes.c_int64, I, ctypes.POINTER(ctypes.c_uint64)]
+    lib.lms_stream_device_bytes.restype = I
+    lib.lms_stream_device_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_uint64)]
+    lib.lms_server_create.restype = I
+    lib.lms_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(P)]
+    lib.lms_server_create_ops.restype = I
+    lib.lms_server_create_ops.argtypes = [ctypes.POINTER(ServerConfig),
+                                          ctypes.POINTER(ServerOps), ctypes.POINTER(P)]
+    lib.lms_server_submit.restype = I
+    lib.lms_server_submit.argtypes = [P, P, ctypes.POINTER(BatchC),
+                                      ctypes.POINTER(ctypes.c_uint64)]
+    lib.lms_server_wait.restype = I
+    lib.lms_server_wait.argtypes = [P, ctypes.c_uint64, I, ctypes.POINTER(I), ctypes.POINTER(D),
+                                    ctypes.POINTER(D)]
+    lib.lms_server_forget.restype = I
+    lib.lms_server_forget.argtypes = [P, P]
+    lib.lms_server_get_stats.restype = I
+    lib.lms_server_get_stats.argtypes = [P, ctypes.POINTER(ServerStats)]
+    lib.lms_server_destroy.restype = I
+    lib.lms_server_destroy.argtypes = [P]
     lib.lms_serve_gpu_device_input.restype = I
     lib.lms_serve_gpu_device_input.argtypes = [P]
     lib.lms_serve_gpu_stream.restype = P
@@ -343,25 +393,29 @@ class Stream:
         self.queries.append((size_ms, slide_ms or size_ms))
         return qid.value
 
-    def push(self, ts, key, value, type_=None, eos: bool = False, arrival_ns: int = 0) -> int:
-        """Pushes one micro-batch (numpy host arrays or torch host/device tensors)."""
+    def make_batch(self, ts, key, value, type_=None, eos: bool = False, arrival_ns: int = 0):
+        """(lms_batch, keepalive objects) for the given columns."""
         pt, mem, k0 = _ptr_and_mem(ts)
         pk, mk, k1 = _ptr_and_mem(key)
         pv, mv, k2 = _ptr_and_mem(value)
         py, my, k3 = _ptr_and_mem(type_ if self.has_type else None)
-        n = int(ts.shape[0])
         if len({m for m in (mem, mk, mv, my) if m is not None}) > 1:
             raise ValueError("all columns of a batch must live in the same memory")
         b = BatchC()
-        b.n_rows = n
+        b.n_rows = int(ts.shape[0])
         b.ts, b.key, b.value, b.type = pt, pk, pv, py
         b.memory = MEM_HOST if mem is None else mem
         b.flags = BATCH_EOS if eos else 0
         b.arrival_ns = int(arrival_ns)
+        return b, (k0, k1, k2, k3)
+
+    def push(self, ts, key, value, type_=None, eos: bool = False, arrival_ns: int = 0) -> int:
+        """Pushes one micro-batch (numpy host arrays or torch host/device tensors)."""
+        b, keep = self.make_batch(ts, key, value, type_, eos, arrival_ns)
         st = self._lib.push_microbatch(self._h, ctypes.byref(b))
-        del k0, k1, k2, k3
+        del keep
         self._check(st, "push_microbatch")
-        return n
+        return int(b.n_rows)
 
     def poll(self, qid: int, max_rows: Optional[int] = None) -> np.ndarray:
         """All (or up to max_rows) pending rows of query qid, oldest first."""
@@ -825,6 +879,89 @@ class Learned:
         if getattr(self, "_h", None):
             self._lib.lms_learned_destroy(self._h)
             self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous batching across streams (lms_server_*): `slots` concurrent
+    micro-batches, admission by a device memory budget."""
+
+    def __init__(self, slots: int, memory_budget_bytes: int = 0, ops=None):
+        """ops: None for the engine, or Python callables (push(stream, batch) ->
+        status, push_bytes(stream, n_rows, host_input) -> bytes,
+        device_bytes(stream) -> bytes) to exercise the scheduling alone."""
+        self._lib = load()
+        cfg = ServerConfig(slots=int(slots), memory_budget_bytes=int(memory_budget_bytes))
+        h = ctypes.c_void_p()
+        if ops is None:
+            st = self._lib.lms_server_create(ctypes.byref(cfg), ctypes.byref(h))
+        else:
+            push, push_bytes, device_bytes = ops
+
+            def _pb(ctx, s, n, host, out):
+                out[0] = int(push_bytes(s, n, host))
+                return LMS_OK
+
+            def _db(ctx, s, out):
+                out[0] = int(device_bytes(s))
+                return LMS_OK
+            self._cbs = (SERVER_PUSH(lambda ctx, s, b: int(push(s, b[0]))),
+                         SERVER_PUSH_BYTES(_pb), SERVER_DEVICE_BYTES(_db))
+            o = ServerOps(None, *[ctypes.cast(c, ctypes.c_void_p).value for c in self._cbs])
+            st = self._lib.lms_server_create_ops(ctypes.byref(cfg), ctypes.byref(o),
+                                                 ctypes.byref(h))
+        if st != LMS_OK:
+            raise LmsError(st, "lms_server_create")
+        self._h = h.value
+        self._keep = {}
+
+    def submit(self, stream, ts=None, key=None, value=None, type_=None, eos: bool = False,
+               batch=None) -> int:
+        """Queues a push of the columns on `stream` (a Stream), or of a ready
+        BatchC `batch` on a raw stream handle."""
+        if batch is None:
+            b, keep = stream.make_batch(ts, key, value, type_, eos)
+            handle = stream._h
+        else:
+            b, keep, handle = batch, None, stream
+        t = ctypes.c_uint64()
+        st = self._lib.lms_server_submit(self._h, handle, ctypes.byref(b), ctypes.byref(t))
+        if st != LMS_OK:
+            raise LmsError(st, "lms_server_submit")
+        self._keep[t.value] = keep  # columns must outlive the request
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        """(status of the push, start ms, end ms) of a ticket."""
+        res = ctypes.c_int32()
+        a, b = ctypes.c_double(), ctypes.c_double()
+        st = self._lib.lms_server_wait(self._h, int(ticket), int(timeout_ms), ctypes.byref(res),
+                                       ctypes.byref(a), ctypes.byref(b))
+        if st != LMS_OK:
+            raise LmsError(st, "lms_server_wait")
+        self._keep.pop(int(ticket), None)
+        return res.value, a.value, b.value
+
+    def forget(self, stream):
+        st = self._lib.lms_server_forget(self._h, getattr(stream, "_h", stream))
+        if st != LMS_OK:
+            raise LmsError(st, "lms_server_forget")
+
+    def stats(self) -> dict:
+        out = ServerStats()
+        self._lib.lms_server_get_stats(self._h, ctypes.byref(out))
+        return {f[0]: getattr(out, f[0]) for f in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lms_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
 
     def __del__(self):
         try:
