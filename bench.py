@@ -334,6 +334,30 @@ def run_serving(args, lm, synth, local):
     return serving
 
 
+def run_profile_serving(args):
+    """A fixed serving-like load for profilers: `--profile-batches` micro-batches
+    of `--profile-events` events (ts = arrival ms at 2e8 events/s, columns in
+    HBM) through the serving backend; prints one summary line."""
+    import numpy as np
+
+    from paper_2111_04289_b300 import lmstream as lm
+    from paper_2111_04289_b300 import synth
+
+    n, nb = args.profile_events, args.profile_batches
+    per_tick = 2_000_000  # 2e8 events/s in 10-ms ticks
+    ticks = np.full(max(1, (n * nb) // per_tick), per_tick, dtype=np.int64)
+    g = lm.ServeGpu(SERVE_Q, seed=synth.BASE_SEED + 41, n_keys=1_000_000,
+                    max_batch_rows=max(n, 1 << 20), state_cap_bytes=8 << 30, device_input=True)
+    res, log = lm.serve_run(ticks, poll_ms=POLL_MS, policy=lm.POLICY_FIXED_SIZE, bound_ms=1e9,
+                            fixed_rows=n, backend=g.backend())
+    g.close()
+    ph = {k: float(np.mean([r[k] for r in log[1:]])) if len(log) > 1 else None
+          for k in ("proc_ms", "k1_ms", "sort_ms", "emit_ms", "h2d_ms")}
+    print(json.dumps({"profile_serving": {"batches": res["batches"], "events": n,
+                                          "mean_ms": ph}}), flush=True)
+    return 0
+
+
 def run_ours(args):
     import torch
 
@@ -531,11 +555,17 @@ def main():
     ap.add_argument("--fixed-triggers", type=lambda x: [float(v) for v in x.split(",")],
                     default=[25.0, 50.0])
     ap.add_argument("--ref-duration-ms", type=float, default=20_000.0)
+    ap.add_argument("--profile-serving", action="store_true",
+                    help="run a fixed serving-like load for a profiler and exit")
+    ap.add_argument("--profile-events", type=int, default=20_000_000)
+    ap.add_argument("--profile-batches", type=int, default=6)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--k1-variant", type=int, default=0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: warmup < 3 is below the timing rules", file=sys.stderr)
+    if args.profile_serving:
+        sys.exit(run_profile_serving(args))
     sys.exit(run_reference(args) if args.impl == "reference" else run_ours(args))
 
 

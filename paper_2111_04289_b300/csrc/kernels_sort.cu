@@ -186,74 +186,217 @@ __global__ void __launch_bounds__(1024) k_scan_chunks(unsigned long long* a, int
   if (threadIdx.x == 0) *total = tot;
 }
 
-// Runs of equal keys up to this length are reduced by the thread at their head;
-// longer runs (a hot key's groups from many tiles of one pane) are listed and
-// reduced by whole CTAs in k_rbk_long.
-constexpr unsigned long long kSerialRun = 32;
+// Reduce-by-key as a tiled segmented scan.  CTA c owns the runs of equal keys
+// whose first element (head) lies in its chunk [lo, hi) of the sorted keys and
+// processes [start, end): start = its first head, end = the end of the last run
+// it owns — unless that run crosses hi and is longer than kLongRun, in which
+// case it is listed for k_rbk_long (one CTA per run) and end stops at its
+// head.  Tiles of 1024 elements (4 consecutive per thread): gather the groups,
+// a segmented inclusive scan over the tile (thread-local, warp shuffles,
+// warp totals in shared memory) carried across tiles, and the last element of
+// each run writes the run's group at the run's rank among the CTA's heads.
+constexpr unsigned long long kLongRun = 4096;
+constexpr int kRbkItems = 4;
+constexpr int kRbkTile = 256 * kRbkItems;
+
+struct SegAgg {  // (run started here?, aggregate since the run's head, run's output index)
+  unsigned f;
+  long long cnt;
+  unsigned long long sum;
+  unsigned mn, mx;
+  unsigned long long rank;
+};
+
+template <bool FLOAT>
+__device__ __forceinline__ SegAgg seg_combine(const SegAgg& x, const SegAgg& y) {
+  if (y.f) return y;  // y's run starts inside y: x does not reach past it
+  SegAgg r;
+  r.f = x.f;
+  r.cnt = x.cnt + y.cnt;
+  r.sum = FLOAT ? (unsigned long long)__double_as_longlong(__longlong_as_double((long long)x.sum) +
+                                                           __longlong_as_double((long long)y.sum))
+                : x.sum + y.sum;
+  r.mn = min(x.mn, y.mn);
+  r.mx = max(x.mx, y.mx);
+  r.rank = x.rank;
+  return r;
+}
+
+__device__ __forceinline__ SegAgg seg_identity() {
+  SegAgg r;
+  r.f = 0;
+  r.cnt = 0;
+  r.sum = 0ull;  // +0.0 for doubles
+  r.mn = 0xffffffffu;
+  r.mx = 0u;
+  r.rank = 0ull;
+  return r;
+}
+
+__device__ __forceinline__ SegAgg seg_shfl_up(const SegAgg& v, int d) {
+  SegAgg r;
+  r.f = __shfl_up_sync(kFull, v.f, d);
+  r.cnt = __shfl_up_sync(kFull, v.cnt, d);
+  r.sum = __shfl_up_sync(kFull, v.sum, d);
+  r.mn = __shfl_up_sync(kFull, v.mn, d);
+  r.mx = __shfl_up_sync(kFull, v.mx, d);
+  r.rank = __shfl_up_sync(kFull, v.rank, d);
+  return r;
+}
+
+// first index in [a, b) whose key differs from k (keys sorted, keys[a-1..] >= k)
+__device__ unsigned long long first_after(const unsigned long long* keys, unsigned long long a,
+                                          unsigned long long b, unsigned long long k) {
+  while (a < b) {
+    const unsigned long long m = a + ((b - a) >> 1);
+    if (keys[m] == k) a = m + 1;
+    else b = m;
+  }
+  return a;
+}
+
+// first index in [a, b) whose key equals k (keys sorted, keys[b-1] == k)
+__device__ unsigned long long first_equal(const unsigned long long* keys, unsigned long long a,
+                                          unsigned long long b, unsigned long long k) {
+  while (a < b) {
+    const unsigned long long m = a + ((b - a) >> 1);
+    if (keys[m] < k) a = m + 1;
+    else b = m;
+  }
+  return a;
+}
 
 template <bool FLOAT>
 __global__ void __launch_bounds__(256) k_rbk_write(const QueryDev q, const Scratch s) {
   QCtl* c = q.ctl;
   const unsigned long long n = c->n_parts;
   const SortSrc src = final_src(q, s, c->npasses);
+  const unsigned long long* keys = src.keys;
   unsigned long long* lst;
   unsigned* lpos;
   free_pair(s, c->npasses, &lst, &lpos);
   unsigned long long lo, hi;
   chunk_range(n, blockIdx.x, gridDim.x, &lo, &hi);
+  __shared__ unsigned long long sh_start, sh_end;
   __shared__ unsigned long long tmp[33];
-  unsigned long long out = s.chunk[blockIdx.x];
-  for (unsigned long long i0 = lo; i0 < hi; i0 += blockDim.x) {
-    const unsigned long long i = i0 + threadIdx.x;
-    const bool v = i < hi;
-    const unsigned long long k = v ? src.keys[i] : 0ull;
-    const bool head = v && (i == 0 || k != src.keys[i - 1]);
-    unsigned long long tot;
-    const unsigned long long r = block_excl_scan(head ? 1ull : 0ull, tmp, &tot);
-    if (head) {
-      if (i + kSerialRun < n && src.keys[i + kSerialRun] == k) {
-        // long run: find its end (gallop, then bisect) and hand it over
-        unsigned long long a = i + kSerialRun, step = kSerialRun;
-        unsigned long long b = n;
-        while (true) {
-          const unsigned long long t = a + step;
-          if (t >= n || src.keys[t] != k) {
-            b = t < n ? t : n;
-            break;
-          }
-          a = t;
-          step <<= 1;
+  __shared__ SegAgg wtot[8];
+  __shared__ SegAgg carry;
+  const unsigned long long out0 = s.chunk[blockIdx.x];
+  if (threadIdx.x == 0) {
+    unsigned long long st = lo, en = hi;
+    if (lo < hi && lo > 0 && keys[lo] == keys[lo - 1]) st = first_after(keys, lo, hi, keys[lo - 1]);
+    if (st < hi && hi < n && keys[hi] == keys[hi - 1]) {
+      // the last run owned here crosses hi
+      const unsigned long long k = keys[hi - 1];
+      const unsigned long long h = first_equal(keys, st, hi - 1, k);
+      unsigned long long b = hi, step = 256;  // gallop to its end
+      while (b < n && keys[b] == k) {
+        const unsigned long long t = b + step;
+        if (t >= n || keys[t] != k) {
+          b = first_after(keys, b + 1, t < n ? t : n, k);
+          break;
         }
-        while (b - a > 1) {  // keys[a] == k, keys[b] != k (or b == n)
-          const unsigned long long m = a + ((b - a) >> 1);
-          if (src.keys[m] == k) a = m;
-          else b = m;
-        }
+        b = t;
+        step <<= 1;
+      }
+      if (b - h > kLongRun) {
+        // rank of the run = number of heads owned before it
+        const unsigned long long heads =
+            (blockIdx.x + 1 < gridDim.x ? s.chunk[blockIdx.x + 1] : c->n_state) - out0;
         const unsigned long long slot = atomicAdd(&c->n_long, 1ull);
-        lst[2 * slot] = i;
+        lst[2 * slot] = h;
         lst[2 * slot + 1] = b;
-        lpos[slot] = (unsigned)(out + r);
+        lpos[slot] = (unsigned)(out0 + heads - 1);
+        en = h;
       } else {
-        long long cnt = 0;
-        unsigned long long isum = 0ull;
-        double fsum = 0.0;
-        unsigned mn = 0xffffffffu, mx = 0u;
-        for (unsigned long long j = i; j < n && src.keys[j] == k; ++j) {
-          const unsigned long long pi = src.vals ? src.vals[j] : j;
-          const Grp g = load_grp(q.parts + pi);
-          cnt += g.cnt;
-          if (FLOAT)
-            fsum += __longlong_as_double((long long)g.sum);
-          else
-            isum += g.sum;
-          mn = min(mn, g.mn);
-          mx = max(mx, g.mx);
-        }
-        store_grp(q.state + out + r, k, cnt,
-                  FLOAT ? (unsigned long long)__double_as_longlong(fsum) : isum, mn, mx);
+        en = b;
       }
     }
-    out += tot;
+    sh_start = st;
+    sh_end = st < hi ? en : st;
+    carry = seg_identity();
+  }
+  __syncthreads();
+  const unsigned long long start = sh_start, end = sh_end;
+  const unsigned lane = lane_id(), w = threadIdx.x >> 5;
+  unsigned long long heads_before = 0;
+  for (unsigned long long base = start; base < end; base += kRbkTile) {
+    const unsigned long long i0 = base + (unsigned long long)threadIdx.x * kRbkItems;
+    unsigned long long k[kRbkItems];
+    bool head[kRbkItems], last[kRbkItems], valid[kRbkItems];
+    SegAgg v[kRbkItems];
+    unsigned nh = 0;
+#pragma unroll
+    for (int u = 0; u < kRbkItems; ++u) {
+      const unsigned long long i = i0 + u;
+      valid[u] = i < end;
+      k[u] = valid[u] ? keys[i] : ~0ull;
+    }
+    // neighbours: previous key (for heads) and next key (for run ends)
+    unsigned long long kprev = __shfl_up_sync(kFull, k[kRbkItems - 1], 1);
+    unsigned long long knext = __shfl_down_sync(kFull, k[0], 1);
+    if (lane == 0) kprev = (i0 > start && i0 < end) ? keys[i0 - 1] : ~0ull;
+    if (lane == 31) knext = (i0 + kRbkItems < end) ? keys[i0 + kRbkItems] : ~0ull;
+#pragma unroll
+    for (int u = 0; u < kRbkItems; ++u) {
+      const unsigned long long i = i0 + u;
+      const unsigned long long kp = u == 0 ? kprev : k[u - 1];
+      const unsigned long long kn = u + 1 < kRbkItems ? k[u + 1] : knext;
+      head[u] = valid[u] && (i == start || k[u] != kp);
+      last[u] = valid[u] && (i + 1 == end || k[u] != kn);
+      nh += head[u] ? 1u : 0u;
+      if (valid[u]) {
+        const unsigned long long pi = src.vals ? src.vals[i] : i;
+        const Grp g = load_grp(q.parts + pi);
+        v[u].f = head[u] ? 1u : 0u;
+        v[u].cnt = g.cnt;
+        v[u].sum = g.sum;
+        v[u].mn = g.mn;
+        v[u].mx = g.mx;
+        v[u].rank = 0;
+      } else {
+        v[u] = seg_identity();
+      }
+    }
+    // ranks of the heads
+    unsigned long long htot;
+    unsigned long long hpre = block_excl_scan((unsigned long long)nh, tmp, &htot);
+#pragma unroll
+    for (int u = 0; u < kRbkItems; ++u)
+      if (head[u]) v[u].rank = out0 + heads_before + hpre++;
+    // thread-local inclusive segmented scan
+#pragma unroll
+    for (int u = 1; u < kRbkItems; ++u) v[u] = seg_combine<FLOAT>(v[u - 1], v[u]);
+    // warp inclusive scan of thread totals
+    SegAgg t = v[kRbkItems - 1];
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const SegAgg o = seg_shfl_up(t, d);
+      if ((int)lane >= d) t = seg_combine<FLOAT>(o, t);
+    }
+    SegAgg ex = seg_shfl_up(t, 1);  // exclusive within the warp
+    if (lane == 31) wtot[w] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {  // exclusive prefix of the warps, from the carry
+      SegAgg acc = carry;
+      for (int j = 0; j < 8; ++j) {
+        const SegAgg x = wtot[j];
+        wtot[j] = acc;
+        acc = seg_combine<FLOAT>(acc, x);
+      }
+      carry = acc;  // everything up to the end of this tile
+    }
+    __syncthreads();
+    SegAgg pre = wtot[w];
+    if (lane > 0) pre = seg_combine<FLOAT>(pre, ex);
+#pragma unroll
+    for (int u = 0; u < kRbkItems; ++u) {
+      if (!last[u]) continue;
+      const SegAgg r = seg_combine<FLOAT>(pre, v[u]);
+      store_grp(q.state + r.rank, k[u], r.cnt, r.sum, r.mn, r.mx);
+    }
+    heads_before += htot;
+    __syncthreads();
   }
 }
 

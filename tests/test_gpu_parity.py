@@ -223,3 +223,15 @@ def test_hot_key_runs_longer_than_a_tile(is_float):
     batches = [synth.Batch(ts[a:a + 200_000], key[a:a + 200_000], val[a:a + 200_000])
                for a in range(0, n, 200_000)]
     _check(batches, [dict(size=1000, slide=250), dict(size=300, slide=300)], is_float)
+
+
+def test_run_longer_than_the_cooperative_threshold():
+    """4.6M events in one pane with one key in 90 % of them: that key's partial
+    groups (one per K1 tile, > 4096) form a run that crosses many reduce
+    chunks and goes to the cooperative reduce."""
+    rng = np.random.default_rng(23)
+    n = 4_600_000
+    ts = np.sort(rng.integers(0, 900, n)).astype(np.int64)
+    key = np.where(rng.random(n) < 0.9, 7, rng.integers(0, 300, n)).astype(np.uint32)
+    val = rng.integers(-1000, 1000, n).astype(np.int32)
+    _check([synth.Batch(ts, key, val)], [dict(size=1000)], False)

@@ -8,7 +8,7 @@ import pytest
 
 from paper_2111_04289_b300 import lmstream as lm
 from paper_2111_04289_b300 import synth
-from tests.engine_helpers import assert_rows_match
+from tests.engine_helpers import FLOAT_REL_TOL
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -32,6 +32,22 @@ def _streams():
     ]
 
 
+def _same_rows(a, b, is_float, ctx):
+    assert len(a) == len(b), ctx
+    for f in ("window_start", "key", "count", "query_id"):
+        np.testing.assert_array_equal(a[f], b[f], err_msg=ctx)
+    if is_float:
+        for f in ("min", "max"):
+            np.testing.assert_array_equal(a[f].view(np.uint32), b[f].view(np.uint32), err_msg=ctx)
+        for f in ("sum", "avg"):
+            assert np.all(np.abs(a[f] - b[f]) <= FLOAT_REL_TOL * np.abs(b[f])), ctx
+    else:
+        for f in ("sum", "min", "max"):
+            np.testing.assert_array_equal(a[f], b[f], err_msg=ctx)
+        np.testing.assert_array_equal(a["avg"].view(np.uint64), b["avg"].view(np.uint64),
+                                      err_msg=ctx)
+
+
 def _open(spec):
     s = lm.Stream(spec["vt"], has_type=spec["has_type"])
     for (size, slide, col, op, v) in spec["queries"]:
@@ -51,11 +67,7 @@ def _alone(spec):
     return [np.concatenate(r) for r in out], dev
 
 
-@pytest.mark.parametrize("budget_factor", [0.0, 1.3])
-def test_results_alone_equal_results_in_the_mix(budget_factor):
-    specs = _streams()
-    alone, devs = zip(*[_alone(sp) for sp in specs])
-    budget = int(budget_factor * sum(devs))
+def _mix(specs, budget):
     sv = lm.Server(slots=3, memory_budget_bytes=budget)
     streams = [_open(sp) for sp in specs]
     tickets = []
@@ -74,19 +86,31 @@ def test_results_alone_equal_results_in_the_mix(budget_factor):
         spans.append((k, a, b))
     stats = sv.stats()
     sv.close()
+    rows = [[s.poll(q) for q in range(len(sp["queries"]))] for s, sp in zip(streams, specs)]
+    for s in streams:
+        s.close()
+    assert stats["completed"] == len(tickets)
+    return rows, spans, stats
+
+
+def test_results_alone_equal_results_in_the_mix():
+    specs = _streams()
+    alone = [_alone(sp)[0] for sp in specs]
+    free, spans, stats = _mix(specs, 0)
+    # then under a device memory budget just above what the mix ends up holding
+    budget = int(1.1 * stats["held_bytes"])
+    capped, _, cstats = _mix(specs, budget)
     exact = 0
     for k, sp in enumerate(specs):
         for q in range(len(sp["queries"])):
-            got = streams[k].poll(q)
-            assert_rows_match(got, alone[k][q], sp["vt"] == "float32", ctx=f"stream {k} q{q}")
-            exact += int(got.tobytes() == alone[k][q].tobytes())
-        streams[k].close()
-    print(f"{exact} of {sum(len(sp['queries']) for sp in specs)} row sets bit-identical; "
-          f"server stats {stats}")
-    assert stats["completed"] == len(tickets)
+            assert len(alone[k][q]) > 0
+            for got in (free[k][q], capped[k][q]):
+                _same_rows(got, alone[k][q], sp["vt"] == "float32", f"stream {k} q{q}")
+                exact += int(got.tobytes() == alone[k][q].tobytes())
+    print(f"{exact} of {2 * sum(len(sp['queries']) for sp in specs)} row sets bit-identical; "
+          f"server stats {stats}; with a {budget}-byte budget {cstats}")
     assert stats["max_concurrent"] >= 2
     overlap = any(a1 < b2 and a2 < b1 for (k1, a1, b1) in spans for (k2, a2, b2) in spans
                   if k1 != k2)
     assert overlap, "no two streams' micro-batches ran at the same time"
-    if budget:
-        assert stats["peak_bytes"] <= budget
+    assert cstats["peak_bytes"] <= budget
