@@ -530,7 +530,9 @@ void lms_cost_features(double rows, double carried_groups, double key_card, doub
  * the backend (whose stream's carried groups the features read, and whose
  * input mode decides whether the host-to-device copy is one of the operators)
  * and restarts Eq. 5's history and the judge's errors; the network and its
- * samples are kept. */
+ * samples are kept.  A candidate larger than the backend's stream admits
+ * (lms_stream_admissible_rows) is predicted as the capped batches it will
+ * run as. */
 typedef struct lms_learned lms_learned;
 lms_learned *lms_learned_create(lms_mlp *m, lms_serve_gpu *g, double key_card,
                                 double selectivity, double panes_per_window, double n_queries,

@@ -37,18 +37,22 @@ struct lms_learned {
 
 namespace {
 
-// Sum over the batch's operators (no H2D when the input is already on the
-// device) of the network's exp(output) us, in ms.
-double net_predict_ms(lms_learned* l, double rows, double carried, double span_panes) {
-  float x[LMS_N_OPS * LMS_MLP_INPUTS], y[LMS_N_OPS];
+// Sum over the operators (no H2D when the input is already on the device) of
+// the network's exp(output) us, in ms, for `nb` batches of `rows` rows plus
+// one of `rest` rows (rest = 0: none).
+double net_predict_ms(lms_learned* l, double rows, double carried, double span_panes,
+                      double nb = 1.0, double rest = 0.0) {
+  float x[2 * LMS_N_OPS * LMS_MLP_INPUTS], y[2 * LMS_N_OPS];
   const int op0 = l->host_input ? 0 : 1;
   const int nops = LMS_N_OPS - op0;
-  for (int op = op0; op < LMS_N_OPS; ++op)
-    lms_cost_features(rows, carried, l->key_card, l->selectivity, l->panes, l->nq, span_panes, op,
-                      x + (op - op0) * LMS_MLP_INPUTS);
-  if (lms_mlp_forward(l->m, x, nops, y) != LMS_OK) return -1.0;
+  int m = 0;
+  for (int part = 0; part < (rest > 0 ? 2 : 1); ++part)
+    for (int op = op0; op < LMS_N_OPS; ++op)
+      lms_cost_features(part ? rest : rows, carried, l->key_card, l->selectivity, l->panes, l->nq,
+                        span_panes, op, x + (m++) * LMS_MLP_INPUTS);
+  if (lms_mlp_forward(l->m, x, m, y) != LMS_OK) return -1.0;
   double us = 0.0;
-  for (int i = 0; i < nops; ++i) us += std::exp((double)y[i]);
+  for (int i = 0; i < m; ++i) us += (i < nops ? nb : 1.0) * std::exp((double)y[i]);
   return us * 1e-3;
 }
 
@@ -185,14 +189,25 @@ double lms_learned_predict(void* ctx, double batch_bytes, int32_t n_datasets) {
     ++l->uses_eq5;
     return eq5;  // fallback: the analytic estimate
   }
-  double carried = 0.0;
+  double carried = 0.0, cap = -1.0;
   if (l->g) {
+    lms_stream* s = lms_serve_gpu_stream(l->g);
     lms_stats st{};
-    if (lms_stream_stats(lms_serve_gpu_stream(l->g), &st) == LMS_OK)
-      carried = (double)st.state_groups;
+    if (lms_stream_stats(s, &st) == LMS_OK) carried = (double)st.state_groups;
+    int64_t adm = -1;
+    if (lms_stream_admissible_rows(s, l->host_input ? 1 : 0, &adm) == LMS_OK && adm > 0)
+      cap = (double)adm;
   }
-  const double p = net_predict_ms(l, batch_bytes / l->bpe, carried,
-                                  (double)n_datasets * l->poll_ms / l->slide_ms);
+  // a candidate larger than the memory admits runs as several capped batches
+  const double rows = batch_bytes / l->bpe;
+  const double span = (double)n_datasets * l->poll_ms / l->slide_ms;
+  double p;
+  if (cap > 0 && rows > cap) {
+    const double nb = std::floor(rows / cap);
+    p = net_predict_ms(l, cap, carried, span * cap / rows, nb, rows - nb * cap);
+  } else {
+    p = net_predict_ms(l, rows, carried, span);
+  }
   if (p < 0) {
     ++l->uses_eq5;
     return eq5;
