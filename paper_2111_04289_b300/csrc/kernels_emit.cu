@@ -264,40 +264,6 @@ __device__ __forceinline__ void write_row(const QueryDev& q, ResultRowDev* out, 
   o[2] = make_uint4(key, mnv, mxv, (unsigned)q.qid);
 }
 
-// Combines the state groups S[i..e) (one key, pane order) of a window; the low
-// 32 bits of an entry are the group's index in the window state.  Loads are
-// issued two records at a time so that their latencies overlap.
-template <bool FLOAT, bool PAD>
-__device__ __forceinline__ void combine_run(const QueryDev& q, const unsigned long long* S,
-                                            unsigned i, unsigned e, long long* cnt,
-                                            unsigned long long* sbits, unsigned* mn,
-                                            unsigned* mx) {
-  long long c = 0;
-  unsigned long long isum = 0ull;
-  double fsum = 0.0;
-  unsigned lo = 0xffffffffu, hi = 0u;
-  for (unsigned t = i; t < e; t += 2) {
-    Grp g[2];
-#pragma unroll
-    for (int u = 0; u < 2; ++u)
-      if (t + u < e) g[u] = load_grp(q.state + (S[pix<PAD>(t + u)] & 0xffffffffull));
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      if (t + u < e) {
-        c += g[u].cnt;
-        if (FLOAT) fsum += __longlong_as_double((long long)g[u].sum);
-        else isum += g[u].sum;
-        lo = min(lo, g[u].mn);
-        hi = max(hi, g[u].mx);
-      }
-    }
-  }
-  *cnt = c;
-  *sbits = FLOAT ? (unsigned long long)__double_as_longlong(fsum) : isum;
-  *mn = lo;
-  *mx = hi;
-}
-
 // Exclusive scan of one count per thread over the block; returns the prefix
 // and writes the block total to *total.  wt holds 33 counters.
 __device__ __forceinline__ unsigned block_scan_u32(unsigned v, unsigned* wt, unsigned* total) {
@@ -353,33 +319,89 @@ __device__ __forceinline__ unsigned long long count_distinct(const unsigned long
   return tot;
 }
 
-// One row per distinct key of the merged window, written from out[0]; returns
-// the number of rows.  Each thread owns a contiguous chunk of the list and
-// writes the rows of the keys that start in it.
+// One row per distinct key of the merged window S[0..len) (entries key << 32 |
+// state index, key-sorted), written from out[0] in key order; returns the
+// number of rows.  Tiles of 4 consecutive entries per thread: every entry's
+// state group is gathered (independent loads), a segmented scan combines the
+// groups of each key across threads and tiles, and the thread holding a key's
+// last entry writes its row at the key's rank.
 template <bool FLOAT, bool PAD>
-__device__ __forceinline__ unsigned write_distinct(const QueryDev& q, const unsigned long long* S,
-                                                   unsigned len, long long wstart,
-                                                   ResultRowDev* out, unsigned* wt) {
-  const unsigned per = (len + blockDim.x - 1) / blockDim.x;
-  const unsigned a = min(len, threadIdx.x * per), b = min(len, a + per);
-  unsigned tot;
-  unsigned r = block_scan_u32(chunk_heads<PAD>(S, len, a, b), wt, &tot);
-  unsigned prev = a > 0 ? (unsigned)(S[pix<PAD>(a - 1)] >> 32) : 0u;
-  for (unsigned i = a; i < b; ++i) {
-    const unsigned key = (unsigned)(S[pix<PAD>(i)] >> 32);
-    if (i == 0 || key != prev) {
-      unsigned e = i + 1;
-      while (e < len && (unsigned)(S[pix<PAD>(e)] >> 32) == key) ++e;
-      long long cnt;
-      unsigned long long sb;
-      unsigned mn, mx;
-      combine_run<FLOAT, PAD>(q, S, i, e, &cnt, &sb, &mn, &mx);
-      write_row<FLOAT>(q, out + r, wstart, key, cnt, sb, mn, mx);
-      ++r;
+__device__ unsigned write_distinct(const QueryDev& q, const unsigned long long* S, unsigned len,
+                                   long long wstart, ResultRowDev* out) {
+  constexpr int kItems = 4;
+  constexpr int kWarps = kEmitThreads / 32;
+  __shared__ SegAgg wtot[kWarps];
+  __shared__ SegAgg carry;
+  __shared__ unsigned long long hs[33];
+  const unsigned lane = lane_id(), w = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry = seg_identity();
+  __syncthreads();
+  unsigned long long heads_before = 0;
+  for (unsigned base = 0; base < len; base += kEmitThreads * kItems) {
+    const unsigned i0 = base + threadIdx.x * kItems;
+    unsigned key[kItems];
+    bool head[kItems], last[kItems];
+    SegAgg v[kItems];
+    unsigned nh = 0;
+#pragma unroll
+    for (int u = 0; u < kItems; ++u) {
+      const unsigned i = i0 + u;
+      const bool valid = i < len;
+      unsigned long long e = valid ? S[pix<PAD>(i)] : 0ull;
+      key[u] = (unsigned)(e >> 32);
+      head[u] = valid && (i == 0 || (unsigned)(S[pix<PAD>(i - 1)] >> 32) != key[u]);
+      last[u] = valid && (i + 1 == len || (unsigned)(S[pix<PAD>(i + 1)] >> 32) != key[u]);
+      nh += head[u] ? 1u : 0u;
+      if (valid) {
+        const Grp g = load_grp(q.state + (e & 0xffffffffull));
+        v[u].f = head[u] ? 1u : 0u;
+        v[u].cnt = g.cnt;
+        v[u].sum = g.sum;
+        v[u].mn = g.mn;
+        v[u].mx = g.mx;
+        v[u].rank = 0ull;
+      } else {
+        v[u] = seg_identity();
+      }
     }
-    prev = key;
+    unsigned long long htot;
+    unsigned long long hpre = block_excl_scan((unsigned long long)nh, hs, &htot);
+#pragma unroll
+    for (int u = 0; u < kItems; ++u)
+      if (head[u]) v[u].rank = heads_before + hpre++;
+#pragma unroll
+    for (int u = 1; u < kItems; ++u) v[u] = seg_combine<FLOAT>(v[u - 1], v[u]);
+    SegAgg t = v[kItems - 1];
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const SegAgg o = seg_shfl_up(t, d);
+      if ((int)lane >= d) t = seg_combine<FLOAT>(o, t);
+    }
+    const SegAgg ex = seg_shfl_up(t, 1);
+    if (lane == 31) wtot[w] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      SegAgg acc = carry;
+      for (int j = 0; j < kWarps; ++j) {
+        const SegAgg x = wtot[j];
+        wtot[j] = acc;
+        acc = seg_combine<FLOAT>(acc, x);
+      }
+      carry = acc;
+    }
+    __syncthreads();
+    SegAgg pre = wtot[w];
+    if (lane > 0) pre = seg_combine<FLOAT>(pre, ex);
+#pragma unroll
+    for (int u = 0; u < kItems; ++u) {
+      if (!last[u]) continue;
+      const SegAgg r = seg_combine<FLOAT>(pre, v[u]);
+      write_row<FLOAT>(q, out + r.rank, wstart, key[u], r.cnt, r.sum, r.mn, r.mx);
+    }
+    heads_before += htot;
+    __syncthreads();
   }
-  return tot;
+  return (unsigned)heads_before;
 }
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -536,7 +558,7 @@ __device__ unsigned long long run_range(const QueryDev& q, const Scratch& s, QCt
         m.bnd0[r] = (unsigned)(s.pane_begin[j0 + r] - b0);
       __syncthreads();
       const unsigned long long* S = merge_runs<false>(A, B, m.bnd0, m.bnd1, nr, len);
-      if (WRITE) acc += write_distinct<FLOAT, false>(q, S, len, wstart, out + acc, m.wt);
+      if (WRITE) acc += write_distinct<FLOAT, false>(q, S, len, wstart, out + acc);
       else acc += count_distinct<false>(S, len, m.wt);
       __syncthreads();
       continue;
@@ -574,7 +596,7 @@ __device__ unsigned long long run_range(const QueryDev& q, const Scratch& s, QCt
     cj1 = j1;
     n = len;
     __syncthreads();
-    if (WRITE) acc += write_distinct<FLOAT, true>(q, m.L, len, wstart, out + acc, m.wt);
+    if (WRITE) acc += write_distinct<FLOAT, true>(q, m.L, len, wstart, out + acc);
     else acc += count_distinct<true>(m.L, len, m.wt);
   }
   __syncthreads();

@@ -8,23 +8,21 @@
 // with vector loads, for all queries together.
 //
 // Per tile of 1024 events and per query, the groups are built in shared
-// memory without any floating-point atomics:
+// memory with integer atomics only:
 //   A. every surviving event inserts its group key into an open-addressing
-//      table (integer CAS on the key only); a new key is appended to the
-//      tile's group list;
-//   B. each event takes a rank inside its group (warp-aggregated atomic add
-//      on the group's counter);
-//   C. a scan of the group counters gives every group a contiguous range and
-//      the events scatter their values into it;
-//   D. each group is reduced (count, sum, min, max) — one thread per small
-//      group, one warp per large one — and appended to the query's
-//      partial-group array in HBM.  Float32 values are summed on the integer
-//      pipe: every value is aligned to the group's largest exponent B as a
-//      64-bit fixed-point number whose unit is 2^(B-178) (the largest value
-//      occupies bits 28..51, so 2048 of them could not overflow), then the sum is
-//      converted to double once.  The error is at most 2^-41 of the group's
-//      largest |value| (FP64 is slow on this part; groups holding Inf or NaN
-//      are summed in FP64 instead).
+//      table (CAS on the key; a new key is appended to the tile's group list)
+//      and updates the group's min and max (order-preserving u32 codes) and
+//      its count (for int32 values, count and sum share one 64-bit word);
+//   B. (float32 values) every event adds its value to the group's sum as a
+//      64-bit fixed-point number whose unit is 2^(B-178), B the largest
+//      exponent in the group (that of its min or its max; the largest value
+//      occupies bits 28..51, so 2^11 of them cannot overflow): integer adds,
+//      so the sum is exact and independent of the order; it is converted to
+//      double once.  The error is at most 2^-41 of the group's largest
+//      |value| (FP64 is slow on this part; a group holding Inf or NaN is
+//      summed in FP64 instead).  Int32 values are summed exactly in A;
+//   C. each group of the list is appended to the query's partial-group array
+//      in HBM and its slot is cleared for the next tile.
 #include <climits>
 
 #include "lms_device.cuh"
@@ -33,23 +31,24 @@ namespace lms {
 namespace {
 
 constexpr int kK1Threads = 512;                  // two CTAs per SM
-constexpr int kK1Warps = kK1Threads / 32;
 constexpr int kK1Items = 2;                      // events per thread per tile
 constexpr int kK1Tile = kK1Threads * kK1Items;   // 1024 events
 constexpr int kK1HashBits = 11;                  // 2048 slots >= 2 * tile
 constexpr int kK1Hash = 1 << kK1HashBits;
-constexpr unsigned kBigGroup = 32;               // groups above this are reduced by a warp
-constexpr unsigned kNoSlot = 0xffffu;
+constexpr unsigned kNoSlot = 0xffffffffu;
 
-// hkey u64[H] | hidx u16[H] | list u16[T] | lcnt u32[T] | loff u32[T+4] | vals u32[T]
-constexpr size_t kK1Smem = (size_t)kK1Hash * 8 + kK1Hash * 2 + kK1Tile * 2 + kK1Tile * 4 +
-                           (kK1Tile + 4) * 4 + kK1Tile * 4;
+// hkey u64[H] | gsum u64[H] | gcnt u32[H] | gmn u32[H] | gmx u32[H] | list u16[T]
+constexpr size_t kK1Smem = (size_t)kK1Hash * (8 + 8 + 4 + 4 + 4) + kK1Tile * 2;
+
+// Int32 values: count and sum share one 64-bit word: each event adds
+// 2^42 + (value + 2^31), so count = word >> 42 and sum = low 42 bits - count * 2^31
+// (at most 1024 events of at most 2^32 each: the low part stays below 2^42).
+constexpr int kCntShift = 42;
 
 // Phase A: the slot of group key g (inserted if new).  Returns the slot, or
 // kNoSlot if the probe bound is hit (cannot happen: a tile has <= H/2 groups).
-__device__ __forceinline__ unsigned insert_key(unsigned long long* hkey, unsigned short* hidx,
-                                               unsigned short* list, unsigned* nlist,
-                                               unsigned long long g) {
+__device__ __forceinline__ unsigned insert_key(unsigned long long* hkey, unsigned short* list,
+                                               unsigned* nlist, unsigned long long g) {
   unsigned slot = hash_slot(g, kK1HashBits);
   for (int probes = 0; probes < kK1Hash; ++probes) {
     const unsigned long long cur = *((volatile unsigned long long*)&hkey[slot]);
@@ -59,7 +58,6 @@ __device__ __forceinline__ unsigned insert_key(unsigned long long* hkey, unsigne
       if (prev == kEmpty) {
         const unsigned li = atomicAdd(nlist, 1u);
         list[li] = (unsigned short)slot;
-        hidx[slot] = (unsigned short)li;
         return slot;
       }
       if (prev == g) return slot;
@@ -69,12 +67,17 @@ __device__ __forceinline__ unsigned insert_key(unsigned long long* hkey, unsigne
   return kNoSlot;
 }
 
-// Biased exponent used for alignment (denormals count as exponent 1) and the
-// 24-bit significand of a float32 given by its bits.
+// Biased exponent used for alignment (denormals count as exponent 1).
 __device__ __forceinline__ unsigned f32_exp(unsigned x) {
   const unsigned be = (x >> 23) & 0xffu;
   return be ? be : 1u;
 }
+// Largest exponent among a group's values, from its min and max codes: the
+// value of largest magnitude is the group's min or its max.
+__device__ __forceinline__ unsigned group_exp(unsigned mn_code, unsigned mx_code) {
+  return max(f32_exp(dec_f32_bits(mn_code)), f32_exp(dec_f32_bits(mx_code)));
+}
+// x as a fixed-point number with unit 2^(B - 178) (B >= exponent of x).
 __device__ __forceinline__ long long f32_fixed(unsigned x, unsigned B) {
   const unsigned be = (x >> 23) & 0xffu;
   const long long m = be ? (long long)((x & 0x7fffffu) | 0x800000u) : (long long)(x & 0x7fffffu);
@@ -89,56 +92,25 @@ __device__ __forceinline__ long long f32_fixed(unsigned x, unsigned B) {
 __device__ __forceinline__ double fixed_to_double(long long t, unsigned B) {
   return (double)t * __longlong_as_double((long long)(1023 + (int)B - 178) << 52);
 }
-
-// Count of values, sum (int64, or double bits) and encoded min/max of
-// v[b], v[b + step], ... below e.  With step = 32 every lane of a warp calls it
-// and the caller combines the lanes with warp reductions.
-template <bool FLOAT>
-__device__ __forceinline__ void reduce_values(const unsigned* v, unsigned b, unsigned e,
-                                              unsigned step, unsigned* bmax, long long* fixed,
-                                              double* fsum, unsigned* mn, unsigned* mx) {
-  unsigned lo = 0xffffffffu, hi = 0u, B = 1u;
-  for (unsigned t = b; t < e; t += step) {
-    const unsigned x = v[t];
-    const unsigned enc = FLOAT ? enc_f32(__uint_as_float(x)) : enc_i32((int)x);
-    lo = min(lo, enc);
-    hi = max(hi, enc);
-    if (FLOAT) B = max(B, f32_exp(x));
-  }
-  *mn = lo;
-  *mx = hi;
-  *bmax = B;
-  *fsum = 0.0;
-  long long acc = 0;
-  if (!FLOAT) {
-    for (unsigned t = b; t < e; t += step) acc += (long long)(int)v[t];
-  }
-  *fixed = acc;
-}
-
-template <bool FLOAT>
-__device__ __forceinline__ long long fixed_sum(const unsigned* v, unsigned b, unsigned e,
-                                               unsigned step, unsigned B, double* fsum) {
-  long long acc = 0;
-  if (B == 255u) {  // Inf or NaN present: plain FP64 sum
-    double d = 0.0;
-    for (unsigned t = b; t < e; t += step) d += (double)__uint_as_float(v[t]);
-    *fsum = d;
-    return 0;
-  }
-  for (unsigned t = b; t < e; t += step) acc += f32_fixed(v[t], B);
-  return acc;
+// FP64 add into a shared-memory word (groups holding Inf or NaN only)
+__device__ __forceinline__ void shared_add_f64(unsigned long long* p, double v) {
+  unsigned long long old = *p, assumed;
+  do {
+    assumed = old;
+    old = atomicCAS(p, assumed,
+                    (unsigned long long)__double_as_longlong(__longlong_as_double((long long)assumed) + v));
+  } while (old != assumed);
 }
 
 template <bool FLOAT>
 __global__ void __launch_bounds__(kK1Threads, 2) k1_fused(const __grid_constant__ K1Args a) {
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned long long* hkey = reinterpret_cast<unsigned long long*>(smem);
-  unsigned short* hidx = reinterpret_cast<unsigned short*>(hkey + kK1Hash);
-  unsigned short* list = hidx + kK1Hash;
-  unsigned* lcnt = reinterpret_cast<unsigned*>(list + kK1Tile);
-  unsigned* loff = lcnt + kK1Tile;
-  unsigned* vals = loff + kK1Tile + 4;
+  unsigned long long* gsum = hkey + kK1Hash;
+  unsigned* gcnt = reinterpret_cast<unsigned*>(gsum + kK1Hash);
+  unsigned* gmn = gcnt + kK1Hash;
+  unsigned* gmx = gmn + kK1Hash;
+  unsigned short* list = reinterpret_cast<unsigned short*>(gmx + kK1Hash);
 
   __shared__ unsigned long long s_or[kMaxQueries], s_and[kMaxQueries];
   __shared__ unsigned long long s_late[kMaxQueries], s_range[kMaxQueries];
@@ -146,15 +118,17 @@ __global__ void __launch_bounds__(kK1Threads, 2) k1_fused(const __grid_constant_
   __shared__ unsigned long long s_base;
   __shared__ long long s_maxts;
   __shared__ unsigned s_err[kMaxQueries];
-  __shared__ unsigned s_nlist, s_nbig;
-  __shared__ unsigned s_wsum[kK1Warps + 1];
-  __shared__ unsigned short s_big[kK1Tile];
+  __shared__ unsigned s_nlist;
 
   const int tid = threadIdx.x;
   const unsigned lane = lane_id();
-  const int warp = tid >> 5;
-  for (int s = tid; s < kK1Hash; s += kK1Threads) hkey[s] = kEmpty;
-  for (int s = tid; s < kK1Tile; s += kK1Threads) lcnt[s] = 0u;
+  for (int s = tid; s < kK1Hash; s += kK1Threads) {
+    hkey[s] = kEmpty;
+    gsum[s] = 0ull;
+    gcnt[s] = 0u;
+    gmn[s] = 0xffffffffu;
+    gmx[s] = 0u;
+  }
   if (tid < a.nq) {
     s_or[tid] = 0ull;
     s_and[tid] = ~0ull;
@@ -166,7 +140,6 @@ __global__ void __launch_bounds__(kK1Threads, 2) k1_fused(const __grid_constant_
   if (tid == 0) {
     s_maxts = LLONG_MIN;
     s_nlist = 0u;
-    s_nbig = 0u;
   }
   __syncthreads();
 
@@ -220,7 +193,7 @@ __global__ void __launch_bounds__(kK1Threads, 2) k1_fused(const __grid_constant_
       const long long cursor = s_cursor[qi];
       unsigned n_late = 0, n_range = 0;
       unsigned slot[kK1Items];
-      // ---- A: filter, pane id, insert the group key ----
+      // ---- A: filter, pane id, insert the group key, count / min / max / exponent ----
 #pragma unroll
       for (int i = 0; i < kK1Items; ++i) {
         bool ok = valid[i];
@@ -246,8 +219,19 @@ __global__ void __launch_bounds__(kK1Threads, 2) k1_fused(const __grid_constant_
             if ((long long)prel < cursor) {  // every window of this event was emitted
               ++n_late;
             } else {
-              slot[i] = insert_key(hkey, hidx, list, &s_nlist, (prel << 32) | key[i]);
-              if (slot[i] == kNoSlot) atomicOr(&s_err[qi], kErrProbe);
+              const unsigned sl = insert_key(hkey, list, &s_nlist, (prel << 32) | key[i]);
+              if (sl == kNoSlot) {
+                atomicOr(&s_err[qi], kErrProbe);
+              } else {
+                slot[i] = sl;
+                const unsigned enc = FLOAT ? enc_f32(__uint_as_float(val[i])) : enc_i32((int)val[i]);
+                atomicMin(&gmn[sl], enc);
+                atomicMax(&gmx[sl], enc);
+                if (FLOAT)
+                  atomicAdd(&gcnt[sl], 1u);
+                else  // count and sum in one word (enc = value + 2^31)
+                  atomicAdd(&gsum[sl], (1ull << kCntShift) + (unsigned long long)enc);
+              }
             }
           }
         }
@@ -259,147 +243,62 @@ __global__ void __launch_bounds__(kK1Threads, 2) k1_fused(const __grid_constant_
         atomicAdd(&s_range[qi], (unsigned long long)n_range);
       }
       __syncthreads();
-      // ---- B: rank inside the group (one atomic per group and warp) ----
-      unsigned rank[kK1Items], gi[kK1Items];
+      // ---- B: float sums in fixed point at the group's exponent ----
+      if (FLOAT) {
 #pragma unroll
-      for (int i = 0; i < kK1Items; ++i) {
-        const bool has = slot[i] != kNoSlot;
-        gi[i] = has ? (unsigned)hidx[slot[i]] : 0xffffffffu;
-        const unsigned act = __ballot_sync(kFull, has);
-        rank[i] = 0;
-        if (has) {
-          const unsigned peers = __match_any_sync(act, gi[i]);
-          const int leader = __ffs(peers) - 1;
-          unsigned base = 0;
-          if ((int)lane == leader) base = atomicAdd(&lcnt[gi[i]], (unsigned)__popc(peers));
-          base = __shfl_sync(peers, base, leader);
-          rank[i] = base + __popc(peers & ((1u << lane) - 1u));
+        for (int i = 0; i < kK1Items; ++i) {
+          if (slot[i] == kNoSlot) continue;
+          const unsigned B = group_exp(gmn[slot[i]], gmx[slot[i]]);
+          if (B == 255u)
+            shared_add_f64(&gsum[slot[i]], (double)__uint_as_float(val[i]));
+          else
+            atomicAdd(&gsum[slot[i]], (unsigned long long)f32_fixed(val[i], B));
         }
       }
-      __syncthreads();
-      // ---- C: group ranges (scan of the counters in list order), scatter ----
       const unsigned nl = s_nlist;
-      {
-        const unsigned i0 = 2u * tid;
-        const unsigned c0 = i0 < nl ? lcnt[i0] : 0u;
-        const unsigned c1 = i0 + 1 < nl ? lcnt[i0 + 1] : 0u;
-        const unsigned x = c0 + c1;
-        unsigned inc = x;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const unsigned y = __shfl_up_sync(kFull, inc, o);
-          if ((int)lane >= o) inc += y;
-        }
-        if (lane == 31) s_wsum[warp] = inc;
-        __syncthreads();
-        if (warp == 0) {
-          const unsigned w = lane < kK1Warps ? s_wsum[lane] : 0u;
-          unsigned wi = w;
-#pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const unsigned y = __shfl_up_sync(kFull, wi, o);
-            if ((int)lane >= o) wi += y;
-          }
-          if (lane < kK1Warps) s_wsum[lane] = wi - w;
-          if (lane == kK1Warps - 1) s_wsum[kK1Warps] = wi;
-        }
-        __syncthreads();
-        const unsigned ex = s_wsum[warp] + inc - x;
-        if (i0 < nl) loff[i0] = ex;
-        if (i0 + 1 < nl) loff[i0 + 1] = ex + c0;
-        if (tid == 0) loff[nl] = s_wsum[kK1Warps];
-      }
-      __syncthreads();
-#pragma unroll
-      for (int i = 0; i < kK1Items; ++i)
-        if (slot[i] != kNoSlot) vals[loff[gi[i]] + rank[i]] = val[i];
       if (tid == 0) s_base = nl ? atomicAdd(&Q.ctl->n_parts, (unsigned long long)nl) : 0ull;
       __syncthreads();
-      // ---- D: reduce every group and append it to the partial arrays ----
+      // ---- C: append every group to the partial arrays, clear its slot ----
       const unsigned long long base = s_base;
       const bool fits = base + nl <= Q.parts_cap;
       if (tid == 0 && !fits) atomicOr(&s_err[qi], kErrPartsOverflow);
       unsigned long long o_acc = 0ull, a_acc = ~0ull;
       for (unsigned i = tid; i < nl; i += kK1Threads) {
-        const unsigned b = loff[i], e = loff[i + 1];
-        if (e - b > kBigGroup) {
-          s_big[atomicAdd(&s_nbig, 1u)] = (unsigned short)i;
-          continue;
-        }
-        const unsigned long long g = hkey[list[i]];
-        unsigned B, mn, mx;
-        long long acc;
-        double fs;
-        reduce_values<FLOAT>(vals, b, e, 1u, &B, &acc, &fs, &mn, &mx);
-        unsigned long long sb = (unsigned long long)acc;
+        const unsigned sl = list[i];
+        const unsigned long long g = hkey[sl];
+        unsigned long long sb = gsum[sl];
+        const unsigned mn = gmn[sl], mx = gmx[sl];
+        long long cnt;
         if (FLOAT) {
-          acc = fixed_sum<FLOAT>(vals, b, e, 1u, B, &fs);
-          sb = (unsigned long long)__double_as_longlong(B == 255u ? fs : fixed_to_double(acc, B));
+          cnt = (long long)gcnt[sl];
+          const unsigned B = group_exp(mn, mx);
+          if (B != 255u)
+            sb = (unsigned long long)__double_as_longlong(fixed_to_double((long long)sb, B));
+        } else {
+          cnt = (long long)(sb >> kCntShift);
+          sb = (sb & ((1ull << kCntShift) - 1ull)) - ((unsigned long long)cnt << 31);
         }
         if (fits) {
-          store_grp(Q.parts + base + i, g, (long long)(e - b), sb, mn, mx);
+          store_grp(Q.parts + base + i, g, cnt, sb, mn, mx);
           Q.pkeys[base + i] = g;
         }
         o_acc |= g;
         a_acc &= g;
-      }
-      __syncthreads();
-      const unsigned nbig = s_nbig;
-      for (unsigned bi = warp; bi < nbig; bi += kK1Warps) {
-        const unsigned i = s_big[bi];
-        const unsigned b = loff[i], e = loff[i + 1];
-        unsigned B, mn, mx;
-        long long acc;
-        double fs;
-        reduce_values<FLOAT>(vals, b + lane, e, 32u, &B, &acc, &fs, &mn, &mx);
-        mn = __reduce_min_sync(kFull, mn);
-        mx = __reduce_max_sync(kFull, mx);
-        unsigned long long sb;
-        if (FLOAT) {
-          B = __reduce_max_sync(kFull, B);
-          acc = fixed_sum<FLOAT>(vals, b + lane, e, 32u, B, &fs);
-          if (B == 255u) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) fs += __shfl_xor_sync(kFull, fs, o);
-            sb = (unsigned long long)__double_as_longlong(fs);
-          } else {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-            sb = (unsigned long long)__double_as_longlong(fixed_to_double(acc, B));
-          }
-        } else {
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-          sb = (unsigned long long)acc;
-        }
-        if (lane == 0) {
-          const unsigned long long g = hkey[list[i]];
-          if (fits) {
-            store_grp(Q.parts + base + i, g, (long long)(e - b), sb, mn, mx);
-            Q.pkeys[base + i] = g;
-          }
-          o_acc |= g;
-          a_acc &= g;
-        }
+        hkey[sl] = kEmpty;
+        gsum[sl] = 0ull;
+        gcnt[sl] = 0u;
+        gmn[sl] = 0xffffffffu;
+        gmx[sl] = 0u;
       }
       const unsigned olo = __reduce_or_sync(kFull, (unsigned)o_acc);
       const unsigned ohi = __reduce_or_sync(kFull, (unsigned)(o_acc >> 32));
       const unsigned alo = __reduce_and_sync(kFull, (unsigned)a_acc);
       const unsigned ahi = __reduce_and_sync(kFull, (unsigned)(a_acc >> 32));
-      if (lane == 0) {
+      if (lane == 0 && nl) {
         atomicOr(&s_or[qi], ((unsigned long long)ohi << 32) | olo);
         atomicAnd(&s_and[qi], ((unsigned long long)ahi << 32) | alo);
       }
-      __syncthreads();
-      // ---- reset the table for the next tile / query ----
-      for (unsigned i = tid; i < nl; i += kK1Threads) {
-        hkey[list[i]] = kEmpty;
-        lcnt[i] = 0u;
-      }
-      if (tid == 0) {
-        s_nlist = 0u;
-        s_nbig = 0u;
-      }
+      if (tid == 0) s_nlist = 0u;
       __syncthreads();
     }
   }

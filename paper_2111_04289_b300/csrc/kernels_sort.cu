@@ -199,51 +199,6 @@ constexpr unsigned long long kLongRun = 4096;
 constexpr int kRbkItems = 4;
 constexpr int kRbkTile = 256 * kRbkItems;
 
-struct SegAgg {  // (run started here?, aggregate since the run's head, run's output index)
-  unsigned f;
-  long long cnt;
-  unsigned long long sum;
-  unsigned mn, mx;
-  unsigned long long rank;
-};
-
-template <bool FLOAT>
-__device__ __forceinline__ SegAgg seg_combine(const SegAgg& x, const SegAgg& y) {
-  if (y.f) return y;  // y's run starts inside y: x does not reach past it
-  SegAgg r;
-  r.f = x.f;
-  r.cnt = x.cnt + y.cnt;
-  r.sum = FLOAT ? (unsigned long long)__double_as_longlong(__longlong_as_double((long long)x.sum) +
-                                                           __longlong_as_double((long long)y.sum))
-                : x.sum + y.sum;
-  r.mn = min(x.mn, y.mn);
-  r.mx = max(x.mx, y.mx);
-  r.rank = x.rank;
-  return r;
-}
-
-__device__ __forceinline__ SegAgg seg_identity() {
-  SegAgg r;
-  r.f = 0;
-  r.cnt = 0;
-  r.sum = 0ull;  // +0.0 for doubles
-  r.mn = 0xffffffffu;
-  r.mx = 0u;
-  r.rank = 0ull;
-  return r;
-}
-
-__device__ __forceinline__ SegAgg seg_shfl_up(const SegAgg& v, int d) {
-  SegAgg r;
-  r.f = __shfl_up_sync(kFull, v.f, d);
-  r.cnt = __shfl_up_sync(kFull, v.cnt, d);
-  r.sum = __shfl_up_sync(kFull, v.sum, d);
-  r.mn = __shfl_up_sync(kFull, v.mn, d);
-  r.mx = __shfl_up_sync(kFull, v.mx, d);
-  r.rank = __shfl_up_sync(kFull, v.rank, d);
-  return r;
-}
-
 // first index in [a, b) whose key differs from k (keys sorted, keys[a-1..] >= k)
 __device__ unsigned long long first_after(const unsigned long long* keys, unsigned long long a,
                                           unsigned long long b, unsigned long long k) {

@@ -127,6 +127,53 @@ __device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long
   return r;
 }
 
+// ---- segmented scans (reduce-by-key, window rows) ----------------------
+
+struct SegAgg {  // (run started here?, aggregate since the run's head, run's output index)
+  unsigned f;
+  long long cnt;
+  unsigned long long sum;
+  unsigned mn, mx;
+  unsigned long long rank;
+};
+
+template <bool FLOAT>
+__device__ __forceinline__ SegAgg seg_combine(const SegAgg& x, const SegAgg& y) {
+  if (y.f) return y;  // y's run starts inside y: x does not reach past it
+  SegAgg r;
+  r.f = x.f;
+  r.cnt = x.cnt + y.cnt;
+  r.sum = FLOAT ? (unsigned long long)__double_as_longlong(__longlong_as_double((long long)x.sum) +
+                                                           __longlong_as_double((long long)y.sum))
+                : x.sum + y.sum;
+  r.mn = min(x.mn, y.mn);
+  r.mx = max(x.mx, y.mx);
+  r.rank = x.rank;
+  return r;
+}
+
+__device__ __forceinline__ SegAgg seg_identity() {
+  SegAgg r;
+  r.f = 0;
+  r.cnt = 0;
+  r.sum = 0ull;  // +0.0 for doubles
+  r.mn = 0xffffffffu;
+  r.mx = 0u;
+  r.rank = 0ull;
+  return r;
+}
+
+__device__ __forceinline__ SegAgg seg_shfl_up(const SegAgg& v, int d) {
+  SegAgg r;
+  r.f = __shfl_up_sync(kFull, v.f, d);
+  r.cnt = __shfl_up_sync(kFull, v.cnt, d);
+  r.sum = __shfl_up_sync(kFull, v.sum, d);
+  r.mn = __shfl_up_sync(kFull, v.mn, d);
+  r.mx = __shfl_up_sync(kFull, v.mx, d);
+  r.rank = __shfl_up_sync(kFull, v.rank, d);
+  return r;
+}
+
 // Contiguous chunk [lo, hi) of n items owned by chunk c of g chunks.
 __device__ __forceinline__ void chunk_range(unsigned long long n, int c, int g,
                                             unsigned long long* lo, unsigned long long* hi) {
