@@ -334,6 +334,81 @@ def run_serving(args, lm, synth, local):
     return serving
 
 
+def run_small_configs(args, torch, lm, synth, dev, local):
+    """Two more workloads, device-resident input, graph replay on (default) and
+    off: the tiny int stream (100 micro-batches of 65,536 events, type == 0,
+    tumbling 10 s, count + sum) and eight fused queries on one stream (key
+    Zipf(1.3) over 1e6, value lognormal; filters value > 10.24 / 3.602 / 1.0 /
+    0.2776 (selectivity 1 / 10 / 50 / 90 %) x windows tumbling 10 s and sliding
+    30 s / 1 s; ts at 1e7 events/s; 24 micro-batches log-uniform in 2^12..2^24)."""
+    import numpy as np
+
+    out = {}
+    g = torch.Generator(device=dev)
+    g.manual_seed(synth.BASE_SEED + 300)
+    # tiny int stream
+    nb, n = 100, 65_536
+    gaps = torch.randint(0, 6, (nb * n,), device=dev, generator=g, dtype=torch.int64)
+    ts = torch.cumsum(gaps, 0)
+    key = torch.randint(0, 1024, (nb * n,), device=dev, generator=g, dtype=torch.int32)
+    val = torch.randint(0, 1000, (nb * n,), device=dev, generator=g, dtype=torch.int32)
+    typ = torch.randint(0, 3, (nb * n,), device=dev, generator=g, dtype=torch.uint8)
+    tiny = {}
+    for mode, gm in (("graph", lm.GRAPH_ON), ("plain_launches", lm.GRAPH_OFF)):
+        s = lm.Stream("int32", has_type=True, device=local, graph_mode=gm)
+        qid = s.register_query(10_000, 0, "type", "eq", 0)
+        for i in range(3):  # warm-up on the stream's own buffers
+            sl = slice(i * n, (i + 1) * n)
+            s.push(ts[sl], key[sl], val[sl], typ[sl])
+            s.discard(qid)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(3, nb):
+            sl = slice(i * n, (i + 1) * n)
+            s.push(ts[sl], key[sl], val[sl], typ[sl])
+            s.discard(qid)
+        dt = time.perf_counter() - t0
+        st = s.stats()
+        s.close()
+        tiny[mode] = {"events_per_s": (nb - 3) * n / dt, "ms_per_batch": 1e3 * dt / (nb - 3),
+                      "graph_launches": st["graph_launches"]}
+    out["tiny_int_stream"] = tiny
+    del ts, key, val, typ
+    # eight fused queries, uneven batches
+    rng = np.random.default_rng(synth.BASE_SEED + 301)
+    sizes = [int(2 ** x) for x in rng.uniform(12, 24, 24)]
+    total = sum(sizes)
+    zipf = synth.ZipfKeys(1_000_000, 1.3)
+    keys = torch.from_numpy(zipf.sample(rng, total).astype(np.int32)).to(dev)
+    vals = torch.exp(torch.randn(total, device=dev, generator=g)).to(torch.float32)
+    tss = torch.arange(total, device=dev, dtype=torch.int64) // 10_000
+    fused = {}
+    for mode, gm in (("graph", lm.GRAPH_ON), ("plain_launches", lm.GRAPH_OFF)):
+        s = lm.Stream("float32", device=local, graph_mode=gm, enable_timing=True)
+        for theta in (10.24, 3.602, 1.0, 0.2776):
+            s.register_query(10_000, 0, "value", "gt", theta)
+            s.register_query(30_000, 1_000, "value", "gt", theta)
+        warm = 4
+        off = 0
+        for i, m in enumerate(sizes):
+            if i == warm:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                ev0 = off
+            s.push(tss[off:off + m], keys[off:off + m], vals[off:off + m])
+            for q in range(8):
+                s.discard(q)
+            off += m
+        dt = time.perf_counter() - t0
+        st = s.stats()
+        s.close()
+        fused[mode] = {"events_per_s": (off - ev0) / dt, "batches": len(sizes) - warm,
+                       "graph_launches": st["graph_launches"], "k1_tile_events": st["k1_tile_events"],
+                       "autotune_samples": st["autotune_samples"]}
+    out["eight_fused_queries"] = fused
+    return out
+
+
 def run_profile_serving(args):
     """A fixed serving-like load for profilers: `--profile-batches` micro-batches
     of `--profile-events` events (ts = arrival ms at 2e8 events/s, columns in
@@ -459,6 +534,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     if args.plain_e2e:
         plain["e2e"] = run_e2e(args, torch, lm, synth, dev, local, rank, world, dist)
+    if not args.no_small:
+        line["other_workloads"] = run_small_configs(args, torch, lm, synth, dev, local)
     if not args.no_serve:
         sampler = ClockSampler(local)
         sampler.start()
@@ -544,6 +621,7 @@ def main():
     ap.add_argument("--plain-e2e", action="store_true",
                     help="also time the kernel step through host buffers")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-small", action="store_true")
     ap.add_argument("--serve-duration-ms", type=float, default=20_000.0)
     ap.add_argument("--start-device", type=float, default=4.0)
     ap.add_argument("--start-host", type=float, default=2.0)

@@ -105,9 +105,18 @@ typedef struct lms_stream_config {
                                   are kept relative to it: events must satisfy
                                   |floor(ts/slide) - floor(origin_ts/slide)| < 2^31 - 1,
                                   others are dropped and counted (stats.range_rows). */
-  int32_t k1_variant;          /* 0 = default (= 1); 1 = no warp aggregation; 2 = warp match_any aggregation */
-  int32_t reserved[7];
+  int32_t k1_variant;          /* fused-pass tile: 0 = autotuned per batch-size class,
+                                  1 = 1024 events (two CTAs per SM), 2 = 2048 events (one) */
+  int32_t graph_mode;          /* LMS_GRAPH_*: replay the per-batch launch sequence from a CUDA graph */
+  int32_t reserved[6];
 } lms_stream_config;
+
+/* graph_mode.  Everything a push launches after the fused pass reads its sizes
+ * on the device, so the sequence is captured once into a CUDA graph and
+ * replayed; a new capture follows every reallocation of a stream buffer. */
+#define LMS_GRAPH_DEFAULT 0 /* = LMS_GRAPH_ON */
+#define LMS_GRAPH_OFF 1     /* plain launches */
+#define LMS_GRAPH_ON 2
 
 typedef struct lms_query_spec {
   int32_t filter_col;     /* LMS_COL_* */
@@ -167,6 +176,10 @@ typedef struct lms_stats {
   double e2_ms;            /* window assembly + row write */
   uint64_t partials;       /* partial groups written by the fused pass (all batches, queries) */
   uint64_t groups_built;   /* window-state groups produced by the reduce (all batches, queries) */
+  uint64_t graph_launches; /* pushes whose tail ran as one CUDA graph launch */
+  uint64_t graph_captures; /* graph (re)captures */
+  uint64_t k1_tile_events; /* tile of the last fused pass */
+  uint64_t autotune_samples; /* fused passes timed by the autotuner */
 } lms_stats;
 
 /* Opens a stream on cfg->device.  Defined by the paper's problem statement

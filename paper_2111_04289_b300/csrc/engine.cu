@@ -73,8 +73,21 @@ struct QueryHost {
 
 }  // namespace
 
+namespace {
+struct GraphSlot {  // captured tail of a push
+  cudaGraphExec_t exec = nullptr;
+  unsigned long long gen = 0;
+  int timing = 0;
+  int launches = 0;
+};
+}  // namespace
+
 struct lms_stream {
   lms_stream_config cfg{};
+  unsigned long long gen = 0;  // bumped by every device allocation (pointers change)
+  unsigned long long gen_prev = ~0ull;
+  bool graph_ok = true;
+  GraphSlot graphs[1];
   cudaStream_t st = nullptr;
   bool own_stream = false;
   int sms = 148;
@@ -96,6 +109,14 @@ struct lms_stream {
   unsigned long long dev_bytes = 0;
   std::vector<std::pair<void*, size_t>> allocs;
   cudaEvent_t ev[8] = {};
+  cudaEvent_t tev[2] = {};  // around the fused pass while the autotuner samples
+  // K1 autotuner: per batch-size class (log2 of the rows), time per event of
+  // each tile shape, and the chosen shape once both were sampled
+  struct Tune {
+    double ms_per_row[3] = {0, 0, 0};
+    int samples[3] = {0, 0, 0};
+    int choice = 0;
+  } tune[48];
   cudaEvent_t qev[kMaxQueries][6] = {};  // E1, E2, sort/reduce
   lms_stats stats{};
   long long wm = LLONG_MIN;
@@ -133,6 +154,7 @@ lms_status dalloc(lms_stream* s, void** p, size_t bytes) {
   }
   s->dev_bytes += bytes;
   s->allocs.emplace_back(*p, bytes);
+  s->gen += 1;
   return LMS_OK;
 }
 
@@ -268,6 +290,35 @@ lms_status read_ctls(lms_stream* s, QCtl* h) {
   return LMS_OK;
 }
 
+// The fused pass's tile shape for a batch of n rows: the configured one, or the
+// autotuner's.  Below 2^15 rows the 1024-event tile is used; above, each
+// size class (log2 n) first runs each shape kSamples times (timed with CUDA
+// events) and then keeps the faster per row.  Results do not depend on it.
+constexpr int kTuneSamples = 2;
+
+int pick_k1_variant(lms_stream* s, long long n, bool* tuning) {
+  *tuning = false;
+  if (s->cfg.k1_variant == 1 || s->cfg.k1_variant == 2) return s->cfg.k1_variant;
+  if (n < (1ll << 15)) return 1;
+  int b = 0;
+  while ((1ll << (b + 1)) <= n && b < 47) ++b;
+  lms_stream::Tune& t = s->tune[b];
+  if (t.choice) return t.choice;
+  *tuning = true;
+  return t.samples[1] <= t.samples[2] ? 1 : 2;
+}
+
+void record_k1_sample(lms_stream* s, long long n, int variant, float ms) {
+  int b = 0;
+  while ((1ll << (b + 1)) <= n && b < 47) ++b;
+  lms_stream::Tune& t = s->tune[b];
+  t.ms_per_row[variant] += (double)ms / (double)n;
+  t.samples[variant] += 1;
+  s->stats.autotune_samples += 1;
+  if (t.samples[1] >= kTuneSamples && t.samples[2] >= kTuneSamples)
+    t.choice = t.ms_per_row[2] / t.samples[2] < t.ms_per_row[1] / t.samples[1] ? 2 : 1;
+}
+
 }  // namespace
 
 extern "C" {
@@ -285,6 +336,7 @@ lms_status stream_open(const lms_stream_config* cfg, lms_stream** out) {
   if (!cfg || !out) return LMS_EINVAL;
   if (cfg->value_type != LMS_VALUE_INT32 && cfg->value_type != LMS_VALUE_FLOAT32) return LMS_EINVAL;
   if (cfg->allowed_lateness_ms < 0 || cfg->max_batch_rows < 0) return LMS_EINVAL;
+  if (cfg->graph_mode < LMS_GRAPH_DEFAULT || cfg->graph_mode > LMS_GRAPH_ON) return LMS_EINVAL;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
     cudaGetLastError();
@@ -327,6 +379,7 @@ lms_status stream_open(const lms_stream_config* cfg, lms_stream** out) {
   }
   s->scr.chunk = static_cast<unsigned long long*>(p);
   for (int i = 0; i < 8; ++i) cudaEventCreate(&s->ev[i]);
+  for (int i = 0; i < 2; ++i) cudaEventCreate(&s->tev[i]);
   for (int i = 0; i < kMaxQueries; ++i)
     for (int j = 0; j < 6; ++j) cudaEventCreate(&s->qev[i][j]);
   s->stats.watermark = LLONG_MIN;
@@ -434,6 +487,8 @@ lms_status push_microbatch(lms_stream* s, const lms_batch* b) {
   }
   if (timing) LMS_CK(cudaEventRecord(s->ev[5], s->st));
   int launches = 0;
+  int variant = 1;
+  bool tuning = false;
   QCtl* ctls[kMaxQueries];
   const int nq = (int)s->qs.size();
   for (int i = 0; i < nq; ++i) ctls[i] = s->qs[i].dev.ctl;
@@ -451,37 +506,92 @@ lms_status push_microbatch(lms_stream* s, const lms_batch* b) {
     a.value_is_float = s->cfg.value_type == LMS_VALUE_FLOAT32;
     a.sctl = s->sctl;
     for (int i = 0; i < nq; ++i) a.q[i] = s->qs[i].dev;
-    const long long ntiles = (n + k1_tile_events() - 1) / k1_tile_events();
-    const int grid = (int)std::min<long long>(ntiles, k1_max_grid(s->cfg.device, 0, 0));
-    LMS_CK(launch_k1(a, s->cfg.k1_variant, grid, s->st));
+    variant = pick_k1_variant(s, n, &tuning);
+    const long long ntiles = (n + k1_tile_events(variant) - 1) / k1_tile_events(variant);
+    const int grid = (int)std::min<long long>(ntiles, k1_max_grid(s->cfg.device, variant, 0));
+    if (tuning) LMS_CK(cudaEventRecord(s->tev[0], s->st));
+    LMS_CK(launch_k1(a, variant, grid, s->st));
+    if (tuning) LMS_CK(cudaEventRecord(s->tev[1], s->st));
     ++launches;
     ++s->stats.k1_launches;
+    s->stats.k1_tile_events = (uint64_t)k1_tile_events(variant);
   }
   if (timing) LMS_CK(cudaEventRecord(s->ev[2], s->st));
   std::vector<QueryDev> qd(nq);
   for (int i = 0; i < nq; ++i) qd[i] = s->qs[i].dev;
-  LMS_CK(launch_watermark(s->sctl, qd.data(), nq, s->cfg.allowed_lateness_ms, eos, s->st));
-  ++launches;
   // emission needs window/pool/row buffers; make sure something exists
   if ((r = ensure_windows(s, 1024)) != LMS_OK) return r;
   if ((r = ensure_pool(s, 1ull << 16)) != LMS_OK) return r;
   for (QueryHost& q : s->qs)
     if ((r = ensure_rows(s, q, q.row_base + 4096)) != LMS_OK) return r;
-  // per query, back to back (they share the scratch): sort/reduce into the
-  // window state, pane index, emission of closed windows, carry of open panes
-  for (int i = 0; i < nq; ++i) {
-    QueryHost& q = s->qs[i];
-    if (timing) LMS_CK(cudaEventRecord(s->qev[i][4], s->st));
-    LMS_CK(launch_sort_reduce(qd[i], s->scr, s->st, &launches));
-    if (timing) LMS_CK(cudaEventRecord(s->qev[i][5], s->st));
-    LMS_CK(launch_pane_index(q.dev, s->scr, s->st, &launches));
-    LMS_CK(launch_emit(q.dev, s->scr, q.rows, q.rows_cap, s->sms, s->st, &launches,
-                       timing ? s->qev[i] : nullptr));
-    LMS_CK(launch_trim(q.dev, s->scr, s->sms, s->st, &launches));
+  // (Timing events inside the tail are recorded as external event nodes so that
+  // a replayed graph still records them.)
+  // The rest of the batch's work — watermark, then per query (back to back:
+  // they share the scratch) sort/reduce into the window state, pane index,
+  // emission of closed windows, carry of open panes — reads every size on the
+  // device, so it is the same launch sequence for every batch until a buffer
+  // is reallocated: it is captured once into a CUDA graph and replayed.
+  auto enqueue_tail = [&](int* nl) -> cudaError_t {
+    cudaError_t e = launch_watermark(s->sctl, qd.data(), nq, s->cfg.allowed_lateness_ms, eos, s->st);
+    ++*nl;
+    for (int i = 0; i < nq && e == cudaSuccess; ++i) {
+      QueryHost& q = s->qs[i];
+      if (timing && (e = record_event(s->qev[i][4], s->st)) != cudaSuccess) break;
+      if ((e = launch_sort_reduce(qd[i], s->scr, s->st, nl)) != cudaSuccess) break;
+      if (timing && (e = record_event(s->qev[i][5], s->st)) != cudaSuccess) break;
+      if ((e = launch_pane_index(q.dev, s->scr, s->st, nl)) != cudaSuccess) break;
+      if ((e = launch_emit(q.dev, s->scr, q.rows, q.rows_cap, s->sms, s->st, nl,
+                           timing ? s->qev[i] : nullptr)) != cudaSuccess)
+        break;
+      e = launch_trim(q.dev, s->scr, s->sms, s->st, nl);
+    }
+    if (e == cudaSuccess && timing) e = record_event(s->ev[4], s->st);
+    return e;
+  };
+  // Replay only once the buffers are stable (the previous push saw the same
+  // ones), and not for the one-off end-of-stream push; the first launches of
+  // a stream also run plainly, so one-time kernel set-up never happens inside
+  // a capture.
+  const bool stable = s->gen == s->gen_prev;
+  s->gen_prev = s->gen;
+  GraphSlot& g = s->graphs[0];
+  bool use_graph = s->cfg.graph_mode != LMS_GRAPH_OFF && stable && !eos && s->graph_ok;
+  if (use_graph && (!g.exec || g.gen != s->gen || g.timing != (int)timing)) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+    if (cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();  // this stream cannot be captured (e.g. a legacy stream)
+      s->graph_ok = false;
+      use_graph = false;
+    } else {
+      cudaGraph_t graph = nullptr;
+      int nl = 0;
+      const cudaError_t ce = enqueue_tail(&nl);
+      const cudaError_t ee = cudaStreamEndCapture(s->st, &graph);
+      LMS_CK(ce);
+      LMS_CK(ee);
+      const cudaError_t ie = cudaGraphInstantiate(&g.exec, graph, 0);
+      cudaGraphDestroy(graph);
+      LMS_CK(ie);
+      g.gen = s->gen;
+      g.timing = (int)timing;
+      g.launches = nl;
+      s->stats.graph_captures += 1;
+    }
   }
-  if (timing) LMS_CK(cudaEventRecord(s->ev[4], s->st));
+  if (use_graph) {
+    LMS_CK(cudaGraphLaunch(g.exec, s->st));
+    launches += g.launches;
+    s->stats.graph_launches += 1;
+  } else {
+    LMS_CK(enqueue_tail(&launches));
+  }
   std::vector<QCtl> hc(nq);
   if ((r = read_ctls(s, hc.data())) != LMS_OK) return r;
+  if (tuning) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, s->tev[0], s->tev[1]) == cudaSuccess) record_k1_sample(s, n, variant, ms);
+  }
   // retry emission for queries whose buffers were too small
   bool retried = false;
   for (int i = 0; i < nq; ++i) {
@@ -540,6 +650,7 @@ lms_status push_microbatch(lms_stream* s, const lms_batch* b) {
     cudaEventElapsedTime(&a, s->ev[0], s->ev[5]);
     cudaEventElapsedTime(&bms, s->ev[1], s->ev[2]);
     cudaEventElapsedTime(&all, s->ev[2], s->ev[4]);
+    cudaGetLastError();  // a failed timing read must not poison later calls
     s->stats.h2d_ms += a;
     s->stats.k1_ms += bms;
     s->stats.sort_ms += sort_ms;
@@ -552,6 +663,7 @@ lms_status push_microbatch(lms_stream* s, const lms_batch* b) {
         s->stats.e1_ms += e1;
         s->stats.e2_ms += e2;
       }
+      cudaGetLastError();
     }
   }
   s->stats.batches += 1;
@@ -723,8 +835,12 @@ lms_status stream_close(lms_stream* s) {
     if (s->st) cudaStreamSynchronize(s->st);
     for (auto& a : s->allocs) cudaFree(a.first);
     s->allocs.clear();
+    for (GraphSlot& g : s->graphs)
+      if (g.exec) cudaGraphExecDestroy(g.exec);
     for (int i = 0; i < 8; ++i)
       if (s->ev[i]) cudaEventDestroy(s->ev[i]);
+    for (int i = 0; i < 2; ++i)
+      if (s->tev[i]) cudaEventDestroy(s->tev[i]);
     for (int i = 0; i < kMaxQueries; ++i)
       for (int j = 0; j < 6; ++j)
         if (s->qev[i][j]) cudaEventDestroy(s->qev[i][j]);

@@ -750,13 +750,13 @@ cudaError_t launch_emit(const QueryDev& q, const Scratch& s, ResultRowDev* rows,
   const size_t smem = q.k > 1 ? emit_smem(q.k) : 0;
   const int grid = q.k > 1 ? sms : 4 * sms;
   if (ev4) {
-    cudaEventRecord(ev4[0], st);
-    cudaEventRecord(ev4[1], st);
-    cudaEventRecord(ev4[2], st);
+    record_event(ev4[0], st);
+    record_event(ev4[1], st);
+    record_event(ev4[2], st);
   }
   cudaError_t e = q.value_is_float ? launch_emit_t<true>(q, s, rows, grid, smem, rows_cap, st)
                                    : launch_emit_t<false>(q, s, rows, grid, smem, rows_cap, st);
-  if (ev4) cudaEventRecord(ev4[3], st);
+  if (ev4) record_event(ev4[3], st);
   if (launches) *launches += 5;
   return e;
 }

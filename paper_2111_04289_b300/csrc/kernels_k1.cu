@@ -16,7 +16,7 @@
 //   B. (float32 values) every event adds its value to the group's sum as a
 //      64-bit fixed-point number whose unit is 2^(B-178), B the largest
 //      exponent in the group (that of its min or its max; the largest value
-//      occupies bits 28..51, so 2^11 of them cannot overflow): integer adds,
+//      occupies bits 28..51, so 2^11 of them cannot overflow int64): integer adds,
 //      so the sum is exact and independent of the order; it is converted to
 //      double once.  The error is at most 2^-41 of the group's largest
 //      |value| (FP64 is slow on this part; a group holding Inf or NaN is
@@ -30,27 +30,34 @@
 namespace lms {
 namespace {
 
-constexpr int kK1Threads = 512;                  // two CTAs per SM
-constexpr int kK1Items = 2;                      // events per thread per tile
-constexpr int kK1Tile = kK1Threads * kK1Items;   // 1024 events
-constexpr int kK1HashBits = 11;                  // 2048 slots >= 2 * tile
-constexpr int kK1Hash = 1 << kK1HashBits;
+// Two tile shapes (the autotuner in the engine picks one per batch-size
+// class): ITEMS events per thread, 512 threads, a table of 4 * ITEMS * 512
+// slots (load factor <= 1/2).  ITEMS = 2: 1024-event tiles, two CTAs per SM;
+// ITEMS = 4: 2048-event tiles (fewer partial groups), one CTA per SM.
+constexpr int kK1Threads = 512;
 constexpr unsigned kNoSlot = 0xffffffffu;
-
-// hkey u64[H] | gsum u64[H] | gcnt u32[H] | gmn u32[H] | gmx u32[H] | list u16[T]
-constexpr size_t kK1Smem = (size_t)kK1Hash * (8 + 8 + 4 + 4 + 4) + kK1Tile * 2;
+template <int ITEMS> struct K1Shape {
+  static constexpr int kTile = kK1Threads * ITEMS;
+  static constexpr int kHashBits = ITEMS == 2 ? 11 : 12;
+  static constexpr int kHash = 1 << kHashBits;
+  // hkey u64[H] | gsum u64[H] | gcnt u32[H] | gmn u32[H] | gmx u32[H] | list u16[T]
+  static constexpr size_t kSmem = (size_t)kHash * (8 + 8 + 4 + 4 + 4) + kTile * 2;
+  static constexpr int kCtasPerSm = ITEMS == 2 ? 2 : 1;
+};
 
 // Int32 values: count and sum share one 64-bit word: each event adds
-// 2^42 + (value + 2^31), so count = word >> 42 and sum = low 42 bits - count * 2^31
-// (at most 1024 events of at most 2^32 each: the low part stays below 2^42).
-constexpr int kCntShift = 42;
+// 2^43 + (value + 2^31), so count = word >> 43 and sum = low 43 bits - count * 2^31
+// (at most 2048 events of at most 2^32 each: the low part stays below 2^43).
+constexpr int kCntShift = 43;
 
 // Phase A: the slot of group key g (inserted if new).  Returns the slot, or
 // kNoSlot if the probe bound is hit (cannot happen: a tile has <= H/2 groups).
+template <int BITS>
 __device__ __forceinline__ unsigned insert_key(unsigned long long* hkey, unsigned short* list,
                                                unsigned* nlist, unsigned long long g) {
-  unsigned slot = hash_slot(g, kK1HashBits);
-  for (int probes = 0; probes < kK1Hash; ++probes) {
+  constexpr int H = 1 << BITS;
+  unsigned slot = hash_slot(g, BITS);
+  for (int probes = 0; probes < H; ++probes) {
     const unsigned long long cur = *((volatile unsigned long long*)&hkey[slot]);
     if (cur == g) return slot;
     if (cur == kEmpty) {
@@ -62,7 +69,7 @@ __device__ __forceinline__ unsigned insert_key(unsigned long long* hkey, unsigne
       }
       if (prev == g) return slot;
     }
-    slot = (slot + 1) & (kK1Hash - 1);
+    slot = (slot + 1) & (H - 1);
   }
   return kNoSlot;
 }
@@ -102,8 +109,13 @@ __device__ __forceinline__ void shared_add_f64(unsigned long long* p, double v) 
   } while (old != assumed);
 }
 
-template <bool FLOAT>
-__global__ void __launch_bounds__(kK1Threads, 2) k1_fused(const __grid_constant__ K1Args a) {
+template <bool FLOAT, int ITEMS>
+__global__ void __launch_bounds__(kK1Threads, K1Shape<ITEMS>::kCtasPerSm)
+    k1_fused(const __grid_constant__ K1Args a) {
+  constexpr int kK1Items = ITEMS;
+  constexpr int kK1Tile = K1Shape<ITEMS>::kTile;
+  constexpr int kK1HashBits = K1Shape<ITEMS>::kHashBits;
+  constexpr int kK1Hash = K1Shape<ITEMS>::kHash;
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned long long* hkey = reinterpret_cast<unsigned long long*>(smem);
   unsigned long long* gsum = hkey + kK1Hash;
@@ -158,18 +170,34 @@ __global__ void __launch_bounds__(kK1Threads, 2) k1_fused(const __grid_constant_
     unsigned key[kK1Items], val[kK1Items], typ[kK1Items];
     bool valid[kK1Items];
     if (vec_ok && e0 + kK1Items <= n) {
-      const longlong2 t01 = __ldcs(reinterpret_cast<const longlong2*>(a.ts + e0));
-      const uint2 k2 = __ldcs(reinterpret_cast<const uint2*>(a.key + e0));
-      const uint2 v2 =
-          __ldcs(reinterpret_cast<const uint2*>(static_cast<const unsigned*>(a.value) + e0));
-      ts[0] = t01.x; ts[1] = t01.y;
-      key[0] = k2.x; key[1] = k2.y;
-      val[0] = v2.x; val[1] = v2.y;
-      const unsigned t2 =
-          a.type ? (unsigned)__ldcs(reinterpret_cast<const unsigned short*>(a.type + e0)) : 0u;
+#pragma unroll
+      for (int h = 0; h < kK1Items; h += 2) {
+        const longlong2 t01 = __ldcs(reinterpret_cast<const longlong2*>(a.ts + e0 + h));
+        ts[h] = t01.x;
+        ts[h + 1] = t01.y;
+      }
+      unsigned t4 = 0u;
+      if (kK1Items == 2) {
+        const uint2 k2 = __ldcs(reinterpret_cast<const uint2*>(a.key + e0));
+        const uint2 v2 =
+            __ldcs(reinterpret_cast<const uint2*>(static_cast<const unsigned*>(a.value) + e0));
+        key[0] = k2.x; key[1] = k2.y;
+        val[0] = v2.x; val[1] = v2.y;
+        if (a.type) t4 = (unsigned)__ldcs(reinterpret_cast<const unsigned short*>(a.type + e0));
+      } else {
+#pragma unroll
+        for (int h = 0; h < kK1Items; h += 4) {
+          const uint4 k4 = __ldcs(reinterpret_cast<const uint4*>(a.key + e0 + h));
+          const uint4 v4 = __ldcs(
+              reinterpret_cast<const uint4*>(static_cast<const unsigned*>(a.value) + e0 + h));
+          key[h] = k4.x; key[h + 1] = k4.y; key[h + 2] = k4.z; key[h + 3] = k4.w;
+          val[h] = v4.x; val[h + 1] = v4.y; val[h + 2] = v4.z; val[h + 3] = v4.w;
+        }
+        if (a.type) t4 = __ldcs(reinterpret_cast<const unsigned*>(a.type + e0));
+      }
 #pragma unroll
       for (int i = 0; i < kK1Items; ++i) {
-        typ[i] = (t2 >> (8 * i)) & 0xffu;
+        typ[i] = (t4 >> (8 * (i & 3))) & 0xffu;
         valid[i] = true;
       }
     } else {
@@ -219,7 +247,8 @@ __global__ void __launch_bounds__(kK1Threads, 2) k1_fused(const __grid_constant_
             if ((long long)prel < cursor) {  // every window of this event was emitted
               ++n_late;
             } else {
-              const unsigned sl = insert_key(hkey, list, &s_nlist, (prel << 32) | key[i]);
+              const unsigned sl =
+                  insert_key<kK1HashBits>(hkey, list, &s_nlist, (prel << 32) | key[i]);
               if (sl == kNoSlot) {
                 atomicOr(&s_err[qi], kErrProbe);
               } else {
@@ -322,31 +351,33 @@ __global__ void __launch_bounds__(kK1Threads, 2) k1_fused(const __grid_constant_
   }
 }
 
-template <bool FLOAT>
+template <bool FLOAT, int ITEMS>
 cudaError_t launch_k1_t(const K1Args& a, int grid, cudaStream_t st) {
   // once per process and instantiation (thread-safe static initialisation)
-  static const cudaError_t attr = cudaFuncSetAttribute(
-      k1_fused<FLOAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kK1Smem);
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(k1_fused<FLOAT, ITEMS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)K1Shape<ITEMS>::kSmem);
   if (attr != cudaSuccess) return attr;
-  k1_fused<FLOAT><<<grid, kK1Threads, kK1Smem, st>>>(a);
+  k1_fused<FLOAT, ITEMS><<<grid, kK1Threads, K1Shape<ITEMS>::kSmem, st>>>(a);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_k1(const K1Args& a, int variant, int grid, cudaStream_t st) {
-  (void)variant;  // a single variant; the config field is kept for ABI stability
-  return a.value_is_float ? launch_k1_t<true>(a, grid, st) : launch_k1_t<false>(a, grid, st);
+  if (variant == 2)
+    return a.value_is_float ? launch_k1_t<true, 4>(a, grid, st) : launch_k1_t<false, 4>(a, grid, st);
+  return a.value_is_float ? launch_k1_t<true, 2>(a, grid, st) : launch_k1_t<false, 2>(a, grid, st);
 }
 
-int k1_tile_events() { return kK1Tile; }
+int k1_tile_events(int variant) { return variant == 2 ? K1Shape<4>::kTile : K1Shape<2>::kTile; }
 
 int k1_max_grid(int device, int variant, int value_is_float) {
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-  (void)variant;
   (void)value_is_float;
-  return 2 * (sms > 0 ? sms : 148);  // two resident CTAs per SM
+  const int per = variant == 2 ? K1Shape<4>::kCtasPerSm : K1Shape<2>::kCtasPerSm;
+  return per * (sms > 0 ? sms : 148);  // resident CTAs
 }
 
 }  // namespace lms

@@ -162,7 +162,7 @@ constexpr int kChunkThreads = 256;
 cudaError_t launch_batch_begin(SCtl* sctl, QCtl* const* ctls, int nq, cudaStream_t st);
 cudaError_t launch_k1(const K1Args& a, int variant, int grid, cudaStream_t st);
 int k1_max_grid(int device, int variant, int value_is_float);
-int k1_tile_events();
+int k1_tile_events(int variant);
 cudaError_t launch_watermark(SCtl* sctl, const QueryDev* qs, int nq, long long lateness, int eos,
                              cudaStream_t st);
 cudaError_t launch_sort_reduce(const QueryDev& q, const Scratch& s, cudaStream_t st,
@@ -186,6 +186,15 @@ cudaError_t launch_gen_pool(unsigned long long seed, const double* cdf, unsigned
                             cudaStream_t st);
 cudaError_t launch_gen_ts(const GenChunk* chunks, int n_chunks, long long n, long long* ts,
                           int sms, cudaStream_t st);
+
+// Records a timing event on st; while st is being captured into a graph the
+// record becomes an external event node, so that every replay records it.
+inline cudaError_t record_event(cudaEvent_t e, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+    return cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+  return cudaEventRecord(e, st);
+}
 
 // Fills filter_lo / filter_hi / filter_exact from filter_f.
 void set_float_filter(QueryDev* d);

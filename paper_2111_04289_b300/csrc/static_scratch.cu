@@ -213,9 +213,9 @@ extern "C" lms_status lms_aggregate_batch_static(const lms_query_spec* q, int32_
     a.value_is_float = d.value_is_float;
     a.sctl = sctl;
     a.q[0] = d;
-    const long long ntiles = (n_rows + k1_tile_events() - 1) / k1_tile_events();
+    const long long ntiles = (n_rows + k1_tile_events(1) - 1) / k1_tile_events(1);
     const int grid = (int)(ntiles < sms ? ntiles : sms);
-    if (launch_k1(a, 0, grid, st) != cudaSuccess) return LMS_ECUDA;
+    if (launch_k1(a, 1, grid, st) != cudaSuccess) return LMS_ECUDA;
   }
   if (launch_watermark(sctl, &d, 1, 0, 1, st) != cudaSuccess) return LMS_ECUDA;
   if (launch_sort_reduce(d, s, st, nullptr) != cudaSuccess) return LMS_ECUDA;

@@ -26,6 +26,7 @@ OPS = {"none": 0, "eq": 1, "ne": 2, "lt": 3, "le": 4, "gt": 5, "ge": 6}
 AGG_COUNT, AGG_SUM, AGG_MIN, AGG_MAX, AGG_AVG, AGG_ALL = 1, 2, 4, 8, 16, 31
 MEM_HOST, MEM_DEVICE = 0, 1
 BATCH_EOS = 1
+GRAPH_DEFAULT, GRAPH_OFF, GRAPH_ON = 0, 1, 2
 ORIGIN_AUTO = -(2 ** 63)
 
 # numpy images of lms_result_row (48 bytes) for the two value types
@@ -43,7 +44,7 @@ class StreamConfig(ctypes.Structure):
                 ("allowed_lateness_ms", ctypes.c_int64), ("max_batch_rows", ctypes.c_int64),
                 ("state_cap_bytes", ctypes.c_uint64), ("cuda_stream", ctypes.c_void_p),
                 ("origin_ts", ctypes.c_int64), ("k1_variant", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 7)]
+                ("graph_mode", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 class QuerySpec(ctypes.Structure):
@@ -70,7 +71,9 @@ class StatsC(ctypes.Structure):
                 ("emit_ms", ctypes.c_double), ("h2d_ms", ctypes.c_double),
                 ("k1_launches", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
                 ("e1_ms", ctypes.c_double), ("e2_ms", ctypes.c_double),
-                ("partials", ctypes.c_uint64), ("groups_built", ctypes.c_uint64)]
+                ("partials", ctypes.c_uint64), ("groups_built", ctypes.c_uint64),
+                ("graph_launches", ctypes.c_uint64), ("graph_captures", ctypes.c_uint64),
+                ("k1_tile_events", ctypes.c_uint64), ("autotune_samples", ctypes.c_uint64)]
 
 
 EXPORTED_SYMBOLS = ("stream_open", "query_register", "push_microbatch", "poll_results",
@@ -346,7 +349,7 @@ class Stream:
     def __init__(self, value_type: str = "int32", has_type: bool = False, device: int = 0,
                  allowed_lateness_ms: int = 0, max_batch_rows: int = 0, state_cap_bytes: int = 0,
                  cuda_stream: Optional[int] = None, origin_ts: Optional[int] = None,
-                 enable_timing: bool = False, k1_variant: int = 0):
+                 enable_timing: bool = False, k1_variant: int = 0, graph_mode: int = 0):
         self._lib = load()
         self.value_type = value_type
         self.is_float = value_type == "float32"
@@ -361,6 +364,7 @@ class Stream:
         cfg.cuda_stream = cuda_stream
         cfg.origin_ts = ORIGIN_AUTO if origin_ts is None else int(origin_ts)
         cfg.k1_variant = int(k1_variant)
+        cfg.graph_mode = int(graph_mode)
         h = ctypes.c_void_p()
         st = self._lib.stream_open(ctypes.byref(cfg), ctypes.byref(h))
         if st != LMS_OK:

@@ -192,9 +192,40 @@ def test_device_input_equals_host_input():
 
 @pytest.mark.parametrize("variant", [1, 2])
 def test_k1_variants_agree(variant):
+    """Both tile shapes of the fused pass (1024 and 2048 events), float and int
+    values, ragged batch ends."""
     s = synth.LargeFloatStream(seed=73, card=100, s=1.3)
-    batches = [s.next_batch(40_000)]
-    _check(batches, [dict(size=5_000, slide=1_000)], True, k1_variant=variant)
+    batches = [s.next_batch(40_000), s.next_batch(2049), s.next_batch(70_001)]
+    _check(batches, [dict(size=5_000, slide=1_000), dict(size=900, col="value", op="gt",
+                                                         value=1.0)], True, k1_variant=variant)
+    t = synth.TinyIntStream(seed=74, card=300)
+    _check([t.next_batch(33_333), t.next_batch(4097)],
+           [dict(size=2_000, slide=500, col="type", op="eq", value=1)], False, k1_variant=variant)
+
+
+def test_autotuner_samples_both_tiles_then_settles():
+    s = synth.LargeFloatStream(seed=75, card=5_000)
+    batches = [s.next_batch(1 << 16) for _ in range(8)]
+    eng, st = _check(batches, [dict(size=10_000, slide=2_000)], True, k1_variant=0)
+    assert st["autotune_samples"] == 4  # two timed passes of each tile, then its choice
+    assert st["k1_tile_events"] in (1024, 2048)
+
+
+@pytest.mark.parametrize("timing", [False, True])
+def test_graph_replay_equals_plain_launches(timing):
+    """The tail of a push (watermark, sort/reduce, pane index, emission, carry)
+    replayed from a CUDA graph gives the rows of plain launches."""
+    t = synth.TinyIntStream(seed=82, card=700)
+    batches = [t.next_batch(n) for n in [6000] * 10 + [9000] * 4 + [20]]
+    q = [dict(size=3_000, slide=1_000), dict(size=2_000, col="type", op="eq", value=0)]
+    plain, st0 = run_engine(batches, q, False, graph_mode=1, enable_timing=timing)
+    graph, st1 = run_engine(batches, q, False, graph_mode=2, enable_timing=timing)
+    orc, _ = run_oracle(batches, q, False)
+    for j in range(len(q)):
+        assert_rows_match(graph[j], orc[j], False, ctx=f"graph q{j}")
+        assert graph[j].tobytes() == plain[j].tobytes()
+    assert st0["graph_launches"] == 0
+    assert st1["graph_launches"] >= 8 and st1["graph_captures"] >= 1
 
 
 def test_batching_invariance_on_gpu():
