@@ -105,8 +105,9 @@ typedef struct lms_stream_config {
                                   are kept relative to it: events must satisfy
                                   |floor(ts/slide) - floor(origin_ts/slide)| < 2^31 - 1,
                                   others are dropped and counted (stats.range_rows). */
-  int32_t k1_variant;          /* fused-pass tile: 0 = autotuned per batch-size class,
-                                  1 = 1024 events (two CTAs per SM), 2 = 2048 events (one) */
+  int32_t k1_variant;          /* fused pass: 0 = autotuned per batch-size class; 1 = 1024-event
+                                  tiles (two CTAs per SM); 2 = 2048-event tiles (one CTA per SM);
+                                  3 / 4 = 1 / 2 with warp aggregation of equal group keys */
   int32_t graph_mode;          /* LMS_GRAPH_*: replay the per-batch launch sequence from a CUDA graph */
   int32_t reserved[6];
 } lms_stream_config;

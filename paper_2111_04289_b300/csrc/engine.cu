@@ -110,13 +110,6 @@ struct lms_stream {
   std::vector<std::pair<void*, size_t>> allocs;
   cudaEvent_t ev[8] = {};
   cudaEvent_t tev[2] = {};  // around the fused pass while the autotuner samples
-  // K1 autotuner: per batch-size class (log2 of the rows), time per event of
-  // each tile shape, and the chosen shape once both were sampled
-  struct Tune {
-    double ms_per_row[3] = {0, 0, 0};
-    int samples[3] = {0, 0, 0};
-    int choice = 0;
-  } tune[48];
   cudaEvent_t qev[kMaxQueries][6] = {};  // E1, E2, sort/reduce
   lms_stats stats{};
   long long wm = LLONG_MIN;
@@ -290,33 +283,62 @@ lms_status read_ctls(lms_stream* s, QCtl* h) {
   return LMS_OK;
 }
 
-// The fused pass's tile shape for a batch of n rows: the configured one, or the
-// autotuner's.  Below 2^15 rows the 1024-event tile is used; above, each
-// size class (log2 n) first runs each shape kSamples times (timed with CUDA
-// events) and then keeps the faster per row.  Results do not depend on it.
+// The fused pass's variant (tile of 1024 or 2048 events, with or without warp
+// aggregation of equal group keys) for a batch of n rows: the configured one,
+// or the autotuner's.  Below 2^15 rows variant 1 is used; above, each size
+// class (log2 n) first runs every variant kTuneSamples times (timed with CUDA
+// events) and then keeps the fastest per row.  Results do not depend on it.
+// The table is shared by every stream of the process and keyed by (value type,
+// number of queries, size class); the first timed pass of each variant in a
+// class only warms it up and is not counted.
 constexpr int kTuneSamples = 2;
+
+struct Tune {
+  double ms_per_row[5] = {0, 0, 0, 0, 0};
+  int samples[5] = {0, 0, 0, 0, 0};  // -1: warm-up pending
+  int choice = 0;
+};
+std::mutex g_tune_mu;
+Tune g_tune[2][kMaxQueries + 1][48];
+
+Tune& tune_slot(const lms_stream* s, long long n) {
+  int b = 0;
+  while ((1ll << (b + 1)) <= n && b < 47) ++b;
+  return g_tune[s->cfg.value_type == LMS_VALUE_FLOAT32 ? 1 : 0][s->qs.size()][b];
+}
 
 int pick_k1_variant(lms_stream* s, long long n, bool* tuning) {
   *tuning = false;
-  if (s->cfg.k1_variant == 1 || s->cfg.k1_variant == 2) return s->cfg.k1_variant;
+  if (s->cfg.k1_variant >= 1 && s->cfg.k1_variant <= 4) return s->cfg.k1_variant;
   if (n < (1ll << 15)) return 1;
-  int b = 0;
-  while ((1ll << (b + 1)) <= n && b < 47) ++b;
-  lms_stream::Tune& t = s->tune[b];
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  Tune& t = tune_slot(s, n);
   if (t.choice) return t.choice;
   *tuning = true;
-  return t.samples[1] <= t.samples[2] ? 1 : 2;
+  int v = 1;
+  for (int k = 2; k <= 4; ++k)
+    if (t.samples[k] < t.samples[v]) v = k;
+  return v;
 }
 
 void record_k1_sample(lms_stream* s, long long n, int variant, float ms) {
-  int b = 0;
-  while ((1ll << (b + 1)) <= n && b < 47) ++b;
-  lms_stream::Tune& t = s->tune[b];
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  Tune& t = tune_slot(s, n);
+  s->stats.autotune_samples += 1;
+  if (t.choice) return;
+  if (t.samples[variant] == 0 && t.ms_per_row[variant] == 0.0) {
+    t.ms_per_row[variant] = -1.0;  // the warm-up pass: not counted
+    return;
+  }
+  if (t.ms_per_row[variant] < 0) t.ms_per_row[variant] = 0.0;
   t.ms_per_row[variant] += (double)ms / (double)n;
   t.samples[variant] += 1;
-  s->stats.autotune_samples += 1;
-  if (t.samples[1] >= kTuneSamples && t.samples[2] >= kTuneSamples)
-    t.choice = t.ms_per_row[2] / t.samples[2] < t.ms_per_row[1] / t.samples[1] ? 2 : 1;
+  for (int k = 1; k <= 4; ++k)
+    if (t.samples[k] < kTuneSamples) return;
+  int best = 1;
+  for (int k = 2; k <= 4; ++k)
+    if (t.ms_per_row[k] / t.samples[k] < t.ms_per_row[best] / t.samples[best]) best = k;
+  t.choice = best;
 }
 
 }  // namespace

@@ -109,7 +109,7 @@ __device__ __forceinline__ void shared_add_f64(unsigned long long* p, double v) 
   } while (old != assumed);
 }
 
-template <bool FLOAT, int ITEMS>
+template <bool FLOAT, int ITEMS, bool WAGG>
 __global__ void __launch_bounds__(kK1Threads, K1Shape<ITEMS>::kCtasPerSm)
     k1_fused(const __grid_constant__ K1Args a) {
   constexpr int kK1Items = ITEMS;
@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(kK1Threads, K1Shape<ITEMS>::kCtasPerSm)
       const int fcol = Q.filter_col, fop = Q.filter_op;
       const long long cursor = s_cursor[qi];
       unsigned n_late = 0, n_range = 0;
-      unsigned slot[kK1Items];
+      unsigned slot[kK1Items], peer[kK1Items];
       // ---- A: filter, pane id, insert the group key, count / min / max / exponent ----
 #pragma unroll
       for (int i = 0; i < kK1Items; ++i) {
@@ -238,30 +238,58 @@ __global__ void __launch_bounds__(kK1Threads, K1Shape<ITEMS>::kCtasPerSm)
           }
         }
         slot[i] = kNoSlot;
+        unsigned long long g = kEmpty;  // the event's group key, if it is aggregated
         if (ok) {
           const unsigned long long u = (unsigned long long)ts[i] + Q.ts_off;
           if (u >= Q.u_limit) {
             ++n_range;
           } else {
             const unsigned long long prel = udiv_inv(u, Q.magic, Q.sh1, Q.sh2);
-            if ((long long)prel < cursor) {  // every window of this event was emitted
-              ++n_late;
+            if ((long long)prel < cursor) ++n_late;  // every window of this event was emitted
+            else g = (prel << 32) | key[i];
+          }
+        }
+        const unsigned enc = FLOAT ? enc_f32(__uint_as_float(val[i])) : enc_i32((int)val[i]);
+        if (WAGG) {
+          // lanes of the warp with the same group key update it once, through
+          // a leader: count, min, max (and the int sum) reduced over the peers
+          const unsigned peers = __match_any_sync(kFull, g);
+          peer[i] = peers;
+          const int leader = __ffs(peers) - 1;
+          const unsigned mn = __reduce_min_sync(peers, enc);
+          const unsigned mx = __reduce_max_sync(peers, enc);
+          unsigned long long add = 0ull;
+          if (!FLOAT) {
+            const unsigned lo = __reduce_add_sync(peers, enc & 0xffffu);
+            const unsigned hi = __reduce_add_sync(peers, enc >> 16);
+            add = ((unsigned long long)__popc(peers) << kCntShift) + lo + ((unsigned long long)hi << 16);
+          }
+          unsigned sl = kNoSlot;
+          if (g != kEmpty && (int)lane == leader) {
+            sl = insert_key<kK1HashBits>(hkey, list, &s_nlist, g);
+            if (sl == kNoSlot) {
+              atomicOr(&s_err[qi], kErrProbe);
             } else {
-              const unsigned sl =
-                  insert_key<kK1HashBits>(hkey, list, &s_nlist, (prel << 32) | key[i]);
-              if (sl == kNoSlot) {
-                atomicOr(&s_err[qi], kErrProbe);
-              } else {
-                slot[i] = sl;
-                const unsigned enc = FLOAT ? enc_f32(__uint_as_float(val[i])) : enc_i32((int)val[i]);
-                atomicMin(&gmn[sl], enc);
-                atomicMax(&gmx[sl], enc);
-                if (FLOAT)
-                  atomicAdd(&gcnt[sl], 1u);
-                else  // count and sum in one word (enc = value + 2^31)
-                  atomicAdd(&gsum[sl], (1ull << kCntShift) + (unsigned long long)enc);
-              }
+              atomicMin(&gmn[sl], mn);
+              atomicMax(&gmx[sl], mx);
+              if (FLOAT) atomicAdd(&gcnt[sl], (unsigned)__popc(peers));
+              else atomicAdd(&gsum[sl], add);
             }
+          }
+          sl = __shfl_sync(peers, sl, leader);
+          slot[i] = g != kEmpty ? sl : kNoSlot;
+        } else if (g != kEmpty) {
+          const unsigned sl = insert_key<kK1HashBits>(hkey, list, &s_nlist, g);
+          if (sl == kNoSlot) {
+            atomicOr(&s_err[qi], kErrProbe);
+          } else {
+            slot[i] = sl;
+            atomicMin(&gmn[sl], enc);
+            atomicMax(&gmx[sl], enc);
+            if (FLOAT)
+              atomicAdd(&gcnt[sl], 1u);
+            else  // count and sum in one word (enc = value + 2^31)
+              atomicAdd(&gsum[sl], (1ull << kCntShift) + (unsigned long long)enc);
           }
         }
       }
@@ -276,12 +304,30 @@ __global__ void __launch_bounds__(kK1Threads, K1Shape<ITEMS>::kCtasPerSm)
       if (FLOAT) {
 #pragma unroll
         for (int i = 0; i < kK1Items; ++i) {
-          if (slot[i] == kNoSlot) continue;
-          const unsigned B = group_exp(gmn[slot[i]], gmx[slot[i]]);
-          if (B == 255u)
-            shared_add_f64(&gsum[slot[i]], (double)__uint_as_float(val[i]));
-          else
-            atomicAdd(&gsum[slot[i]], (unsigned long long)f32_fixed(val[i], B));
+          const bool has = slot[i] != kNoSlot;
+          const unsigned B = has ? group_exp(gmn[slot[i]], gmx[slot[i]]) : 0u;
+          if (WAGG) {
+            // all peers share the slot (and B): one add of the peers' sum,
+            // reduced in three 26-bit slices so that no partial sum overflows
+            if (!has) continue;
+            if (B == 255u) {
+              shared_add_f64(&gsum[slot[i]], (double)__uint_as_float(val[i]));
+              continue;
+            }
+            const unsigned long long x = (unsigned long long)f32_fixed(val[i], B);
+            const unsigned s0 = __reduce_add_sync(peer[i], (unsigned)(x & 0x3ffffffull));
+            const unsigned s1 = __reduce_add_sync(peer[i], (unsigned)((x >> 26) & 0x3ffffffull));
+            const unsigned s2 = __reduce_add_sync(peer[i], (unsigned)(x >> 52));
+            if ((int)lane == __ffs(peer[i]) - 1)
+              atomicAdd(&gsum[slot[i]], (unsigned long long)s0 + ((unsigned long long)s1 << 26) +
+                                            ((unsigned long long)s2 << 52));
+          } else {
+            if (!has) continue;
+            if (B == 255u)
+              shared_add_f64(&gsum[slot[i]], (double)__uint_as_float(val[i]));
+            else
+              atomicAdd(&gsum[slot[i]], (unsigned long long)f32_fixed(val[i], B));
+          }
         }
       }
       const unsigned nl = s_nlist;
@@ -351,32 +397,45 @@ __global__ void __launch_bounds__(kK1Threads, K1Shape<ITEMS>::kCtasPerSm)
   }
 }
 
-template <bool FLOAT, int ITEMS>
+template <bool FLOAT, int ITEMS, bool WAGG>
 cudaError_t launch_k1_t(const K1Args& a, int grid, cudaStream_t st) {
   // once per process and instantiation (thread-safe static initialisation)
   static const cudaError_t attr =
-      cudaFuncSetAttribute(k1_fused<FLOAT, ITEMS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)K1Shape<ITEMS>::kSmem);
+      cudaFuncSetAttribute(k1_fused<FLOAT, ITEMS, WAGG>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K1Shape<ITEMS>::kSmem);
   if (attr != cudaSuccess) return attr;
-  k1_fused<FLOAT, ITEMS><<<grid, kK1Threads, K1Shape<ITEMS>::kSmem, st>>>(a);
+  k1_fused<FLOAT, ITEMS, WAGG><<<grid, kK1Threads, K1Shape<ITEMS>::kSmem, st>>>(a);
   return cudaGetLastError();
+}
+
+template <bool FLOAT>
+cudaError_t launch_k1_v(const K1Args& a, int variant, int grid, cudaStream_t st) {
+  switch (variant) {
+    case 2: return launch_k1_t<FLOAT, 4, false>(a, grid, st);
+    case 3: return launch_k1_t<FLOAT, 2, true>(a, grid, st);
+    case 4: return launch_k1_t<FLOAT, 4, true>(a, grid, st);
+    default: return launch_k1_t<FLOAT, 2, false>(a, grid, st);
+  }
 }
 
 }  // namespace
 
+// Variants: 1 = 1024-event tiles, 2 = 2048-event tiles, 3 / 4 = the same with
+// warp aggregation of equal group keys.
 cudaError_t launch_k1(const K1Args& a, int variant, int grid, cudaStream_t st) {
-  if (variant == 2)
-    return a.value_is_float ? launch_k1_t<true, 4>(a, grid, st) : launch_k1_t<false, 4>(a, grid, st);
-  return a.value_is_float ? launch_k1_t<true, 2>(a, grid, st) : launch_k1_t<false, 2>(a, grid, st);
+  return a.value_is_float ? launch_k1_v<true>(a, variant, grid, st)
+                          : launch_k1_v<false>(a, variant, grid, st);
 }
 
-int k1_tile_events(int variant) { return variant == 2 ? K1Shape<4>::kTile : K1Shape<2>::kTile; }
+int k1_tile_events(int variant) {
+  return (variant == 2 || variant == 4) ? K1Shape<4>::kTile : K1Shape<2>::kTile;
+}
 
 int k1_max_grid(int device, int variant, int value_is_float) {
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   (void)value_is_float;
-  const int per = variant == 2 ? K1Shape<4>::kCtasPerSm : K1Shape<2>::kCtasPerSm;
+  const int per = (variant == 2 || variant == 4) ? K1Shape<4>::kCtasPerSm : K1Shape<2>::kCtasPerSm;
   return per * (sms > 0 ? sms : 148);  // resident CTAs
 }
 

@@ -190,10 +190,10 @@ def test_device_input_equals_host_input():
     np.testing.assert_allclose(host[0]["sum"], dev[0]["sum"], rtol=1e-12)
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
 def test_k1_variants_agree(variant):
-    """Both tile shapes of the fused pass (1024 and 2048 events), float and int
-    values, ragged batch ends."""
+    """Every variant of the fused pass (1024 / 2048-event tiles, with and
+    without warp aggregation), float and int values, ragged batch ends."""
     s = synth.LargeFloatStream(seed=73, card=100, s=1.3)
     batches = [s.next_batch(40_000), s.next_batch(2049), s.next_batch(70_001)]
     _check(batches, [dict(size=5_000, slide=1_000), dict(size=900, col="value", op="gt",
@@ -203,11 +203,15 @@ def test_k1_variants_agree(variant):
            [dict(size=2_000, slide=500, col="type", op="eq", value=1)], False, k1_variant=variant)
 
 
-def test_autotuner_samples_both_tiles_then_settles():
-    s = synth.LargeFloatStream(seed=75, card=5_000)
-    batches = [s.next_batch(1 << 16) for _ in range(8)]
-    eng, st = _check(batches, [dict(size=10_000, slide=2_000)], True, k1_variant=0)
-    assert st["autotune_samples"] == 4  # two timed passes of each tile, then its choice
+def test_autotuner_samples_every_variant_then_settles():
+    """Seven int queries on 2^15-row batches (a size class no other test uses):
+    each of the four variants is timed three times (the first as warm-up),
+    then the fastest is kept; the rows match the oracle throughout."""
+    t = synth.TinyIntStream(seed=75, card=2_000)
+    batches = [t.next_batch(1 << 15) for _ in range(15)]
+    q = [dict(size=1_000 * (j + 1), slide=500 * (j + 1) if j % 2 else 0) for j in range(7)]
+    eng, st = _check(batches, q, False, k1_variant=0)
+    assert st["autotune_samples"] == 12
     assert st["k1_tile_events"] in (1024, 2048)
 
 
