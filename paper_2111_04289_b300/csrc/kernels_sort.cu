@@ -80,18 +80,27 @@ __global__ void __launch_bounds__(256) k_sort_hist(const QueryDev q, const Scrat
 }
 
 // Per digit (one CTA each): exclusive scan over the chunks of hist[d][*] in
-// place, digit total -> hist[256 * kGrid + d].
+// place (up to 4 chunks per thread), digit total -> hist[256 * kGrid + d].
+static_assert(kGrid <= 4 * 256, "k_sort_scan covers at most 1024 chunks");
 __global__ void __launch_bounds__(256) k_sort_scan(const QueryDev q, const Scratch s, int p) {
   if (p >= q.ctl->npasses) return;
   __shared__ unsigned long long tmp[33];
   unsigned* h = s.hist + blockIdx.x * kGrid;
-  const int a = 2 * threadIdx.x;
-  const unsigned x0 = a < kGrid ? h[a] : 0u;
-  const unsigned x1 = a + 1 < kGrid ? h[a + 1] : 0u;
+  const int a = 4 * threadIdx.x;
+  unsigned x[4];
+  unsigned sum = 0;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    x[u] = a + u < kGrid ? h[a + u] : 0u;
+    sum += x[u];
+  }
   unsigned long long tot;
-  const unsigned long long r = block_excl_scan((unsigned long long)(x0 + x1), tmp, &tot);
-  if (a < kGrid) h[a] = (unsigned)r;
-  if (a + 1 < kGrid) h[a + 1] = (unsigned)(r + x0);
+  unsigned long long r = block_excl_scan((unsigned long long)sum, tmp, &tot);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    if (a + u < kGrid) h[a + u] = (unsigned)r;
+    r += x[u];
+  }
   if (threadIdx.x == 0) s.hist[256 * kGrid + blockIdx.x] = (unsigned)tot;
 }
 

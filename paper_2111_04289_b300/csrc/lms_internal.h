@@ -154,7 +154,7 @@ struct ResultRowDev {  // device image of lms_result_row (48 bytes)
   unsigned qid;
 };
 
-constexpr int kGrid = 296;         // CTAs of the chunked (count/scan/write) kernels
+constexpr int kGrid = 592;         // CTAs of the chunked (count/scan/write) kernels: 4 per SM
 constexpr int kChunkThreads = 256;
 
 // ---- launch wrappers (kernels_*.cu) -------------------------------------
