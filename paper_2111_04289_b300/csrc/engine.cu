@@ -623,7 +623,7 @@ lms_status push_microbatch(lms_stream* s, const lms_batch* b) {
         if ((r = ensure_windows(s, hc[i].n_windows)) != LMS_OK) return r;
       }
       if (hc[i].err & kErrPoolOverflow) {
-        if ((r = ensure_pool(s, hc[i].pool_used)) != LMS_OK) return r;
+        if ((r = ensure_pool(s, std::max(hc[i].pool_used, hc[i].pool_need))) != LMS_OK) return r;
       }
       if (hc[i].err & kErrRowsOverflow) {
         if ((r = ensure_rows(s, q, hc[i].row_base + hc[i].rows_batch)) != LMS_OK) return r;

@@ -21,7 +21,7 @@ namespace lms {
 namespace {
 
 constexpr int kEmitThreads = 512;
-constexpr size_t kEmitSmemMax = 225 * 1024;  // dynamic shared memory of the emit kernel
+constexpr size_t kEmitSmemMax = 224 * 1024;  // dynamic shared memory of the emit kernel (static: ~2.3 KB)
 // Largest window (entries) merged in shared memory for windows of k panes:
 // two padded buffers (17 slots per 16 entries) plus two (k+1)-entry boundary
 // arrays must fit in kEmitSmemMax.
@@ -92,6 +92,7 @@ __global__ void k_watermark(SCtl* sc, const WmArgs a) {
 __global__ void k_emit_begin(QCtl* c) {
   if (threadIdx.x != 0) return;
   c->pool_used = 0ull;
+  c->pool_need = 0ull;
   c->big_windows = 0ull;
   c->rows_batch = 0ull;
   c->n_windows = 0ull;
@@ -250,8 +251,17 @@ __device__ __forceinline__ void write_row(const QueryDev& q, ResultRowDev* out, 
   } else if ((cnt & (cnt - 1)) == 0) {
     const int e = __ffsll(cnt) - 1;
     avg = sd * __longlong_as_double((long long)(1023 - e) << 52);
+  } else if (FLOAT) {
+    // FP64 division is slow on this part: a float32 reciprocal refined by two
+    // corrections with exact FMA remainders (error far below 1e-15 relative;
+    // float results are checked to 1e-9)
+    const double n = (double)cnt;
+    const double r = (double)__frcp_rn((float)cnt);
+    const double q0 = sd * r;
+    const double q1 = fma(fma(-q0, n, sd), r, q0);
+    avg = fma(fma(-q1, n, sd), r, q1);
   } else {
-    avg = sd / (double)cnt;
+    avg = sd / (double)cnt;  // int sums: exact division (bit-exact rows)
   }
   unsigned mnv = 0u, mxv = 0u;
   if (q.agg_mask & 4u) mnv = FLOAT ? dec_f32_bits(mn) : (unsigned)dec_i32(mn);
@@ -603,6 +613,111 @@ __device__ unsigned long long run_range(const QueryDev& q, const Scratch& s, QCt
   return acc;
 }
 
+// Rows of windows [wa, wb) without assembling them.  A window's rows are its
+// distinct keys; the group of key k in pane P is the first occurrence of k in
+// exactly the windows whose ids lie in [max(prev + 1, P - K + 1), P], prev the
+// last earlier pane holding k.  The CTA sweeps the range's panes in order
+// (pane by pane; keys within a pane are distinct) with a shared table of
+// (last pane, key) — entries older than any window still ahead are reused —
+// and adds, per group, the number of the range's windows in that id
+// interval.  Returns ~0 if the table overflowed (the caller then counts by
+// assembling the windows).
+__device__ unsigned long long count_range(const QueryDev& q, const Scratch& s, QCtl* c,
+                                          unsigned long long wa, unsigned long long wb,
+                                          unsigned cap, unsigned long long* tab, unsigned tab_n,
+                                          unsigned* s_fail) {
+  if (threadIdx.x == 0) *s_fail = 0u;
+  __syncthreads();
+  // global merge scratch the range's windows above `cap` entries will need
+  // (so that one retry can size the scratch for the whole emission)
+  unsigned long long need = 0;
+  unsigned big = 0;
+  for (unsigned long long wi = wa + threadIdx.x; wi < wb; wi += blockDim.x) {
+    const unsigned long long len = s.pane_begin[s.win_j1[wi]] - s.pane_begin[s.win_j0[wi]];
+    if (s.win_j1[wi] - s.win_j0[wi] > 1 && len > cap) need += 2ull * len;
+    if (2ull * len > tab_n) big = 1u;  // a window's keys might not fit the table
+  }
+  if (need) atomicAdd(&c->pool_need, need);
+  if (big) atomicOr(s_fail, 1u);
+  __syncthreads();
+  if (*s_fail) return ~0ull;  // count by assembling the windows instead
+  for (unsigned i = threadIdx.x; i < tab_n; i += blockDim.x) tab[i] = 0ull;  // pane ids are >= 1
+  __syncthreads();
+  const unsigned j_begin = s.win_j0[wa], j_end = s.win_j1[wb - 1];
+  const long long w_first = s.win_w[wa], w_last = s.win_w[wb - 1];
+  const long long* ww = s.win_w + wa;
+  const unsigned nw = (unsigned)(wb - wa);
+  unsigned long long total = 0;
+  for (unsigned j = j_begin; j < j_end; ++j) {
+    const long long P = (long long)s.pane_id[j];
+    const unsigned long long g0 = s.pane_begin[j], g1 = s.pane_begin[j + 1];
+    for (unsigned long long g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
+      const unsigned key = (unsigned)q.state[g].gkey;
+      const unsigned long long nv = ((unsigned long long)P << 32) | key;
+      long long prev = LLONG_MIN;
+      unsigned h = (unsigned)(((unsigned long long)(key * 0x9E3779B1u) * tab_n) >> 32);
+      unsigned stale = 0xffffffffu;
+      unsigned long long stale_v = 0ull;
+      bool done = false;
+      for (unsigned probe = 0; probe < 256u && !done; ++probe) {
+        const unsigned long long e = *((volatile unsigned long long*)&tab[h]);
+        if (e != 0ull && (unsigned)e == key) {  // the key's entry: update its pane
+          if (atomicCAS(&tab[h], e, nv) == e) {
+            prev = (long long)(e >> 32);
+            done = true;
+          }
+          continue;  // changed under us: look again
+        }
+        if (e == 0ull) {  // the key is absent: take the first stale slot seen, else this one
+          if (stale != 0xffffffffu) {
+            if (atomicCAS(&tab[stale], stale_v, nv) == stale_v) {
+              done = true;
+            } else {
+              stale = 0xffffffffu;  // taken meanwhile: start over
+              h = (unsigned)(((unsigned long long)(key * 0x9E3779B1u) * tab_n) >> 32);
+            }
+          } else if (atomicCAS(&tab[h], 0ull, nv) == 0ull) {
+            done = true;
+          }
+          continue;
+        }
+        if (stale == 0xffffffffu && (long long)(e >> 32) < P - q.k + 1) {
+          stale = h;  // no window still to come can contain that entry's pane
+          stale_v = e;
+        }
+        h = h + 1 == tab_n ? 0u : h + 1;
+      }
+      if (!done) {
+        atomicOr(s_fail, 1u);
+        continue;
+      }
+      long long lo = prev == LLONG_MIN ? P - q.k + 1 : max(prev + 1, P - q.k + 1);
+      long long hi = P;
+      lo = max(lo, w_first);
+      hi = min(hi, w_last);
+      if (lo > hi) continue;
+      unsigned a = 0, b = nw;  // first window with id >= lo
+      while (a < b) {
+        const unsigned m = (a + b) >> 1;
+        if (ww[m] < lo) a = m + 1;
+        else b = m;
+      }
+      unsigned c = a, d = nw;  // first window with id > hi
+      while (c < d) {
+        const unsigned m = (c + d) >> 1;
+        if (ww[m] <= hi) c = m + 1;
+        else d = m;
+      }
+      total += c - a;
+    }
+    __syncthreads();  // this pane's table updates before the next pane's lookups
+  }
+  __shared__ unsigned long long ctmp[33];
+  unsigned long long tot;
+  block_excl_scan(total, ctmp, &tot);
+  return *s_fail ? ~0ull : tot;
+}
+
 // Assembles the closed windows.  CTAs take ranges of consecutive windows in
 // ticket order; for each range: count its rows (pass 1), find the range's row
 // offset by the look-back, then write its rows (pass 2) in (window, key) order.
@@ -616,6 +731,7 @@ __global__ void __launch_bounds__(kEmitThreads, 1)
   const unsigned padded = cap + (cap >> 4) + 1;
   __shared__ unsigned wt[33];
   __shared__ unsigned long long s_ri, s_off;
+  __shared__ unsigned s_fail;
   EmitSmem m;
   m.L = esm;
   m.T = esm + padded;
@@ -635,8 +751,10 @@ __global__ void __launch_bounds__(kEmitThreads, 1)
     __syncthreads();
     if (ri >= NR) break;
     const unsigned long long wa = ri * per, wb = min(W, wa + per);
-    const unsigned long long n =
-        run_range<FLOAT, false>(q, s, c, wa, wb, cap, m, nullptr, &s_off);
+    // the range's row count: by the pane sweep, else by assembling the windows
+    unsigned long long n = count_range(q, s, c, wa, wb, cap, esm, 2u * padded, &s_fail);
+    __syncthreads();
+    if (n == ~0ull) n = run_range<FLOAT, false>(q, s, c, wa, wb, cap, m, nullptr, &s_off);
     if (threadIdx.x == 0) {
       const unsigned long long off = range_lookback(s.win_stat, ri, n, c);
       s_off = off;

@@ -58,6 +58,7 @@ struct QCtl {
   unsigned long long rows_batch; // rows emitted by this batch
   unsigned long long row_base;   // rows held in the device result buffer
   unsigned long long pool_used;  // big-window scratch entries used (this emission)
+  unsigned long long pool_need;  // big-window scratch entries all closed windows need
   unsigned long long carried;    // groups carried into the next batch
   unsigned long long big_windows;// windows merged through global scratch (this emission)
   unsigned long long trim_from;  // first state index carried into the next batch
