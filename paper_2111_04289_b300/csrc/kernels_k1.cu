@@ -95,9 +95,32 @@ __device__ __forceinline__ long long f32_fixed(unsigned x, unsigned B) {
   else t = 0;
   return (x & 0x80000000u) ? -t : t;
 }
-// double value of a fixed-point sum with unit 2^(B - 178)
-__device__ __forceinline__ double fixed_to_double(long long t, unsigned B) {
-  return (double)t * __longlong_as_double((long long)(1023 + (int)B - 178) << 52);
+// Bits of the double nearest (ties to even) to the fixed-point sum t with unit
+// 2^(B - 178), built with integer operations (FP64 is slow on this part):
+// normalise |t|, keep 52 fraction bits, round on the 11 dropped ones.  For
+// 1 <= B <= 254 and |t| < 2^63 the result is always a normal double.
+__device__ __forceinline__ unsigned long long fixed_to_double_bits(long long t, unsigned B) {
+  if (t == 0) return 0ull;
+  const unsigned long long sgn = t < 0 ? (1ull << 63) : 0ull;
+  unsigned long long m = t < 0 ? (unsigned long long)(-t) : (unsigned long long)t;
+  const int lz = __clzll((long long)m);
+  m <<= lz;  // leading one at bit 63
+  const unsigned long long e = (unsigned long long)(63 - lz + (int)B - 178 + 1023);
+  const unsigned long long frac = (m >> 11) & ((1ull << 52) - 1ull);
+  const unsigned long long rest = m & 0x7ffull;
+  unsigned long long bits = (e << 52) | frac;
+  if (rest > 0x400ull || (rest == 0x400ull && (frac & 1ull))) bits += 1ull;  // carries into e
+  return sgn | bits;
+}
+// Adds a 64-bit two's-complement value to a shared 64-bit word with 32-bit
+// atomics (faster than the 64-bit one here): the low word's old value tells
+// whether the add carried into the high word.
+__device__ __forceinline__ void shared_add_u64_split(unsigned long long* p, unsigned long long x) {
+  unsigned* w = reinterpret_cast<unsigned*>(p);
+  const unsigned lo = (unsigned)x;
+  const unsigned old = atomicAdd(&w[0], lo);
+  const unsigned hi = (unsigned)(x >> 32) + ((old + lo) < old ? 1u : 0u);
+  if (hi) atomicAdd(&w[1], hi);
 }
 // FP64 add into a shared-memory word (groups holding Inf or NaN only)
 __device__ __forceinline__ void shared_add_f64(unsigned long long* p, double v) {
@@ -163,12 +186,16 @@ __global__ void __launch_bounds__(kK1Threads, K1Shape<ITEMS>::kCtasPerSm)
       (a.type == nullptr || (reinterpret_cast<uintptr_t>(a.type) & 1u) == 0);
   long long tmax = LLONG_MIN;
 
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    // ---- load this thread's 2 consecutive events (16/8/8/2-byte loads) ----
+  // columns of this thread's kK1Items consecutive events of a tile (vector
+  // loads when aligned); the next tile's are loaded while this one is processed
+  auto load_tile = [&](long long tile, long long* ts, unsigned* key, unsigned* val, unsigned* typ,
+                       bool* valid) {
     const long long e0 = tile * kK1Tile + (long long)tid * kK1Items;
-    long long ts[kK1Items];
-    unsigned key[kK1Items], val[kK1Items], typ[kK1Items];
-    bool valid[kK1Items];
+    if (tile >= ntiles) {
+#pragma unroll
+      for (int i = 0; i < kK1Items; ++i) valid[i] = false;
+      return;
+    }
     if (vec_ok && e0 + kK1Items <= n) {
 #pragma unroll
       for (int h = 0; h < kK1Items; h += 2) {
@@ -211,6 +238,24 @@ __global__ void __launch_bounds__(kK1Threads, K1Shape<ITEMS>::kCtasPerSm)
         typ[i] = (valid[i] && a.type) ? a.type[e] : 0u;
       }
     }
+  };
+  long long nts[kK1Items];
+  unsigned nkey[kK1Items], nval[kK1Items], ntyp[kK1Items];
+  bool nvalid[kK1Items];
+  load_tile(blockIdx.x, nts, nkey, nval, ntyp, nvalid);
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    long long ts[kK1Items];
+    unsigned key[kK1Items], val[kK1Items], typ[kK1Items];
+    bool valid[kK1Items];
+#pragma unroll
+    for (int i = 0; i < kK1Items; ++i) {
+      ts[i] = nts[i];
+      key[i] = nkey[i];
+      val[i] = nval[i];
+      typ[i] = ntyp[i];
+      valid[i] = nvalid[i];
+    }
+    load_tile(tile + gridDim.x, nts, nkey, nval, ntyp, nvalid);
 #pragma unroll
     for (int i = 0; i < kK1Items; ++i)
       if (valid[i] && ts[i] > tmax) tmax = ts[i];
@@ -319,14 +364,15 @@ __global__ void __launch_bounds__(kK1Threads, K1Shape<ITEMS>::kCtasPerSm)
             const unsigned s1 = __reduce_add_sync(peer[i], (unsigned)((x >> 26) & 0x3ffffffull));
             const unsigned s2 = __reduce_add_sync(peer[i], (unsigned)(x >> 52));
             if ((int)lane == __ffs(peer[i]) - 1)
-              atomicAdd(&gsum[slot[i]], (unsigned long long)s0 + ((unsigned long long)s1 << 26) +
-                                            ((unsigned long long)s2 << 52));
+              shared_add_u64_split(&gsum[slot[i]], (unsigned long long)s0 +
+                                                       ((unsigned long long)s1 << 26) +
+                                                       ((unsigned long long)s2 << 52));
           } else {
             if (!has) continue;
             if (B == 255u)
               shared_add_f64(&gsum[slot[i]], (double)__uint_as_float(val[i]));
             else
-              atomicAdd(&gsum[slot[i]], (unsigned long long)f32_fixed(val[i], B));
+              shared_add_u64_split(&gsum[slot[i]], (unsigned long long)f32_fixed(val[i], B));
           }
         }
       }
@@ -348,7 +394,7 @@ __global__ void __launch_bounds__(kK1Threads, K1Shape<ITEMS>::kCtasPerSm)
           cnt = (long long)gcnt[sl];
           const unsigned B = group_exp(mn, mx);
           if (B != 255u)
-            sb = (unsigned long long)__double_as_longlong(fixed_to_double((long long)sb, B));
+            sb = fixed_to_double_bits((long long)sb, B);
         } else {
           cnt = (long long)(sb >> kCntShift);
           sb = (sb & ((1ull << kCntShift) - 1ull)) - ((unsigned long long)cnt << 31);
