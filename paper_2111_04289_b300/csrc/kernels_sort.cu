@@ -104,11 +104,21 @@ __global__ void __launch_bounds__(256) k_sort_scan(const QueryDev q, const Scrat
   if (threadIdx.x == 0) s.hist[256 * kGrid + blockIdx.x] = (unsigned)tot;
 }
 
-__global__ void __launch_bounds__(256) k_sort_scatter(const QueryDev q, const Scratch s, int p) {
+// One pass of the stable scatter.  Per tile of 2048 items: warp-aggregated
+// ranks inside each warp's 256 items (match_any per round), the tile's
+// per-digit counts and offsets, then the items are placed in shared memory in
+// (digit, original order) and written out from there, so that consecutive
+// threads write consecutive positions of each digit's run (coalesced).
+__global__ void __launch_bounds__(256, 4) k_sort_scatter(const QueryDev q, const Scratch s, int p) {
   const QCtl* c = q.ctl;
   if (p >= c->npasses) return;
-  __shared__ unsigned run[256];
+  __shared__ unsigned run[256];   // the CTA's next global position per digit
+  __shared__ unsigned lbase[256]; // the tile's first local position per digit
+  __shared__ unsigned tcnt[256];  // the tile's items per digit
   __shared__ unsigned wcnt[8][256];
+  __shared__ unsigned long long skey[kScatterTile];
+  __shared__ unsigned sval[kScatterTile];
+  __shared__ unsigned long long tmp[33];
   const int tid = threadIdx.x, w = tid >> 5;
   const unsigned lane = lane_id();
   const int shift = c->shifts[p];
@@ -118,7 +128,6 @@ __global__ void __launch_bounds__(256) k_sort_scatter(const QueryDev q, const Sc
   unsigned long long lo, hi;
   chunk_range(c->n_parts, blockIdx.x, gridDim.x, &lo, &hi);
   {
-    __shared__ unsigned long long tmp[33];
     unsigned long long tot;
     const unsigned long long base =
         block_excl_scan((unsigned long long)s.hist[256 * kGrid + tid], tmp, &tot);
@@ -145,25 +154,38 @@ __global__ void __launch_bounds__(256) k_sort_scatter(const QueryDev q, const Sc
       __syncwarp();
     }
     __syncthreads();
-    {
-      unsigned acc = run[tid];
+    {  // thread tid = digit: offsets of the warps inside the tile's digit run
+      unsigned acc = 0;
 #pragma unroll
       for (int ww = 0; ww < 8; ++ww) {
         const unsigned cnt = wcnt[ww][tid];
         wcnt[ww][tid] = acc;
         acc += cnt;
       }
-      run[tid] = acc;
+      tcnt[tid] = acc;
+      unsigned long long tot;
+      lbase[tid] = (unsigned)block_excl_scan((unsigned long long)acc, tmp, &tot);
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
       if (dd[r] < 256u) {
-        const unsigned pos = wcnt[w][dd[r]] + rr[r];
-        dk[pos] = kk[r];
-        dv[pos] = vv[r];
+        const unsigned lp = lbase[dd[r]] + wcnt[w][dd[r]] + rr[r];
+        skey[lp] = kk[r];
+        sval[lp] = vv[r];
       }
     }
+    __syncthreads();
+    const unsigned nt = (unsigned)min((unsigned long long)kScatterTile, hi - tb);
+    for (unsigned i = tid; i < nt; i += blockDim.x) {
+      const unsigned long long k = skey[i];
+      const unsigned d = (unsigned)((k >> shift) & 0xffull);
+      const unsigned pos = run[d] + (i - lbase[d]);
+      dk[pos] = k;
+      dv[pos] = sval[i];
+    }
+    __syncthreads();
+    run[tid] += tcnt[tid];
     __syncthreads();
   }
 }
