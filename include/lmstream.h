@@ -656,6 +656,11 @@ lms_status lms_aggregate_batch_static(const lms_query_spec *q, int32_t value_typ
                                       const uint8_t *type, int64_t n_rows, void *cuda_stream,
                                       lms_result_row *rows, size_t rows_cap, size_t *n_out);
 
+/* The fused-pass variant the autotuner chose for batches of `rows` rows of a
+ * stream with this value type and number of queries (process-wide; 1 below
+ * 2^15 rows), or 0 while it is still timing the variants of that size class. */
+int32_t lms_k1_tuned_variant(int32_t value_type, int32_t n_queries, int64_t rows);
+
 /* Floor division helper the kernels use for window ids, exposed so that host
  * tests can check it: returns n / d for d >= 1 computed by the invariant
  * multiply-and-shift method of Granlund & Montgomery (1994). */

@@ -345,6 +345,14 @@ void record_k1_sample(lms_stream* s, long long n, int variant, float ms) {
 
 extern "C" {
 
+int32_t lms_k1_tuned_variant(int32_t value_type, int32_t n_queries, int64_t rows) {
+  if (n_queries < 1 || n_queries > kMaxQueries || rows < (1ll << 15)) return 1;
+  int b = 0;
+  while ((1ll << (b + 1)) <= rows && b < 47) ++b;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return g_tune[value_type == LMS_VALUE_FLOAT32 ? 1 : 0][n_queries][b].choice;
+}
+
 uint64_t lms_udiv_invariant(uint64_t n, uint64_t d) {
   if (d == 0) return 0;
   unsigned long long m;

@@ -266,6 +266,33 @@ lms_status lms_serve_gpu_create(const lms_stream_config* cfg, const lms_query_sp
       wr = push_microbatch(w, &b);
     }
     if (w) stream_close(w);
+    // let the autotuner settle every size class a batch can have, so that no
+    // measured batch runs a variant under trial
+    for (int c = 15; wr == LMS_OK && cfg->k1_variant == 0 && (1ll << c) <= max_batch_rows; ++c) {
+      const int64_t rows = 1ll << c;
+      if (lms_k1_tuned_variant(cfg->value_type, nq, rows) != 0) continue;
+      lms_stream* t = nullptr;
+      wr = stream_open(&wc, &t);
+      for (int i = 0; wr == LMS_OK && i < nq; ++i) {
+        int32_t id = 0;
+        wr = query_register(t, &qs[i], &id);
+      }
+      for (int rep = 0; wr == LMS_OK && rep < 16 && lms_k1_tuned_variant(cfg->value_type, nq, rows) == 0;
+           ++rep) {
+        lms_serve_chunk tc{(double)rep * 100.0, 100.0, rows, 0, rows, (int64_t)rep * rows};
+        long long toff = 0;
+        if ((wr = make_batch(g, &tc, 1, rows, &toff)) != LMS_OK) break;
+        lms_batch b{};
+        b.n_rows = rows;
+        b.ts = reinterpret_cast<const int64_t*>(g->ts);
+        b.key = g->key + toff;
+        b.value = g->val + toff;
+        b.memory = g->device_input ? LMS_MEM_DEVICE : LMS_MEM_HOST;
+        wr = push_microbatch(t, &b);
+        for (int q = 0; wr == LMS_OK && q < nq; ++q) wr = lms_results_discard(t, q);
+      }
+      if (t) stream_close(t);
+    }
     int64_t adm = -1;
     if (wr == LMS_OK) wr = lms_stream_admissible_rows(g->s, g->device_input ? 0 : 1, &adm);
     const int64_t res = (adm < 0 || adm > max_batch_rows) ? max_batch_rows : adm;

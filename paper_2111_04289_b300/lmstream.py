@@ -95,7 +95,7 @@ EXPORTED_SYMBOLS = ("stream_open", "query_register", "push_microbatch", "poll_re
                     "lms_serve_gpu_device_input", "lms_stream_push_bytes",
                     "lms_stream_device_bytes", "lms_server_create", "lms_server_submit",
                     "lms_server_wait", "lms_server_forget", "lms_server_get_stats",
-                    "lms_server_destroy", "lms_server_create_ops")
+                    "lms_server_destroy", "lms_server_create_ops", "lms_k1_tuned_variant")
 ADMIT_PAPER, ADMIT_GUARDED = 0, 1
 QOPS = {"aggregation": 0, "filter": 1, "shuffle": 2, "project": 3, "join": 4, "expand": 5,
         "scan": 6, "sort": 7}
@@ -295,6 +295,8 @@ def load(build_if_missing: bool = True):
     lib.lms_stream_device_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_uint64)]
     lib.lms_server_create.restype = I
     lib.lms_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(P)]
+    lib.lms_k1_tuned_variant.restype = I
+    lib.lms_k1_tuned_variant.argtypes = [I, I, ctypes.c_int64]
     lib.lms_server_create_ops.restype = I
     lib.lms_server_create_ops.argtypes = [ctypes.POINTER(ServerConfig),
                                           ctypes.POINTER(ServerOps), ctypes.POINTER(P)]
@@ -480,6 +482,12 @@ class Stream:
             self.close()
         except Exception:
             pass
+
+
+def k1_tuned_variant(value_type: str, n_queries: int, rows: int) -> int:
+    """The autotuner's fused-pass variant for this size class (0: still timing)."""
+    return int(load().lms_k1_tuned_variant(VALUE_FLOAT32 if value_type == "float32" else VALUE_INT32,
+                                           int(n_queries), int(rows)))
 
 
 def udiv_invariant(n: int, d: int) -> int:
