@@ -390,15 +390,7 @@ __device__ unsigned write_distinct(const QueryDev& q, const unsigned long long* 
     const SegAgg ex = seg_shfl_up(t, 1);
     if (lane == 31) wtot[w] = t;
     __syncthreads();
-    if (threadIdx.x == 0) {
-      SegAgg acc = carry;
-      for (int j = 0; j < kWarps; ++j) {
-        const SegAgg x = wtot[j];
-        wtot[j] = acc;
-        acc = seg_combine<FLOAT>(acc, x);
-      }
-      carry = acc;
-    }
+    seg_scan_warp_totals<FLOAT>(wtot, kWarps, &carry);
     __syncthreads();
     SegAgg pre = wtot[w];
     if (lane > 0) pre = seg_combine<FLOAT>(pre, ex);

@@ -363,15 +363,7 @@ __global__ void __launch_bounds__(256) k_rbk_write(const QueryDev q, const Scrat
     SegAgg ex = seg_shfl_up(t, 1);  // exclusive within the warp
     if (lane == 31) wtot[w] = t;
     __syncthreads();
-    if (threadIdx.x == 0) {  // exclusive prefix of the warps, from the carry
-      SegAgg acc = carry;
-      for (int j = 0; j < 8; ++j) {
-        const SegAgg x = wtot[j];
-        wtot[j] = acc;
-        acc = seg_combine<FLOAT>(acc, x);
-      }
-      carry = acc;  // everything up to the end of this tile
-    }
+    seg_scan_warp_totals<FLOAT>(wtot, 8, &carry);  // prefixes of the warps, from the carry
     __syncthreads();
     SegAgg pre = wtot[w];
     if (lane > 0) pre = seg_combine<FLOAT>(pre, ex);

@@ -174,6 +174,39 @@ __device__ __forceinline__ SegAgg seg_shfl_up(const SegAgg& v, int d) {
   return r;
 }
 
+__device__ __forceinline__ SegAgg seg_shfl_idx(const SegAgg& v, int src) {
+  SegAgg r;
+  r.f = __shfl_sync(kFull, v.f, src);
+  r.cnt = __shfl_sync(kFull, v.cnt, src);
+  r.sum = __shfl_sync(kFull, v.sum, src);
+  r.mn = __shfl_sync(kFull, v.mn, src);
+  r.mx = __shfl_sync(kFull, v.mx, src);
+  r.rank = __shfl_sync(kFull, v.rank, src);
+  return r;
+}
+
+// Exclusive segmented scan of the warp totals wt[0 .. nw) (nw <= 32), done by
+// warp 0 with shuffles, starting from *carry: wt[j] becomes what precedes warp
+// j and *carry what precedes the next tile.  Every thread of the block calls
+// it between two barriers; only warp 0 works.
+template <bool FLOAT>
+__device__ __forceinline__ void seg_scan_warp_totals(SegAgg* wt, int nw, SegAgg* carry) {
+  if (threadIdx.x >= 32) return;
+  const int lane = (int)threadIdx.x;
+  SegAgg incl = lane < nw ? wt[lane] : seg_identity();
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const SegAgg o = seg_shfl_up(incl, d);
+    if (lane >= d) incl = seg_combine<FLOAT>(o, incl);
+  }
+  const SegAgg ex = seg_shfl_up(incl, 1);
+  const SegAgg tot = seg_shfl_idx(incl, nw - 1);
+  const SegAgg c = *carry;
+  __syncwarp();
+  if (lane < nw) wt[lane] = lane == 0 ? c : seg_combine<FLOAT>(c, ex);
+  if (lane == 0) *carry = seg_combine<FLOAT>(c, tot);
+}
+
 // Contiguous chunk [lo, hi) of n items owned by chunk c of g chunks.
 __device__ __forceinline__ void chunk_range(unsigned long long n, int c, int g,
                                             unsigned long long* lo, unsigned long long* hi) {
