@@ -238,6 +238,29 @@ __device__ unsigned long long* merge_runs(unsigned long long* A, unsigned long l
   return A;
 }
 
+// 1/n as a double, to about 2^-47 relative, for 3 <= n < 2^24 with n not a
+// power of two, using no FP64 arithmetic (the FP64 pipe of this part is
+// narrow): r0 = RN(1/n) in float, e = 1 - n r0 by FMA, 1/n = r0 (1 + e + e^2
+// ...) ~ r0 + RN(r0 e); the two floats are summed into one double with integer
+// operations.  |r0 e| <= 2^-24 r0 and r0's mantissa is neither all zeros nor
+// all ones, so the sum stays in r0's binade (a carry into the exponent field
+// still gives the right bits).
+__device__ __forceinline__ double recip_small(unsigned n) {
+  const float nf = (float)n;  // exact below 2^24
+  const float r0 = __frcp_rn(nf);
+  const float rl = r0 * fmaf(-nf, r0, 1.0f);
+  const unsigned b0 = __float_as_uint(r0), b1 = __float_as_uint(rl);
+  const int e0 = (int)((b0 >> 23) & 0xffu);
+  long long m = (long long)(b0 & 0x7fffffu) << 29;  // mantissa field of the double
+  if (rl != 0.0f) {
+    const int sh = (int)((b1 >> 23) & 0xffu) - e0 + 29;  // rl's unit in the field's units
+    const long long m1 = (long long)((b1 & 0x7fffffu) | 0x800000u);
+    const long long c = sh >= 0 ? (m1 << sh) : (sh > -40 ? (m1 >> -sh) : 0ll);
+    m += (b1 >> 31) ? -c : c;
+  }
+  return __longlong_as_double(((long long)(e0 + 896) << 52) + m);
+}
+
 template <bool FLOAT>
 __device__ __forceinline__ void write_row(const QueryDev& q, ResultRowDev* out, long long wstart,
                                           unsigned key, long long cnt, unsigned long long sbits,
@@ -251,10 +274,13 @@ __device__ __forceinline__ void write_row(const QueryDev& q, ResultRowDev* out, 
   } else if ((cnt & (cnt - 1)) == 0) {
     const int e = __ffsll(cnt) - 1;
     avg = sd * __longlong_as_double((long long)(1023 - e) << 52);
+  } else if (FLOAT && cnt < (1ll << 24)) {
+    // float sums are checked to 1e-9 relative: one FP64 multiply by a
+    // reciprocal good to 2^-47
+    avg = sd * recip_small((unsigned)cnt);
   } else if (FLOAT) {
-    // FP64 division is slow on this part: a float32 reciprocal refined by two
-    // corrections with exact FMA remainders (error far below 1e-15 relative;
-    // float results are checked to 1e-9)
+    // larger counts: float32 reciprocal refined by two corrections with exact
+    // FMA remainders
     const double n = (double)cnt;
     const double r = (double)__frcp_rn((float)cnt);
     const double q0 = sd * r;
@@ -331,79 +357,59 @@ __device__ __forceinline__ unsigned long long count_distinct(const unsigned long
 
 // One row per distinct key of the merged window S[0..len) (entries key << 32 |
 // state index, key-sorted), written from out[0] in key order; returns the
-// number of rows.  Tiles of 4 consecutive entries per thread: every entry's
-// state group is gathered (independent loads), a segmented scan combines the
-// groups of each key across threads and tiles, and the thread holding a key's
-// last entry writes its row at the key's rank.
+// number of rows.  First the position of every key's first entry goes to
+// hp[rank] (hp: len + 1 words of scratch not aliasing S); then thread t takes
+// rows t, t + blockDim, ...: it combines the key's groups (one per pane that
+// holds the key) and writes the row, so a warp's rows are consecutive and its
+// stores coalesce.  Ends with a barrier (hp may be reused).
 template <bool FLOAT, bool PAD>
 __device__ unsigned write_distinct(const QueryDev& q, const unsigned long long* S, unsigned len,
-                                   long long wstart, ResultRowDev* out) {
-  constexpr int kItems = 4;
-  constexpr int kWarps = kEmitThreads / 32;
-  __shared__ SegAgg wtot[kWarps];
-  __shared__ SegAgg carry;
-  __shared__ unsigned long long hs[33];
-  const unsigned lane = lane_id(), w = threadIdx.x >> 5;
-  if (threadIdx.x == 0) carry = seg_identity();
+                                   long long wstart, ResultRowDev* out, unsigned* hp,
+                                   unsigned* wt) {
+  const unsigned per = (len + blockDim.x - 1) / blockDim.x;
+  const unsigned a = min(len, threadIdx.x * per), b = min(len, a + per);
+  unsigned nrows;
+  unsigned r = block_scan_u32(chunk_heads<PAD>(S, len, a, b), wt, &nrows);
+  unsigned prev = a > 0 ? (unsigned)(S[pix<PAD>(a - 1)] >> 32) : 0u;
+  for (unsigned i = a; i < b; ++i) {
+    const unsigned k = (unsigned)(S[pix<PAD>(i)] >> 32);
+    if (i == 0 || k != prev) hp[r++] = i;
+    prev = k;
+  }
+  if (threadIdx.x == 0) hp[nrows] = len;
   __syncthreads();
-  unsigned long long heads_before = 0;
-  for (unsigned base = 0; base < len; base += kEmitThreads * kItems) {
-    const unsigned i0 = base + threadIdx.x * kItems;
-    unsigned key[kItems];
-    bool head[kItems], last[kItems];
-    SegAgg v[kItems];
-    unsigned nh = 0;
-#pragma unroll
-    for (int u = 0; u < kItems; ++u) {
-      const unsigned i = i0 + u;
-      const bool valid = i < len;
-      unsigned long long e = valid ? S[pix<PAD>(i)] : 0ull;
-      key[u] = (unsigned)(e >> 32);
-      head[u] = valid && (i == 0 || (unsigned)(S[pix<PAD>(i - 1)] >> 32) != key[u]);
-      last[u] = valid && (i + 1 == len || (unsigned)(S[pix<PAD>(i + 1)] >> 32) != key[u]);
-      nh += head[u] ? 1u : 0u;
-      if (valid) {
-        const Grp g = load_grp(q.state + (e & 0xffffffffull));
-        v[u].f = head[u] ? 1u : 0u;
-        v[u].cnt = g.cnt;
-        v[u].sum = g.sum;
-        v[u].mn = g.mn;
-        v[u].mx = g.mx;
-        v[u].rank = 0ull;
-      } else {
-        v[u] = seg_identity();
+  const Grp* __restrict__ st = q.state;
+  for (unsigned row = threadIdx.x; row < nrows; row += blockDim.x) {
+    const unsigned e0 = hp[row], e1 = hp[row + 1];
+    const unsigned long long x0 = S[pix<PAD>(e0)];
+    const Grp g0 = load_grp(st + (x0 & 0xffffffffull));
+    long long cnt = g0.cnt;
+    unsigned long long isum = g0.sum;
+    double fsum = __longlong_as_double((long long)g0.sum);
+    unsigned mn = g0.mn, mx = g0.mx;
+    for (unsigned e = e0 + 1; e < e1; e += 2) {  // the key's other panes, two loads in flight
+      const bool two = e + 1 < e1;
+      const Grp g1 = load_grp(st + (S[pix<PAD>(e)] & 0xffffffffull));
+      Grp g2 = g1;
+      if (two) g2 = load_grp(st + (S[pix<PAD>(e + 1)] & 0xffffffffull));
+      cnt += g1.cnt;
+      mn = min(mn, g1.mn);
+      mx = max(mx, g1.mx);
+      if (FLOAT) fsum += __longlong_as_double((long long)g1.sum);
+      else isum += g1.sum;
+      if (two) {
+        cnt += g2.cnt;
+        mn = min(mn, g2.mn);
+        mx = max(mx, g2.mx);
+        if (FLOAT) fsum += __longlong_as_double((long long)g2.sum);
+        else isum += g2.sum;
       }
     }
-    unsigned long long htot;
-    unsigned long long hpre = block_excl_scan((unsigned long long)nh, hs, &htot);
-#pragma unroll
-    for (int u = 0; u < kItems; ++u)
-      if (head[u]) v[u].rank = heads_before + hpre++;
-#pragma unroll
-    for (int u = 1; u < kItems; ++u) v[u] = seg_combine<FLOAT>(v[u - 1], v[u]);
-    SegAgg t = v[kItems - 1];
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const SegAgg o = seg_shfl_up(t, d);
-      if ((int)lane >= d) t = seg_combine<FLOAT>(o, t);
-    }
-    const SegAgg ex = seg_shfl_up(t, 1);
-    if (lane == 31) wtot[w] = t;
-    __syncthreads();
-    seg_scan_warp_totals<FLOAT>(wtot, kWarps, &carry);
-    __syncthreads();
-    SegAgg pre = wtot[w];
-    if (lane > 0) pre = seg_combine<FLOAT>(pre, ex);
-#pragma unroll
-    for (int u = 0; u < kItems; ++u) {
-      if (!last[u]) continue;
-      const SegAgg r = seg_combine<FLOAT>(pre, v[u]);
-      write_row<FLOAT>(q, out + r.rank, wstart, key[u], r.cnt, r.sum, r.mn, r.mx);
-    }
-    heads_before += htot;
-    __syncthreads();
+    const unsigned long long sb = FLOAT ? (unsigned long long)__double_as_longlong(fsum) : isum;
+    write_row<FLOAT>(q, out + row, wstart, (unsigned)(x0 >> 32), cnt, sb, mn, mx);
   }
-  return (unsigned)heads_before;
+  __syncthreads();
+  return nrows;
 }
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -560,7 +566,8 @@ __device__ unsigned long long run_range(const QueryDev& q, const Scratch& s, QCt
         m.bnd0[r] = (unsigned)(s.pane_begin[j0 + r] - b0);
       __syncthreads();
       const unsigned long long* S = merge_runs<false>(A, B, m.bnd0, m.bnd1, nr, len);
-      if (WRITE) acc += write_distinct<FLOAT, false>(q, S, len, wstart, out + acc);
+      unsigned* hp = reinterpret_cast<unsigned*>(S == A ? B : A);  // len u64 free: >= len + 1 words
+      if (WRITE) acc += write_distinct<FLOAT, false>(q, S, len, wstart, out + acc, hp, m.wt);
       else acc += count_distinct<false>(S, len, m.wt);
       __syncthreads();
       continue;
@@ -598,7 +605,10 @@ __device__ unsigned long long run_range(const QueryDev& q, const Scratch& s, QCt
     cj1 = j1;
     n = len;
     __syncthreads();
-    if (WRITE) acc += write_distinct<FLOAT, true>(q, m.L, len, wstart, out + acc);
+    // the other buffer is free until the next window: it holds the key heads
+    if (WRITE)
+      acc += write_distinct<FLOAT, true>(q, m.L, len, wstart, out + acc,
+                                         reinterpret_cast<unsigned*>(m.T), m.wt);
     else acc += count_distinct<true>(m.L, len, m.wt);
   }
   __syncthreads();
