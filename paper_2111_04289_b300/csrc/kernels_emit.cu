@@ -21,6 +21,7 @@ namespace lms {
 namespace {
 
 constexpr int kEmitThreads = 512;
+constexpr unsigned kWwStage = 512;  // window ids of a range staged for the count pass
 constexpr size_t kEmitSmemMax = 224 * 1024;  // dynamic shared memory of the emit kernel (static: ~2.3 KB)
 // Largest window (entries) merged in shared memory for windows of k panes:
 // two padded buffers (17 slots per 16 entries) plus two (k+1)-entry boundary
@@ -378,7 +379,9 @@ __device__ unsigned write_distinct(const QueryDev& q, const unsigned long long* 
   }
   if (threadIdx.x == 0) hp[nrows] = len;
   __syncthreads();
-  const Grp* __restrict__ st = q.state;
+  // Every load is issued unconditionally (an exhausted row re-reads its last
+  // entry) so that a row's gathers are in flight together.
+  const Grp* st = q.state;
   for (unsigned row = threadIdx.x; row < nrows; row += blockDim.x) {
     const unsigned e0 = hp[row], e1 = hp[row + 1];
     const unsigned long long x0 = S[pix<PAD>(e0)];
@@ -389,9 +392,9 @@ __device__ unsigned write_distinct(const QueryDev& q, const unsigned long long* 
     unsigned mn = g0.mn, mx = g0.mx;
     for (unsigned e = e0 + 1; e < e1; e += 2) {  // the key's other panes, two loads in flight
       const bool two = e + 1 < e1;
-      const Grp g1 = load_grp(st + (S[pix<PAD>(e)] & 0xffffffffull));
-      Grp g2 = g1;
-      if (two) g2 = load_grp(st + (S[pix<PAD>(e + 1)] & 0xffffffffull));
+      const unsigned long long x1 = S[pix<PAD>(e)], x2 = S[pix<PAD>(two ? e + 1 : e)];
+      const Grp g1 = load_grp(st + (x1 & 0xffffffffull));
+      const Grp g2 = load_grp(st + (x2 & 0xffffffffull));
       cnt += g1.cnt;
       mn = min(mn, g1.mn);
       mx = max(mx, g1.mx);
@@ -644,11 +647,18 @@ __device__ unsigned long long count_range(const QueryDev& q, const Scratch& s, Q
   __syncthreads();
   if (*s_fail) return ~0ull;  // count by assembling the windows instead
   for (unsigned i = threadIdx.x; i < tab_n; i += blockDim.x) tab[i] = 0ull;  // pane ids are >= 1
-  __syncthreads();
   const unsigned j_begin = s.win_j0[wa], j_end = s.win_j1[wb - 1];
   const long long w_first = s.win_w[wa], w_last = s.win_w[wb - 1];
   const long long* ww = s.win_w + wa;
   const unsigned nw = (unsigned)(wb - wa);
+  // the range's window ids: consecutive (counts by arithmetic), else searched
+  // in shared memory when they fit, else in global memory
+  __shared__ unsigned s_ww[kWwStage];
+  const bool contig = w_last - w_first + 1 == (long long)nw;
+  const bool staged = !contig && nw <= kWwStage && w_last - w_first < (1ll << 32);
+  if (staged)
+    for (unsigned i = threadIdx.x; i < nw; i += blockDim.x) s_ww[i] = (unsigned)(ww[i] - w_first);
+  __syncthreads();
   unsigned long long total = 0;
   for (unsigned j = j_begin; j < j_end; ++j) {
     const long long P = (long long)s.pane_id[j];
@@ -698,6 +708,27 @@ __device__ unsigned long long count_range(const QueryDev& q, const Scratch& s, Q
       lo = max(lo, w_first);
       hi = min(hi, w_last);
       if (lo > hi) continue;
+      if (contig) {
+        total += (unsigned long long)(hi - lo + 1);
+        continue;
+      }
+      if (staged) {  // ids relative to w_first (their span is below 2^32)
+        const unsigned rl = (unsigned)(lo - w_first), rh = (unsigned)(hi - w_first);
+        unsigned a = 0, b = nw;  // first window with id >= lo
+        while (a < b) {
+          const unsigned m = (a + b) >> 1;
+          if (s_ww[m] < rl) a = m + 1;
+          else b = m;
+        }
+        unsigned c = a, d = nw;  // first window with id > hi
+        while (c < d) {
+          const unsigned m = (c + d) >> 1;
+          if (s_ww[m] <= rh) c = m + 1;
+          else d = m;
+        }
+        total += c - a;
+        continue;
+      }
       unsigned a = 0, b = nw;  // first window with id >= lo
       while (a < b) {
         const unsigned m = (a + b) >> 1;

@@ -85,6 +85,27 @@ def test_ragged_batch_sizes(n):
     _check(batches, [dict(size=1_000, slide=250), dict(size=700)], False)
 
 
+def _gapped(n, gap, seed, card=50):
+    """One batch whose events sit every `gap` ms: windows anchored at absent
+    panes do not exist, so a range's window ids are not consecutive."""
+    b = synth.TinyIntStream(seed=seed, card=card).next_batch(n)
+    b.ts = np.arange(n, dtype=np.int64) * gap
+    return b
+
+
+def test_gapped_panes_few_windows_per_range():
+    """Non-consecutive window ids, few per range (searched in shared memory)."""
+    b = _gapped(40_000, 3, seed=61)
+    _check([b], [dict(size=2, slide=1), dict(size=4, slide=2)], False)
+
+
+def test_gapped_panes_many_windows_per_range():
+    """Non-consecutive window ids, more per range than are staged (searched in
+    global memory): over 512 windows for each of the kernel's ranges."""
+    b = _gapped(1_300_000, 2, seed=67)
+    _check([b], [dict(size=1)], False)
+
+
 def test_empty_stream_and_eos_only():
     b = synth.TinyIntStream().next_batch(0)
     eng, st = _check([b, b], [dict(size=1_000)], False)
