@@ -660,90 +660,114 @@ __device__ unsigned long long count_range(const QueryDev& q, const Scratch& s, Q
     for (unsigned i = threadIdx.x; i < nw; i += blockDim.x) s_ww[i] = (unsigned)(ww[i] - w_first);
   __syncthreads();
   unsigned long long total = 0;
-  for (unsigned j = j_begin; j < j_end; ++j) {
-    const long long P = (long long)s.pane_id[j];
-    const unsigned long long g0 = s.pane_begin[j], g1 = s.pane_begin[j + 1];
-    for (unsigned long long g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
-      const unsigned key = (unsigned)q.state[g].gkey;
-      const unsigned long long nv = ((unsigned long long)P << 32) | key;
-      long long prev = LLONG_MIN;
-      unsigned h = (unsigned)(((unsigned long long)(key * 0x9E3779B1u) * tab_n) >> 32);
-      unsigned stale = 0xffffffffu;
-      unsigned long long stale_v = 0ull;
-      bool done = false;
-      for (unsigned probe = 0; probe < 256u && !done; ++probe) {
-        const unsigned long long e = *((volatile unsigned long long*)&tab[h]);
-        if (e != 0ull && (unsigned)e == key) {  // the key's entry: update its pane
-          if (atomicCAS(&tab[h], e, nv) == e) {
-            prev = (long long)(e >> 32);
+  // one group (key of pane P): update the key's last pane in the table and add
+  // the range's windows in which this group is the key's first occurrence
+  auto group = [&](unsigned key, long long P) {
+    const unsigned long long nv = ((unsigned long long)P << 32) | key;
+    long long prev = LLONG_MIN;
+    unsigned h = (unsigned)(((unsigned long long)(key * 0x9E3779B1u) * tab_n) >> 32);
+    unsigned stale = 0xffffffffu;
+    unsigned long long stale_v = 0ull;
+    bool done = false;
+    for (unsigned probe = 0; probe < 256u && !done; ++probe) {
+      const unsigned long long e = *((volatile unsigned long long*)&tab[h]);
+      if (e != 0ull && (unsigned)e == key) {  // the key's entry: update its pane
+        if (atomicCAS(&tab[h], e, nv) == e) {
+          prev = (long long)(e >> 32);
+          done = true;
+        }
+        continue;  // changed under us: look again
+      }
+      if (e == 0ull) {  // the key is absent: take the first stale slot seen, else this one
+        if (stale != 0xffffffffu) {
+          if (atomicCAS(&tab[stale], stale_v, nv) == stale_v) {
             done = true;
+          } else {
+            stale = 0xffffffffu;  // taken meanwhile: start over
+            h = (unsigned)(((unsigned long long)(key * 0x9E3779B1u) * tab_n) >> 32);
           }
-          continue;  // changed under us: look again
+        } else if (atomicCAS(&tab[h], 0ull, nv) == 0ull) {
+          done = true;
         }
-        if (e == 0ull) {  // the key is absent: take the first stale slot seen, else this one
-          if (stale != 0xffffffffu) {
-            if (atomicCAS(&tab[stale], stale_v, nv) == stale_v) {
-              done = true;
-            } else {
-              stale = 0xffffffffu;  // taken meanwhile: start over
-              h = (unsigned)(((unsigned long long)(key * 0x9E3779B1u) * tab_n) >> 32);
-            }
-          } else if (atomicCAS(&tab[h], 0ull, nv) == 0ull) {
-            done = true;
-          }
-          continue;
-        }
-        if (stale == 0xffffffffu && (long long)(e >> 32) < P - q.k + 1) {
-          stale = h;  // no window still to come can contain that entry's pane
-          stale_v = e;
-        }
-        h = h + 1 == tab_n ? 0u : h + 1;
-      }
-      if (!done) {
-        atomicOr(s_fail, 1u);
         continue;
       }
-      long long lo = prev == LLONG_MIN ? P - q.k + 1 : max(prev + 1, P - q.k + 1);
-      long long hi = P;
-      lo = max(lo, w_first);
-      hi = min(hi, w_last);
-      if (lo > hi) continue;
-      if (contig) {
-        total += (unsigned long long)(hi - lo + 1);
-        continue;
+      if (stale == 0xffffffffu && (long long)(e >> 32) < P - q.k + 1) {
+        stale = h;  // no window still to come can contain that entry's pane
+        stale_v = e;
       }
-      if (staged) {  // ids relative to w_first (their span is below 2^32)
-        const unsigned rl = (unsigned)(lo - w_first), rh = (unsigned)(hi - w_first);
-        unsigned a = 0, b = nw;  // first window with id >= lo
-        while (a < b) {
-          const unsigned m = (a + b) >> 1;
-          if (s_ww[m] < rl) a = m + 1;
-          else b = m;
-        }
-        unsigned c = a, d = nw;  // first window with id > hi
-        while (c < d) {
-          const unsigned m = (c + d) >> 1;
-          if (s_ww[m] <= rh) c = m + 1;
-          else d = m;
-        }
-        total += c - a;
-        continue;
-      }
+      h = h + 1 == tab_n ? 0u : h + 1;
+    }
+    if (!done) {
+      atomicOr(s_fail, 1u);
+      return;
+    }
+    long long lo = prev == LLONG_MIN ? P - q.k + 1 : max(prev + 1, P - q.k + 1);
+    long long hi = P;
+    lo = max(lo, w_first);
+    hi = min(hi, w_last);
+    if (lo > hi) return;
+    if (contig) {
+      total += (unsigned long long)(hi - lo + 1);
+      return;
+    }
+    if (staged) {  // ids relative to w_first (their span is below 2^32)
+      const unsigned rl = (unsigned)(lo - w_first), rh = (unsigned)(hi - w_first);
       unsigned a = 0, b = nw;  // first window with id >= lo
       while (a < b) {
         const unsigned m = (a + b) >> 1;
-        if (ww[m] < lo) a = m + 1;
+        if (s_ww[m] < rl) a = m + 1;
         else b = m;
       }
       unsigned c = a, d = nw;  // first window with id > hi
       while (c < d) {
         const unsigned m = (c + d) >> 1;
-        if (ww[m] <= hi) c = m + 1;
+        if (s_ww[m] <= rh) c = m + 1;
         else d = m;
       }
       total += c - a;
+      return;
     }
-    __syncthreads();  // this pane's table updates before the next pane's lookups
+    unsigned a = 0, b = nw;  // first window with id >= lo
+    while (a < b) {
+      const unsigned m = (a + b) >> 1;
+      if (ww[m] < lo) a = m + 1;
+      else b = m;
+    }
+    unsigned c = a, d = nw;  // first window with id > hi
+    while (c < d) {
+      const unsigned m = (c + d) >> 1;
+      if (ww[m] <= hi) c = m + 1;
+      else d = m;
+    }
+    total += c - a;
+  };
+  // Panes in order, one barrier per pane (its table updates before the next
+  // pane's lookups).  The next pane's bounds and this thread's first two keys
+  // of it are loaded while the current pane is processed.
+  const Grp* st = q.state;
+  const unsigned bd = blockDim.x;
+  long long nP = 0;
+  unsigned long long ng0 = 0, ng1 = 0;
+  unsigned nk0 = 0, nk1 = 0;
+  auto fetch = [&](unsigned jj) {
+    nP = (long long)s.pane_id[jj];
+    ng0 = s.pane_begin[jj];
+    ng1 = s.pane_begin[jj + 1];
+    const unsigned long long ga = ng0 + threadIdx.x, gb = ga + bd;
+    nk0 = ga < ng1 ? (unsigned)st[ga].gkey : 0u;
+    nk1 = gb < ng1 ? (unsigned)st[gb].gkey : 0u;
+  };
+  if (j_begin < j_end) fetch(j_begin);
+  for (unsigned j = j_begin; j < j_end; ++j) {
+    const long long P = nP;
+    const unsigned long long g0 = ng0, g1 = ng1;
+    const unsigned k0 = nk0, k1 = nk1;
+    if (j + 1 < j_end) fetch(j + 1);
+    const unsigned long long ga = g0 + threadIdx.x;
+    if (ga < g1) group(k0, P);
+    if (ga + bd < g1) group(k1, P);
+    for (unsigned long long g = ga + 2ull * bd; g < g1; g += bd) group((unsigned)st[g].gkey, P);
+    __syncthreads();
   }
   __shared__ unsigned long long ctmp[33];
   unsigned long long tot;
