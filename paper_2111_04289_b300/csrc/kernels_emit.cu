@@ -293,12 +293,15 @@ __device__ __forceinline__ void write_row(const QueryDev& q, ResultRowDev* out, 
   unsigned mnv = 0u, mxv = 0u;
   if (q.agg_mask & 4u) mnv = FLOAT ? dec_f32_bits(mn) : (unsigned)dec_i32(mn);
   if (q.agg_mask & 8u) mxv = FLOAT ? dec_f32_bits(mx) : (unsigned)dec_i32(mx);
+  // rows are written once and read only by the host: streaming stores, so
+  // that they do not displace the state groups the next windows gather
   uint4* o = reinterpret_cast<uint4*>(out);
-  o[0] = make_uint4((unsigned)wstart, (unsigned)((unsigned long long)wstart >> 32), (unsigned)cnt,
-                    (unsigned)((unsigned long long)cnt >> 32));
+  __stcs(o, make_uint4((unsigned)wstart, (unsigned)((unsigned long long)wstart >> 32),
+                       (unsigned)cnt, (unsigned)((unsigned long long)cnt >> 32)));
   const unsigned long long ab = (unsigned long long)__double_as_longlong(avg);
-  o[1] = make_uint4((unsigned)sbits, (unsigned)(sbits >> 32), (unsigned)ab, (unsigned)(ab >> 32));
-  o[2] = make_uint4(key, mnv, mxv, (unsigned)q.qid);
+  __stcs(o + 1,
+         make_uint4((unsigned)sbits, (unsigned)(sbits >> 32), (unsigned)ab, (unsigned)(ab >> 32)));
+  __stcs(o + 2, make_uint4(key, mnv, mxv, (unsigned)q.qid));
 }
 
 // Exclusive scan of one count per thread over the block; returns the prefix
