@@ -68,12 +68,20 @@ __global__ void __launch_bounds__(256) k_sort_hist(const QueryDev q, const Scrat
   const SortSrc src = pass_src(q, s, p);
   unsigned long long lo, hi;
   chunk_range(c->n_parts, blockIdx.x, gridDim.x, &lo, &hi);
-  for (unsigned long long i0 = lo; i0 < hi; i0 += blockDim.x) {
-    const unsigned long long i = i0 + threadIdx.x;
-    const bool v = i < hi;
-    const unsigned d = v ? (unsigned)((src.keys[i] >> shift) & 0xffull) : 256u;
-    const unsigned peers = __match_any_sync(kFull, d);
-    if (v && (int)lane_id() == __ffs(peers) - 1) atomicAdd(&h[d], (unsigned)__popc(peers));
+  constexpr int kU = 8;  // keys loaded per thread before any is counted
+  for (unsigned long long i0 = lo; i0 < hi; i0 += kU * blockDim.x) {
+    unsigned d[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const unsigned long long i = i0 + u * blockDim.x + threadIdx.x;
+      d[u] = i < hi ? (unsigned)((src.keys[i] >> shift) & 0xffull) : 256u;
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const unsigned peers = __match_any_sync(kFull, d[u]);
+      if (d[u] < 256u && (int)lane_id() == __ffs(peers) - 1)
+        atomicAdd(&h[d[u]], (unsigned)__popc(peers));
+    }
   }
   __syncthreads();
   s.hist[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
@@ -108,16 +116,36 @@ __global__ void __launch_bounds__(256) k_sort_scan(const QueryDev q, const Scrat
 // ranks inside each warp's 256 items (match_any per round), the tile's
 // per-digit counts and offsets, then the items are placed in shared memory in
 // (digit, original order) and written out from there, so that consecutive
-// threads write consecutive positions of each digit's run (coalesced).
+// threads write consecutive positions of each digit's run (coalesced).  The
+// next tile's items are fetched into shared memory by asynchronous copies
+// while the current tile is processed: each thread copies, and later reads,
+// its own items only, so its own wait on the copies is all the ordering this
+// needs.
+constexpr size_t kScatterSmem = kScatterTile * (8 + 4)      // next tile's items (async copies)
+                                + kScatterTile * (8 + 4)    // the tile in digit order
+                                + 8 * 256 * 2;              // per-warp digit counts / offsets
+
+__device__ __forceinline__ void cp_async(void* sdst, const void* gsrc, int bytes, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+  if (bytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(gsrc),
+                 "r"(valid ? 8 : 0) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(gsrc),
+                 "r"(valid ? 4 : 0) : "memory");
+}
+
 __global__ void __launch_bounds__(256, 4) k_sort_scatter(const QueryDev q, const Scratch s, int p) {
   const QCtl* c = q.ctl;
   if (p >= c->npasses) return;
-  __shared__ unsigned run[256];   // the CTA's next global position per digit
-  __shared__ unsigned lbase[256]; // the tile's first local position per digit
-  __shared__ unsigned tcnt[256];  // the tile's items per digit
-  __shared__ unsigned wcnt[8][256];
-  __shared__ unsigned long long skey[kScatterTile];
-  __shared__ unsigned sval[kScatterTile];
+  extern __shared__ __align__(16) unsigned char ssm[];
+  unsigned long long* ikey = reinterpret_cast<unsigned long long*>(ssm);
+  unsigned* ival = reinterpret_cast<unsigned*>(ikey + kScatterTile);
+  unsigned long long* skey = reinterpret_cast<unsigned long long*>(ival + kScatterTile);
+  unsigned* sval = reinterpret_cast<unsigned*>(skey + kScatterTile);
+  unsigned short (*wcnt)[256] = reinterpret_cast<unsigned short (*)[256]>(sval + kScatterTile);
+  __shared__ unsigned run[256];             // the CTA's next global position per digit
+  __shared__ unsigned short lbase[257];     // the tile's first local position per digit
   __shared__ unsigned long long tmp[33];
   const int tid = threadIdx.x, w = tid >> 5;
   const unsigned lane = lane_id();
@@ -134,23 +162,43 @@ __global__ void __launch_bounds__(256, 4) k_sort_scatter(const QueryDev q, const
     run[tid] = (unsigned)base + s.hist[tid * gridDim.x + blockIdx.x];
   }
   const unsigned lt = (1u << lane) - 1u;
+  const unsigned my = (unsigned)(w * 256) + lane;  // this thread's items: my + 32 r of each tile
+  auto fetch = [&](unsigned long long tb) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const unsigned long long i = tb + my + 32 * r;
+      const bool v = i < hi;
+      const unsigned long long ic = v ? i : lo;  // a valid address even when nothing is read
+      cp_async(ikey + my + 32 * r, src.keys + ic, 8, v);
+      if (src.vals) cp_async(ival + my + 32 * r, src.vals + ic, 4, v);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  if (lo < hi) fetch(lo);
   for (unsigned long long tb = lo; tb < hi; tb += kScatterTile) {
 #pragma unroll
     for (int j = 0; j < 8; ++j) wcnt[w][lane + 32 * j] = 0u;
-    __syncthreads();
+    asm volatile("cp.async.wait_all;" ::: "memory");
     unsigned long long kk[8];
-    unsigned vv[8], dd[8], rr[8];
+    unsigned vv[8], rr[4];  // ranks (< 256) packed two per word
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
-      const unsigned long long i = tb + (unsigned long long)(w * 256 + r * 32) + lane;
-      const bool v = i < hi;
-      kk[r] = v ? src.keys[i] : 0ull;
-      vv[r] = v ? (src.vals ? src.vals[i] : (unsigned)i) : 0u;
-      dd[r] = v ? (unsigned)((kk[r] >> shift) & 0xffull) : 256u;
-      const unsigned peers = __match_any_sync(kFull, dd[r]);
-      rr[r] = (v ? wcnt[w][dd[r]] : 0u) + __popc(peers & lt);
+      kk[r] = ikey[my + 32 * r];
+      vv[r] = src.vals ? ival[my + 32 * r] : (unsigned)(tb + my + 32 * r);
+    }
+    if (tb + kScatterTile < hi) fetch(tb + kScatterTile);
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const bool v = tb + my + 32 * r < hi;
+      const unsigned d = v ? (unsigned)((kk[r] >> shift) & 0xffull) : 256u;
+      const unsigned peers = __match_any_sync(kFull, d);
+      const unsigned rk = (v ? (unsigned)wcnt[w][d] : 0u) + __popc(peers & lt);
+      if (r & 1) rr[r >> 1] |= rk << 16;
+      else rr[r >> 1] = rk;
       __syncwarp();
-      if (v && (int)lane == __ffs(peers) - 1) wcnt[w][dd[r]] += __popc(peers);
+      if (v && (int)lane == __ffs(peers) - 1)
+        wcnt[w][d] = (unsigned short)(wcnt[w][d] + __popc(peers));
       __syncwarp();
     }
     __syncthreads();
@@ -159,18 +207,20 @@ __global__ void __launch_bounds__(256, 4) k_sort_scatter(const QueryDev q, const
 #pragma unroll
       for (int ww = 0; ww < 8; ++ww) {
         const unsigned cnt = wcnt[ww][tid];
-        wcnt[ww][tid] = acc;
+        wcnt[ww][tid] = (unsigned short)acc;
         acc += cnt;
       }
-      tcnt[tid] = acc;
       unsigned long long tot;
-      lbase[tid] = (unsigned)block_excl_scan((unsigned long long)acc, tmp, &tot);
+      lbase[tid] = (unsigned short)block_excl_scan((unsigned long long)acc, tmp, &tot);
+      if (tid == 255) lbase[256] = (unsigned short)tot;
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
-      if (dd[r] < 256u) {
-        const unsigned lp = lbase[dd[r]] + wcnt[w][dd[r]] + rr[r];
+      if (tb + my + 32 * r < hi) {
+        const unsigned d = (unsigned)((kk[r] >> shift) & 0xffull);
+        const unsigned rk = (rr[r >> 1] >> (16 * (r & 1))) & 0xffffu;
+        const unsigned lp = (unsigned)lbase[d] + wcnt[w][d] + rk;
         skey[lp] = kk[r];
         sval[lp] = vv[r];
       }
@@ -185,7 +235,7 @@ __global__ void __launch_bounds__(256, 4) k_sort_scatter(const QueryDev q, const
       dv[pos] = sval[i];
     }
     __syncthreads();
-    run[tid] += tcnt[tid];
+    run[tid] += (unsigned)lbase[tid + 1] - (unsigned)lbase[tid];
     __syncthreads();
   }
 }
@@ -491,13 +541,16 @@ __global__ void __launch_bounds__(256) k_pane_write(const QueryDev q, const Scra
 
 cudaError_t launch_sort_reduce(const QueryDev& q, const Scratch& s, cudaStream_t st,
                                int* launches) {
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
+  if (attr != cudaSuccess) return attr;
   int nl = 0;
   k_sort_plan<<<1, 32, 0, st>>>(q.ctl);
   ++nl;
   for (int p = 0; p < 8; ++p) {
     k_sort_hist<<<kGrid, 256, 0, st>>>(q, s, p);
     k_sort_scan<<<256, 256, 0, st>>>(q, s, p);
-    k_sort_scatter<<<kGrid, 256, 0, st>>>(q, s, p);
+    k_sort_scatter<<<kGrid, 256, kScatterSmem, st>>>(q, s, p);
     nl += 3;
   }
   k_rbk_count<<<kGrid, 256, 0, st>>>(q, s);
