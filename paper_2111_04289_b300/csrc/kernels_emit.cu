@@ -388,7 +388,7 @@ __device__ unsigned write_distinct(const QueryDev& q, const unsigned long long* 
   for (unsigned row = threadIdx.x; row < nrows; row += blockDim.x) {
     const unsigned e0 = hp[row], e1 = hp[row + 1];
     const unsigned long long x0 = S[pix<PAD>(e0)];
-    const Grp g0 = load_grp(st + (x0 & 0xffffffffull));
+    const Grp g0 = load_grp_v(st + (x0 & 0xffffffffull));
     long long cnt = g0.cnt;
     unsigned long long isum = g0.sum;
     double fsum = __longlong_as_double((long long)g0.sum);
@@ -396,8 +396,8 @@ __device__ unsigned write_distinct(const QueryDev& q, const unsigned long long* 
     for (unsigned e = e0 + 1; e < e1; e += 2) {  // the key's other panes, two loads in flight
       const bool two = e + 1 < e1;
       const unsigned long long x1 = S[pix<PAD>(e)], x2 = S[pix<PAD>(two ? e + 1 : e)];
-      const Grp g1 = load_grp(st + (x1 & 0xffffffffull));
-      const Grp g2 = load_grp(st + (x2 & 0xffffffffull));
+      const Grp g1 = load_grp_v(st + (x1 & 0xffffffffull));
+      const Grp g2 = load_grp_v(st + (x2 & 0xffffffffull));
       cnt += g1.cnt;
       mn = min(mn, g1.mn);
       mx = max(mx, g1.mx);

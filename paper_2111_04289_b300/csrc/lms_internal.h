@@ -35,7 +35,7 @@ constexpr unsigned kErrNeedRetry = kErrWinOverflow | kErrRowsOverflow | kErrPool
 
 // One (pane, key) group: a 32-byte record, so that a random gather of a group
 // touches one DRAM sector.
-struct __align__(16) Grp {
+struct __align__(32) Grp {
   unsigned long long gkey;
   long long cnt;
   unsigned long long sum;  // int64 sum, or the bits of a double sum
