@@ -448,16 +448,26 @@ __global__ void __launch_bounds__(256) k_rbk_long(const QueryDev q, const Scratc
     unsigned long long isum = 0ull;
     double fsum = 0.0;
     unsigned mn = 0xffffffffu, mx = 0u;
-    for (unsigned long long j = a + threadIdx.x; j < b; j += blockDim.x) {
-      const unsigned long long pi = src.vals ? src.vals[j] : j;
-      const Grp g = load_grp(q.parts + pi);
-      cnt += g.cnt;
-      if (FLOAT)
-        fsum += __longlong_as_double((long long)g.sum);
-      else
-        isum += g.sum;
-      mn = min(mn, g.mn);
-      mx = max(mx, g.mx);
+    constexpr int kU = 4;  // gathers in flight per thread
+    for (unsigned long long j0 = a + threadIdx.x; j0 < b; j0 += kU * blockDim.x) {
+      Grp g[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const unsigned long long j = j0 + (unsigned long long)u * blockDim.x;
+        const unsigned long long pi = j < b ? (src.vals ? src.vals[j] : j) : 0ull;
+        if (j < b) g[u] = load_grp(q.parts + pi);
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        if (j0 + (unsigned long long)u * blockDim.x >= b) break;
+        cnt += g[u].cnt;
+        if (FLOAT)
+          fsum += __longlong_as_double((long long)g[u].sum);
+        else
+          isum += g[u].sum;
+        mn = min(mn, g[u].mn);
+        mx = max(mx, g[u].mx);
+      }
     }
     unsigned long long sbits = FLOAT ? (unsigned long long)__double_as_longlong(fsum) : isum;
 #pragma unroll
