@@ -530,10 +530,27 @@ __device__ unsigned long long run_range(const QueryDev& q, const Scratch& s, QCt
   unsigned long long acc = 0;
   bool have = false;
   unsigned cj0 = 0, cj1 = 0, n = 0;
+  unsigned long long cb1 = 0;  // state index where the carried list's last pane ends
+  // the next window's id, panes and state range are loaded one window ahead
+  long long nw_ = 0;
+  unsigned nj0 = 0, nj1 = 0;
+  unsigned long long nb0 = 0, nb1 = 0;
+  if (wa < wb) {
+    nw_ = s.win_w[wa];
+    nj0 = s.win_j0[wa];
+    nj1 = s.win_j1[wa];
+    nb0 = s.pane_begin[nj0];
+    nb1 = s.pane_begin[nj1];
+  }
   for (unsigned long long wi = wa; wi < wb; ++wi) {
-    const long long w = s.win_w[wi];
-    const unsigned j0 = s.win_j0[wi], j1 = s.win_j1[wi];
-    const unsigned long long b0 = s.pane_begin[j0], b1 = s.pane_begin[j1];
+    const long long w = nw_;
+    const unsigned j0 = nj0, j1 = nj1;
+    const unsigned long long b0 = nb0, b1 = nb1;
+    if (wi + 1 < wb) {
+      nw_ = s.win_w[wi + 1];
+      nj0 = s.win_j0[wi + 1];
+      nj1 = s.win_j1[wi + 1];
+    }
     const unsigned len = (unsigned)(b1 - b0);
     const int nr = (int)(j1 - j0);
     const long long wstart = (w - kPaneBias) * (long long)q.slide + q.base;
@@ -546,6 +563,10 @@ __device__ unsigned long long run_range(const QueryDev& q, const Scratch& s, QCt
       }
       acc += len;
       have = false;
+      if (wi + 1 < wb) {
+        nb0 = s.pane_begin[nj0];
+        nb1 = s.pane_begin[nj1];
+      }
       continue;
     }
     if (len > cap) {  // global-scratch merge of this window alone
@@ -563,7 +584,13 @@ __device__ unsigned long long run_range(const QueryDev& q, const Scratch& s, QCt
       __syncthreads();
       const unsigned long long off = *s_off;
       __syncthreads();
-      if (off == ~0ull) continue;  // the host grows the scratch and runs the emission again
+      if (off == ~0ull) {  // the host grows the scratch and runs the emission again
+        if (wi + 1 < wb) {
+          nb0 = s.pane_begin[nj0];
+          nb1 = s.pane_begin[nj1];
+        }
+        continue;
+      }
       unsigned long long* A = s.pool + off;
       unsigned long long* B = A + len;
       for (unsigned i = tid; i < len; i += blockDim.x)
@@ -576,6 +603,10 @@ __device__ unsigned long long run_range(const QueryDev& q, const Scratch& s, QCt
       if (WRITE) acc += write_distinct<FLOAT, false>(q, S, len, wstart, out + acc, hp, m.wt);
       else acc += count_distinct<false>(S, len, m.wt);
       __syncthreads();
+      if (wi + 1 < wb) {
+        nb0 = s.pane_begin[nj0];
+        nb1 = s.pane_begin[nj1];
+      }
       continue;
     }
     // shared-memory list of this window
@@ -588,12 +619,12 @@ __device__ unsigned long long run_range(const QueryDev& q, const Scratch& s, QCt
       }
       // ... then merge in the runs of the panes that entered
       if (j1 > cj1) {
-        const unsigned long long g0 = s.pane_begin[cj1];
+        const unsigned long long g0 = cb1;  // = pane_begin[cj1]
         load_runs(q, m.L, nk, g0, b1);  // behind the kept entries
         const int add = (int)(j1 - cj1);
         if (tid == 0) m.bnd0[0] = 0u;
         for (int r = tid; r <= add; r += blockDim.x)
-          m.bnd0[1 + r] = nk + (unsigned)(s.pane_begin[cj1 + r] - g0);
+          m.bnd0[1 + r] = nk + (unsigned)((r == 0 ? g0 : r == add ? b1 : s.pane_begin[cj1 + r]) - g0);
         __syncthreads();
         unsigned long long* S = merge_runs<true>(m.L, m.T, m.bnd0, m.bnd1, add + 1, len);
         if (S != m.L) { m.T = m.L; m.L = S; }
@@ -609,7 +640,12 @@ __device__ unsigned long long run_range(const QueryDev& q, const Scratch& s, QCt
     have = true;
     cj0 = j0;
     cj1 = j1;
+    cb1 = b1;
     n = len;
+    if (wi + 1 < wb) {  // the next window's state range (its panes have arrived by now)
+      nb0 = s.pane_begin[nj0];
+      nb1 = s.pane_begin[nj1];
+    }
     __syncthreads();
     // the other buffer is free until the next window: it holds the key heads
     if (WRITE)
