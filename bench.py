@@ -448,6 +448,30 @@ def run_profile_serving(args):
     return 0
 
 
+def max_over_ranks(dist, torch, x, device):
+    """Largest x over the ranks: a job's timed region lasts as long as its
+    slowest rank's."""
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(dist, torch, xs, device):
+    """Elementwise sum over the ranks: independent replicas' rates add up to
+    the whole job's."""
+    t = torch.tensor([float(x) for x in xs], dtype=torch.float64, device=device)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return [float(v) for v in t]
+
+
+def whole_job_rate(steps, events_per_step, world, ms_max):
+    """Events/s of all ranks together: each rank processed `steps` batches of
+    `events_per_step` events within the slowest rank's `ms_max`."""
+    return steps * events_per_step * world / (ms_max / 1e3)
+
+
 def run_ours(args):
     import torch
 
@@ -509,13 +533,9 @@ def run_ours(args):
         dist.barrier()
     clocks = sampler.stop()
     st1 = s.stats()
-    ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(dist, torch, e0.elapsed_time(e1), dev)
     K = args.steps
-    value = K * n * world / (ms_max / 1e3)
+    value = whole_job_rate(K, n, world, ms_max)
     d = {k: st1[k] - st0[k] for k in ("k1_ms", "sort_ms", "emit_ms", "e1_ms", "e2_ms",
                                       "k1_launches", "kernel_launches", "partials",
                                       "groups_built", "rows_emitted", "events")}
@@ -569,14 +589,11 @@ def run_ours(args):
         serving = run_serving(args, lm, synth, local)
         serving["wall_s"] = time.perf_counter() - t0
         serving["clocks"] = sampler.stop()
-        vals = torch.tensor([serving["device_input"]["learned"]["events_per_s"],
-                             serving["host_input"]["learned"]["events_per_s"]],
-                            dtype=torch.float64, device=dev)
-        if dist:  # replicas: whole-job rate = sum over ranks
-            dist.all_reduce(vals, op=dist.ReduceOp.SUM)
-        line["value"] = float(vals[0])
+        vals = sum_over_ranks(dist, torch, [serving["device_input"]["learned"]["events_per_s"],
+                                            serving["host_input"]["learned"]["events_per_s"]], dev)
+        line["value"] = vals[0]
         lh = serving["host_input"]["learned"]
-        line["e2e"] = {"value": float(vals[1]), "unit": "events/s",
+        line["e2e"] = {"value": vals[1], "unit": "events/s",
                        "h2d_bytes_per_step": int(EVENT_BYTES * lh.get("mean_batch_events", 0)),
                        "d2h_bytes_per_step": int(ROW_BYTES * lh.get("mean_rows_per_batch", 0)),
                        "step": "one admitted micro-batch of the serving loop",
@@ -627,10 +644,8 @@ def run_e2e(args, torch, lm, synth, dev, local, rank, world, dist):
             times.append(dt)
             rows_total += got
     s.close()
-    tt = torch.tensor([sum(times)], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-    return {"value": steps * n * world / float(tt.item()), "unit": "events/s",
+    s_max = max_over_ranks(dist, torch, sum(times), dev)
+    return {"value": steps * n * world / s_max, "unit": "events/s",
             "h2d_bytes_per_step": EVENT_BYTES * n, "d2h_bytes_per_step": ROW_BYTES * rows_total // steps,
             "steps": steps, "warmup": 1}
 
