@@ -511,13 +511,58 @@ __global__ void __launch_bounds__(256) k_rbk_long(const QueryDev q, const Scratc
 
 // ---- distinct panes of the window state ------------------------------------
 
-__global__ void __launch_bounds__(256) k_pane_count(const QueryDev q, const Scratch s) {
-  const QCtl* c = q.ctl;
+// Pane ids never decrease along the sorted state and panes are runs of many
+// groups, so each thread finds the pane boundaries of its contiguous share of
+// a chunk by galloping and binary search instead of reading every group.
+__device__ __forceinline__ unsigned pane_of(const QueryDev& q, unsigned long long i) {
+  return (unsigned)(q.state[i].gkey >> 32);
+}
+
+// First index in (a, b) whose pane differs from p (the pane of a), else b.
+__device__ unsigned long long next_pane_change(const QueryDev& q, unsigned long long a,
+                                               unsigned long long b, unsigned p) {
+  unsigned long long lo = a, step = 1;  // pane(lo) == p
+  while (lo + step < b && pane_of(q, lo + step) == p) {
+    lo += step;
+    step <<= 1;
+  }
+  unsigned long long hi = lo + step < b ? lo + step : b;  // pane(hi) != p, or hi == b
+  while (hi - lo > 1) {
+    const unsigned long long mid = lo + ((hi - lo) >> 1);
+    if (pane_of(q, mid) == p) lo = mid;
+    else hi = mid;
+  }
+  return hi;
+}
+
+// Calls f(i, pane) for every first group of a pane in [a, b), in order.
+template <class F>
+__device__ void for_pane_heads(const QueryDev& q, unsigned long long a, unsigned long long b,
+                               F f) {
+  if (a >= b) return;
+  unsigned p = pane_of(q, a);
+  if (a == 0 || pane_of(q, a - 1) != p) f(a, p);
+  for (unsigned long long i = next_pane_change(q, a, b, p); i < b;
+       i = next_pane_change(q, i, b, p)) {
+    p = pane_of(q, i);
+    f(i, p);
+  }
+}
+
+// This thread's share [*a, *b) of the block's chunk of the state.
+__device__ __forceinline__ void pane_share(unsigned long long n, unsigned long long* a,
+                                           unsigned long long* b) {
   unsigned long long lo, hi;
-  chunk_range(c->n_state, blockIdx.x, gridDim.x, &lo, &hi);
-  unsigned long long cnt = 0;
-  for (unsigned long long i = lo + threadIdx.x; i < hi; i += blockDim.x)
-    cnt += (i == 0 || (q.state[i].gkey >> 32) != (q.state[i - 1].gkey >> 32)) ? 1ull : 0ull;
+  chunk_range(n, blockIdx.x, gridDim.x, &lo, &hi);
+  const unsigned long long per = (hi - lo + blockDim.x - 1) / blockDim.x;
+  *a = min(hi, lo + per * threadIdx.x);
+  *b = min(hi, *a + per);
+}
+
+__global__ void __launch_bounds__(256) k_pane_count(const QueryDev q, const Scratch s) {
+  unsigned long long a, b, cnt = 0;
+  pane_share(q.ctl->n_state, &a, &b);
+  for_pane_heads(q, a, b, [&](unsigned long long, unsigned) { ++cnt; });
   __shared__ unsigned long long tmp[33];
   unsigned long long tot;
   block_excl_scan(cnt, tmp, &tot);
@@ -527,24 +572,18 @@ __global__ void __launch_bounds__(256) k_pane_count(const QueryDev q, const Scra
 __global__ void __launch_bounds__(256) k_pane_write(const QueryDev q, const Scratch s) {
   const QCtl* c = q.ctl;
   const unsigned long long n = c->n_state;
-  unsigned long long lo, hi;
-  chunk_range(n, blockIdx.x, gridDim.x, &lo, &hi);
+  unsigned long long a, b, cnt = 0;
+  pane_share(n, &a, &b);
+  for_pane_heads(q, a, b, [&](unsigned long long, unsigned) { ++cnt; });
   __shared__ unsigned long long tmp[33];
-  unsigned long long out = s.chunk[blockIdx.x];
-  for (unsigned long long i0 = lo; i0 < hi; i0 += blockDim.x) {
-    const unsigned long long i = i0 + threadIdx.x;
-    const bool v = i < hi;
-    const unsigned p = v ? (unsigned)(q.state[i].gkey >> 32) : 0u;
-    const bool head = v && (i == 0 || p != (unsigned)(q.state[i - 1].gkey >> 32));
-    unsigned long long tot;
-    const unsigned long long r = block_excl_scan(head ? 1ull : 0ull, tmp, &tot);
-    if (head) {
-      s.pane_id[out + r] = p;
-      s.pane_begin[out + r] = i;
-    }
-    if (v && i == n - 1) s.pane_begin[c->n_panes] = n;
-    out += tot;
-  }
+  unsigned long long tot;
+  unsigned long long out = s.chunk[blockIdx.x] + block_excl_scan(cnt, tmp, &tot);
+  for_pane_heads(q, a, b, [&](unsigned long long i, unsigned p) {
+    s.pane_id[out] = p;
+    s.pane_begin[out] = i;
+    ++out;
+  });
+  if (a < b && b == n) s.pane_begin[c->n_panes] = n;
 }
 
 }  // namespace
