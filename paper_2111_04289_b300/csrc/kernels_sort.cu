@@ -302,8 +302,10 @@ __device__ unsigned long long first_equal(const unsigned long long* keys, unsign
   return a;
 }
 
+// Four CTAs per SM (64 registers, a few spilled): measured faster than two
+// CTAs with every value in registers, the loads' latency being the bound.
 template <bool FLOAT>
-__global__ void __launch_bounds__(256) k_rbk_write(const QueryDev q, const Scratch s) {
+__global__ void __launch_bounds__(256, 4) k_rbk_write(const QueryDev q, const Scratch s) {
   QCtl* c = q.ctl;
   const unsigned long long n = c->n_parts;
   const SortSrc src = final_src(q, s, c->npasses);
