@@ -141,7 +141,7 @@ __device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long
   return r;
 }
 
-// ---- segmented scans (reduce-by-key, window rows) ----------------------
+// ---- segmented scans (reduce-by-key) -------------------------------------
 
 struct SegAgg {  // (run started here?, aggregate since the run's head, run's output index)
   unsigned f;
