@@ -106,6 +106,22 @@ def test_gapped_panes_many_windows_per_range():
     _check([b], [dict(size=1)], False)
 
 
+def test_float_avg_counts_around_2p24():
+    """One tumbling window whose keys hold 2^24 - 1 and 2^24 + 1 events (the
+    two ways an average is divided: below 2^24 counts a float32-built
+    reciprocal, from 2^24 on a refined one), plus 3 and 2^20 events; the hot
+    keys' partial groups form runs far longer than a tile."""
+    rng = np.random.default_rng(71)
+    sizes = {5: (1 << 24) - 1, 9: (1 << 24) + 1, 11: 3, 13: 1 << 20}
+    key = np.concatenate([np.full(c, k, np.uint32) for k, c in sizes.items()])
+    rng.shuffle(key)
+    n = len(key)
+    ts = np.sort(rng.integers(0, 1000, n)).astype(np.int64)
+    val = rng.lognormal(0.0, 1.0, n).astype(np.float32)
+    eng, _ = _check([synth.Batch(ts, key, val)], [dict(size=1000)], True)
+    assert sorted(zip(eng[0]["key"].tolist(), eng[0]["count"].tolist())) == sorted(sizes.items())
+
+
 def test_empty_stream_and_eos_only():
     b = synth.TinyIntStream().next_batch(0)
     eng, st = _check([b, b], [dict(size=1_000)], False)
