@@ -122,6 +122,40 @@ def test_float_avg_counts_around_2p24():
     assert sorted(zip(eng[0]["key"].tolist(), eng[0]["count"].tolist())) == sorted(sizes.items())
 
 
+def test_special_float_values():
+    """Subnormal values, values near the float maximum (sums far beyond it),
+    negative values, signed zeros (min and max in total order: -0.0 < +0.0),
+    and keys holding one +Inf or one -Inf: counts, min and max exact, finite
+    sums and averages within the tolerance, infinite ones equal."""
+    rng = np.random.default_rng(73)
+    v5 = rng.lognormal(0.0, 1.0, 3000)
+    v5[1234] = np.inf
+    v6 = -rng.lognormal(0.0, 1.0, 3000)
+    v6[77] = -np.inf
+    vals = {1: rng.uniform(1e-45, 1e-38, 3000), 2: rng.uniform(1e37, 3.4e38, 3000),
+            3: -rng.lognormal(0.0, 1.0, 3000), 4: np.where(rng.random(3000) < 0.5, -0.0, 0.0),
+            5: v5, 6: v6}
+    key = np.concatenate([np.full(len(v), k, np.uint32) for k, v in vals.items()])
+    val = np.concatenate([np.asarray(v, np.float32) for v in vals.values()])
+    perm = rng.permutation(len(key))
+    key, val = key[perm], val[perm]
+    ts = np.sort(rng.integers(0, 1000, len(key))).astype(np.int64)
+    batches = [synth.Batch(ts, key, val)]
+    q = [dict(size=1000)]
+    eng, _ = run_engine(batches, q, True, torch=torch)
+    orc, _ = run_oracle(batches, q, True)
+    e, o = eng[0], orc[0]
+    assert len(e) == len(o) == 6
+    np.testing.assert_array_equal(e["key"], o["key"])
+    np.testing.assert_array_equal(e["count"], o["count"])
+    np.testing.assert_array_equal(e["min"].view(np.uint32), o["min_f"].view(np.uint32))
+    np.testing.assert_array_equal(e["max"].view(np.uint32), o["max_f"].view(np.uint32))
+    for f, of in (("sum", "sum_f"), ("avg", "avg")):
+        fin = np.isfinite(o[of])
+        assert np.array_equal(e[f][~fin], o[of][~fin]), (f, e[f], o[of])
+        assert np.all(np.abs(e[f][fin] - o[of][fin]) <= 1e-9 * np.abs(o[of][fin]) + 1e-300), f
+
+
 def test_empty_stream_and_eos_only():
     b = synth.TinyIntStream().next_batch(0)
     eng, st = _check([b, b], [dict(size=1_000)], False)
