@@ -156,6 +156,23 @@ def test_special_float_values():
         assert np.all(np.abs(e[f][fin] - o[of][fin]) <= 1e-9 * np.abs(o[of][fin]) + 1e-300), f
 
 
+def test_int32_extreme_values():
+    """Keys whose every value is INT32_MAX, INT32_MIN, alternating extremes or
+    -1, several thousand events each (many per fused-pass tile): the packed
+    count-and-sum words at their limits; all aggregates bit-exact."""
+    rng = np.random.default_rng(79)
+    imax, imin = np.iinfo(np.int32).max, np.iinfo(np.int32).min
+    vals = {1: np.full(5000, imax), 2: np.full(5000, imin),
+            3: np.where(np.arange(5000) % 2 == 0, imax, imin), 4: np.full(5000, -1)}
+    key = np.concatenate([np.full(len(v), k, np.uint32) for k, v in vals.items()])
+    val = np.concatenate([np.asarray(v, np.int32) for v in vals.values()])
+    perm = rng.permutation(len(key))
+    key, val = key[perm], val[perm]
+    ts = np.sort(rng.integers(0, 1000, len(key))).astype(np.int64)
+    eng, _ = _check([synth.Batch(ts, key, val)], [dict(size=1000), dict(size=400, slide=200)], False)
+    assert len(eng[0]) == 4
+
+
 def test_empty_stream_and_eos_only():
     b = synth.TinyIntStream().next_batch(0)
     eng, st = _check([b, b], [dict(size=1_000)], False)
