@@ -212,34 +212,23 @@ lms_status ensure_group_capacity(lms_stream* s, unsigned long long need) {
     if ((r = dgrow(s, &sc.keysB, sc.cap, nc, 0)) != LMS_OK) return r;
     if ((r = dgrow(s, &sc.valsA, sc.cap, nc, 0)) != LMS_OK) return r;
     if ((r = dgrow(s, &sc.valsB, sc.cap, nc, 0)) != LMS_OK) return r;
-    if ((r = dgrow(s, &sc.pane_id, sc.cap, nc + 1, 0)) != LMS_OK) return r;
-    if ((r = dgrow(s, &sc.pane_begin, sc.cap, nc + 1, 0)) != LMS_OK) return r;
+    if ((r = dgrow(s, &sc.blk_id, sc.cap, nc + 1, 0)) != LMS_OK) return r;
+    if ((r = dgrow(s, &sc.blk_begin, sc.cap, nc + 1, 0)) != LMS_OK) return r;
     sc.cap = nc;
-    sc.pane_cap = nc;
+    sc.blk_cap = nc;
   }
   return LMS_OK;
 }
 
-lms_status ensure_windows(lms_stream* s, unsigned long long need) {
+lms_status ensure_items(lms_stream* s, unsigned long long need) {
   Scratch& sc = s->scr;
-  if (sc.win_cap >= need) return LMS_OK;
+  if (sc.item_cap >= need) return LMS_OK;
   const unsigned long long nc = round_cap(need);
   lms_status r;
-  if ((r = dgrow(s, &sc.win_w, sc.win_cap, nc, 0)) != LMS_OK) return r;
-  if ((r = dgrow(s, &sc.win_j0, sc.win_cap, nc, 0)) != LMS_OK) return r;
-  if ((r = dgrow(s, &sc.win_j1, sc.win_cap, nc, 0)) != LMS_OK) return r;
-  if ((r = dgrow(s, &sc.win_stat, sc.win_cap, nc, 0)) != LMS_OK) return r;
-  sc.win_cap = nc;
-  return LMS_OK;
-}
-
-lms_status ensure_pool(lms_stream* s, unsigned long long need) {
-  Scratch& sc = s->scr;
-  if (sc.pool_cap >= need) return LMS_OK;
-  const unsigned long long nc = round_cap(need);
-  lms_status r;
-  if ((r = dgrow(s, &sc.pool, sc.pool_cap, nc, 0)) != LMS_OK) return r;
-  sc.pool_cap = nc;
+  if ((r = dgrow(s, &sc.item_c, sc.item_cap, nc, 0)) != LMS_OK) return r;
+  if ((r = dgrow(s, &sc.item_j, sc.item_cap, nc, 0)) != LMS_OK) return r;
+  if ((r = dgrow(s, &sc.item_stat, sc.item_cap, nc, 0)) != LMS_OK) return r;
+  sc.item_cap = nc;
   return LMS_OK;
 }
 
@@ -449,6 +438,10 @@ lms_status query_register(lms_stream* s, const lms_query_spec* q, int32_t* query
   udiv_constants(d.slide, &d.magic, &d.sh1, &d.sh2);
   d.size = size;
   d.k = h.k;
+  set_block_shape(&d);
+  d.lookback_ns = s->cfg.lookback_limit_us > 0 ? 1000ull * (unsigned long long)s->cfg.lookback_limit_us
+                                               : 4000000000ull;
+  d.debug_flags = s->cfg.debug_flags;
   d.agg_mask = q->agg_mask ? q->agg_mask : LMS_AGG_ALL;
   d.qid = (int)s->qs.size();
   d.value_is_float = s->cfg.value_type == LMS_VALUE_FLOAT32;
@@ -549,9 +542,8 @@ lms_status push_microbatch(lms_stream* s, const lms_batch* b) {
   if (timing) LMS_CK(cudaEventRecord(s->ev[2], s->st));
   std::vector<QueryDev> qd(nq);
   for (int i = 0; i < nq; ++i) qd[i] = s->qs[i].dev;
-  // emission needs window/pool/row buffers; make sure something exists
-  if ((r = ensure_windows(s, 1024)) != LMS_OK) return r;
-  if ((r = ensure_pool(s, 1ull << 16)) != LMS_OK) return r;
+  // emission needs item and row buffers; make sure something exists
+  if ((r = ensure_items(s, 1024)) != LMS_OK) return r;
   for (QueryHost& q : s->qs)
     if ((r = ensure_rows(s, q, q.row_base + 4096)) != LMS_OK) return r;
   // (Timing events inside the tail are recorded as external event nodes so that
@@ -569,7 +561,7 @@ lms_status push_microbatch(lms_stream* s, const lms_batch* b) {
       if (timing && (e = record_event(s->qev[i][4], s->st)) != cudaSuccess) break;
       if ((e = launch_sort_reduce(qd[i], s->scr, s->st, nl)) != cudaSuccess) break;
       if (timing && (e = record_event(s->qev[i][5], s->st)) != cudaSuccess) break;
-      if ((e = launch_pane_index(q.dev, s->scr, s->st, nl)) != cudaSuccess) break;
+      if ((e = launch_block_index(q.dev, s->scr, s->st, nl)) != cudaSuccess) break;
       if ((e = launch_emit(q.dev, s->scr, q.rows, q.rows_cap, s->sms, s->st, nl,
                            timing ? s->qev[i] : nullptr)) != cudaSuccess)
         break;
@@ -627,16 +619,13 @@ lms_status push_microbatch(lms_stream* s, const lms_batch* b) {
   for (int i = 0; i < nq; ++i) {
     QueryHost& q = s->qs[i];
     for (int attempt = 0; (hc[i].err & kErrNeedRetry) && attempt < 4; ++attempt) {
-      if (hc[i].err & kErrWinOverflow) {
-        if ((r = ensure_windows(s, hc[i].n_windows)) != LMS_OK) return r;
-      }
-      if (hc[i].err & kErrPoolOverflow) {
-        if ((r = ensure_pool(s, std::max(hc[i].pool_used, hc[i].pool_need))) != LMS_OK) return r;
+      if (hc[i].err & kErrItemOverflow) {
+        if ((r = ensure_items(s, hc[i].n_items)) != LMS_OK) return r;
       }
       if (hc[i].err & kErrRowsOverflow) {
         if ((r = ensure_rows(s, q, hc[i].row_base + hc[i].rows_batch)) != LMS_OK) return r;
       }
-      LMS_CK(launch_pane_index(q.dev, s->scr, s->st, &launches));
+      LMS_CK(launch_block_index(q.dev, s->scr, s->st, &launches));
       LMS_CK(launch_emit(q.dev, s->scr, q.rows, q.rows_cap, s->sms, s->st, &launches,
                          nullptr));
       LMS_CK(launch_trim(q.dev, s->scr, s->sms, s->st, &launches));
@@ -805,7 +794,7 @@ lms_status lms_stream_push_bytes(lms_stream* s, int64_t n_rows, int32_t host_inp
   }
   // emission buffers a first push allocates (later growth follows the rows
   // a batch emits and is not predicted here)
-  if (s->scr.win_cap == 0) total += 1024ull * (8 + 4 + 4 + 8) + (1ull << 16) * 8;
+  if (s->scr.item_cap == 0) total += 1024ull * (8 + 4 + 8);
   for (const QueryHost& q : s->qs)
     if (q.rows_cap == 0) total += round_cap(4096 + 4096 / 4) * sizeof(lms_result_row);
   *bytes = total;

@@ -1,41 +1,37 @@
-// Watermark, window enumeration, window assembly from panes, row emission and
-// the carry of still-open panes into the next micro-batch.
+// Watermark, emission items, window assembly and row emission, and the carry
+// of still-open panes into the next micro-batch.
 //
 // After a micro-batch the watermark is max(previous, max ts of the batch -
 // allowed lateness); every window whose end is <= the watermark closes (the
 // paper's per-micro-batch output step, Section III-A; window semantics as in
-// the public header).  A window of K panes is assembled from the sorted
-// window state: its panes are K contiguous, key-sorted runs of the state, so
-// a CTA merges the runs (merge path) into the window's key-sorted list in
-// shared memory and emits one row per distinct key, in key order.  A CTA
-// handles a range of consecutive windows and carries the list from window to
-// window (drop the pane that left, merge in the pane that entered).  Windows
-// larger than shared memory are merged in global scratch.  Rows of all closed
-// windows are written in (window_start, key) order; each range finds its row
-// offset by a decoupled look-back over the ranges before it.
+// the public header).  Rows of all closed windows are written in
+// (window_start, key) order.
+//
+// The window state is sorted by (block, key, pane) with blocks of B >= K panes
+// (lms_internal.h).  Closed windows are emitted by "items": an item is a run
+// of up to 64 consecutive window ids that start in one block b, so every
+// window of the item covers panes of blocks b and b + 1 only.  Both blocks
+// are key-major runs of the state; the CTA that takes an item merges the two
+// runs by key (merge path, chunks of 1024 entries through shared memory) and
+// gives each distinct key to one thread.  The thread walks the key's groups
+// (in pane order) once to find the windows of the item that hold the key (a
+// 64-bit mask), and the warp's ballots over the masks give every row its rank
+// among the window's keys, so the rows of one window and one warp land at
+// consecutive positions; then the thread combines, for each of its windows,
+// the groups whose pane lies in the window and writes the row.  Each group is
+// read by the threads of at most two items (instead of once per window that
+// holds it), and no per-window key list is built.
+//
+// An item's row count is found first (the same merge; each group is the key's
+// first group in the windows between its previous pane + 1 and its own pane,
+// added to a difference array over the item's windows), then the item's row
+// offset comes from a decoupled look-back over the items before it.
 #include <climits>
 
 #include "lms_device.cuh"
 
 namespace lms {
 namespace {
-
-constexpr int kEmitThreads = 512;
-constexpr unsigned kWwStage = 512;  // window ids of a range staged for the count pass
-constexpr size_t kEmitSmemMax = 224 * 1024;  // dynamic shared memory of the emit kernel (static: ~2.3 KB)
-// Largest window (entries) merged in shared memory for windows of k panes:
-// two padded buffers (17 slots per 16 entries) plus two (k+1)-entry boundary
-// arrays must fit in kEmitSmemMax.
-inline unsigned emit_cap(int k) {
-  const size_t avail = kEmitSmemMax - 2ull * (k + 2) * sizeof(unsigned) - 64;
-  const size_t padded = avail / (2 * sizeof(unsigned long long));
-  return (unsigned)(((padded - 1) * 16 / 17) & ~size_t(15));
-}
-inline size_t emit_smem(int k) {
-  const unsigned cap = emit_cap(k);
-  return 2ull * (cap + (cap >> 4) + 1) * sizeof(unsigned long long) +
-         2ull * (k + 2) * sizeof(unsigned);
-}
 
 __device__ __forceinline__ long long floor_div_ll(long long a, long long b) {
   long long q = a / b;
@@ -92,39 +88,45 @@ __global__ void k_watermark(SCtl* sc, const WmArgs a) {
 
 __global__ void k_emit_begin(QCtl* c) {
   if (threadIdx.x != 0) return;
-  c->pool_used = 0ull;
-  c->pool_need = 0ull;
-  c->big_windows = 0ull;
   c->rows_batch = 0ull;
-  c->n_windows = 0ull;
-  c->win_ticket = 0ull;
+  c->n_items = 0ull;
+  c->item_ticket = 0ull;
   c->err &= ~kErrNeedRetry;
 }
 
-// Windows anchored at pane j: those whose first present pane is pane j.
-__device__ __forceinline__ void anchored_range(const QueryDev& q, const Scratch& s,
-                                               const QCtl* c, unsigned long long j, long long* lo,
-                                               long long* hi) {
-  const long long p = (long long)s.pane_id[j];
-  long long a = p - q.k + 1;
+// ---- emission items ----------------------------------------------------------
+
+// Items anchored at block index j: the window chunks c (windows [c*nw, c*nw +
+// nw)) whose windows touch block blk_id[j] but not block blk_id[j - 1],
+// clipped to the windows this batch closes, [cursor, w_hi].  A window w covers
+// panes [w, w + K - 1], so it touches block P iff P*B - K + 1 <= w <= P*B + B - 1.
+__device__ __forceinline__ void block_items(const QueryDev& q, const Scratch& s, const QCtl* c,
+                                            unsigned long long j, long long* lo, long long* hi) {
+  *lo = 1;
+  *hi = 0;
+  if (c->w_hi < c->cursor) return;
+  const long long B = 1ll << q.lb, NW = q.nw;
+  const long long P = (long long)s.blk_id[j];
+  long long a = P * B - q.k + 1;
+  a = (a < 0 ? 0 : a) / NW;
+  long long b = (P * B + B - 1) / NW;
   if (j > 0) {
-    const long long prev = (long long)s.pane_id[j - 1] + 1;
-    a = prev > a ? prev : a;
+    const long long prev = ((long long)s.blk_id[j - 1] * B + B - 1) / NW + 1;
+    a = a > prev ? a : prev;
   }
-  a = c->cursor > a ? c->cursor : a;
-  const long long b = p < c->w_hi ? p : c->w_hi;
-  *lo = a;
-  *hi = b;
+  const long long cl = c->cursor / NW, ch = c->w_hi / NW;
+  *lo = a > cl ? a : cl;
+  *hi = b < ch ? b : ch;
 }
 
-__global__ void __launch_bounds__(256) k_win_count(const QueryDev q, const Scratch s) {
+__global__ void __launch_bounds__(256) k_item_count(const QueryDev q, const Scratch s) {
   const QCtl* c = q.ctl;
   unsigned long long lo, hi;
-  chunk_range(c->n_panes, blockIdx.x, gridDim.x, &lo, &hi);
+  chunk_range(c->n_blocks, blockIdx.x, gridDim.x, &lo, &hi);
   unsigned long long cnt = 0;
   for (unsigned long long j = lo + threadIdx.x; j < hi; j += blockDim.x) {
     long long a, b;
-    anchored_range(q, s, c, j, &a, &b);
+    block_items(q, s, c, j, &a, &b);
     if (b >= a) cnt += (unsigned long long)(b - a + 1);
   }
   __shared__ unsigned long long tmp[33];
@@ -133,111 +135,42 @@ __global__ void __launch_bounds__(256) k_win_count(const QueryDev q, const Scrat
   if (threadIdx.x == 0) s.chunk[blockIdx.x] = tot;
 }
 
-__global__ void __launch_bounds__(1024) k_win_scan(const QueryDev q, const Scratch s) {
+__global__ void __launch_bounds__(1024) k_item_scan(const QueryDev q, const Scratch s) {
   __shared__ unsigned long long tmp[33];
   const unsigned long long v = (int)threadIdx.x < kGrid ? s.chunk[threadIdx.x] : 0ull;
   unsigned long long tot;
   const unsigned long long r = block_excl_scan(v, tmp, &tot);
   if ((int)threadIdx.x < kGrid) s.chunk[threadIdx.x] = r;
   if (threadIdx.x == 0) {
-    q.ctl->n_windows = tot;
-    if (tot > s.win_cap) atomicOr(&q.ctl->err, kErrWinOverflow);
+    q.ctl->n_items = tot;
+    if (tot > s.item_cap) atomicOr(&q.ctl->err, kErrItemOverflow);
   }
 }
 
-__global__ void __launch_bounds__(256) k_win_write(const QueryDev q, const Scratch s) {
+__global__ void __launch_bounds__(256) k_item_write(const QueryDev q, const Scratch s) {
   const QCtl* c = q.ctl;
-  if (c->n_windows > s.win_cap) return;
-  const unsigned long long P = c->n_panes;
+  if (c->n_items > s.item_cap) return;
   unsigned long long lo, hi;
-  chunk_range(P, blockIdx.x, gridDim.x, &lo, &hi);
+  chunk_range(c->n_blocks, blockIdx.x, gridDim.x, &lo, &hi);
   __shared__ unsigned long long tmp[33];
   unsigned long long out = s.chunk[blockIdx.x];
   for (unsigned long long j0 = lo; j0 < hi; j0 += blockDim.x) {
     const unsigned long long j = j0 + threadIdx.x;
-    long long a = 0, b = -1;
-    if (j < hi) anchored_range(q, s, c, j, &a, &b);
+    long long a = 1, b = 0;
+    if (j < hi) block_items(q, s, c, j, &a, &b);
     const unsigned long long cnt = b >= a ? (unsigned long long)(b - a + 1) : 0ull;
     unsigned long long tot;
     const unsigned long long r = block_excl_scan(cnt, tmp, &tot);
-    unsigned long long j1 = j + 1;
     for (unsigned long long t = 0; t < cnt; ++t) {
-      const long long w = a + (long long)t;
-      while (j1 < P && (long long)s.pane_id[j1] < w + q.k) ++j1;
-      const unsigned long long o = out + r + t;
-      s.win_w[o] = w;
-      s.win_j0[o] = (unsigned)j;
-      s.win_j1[o] = (unsigned)j1;
-      s.win_stat[o] = 0ull;
+      s.item_c[out + r + t] = (unsigned long long)(a + (long long)t);
+      s.item_j[out + r + t] = (unsigned)j;
+      s.item_stat[out + r + t] = 0ull;
     }
     out += tot;
   }
 }
 
-// Index of element i in a merge buffer.  Shared buffers are padded by one
-// slot per 16 elements so that threads writing consecutive chunks do not all
-// hit the same bank; global scratch is not padded.
-template <bool PAD>
-__device__ __forceinline__ unsigned pix(unsigned i) { return PAD ? i + (i >> 4) : i; }
-
-// Pairwise merge rounds of `nr` sorted runs of A (boundaries bc[0..nr],
-// bc[nr] = len), ping-ponging with B.  Values are distinct.  Returns the
-// buffer holding the fully merged sequence.  All threads must call.  Each
-// round gives every thread one chunk of about len / blockDim outputs.
-template <bool PAD>
-__device__ unsigned long long* merge_runs(unsigned long long* A, unsigned long long* B,
-                                          unsigned* bc, unsigned* bn, int nr, unsigned len) {
-  const unsigned chunk = max(4u, (len + blockDim.x - 1) / blockDim.x);
-  while (nr > 1) {
-    const int np = (nr + 1) >> 1;
-    for (unsigned ch = threadIdx.x; ch * chunk < len; ch += blockDim.x) {
-      unsigned o = ch * chunk;
-      const unsigned oe = min(len, o + chunk);
-      // pair m holding output position o: largest m with bc[2m] <= o
-      int lo = 0, hi = np - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (bc[2 * mid] <= o) lo = mid; else hi = mid - 1;
-      }
-      int m = lo;
-      while (o < oe) {
-        const unsigned s0 = bc[2 * m];
-        const unsigned s1 = bc[min(2 * m + 1, nr)];
-        const unsigned s2 = bc[min(2 * m + 2, nr)];
-        const unsigned la = s1 - s0, lb = s2 - s1, diag = o - s0;
-        unsigned a = diag > lb ? diag - lb : 0u, b = min(diag, la);
-        while (a < b) {
-          const unsigned mid = (a + b) >> 1;
-          if (A[pix<PAD>(s0 + mid)] < A[pix<PAD>(s1 + diag - 1u - mid)]) a = mid + 1u;
-          else b = mid;
-        }
-        unsigned i = a, k = diag - a;
-        const unsigned stop = min(oe, s2);
-        unsigned long long va = i < la ? A[pix<PAD>(s0 + i)] : ~0ull;
-        unsigned long long vb = k < lb ? A[pix<PAD>(s1 + k)] : ~0ull;
-        while (o < stop) {
-          if (k >= lb || (i < la && va < vb)) {
-            B[pix<PAD>(o++)] = va;
-            ++i;
-            va = i < la ? A[pix<PAD>(s0 + i)] : ~0ull;
-          } else {
-            B[pix<PAD>(o++)] = vb;
-            ++k;
-            vb = k < lb ? A[pix<PAD>(s1 + k)] : ~0ull;
-          }
-        }
-        ++m;
-      }
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t <= np; t += blockDim.x) bn[t] = t < np ? bc[2 * t] : len;
-    __syncthreads();
-    unsigned long long* tA = A; A = B; B = tA;
-    unsigned* tb = bc; bc = bn; bn = tb;
-    nr = np;
-  }
-  return A;
-}
+// ---- rows --------------------------------------------------------------------
 
 // 1/n as a double, to about 2^-47 relative, for 3 <= n < 2^24 with n not a
 // power of two, using no FP64 arithmetic (the FP64 pipe of this part is
@@ -281,12 +214,17 @@ __device__ __forceinline__ void write_row(const QueryDev& q, ResultRowDev* out, 
     avg = sd * recip_small((unsigned)cnt);
   } else if (FLOAT) {
     // larger counts: float32 reciprocal refined by two corrections with exact
-    // FMA remainders
+    // FMA remainders; a non-finite sum (a group holding Inf or NaN) has no
+    // remainder to correct (Inf - Inf would turn the quotient into NaN)
     const double n = (double)cnt;
     const double r = (double)__frcp_rn((float)cnt);
     const double q0 = sd * r;
-    const double q1 = fma(fma(-q0, n, sd), r, q0);
-    avg = fma(fma(-q1, n, sd), r, q1);
+    if (!isfinite(sd)) {
+      avg = q0;
+    } else {
+      const double q1 = fma(fma(-q0, n, sd), r, q0);
+      avg = fma(fma(-q1, n, sd), r, q1);
+    }
   } else {
     avg = sd / (double)cnt;  // int sums: exact division (bit-exact rows)
   }
@@ -294,7 +232,7 @@ __device__ __forceinline__ void write_row(const QueryDev& q, ResultRowDev* out, 
   if (q.agg_mask & 4u) mnv = FLOAT ? dec_f32_bits(mn) : (unsigned)dec_i32(mn);
   if (q.agg_mask & 8u) mxv = FLOAT ? dec_f32_bits(mx) : (unsigned)dec_i32(mx);
   // rows are written once and read only by the host: streaming stores, so
-  // that they do not displace the state groups the next windows gather
+  // that they do not displace the state groups the next items read
   uint4* o = reinterpret_cast<uint4*>(out);
   __stcs(o, make_uint4((unsigned)wstart, (unsigned)((unsigned long long)wstart >> 32),
                        (unsigned)cnt, (unsigned)((unsigned long long)cnt >> 32)));
@@ -304,132 +242,19 @@ __device__ __forceinline__ void write_row(const QueryDev& q, ResultRowDev* out, 
   __stcs(o + 2, make_uint4(key, mnv, mxv, (unsigned)q.qid));
 }
 
-// Exclusive scan of one count per thread over the block; returns the prefix
-// and writes the block total to *total.  wt holds 33 counters.
-__device__ __forceinline__ unsigned block_scan_u32(unsigned v, unsigned* wt, unsigned* total) {
-  const unsigned lane = lane_id(), w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  unsigned inc = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned y = __shfl_up_sync(kFull, inc, o);
-    if ((int)lane >= o) inc += y;
-  }
-  if (lane == 31) wt[w] = inc;
-  __syncthreads();
-  if (w == 0) {
-    const unsigned x = lane < nw ? wt[lane] : 0u;
-    unsigned wi = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned y = __shfl_up_sync(kFull, wi, o);
-      if ((int)lane >= o) wi += y;
-    }
-    if (lane < nw) wt[lane] = wi - x;
-    if (lane == 31) wt[32] = wi;
-  }
-  __syncthreads();
-  const unsigned r = wt[w] + inc - v;
-  *total = wt[32];
-  __syncthreads();
-  return r;
-}
-
-// Heads (first entries of a key) in this thread's contiguous chunk of S[0..len).
-template <bool PAD>
-__device__ __forceinline__ unsigned chunk_heads(const unsigned long long* S, unsigned len,
-                                                unsigned a, unsigned b) {
-  unsigned h = 0;
-  unsigned prev = a > 0 ? (unsigned)(S[pix<PAD>(a - 1)] >> 32) : 0u;
-  for (unsigned i = a; i < b; ++i) {
-    const unsigned k = (unsigned)(S[pix<PAD>(i)] >> 32);
-    h += (i == 0 || k != prev) ? 1u : 0u;
-    prev = k;
-  }
-  return h;
-}
-
-// Distinct keys of the merged window S[0..len), in key order: their number.
-template <bool PAD>
-__device__ __forceinline__ unsigned long long count_distinct(const unsigned long long* S,
-                                                             unsigned len, unsigned* wt) {
-  const unsigned per = (len + blockDim.x - 1) / blockDim.x;
-  const unsigned a = min(len, threadIdx.x * per), b = min(len, a + per);
-  unsigned tot;
-  block_scan_u32(chunk_heads<PAD>(S, len, a, b), wt, &tot);
-  return tot;
-}
-
-// One row per distinct key of the merged window S[0..len) (entries key << 32 |
-// state index, key-sorted), written from out[0] in key order; returns the
-// number of rows.  First the position of every key's first entry goes to
-// hp[rank] (hp: len + 1 words of scratch not aliasing S); then thread t takes
-// rows t, t + blockDim, ...: it combines the key's groups (one per pane that
-// holds the key) and writes the row, so a warp's rows are consecutive and its
-// stores coalesce.  Ends with a barrier (hp may be reused).
-template <bool FLOAT, bool PAD>
-__device__ unsigned write_distinct(const QueryDev& q, const unsigned long long* S, unsigned len,
-                                   long long wstart, ResultRowDev* out, unsigned* hp,
-                                   unsigned* wt) {
-  const unsigned per = (len + blockDim.x - 1) / blockDim.x;
-  const unsigned a = min(len, threadIdx.x * per), b = min(len, a + per);
-  unsigned nrows;
-  unsigned r = block_scan_u32(chunk_heads<PAD>(S, len, a, b), wt, &nrows);
-  unsigned prev = a > 0 ? (unsigned)(S[pix<PAD>(a - 1)] >> 32) : 0u;
-  for (unsigned i = a; i < b; ++i) {
-    const unsigned k = (unsigned)(S[pix<PAD>(i)] >> 32);
-    if (i == 0 || k != prev) hp[r++] = i;
-    prev = k;
-  }
-  if (threadIdx.x == 0) hp[nrows] = len;
-  __syncthreads();
-  // Every load is issued unconditionally (an exhausted row re-reads its last
-  // entry) so that a row's gathers are in flight together.
-  const Grp* st = q.state;
-  for (unsigned row = threadIdx.x; row < nrows; row += blockDim.x) {
-    const unsigned e0 = hp[row], e1 = hp[row + 1];
-    const unsigned long long x0 = S[pix<PAD>(e0)];
-    const Grp g0 = load_grp_v(st + (x0 & 0xffffffffull));
-    long long cnt = g0.cnt;
-    unsigned long long isum = g0.sum;
-    double fsum = __longlong_as_double((long long)g0.sum);
-    unsigned mn = g0.mn, mx = g0.mx;
-    for (unsigned e = e0 + 1; e < e1; e += 2) {  // the key's other panes, two loads in flight
-      const bool two = e + 1 < e1;
-      const unsigned long long x1 = S[pix<PAD>(e)], x2 = S[pix<PAD>(two ? e + 1 : e)];
-      const Grp g1 = load_grp_v(st + (x1 & 0xffffffffull));
-      const Grp g2 = load_grp_v(st + (x2 & 0xffffffffull));
-      cnt += g1.cnt;
-      mn = min(mn, g1.mn);
-      mx = max(mx, g1.mx);
-      if (FLOAT) fsum += __longlong_as_double((long long)g1.sum);
-      else isum += g1.sum;
-      if (two) {
-        cnt += g2.cnt;
-        mn = min(mn, g2.mn);
-        mx = max(mx, g2.mx);
-        if (FLOAT) fsum += __longlong_as_double((long long)g2.sum);
-        else isum += g2.sum;
-      }
-    }
-    const unsigned long long sb = FLOAT ? (unsigned long long)__double_as_longlong(fsum) : isum;
-    write_row<FLOAT>(q, out + row, wstart, (unsigned)(x0 >> 32), cnt, sb, mn, mx);
-  }
-  __syncthreads();
-  return nrows;
-}
-
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
 
-// Decoupled look-back over the window ranges before `ri` (ranges are taken in
-// ticket order, so every predecessor is already running or done).  Publishes
-// this range's row count, waits (bounded, ~4 s) for the predecessors' counts
+// Decoupled look-back over the items before `ri` (items are taken in ticket
+// order, so every predecessor is already running or done).  Publishes this
+// item's row count, waits (bounded by limit_ns) for the predecessors' counts
 // and returns the exclusive prefix, or ~0 after setting kErrLookback.
-__device__ unsigned long long range_lookback(unsigned long long* stat, unsigned long long ri,
-                                             unsigned long long n, QCtl* c) {
+__device__ unsigned long long item_lookback(unsigned long long* stat, unsigned long long ri,
+                                            unsigned long long n, QCtl* c,
+                                            unsigned long long limit_ns) {
   constexpr unsigned long long kAgg = 1ull << 62, kPre = 2ull << 62, kVal = kAgg - 1;
   volatile unsigned long long* vs = stat;
   if (ri == 0) {
@@ -444,7 +269,7 @@ __device__ unsigned long long range_lookback(unsigned long long* stat, unsigned 
   while (p >= 0) {
     const unsigned long long v = vs[p];
     if ((v >> 62) == 0) {
-      if ((++spins & 255u) == 0 && global_ns() - t0 > 4000000000ull) {
+      if ((++spins & 63u) == 0 && global_ns() - t0 > limit_ns) {
         atomicOr(&c->err, kErrLookback);
         return ~0ull;
       }
@@ -460,448 +285,530 @@ __device__ unsigned long long range_lookback(unsigned long long* stat, unsigned 
   return acc;
 }
 
-// Copies state entries [g0, g1) as (key << 32 | state index) to T[base ..].
-__device__ __forceinline__ void load_runs(const QueryDev& q, unsigned long long* T, unsigned base,
-                                          unsigned long long g0, unsigned long long g1) {
-  for (unsigned long long g = g0 + threadIdx.x; g < g1; g += blockDim.x)
-    T[pix<true>(base + (unsigned)(g - g0))] = ((q.state[g].gkey & 0xffffffffull) << 32) | g;
-}
+// ---- assembly of an item's windows -------------------------------------------
 
-// Keeps the entries of L[0..n) whose state index is >= lo, in order, in T.
-// Returns their number.  All threads must call.
-__device__ unsigned compact_list(const unsigned long long* L, unsigned n, unsigned long long lo,
-                                 unsigned long long* T, unsigned* wt) {
-  const unsigned per = (n + blockDim.x - 1) / blockDim.x;
-  const unsigned a = min(n, threadIdx.x * per), b = min(n, a + per);
-  unsigned keep = 0;
-  for (unsigned i = a; i < b; ++i) keep += (L[pix<true>(i)] & 0xffffffffull) >= lo ? 1u : 0u;
-  // exclusive scan of `keep` over the block
-  const unsigned lane = lane_id(), w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  unsigned inc = keep;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned y = __shfl_up_sync(kFull, inc, o);
-    if ((int)lane >= o) inc += y;
-  }
-  if (lane == 31) wt[w] = inc;
-  __syncthreads();
-  if (w == 0) {
-    const unsigned x = lane < nw ? wt[lane] : 0u;
-    unsigned wi = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned y = __shfl_up_sync(kFull, wi, o);
-      if ((int)lane >= o) wi += y;
-    }
-    if (lane < nw) wt[lane] = wi - x;
-    if (lane == 31) wt[32] = wi;
-  }
-  __syncthreads();
-  unsigned o = wt[w] + inc - keep;
-  const unsigned total = wt[32];
-  for (unsigned i = a; i < b; ++i) {
-    const unsigned long long x = L[pix<true>(i)];
-    if ((x & 0xffffffffull) >= lo) T[pix<true>(o++)] = x;
-  }
-  __syncthreads();
-  return total;
-}
+constexpr int kEmT = 256;              // threads per CTA
+constexpr int kEmE = 4;                // merged entries per thread and chunk
+constexpr int kEmC = kEmT * kEmE;      // merged entries per chunk
+constexpr int kEmWarps = kEmT / 32;
 
-struct EmitSmem {
-  unsigned long long* L;  // key-sorted list of the current window
-  unsigned long long* T;  // the other buffer
-  unsigned* bnd0;
-  unsigned* bnd1;
-  unsigned* wt;
+struct EmSmem {
+  unsigned long long ga[kEmC];         // the chunk's gkeys from run A (block b)
+  unsigned long long gb[kEmC];         // ... and from run B (block b + 1)
+  unsigned hk[kEmC + 1];               // distinct keys starting in the chunk (heads)
+  unsigned hia[kEmC + 1];              // their first A / B entries (relative to the runs)
+  unsigned hib[kEmC + 1];
+  unsigned long long split[kEmT + 1];  // merge-path A counts at chunk starts
+  long long cnt[kMaxItemWindows + 2];  // difference array, then rows per window
+  unsigned long long woff[kMaxItemWindows + 1];  // rows of the item before window i
+  unsigned wc[kEmWarps][kMaxItemWindows];        // per-warp rows of a round, then their offsets
+  unsigned long long run[kMaxItemWindows];       // rows of window i written by earlier rounds
+  unsigned tkey[kEmT];                 // each thread's last merged entry of the chunk
+  unsigned long long tpane[kEmT];
+  unsigned long long tmp[33];
+  unsigned carry_key;                  // the previous chunk's last entry
+  unsigned long long carry_pane;
+  int carry_valid;
+  unsigned nh;
+  unsigned long long ri, off, total;
 };
 
-// Rows of windows [wa, wb): counted (WRITE=false) or written from out[0]
-// (WRITE=true).  Consecutive windows share most of their panes, so the
-// window's key-sorted list is carried from one window to the next: entries of
-// panes that left are dropped and the runs of panes that entered are merged
-// in.  Windows of one pane need no list; windows above `cap` entries are
-// merged in global scratch on their own.
-template <bool FLOAT, bool WRITE>
-__device__ unsigned long long run_range(const QueryDev& q, const Scratch& s, QCtl* c,
-                                        unsigned long long wa, unsigned long long wb,
-                                        unsigned cap, EmitSmem& m, ResultRowDev* out,
-                                        unsigned long long* s_off) {
+struct Item {
+  const Grp* A;               // run A: block b, key-major (may be empty)
+  unsigned long long na;
+  const Grp* Bv;              // run B: block b + 1 (empty if the item's windows do not reach it)
+  unsigned long long nb;
+  long long wlo, whi;         // the item's closed windows (relative ids, inclusive)
+};
+
+__device__ __forceinline__ Item load_item(const QueryDev& q, const Scratch& s, const QCtl* c,
+                                          unsigned long long ii) {
+  Item it;
+  const long long cc = (long long)s.item_c[ii];
+  const unsigned long long ja = s.item_j[ii];
+  const unsigned long long nblk = c->n_blocks;
+  const long long w0 = cc * q.nw;
+  const unsigned long long b = (unsigned long long)w0 >> q.lb;
+  it.wlo = w0 > c->cursor ? w0 : c->cursor;
+  it.whi = w0 + q.nw - 1 < c->w_hi ? w0 + q.nw - 1 : c->w_hi;
+  unsigned long long jb = ja;
+  it.A = q.state;
+  it.na = 0;
+  if (ja < nblk && s.blk_id[ja] == b) {
+    const unsigned long long a0 = s.blk_begin[ja];
+    it.A = q.state + a0;
+    it.na = s.blk_begin[ja + 1] - a0;
+    jb = ja + 1;
+  }
+  it.Bv = q.state;
+  it.nb = 0;
+  const long long last_pane = it.whi + q.k - 1;
+  if (q.k > 1 && jb < nblk && s.blk_id[jb] == b + 1 &&
+      last_pane >= (long long)((b + 1) << q.lb)) {
+    const unsigned long long b0 = s.blk_begin[jb];
+    it.Bv = q.state + b0;
+    it.nb = s.blk_begin[jb + 1] - b0;
+  }
+  return it;
+}
+
+// Merge order of the two runs: by key; on equal keys run A first.  Number of
+// A entries among the first d merged entries (merge path, global memory).
+__device__ unsigned long long merge_split_g(const Item& it, unsigned long long d, int lb) {
+  unsigned long long lo = d > it.nb ? d - it.nb : 0ull, hi = d < it.na ? d : it.na;
+  while (lo < hi) {
+    const unsigned long long mid = (lo + hi) >> 1;
+    if (gkey_key(it.A[mid].gkey, lb) <= gkey_key(it.Bv[d - 1 - mid].gkey, lb)) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// The same within a chunk staged in shared memory.
+__device__ __forceinline__ unsigned merge_split_s(const unsigned long long* ga, unsigned la,
+                                                  const unsigned long long* gb, unsigned lbn,
+                                                  unsigned d, int lb) {
+  unsigned lo = d > lbn ? d - lbn : 0u, hi = d < la ? d : la;
+  while (lo < hi) {
+    const unsigned mid = (lo + hi) >> 1;
+    if (gkey_key(ga[mid], lb) <= gkey_key(gb[d - 1 - mid], lb)) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Windows of the item [wlo, whi] that contain pane p, as bits relative to wlo.
+__device__ __forceinline__ unsigned long long pane_windows(long long p, int k, long long wlo,
+                                                           long long whi) {
+  long long lo = p - k + 1, hi = p;
+  lo = lo > wlo ? lo : wlo;
+  hi = hi < whi ? hi : whi;
+  if (lo > hi) return 0ull;
+  const int width = (int)(hi - lo + 1);
+  const unsigned long long m = width >= 64 ? ~0ull : ((1ull << width) - 1ull);
+  return m << (int)(lo - wlo);
+}
+
+// One merged chunk of an item: thread t receives entries t*E .. t*E + E - 1
+// of the chunk (key, pane, and the positions in A and B before the entry).
+struct Merged {
+  unsigned key[kEmE];
+  unsigned long long pane[kEmE];
+  unsigned ia[kEmE], ib[kEmE];
+  int n;
+};
+
+// Walks chunk by chunk over the merged runs of the item, calling
+// f(chunk_len, merged) with every thread's entries after a barrier that made
+// each thread's last entry visible in sm.tkey / sm.tpane; sm.carry_* holds the
+// previous chunk's last entry.  f must end with a barrier.
+template <class F>
+__device__ void for_merged_chunks(const QueryDev& q, const Item& it, EmSmem& sm, F f) {
   const int tid = threadIdx.x;
-  unsigned long long acc = 0;
-  bool have = false;
-  unsigned cj0 = 0, cj1 = 0, n = 0;
-  unsigned long long cb1 = 0;  // state index where the carried list's last pane ends
-  // the next window's id, panes and state range are loaded one window ahead
-  long long nw_ = 0;
-  unsigned nj0 = 0, nj1 = 0;
-  unsigned long long nb0 = 0, nb1 = 0;
-  if (wa < wb) {
-    nw_ = s.win_w[wa];
-    nj0 = s.win_j0[wa];
-    nj1 = s.win_j1[wa];
-    nb0 = s.pane_begin[nj0];
-    nb1 = s.pane_begin[nj1];
-  }
-  for (unsigned long long wi = wa; wi < wb; ++wi) {
-    const long long w = nw_;
-    const unsigned j0 = nj0, j1 = nj1;
-    const unsigned long long b0 = nb0, b1 = nb1;
-    if (wi + 1 < wb) {
-      nw_ = s.win_w[wi + 1];
-      nj0 = s.win_j0[wi + 1];
-      nj1 = s.win_j1[wi + 1];
-    }
-    const unsigned len = (unsigned)(b1 - b0);
-    const int nr = (int)(j1 - j0);
-    const long long wstart = (w - kPaneBias) * (long long)q.slide + q.base;
-    if (nr == 1) {  // one pane: its run is already unique and key-sorted
-      if (WRITE) {
-        for (unsigned i = tid; i < len; i += blockDim.x) {
-          const Grp g = load_grp(q.state + b0 + i);
-          write_row<FLOAT>(q, out + acc + i, wstart, (unsigned)g.gkey, g.cnt, g.sum, g.mn, g.mx);
-        }
-      }
-      acc += len;
-      have = false;
-      if (wi + 1 < wb) {
-        nb0 = s.pane_begin[nj0];
-        nb1 = s.pane_begin[nj1];
-      }
-      continue;
-    }
-    if (len > cap) {  // global-scratch merge of this window alone
-      have = false;
-      if (tid == 0) {
-        unsigned long long off = atomicAdd(&c->pool_used, 2ull * len);
-        if (off + 2ull * len > s.pool_cap) {
-          atomicOr(&c->err, kErrPoolOverflow);
-          off = ~0ull;
-        } else {
-          atomicAdd(&c->big_windows, 1ull);
-        }
-        *s_off = off;
-      }
-      __syncthreads();
-      const unsigned long long off = *s_off;
-      __syncthreads();
-      if (off == ~0ull) {  // the host grows the scratch and runs the emission again
-        if (wi + 1 < wb) {
-          nb0 = s.pane_begin[nj0];
-          nb1 = s.pane_begin[nj1];
-        }
-        continue;
-      }
-      unsigned long long* A = s.pool + off;
-      unsigned long long* B = A + len;
-      for (unsigned i = tid; i < len; i += blockDim.x)
-        A[i] = ((q.state[b0 + i].gkey & 0xffffffffull) << 32) | (b0 + i);
-      for (int r = tid; r <= nr; r += blockDim.x)
-        m.bnd0[r] = (unsigned)(s.pane_begin[j0 + r] - b0);
-      __syncthreads();
-      const unsigned long long* S = merge_runs<false>(A, B, m.bnd0, m.bnd1, nr, len);
-      unsigned* hp = reinterpret_cast<unsigned*>(S == A ? B : A);  // len u64 free: >= len + 1 words
-      if (WRITE) acc += write_distinct<FLOAT, false>(q, S, len, wstart, out + acc, hp, m.wt);
-      else acc += count_distinct<false>(S, len, m.wt);
-      __syncthreads();
-      if (wi + 1 < wb) {
-        nb0 = s.pane_begin[nj0];
-        nb1 = s.pane_begin[nj1];
-      }
-      continue;
-    }
-    // shared-memory list of this window
-    if (have && j0 < cj1) {
-      // drop the panes that left (their state indices are below b0) ...
-      unsigned nk = n;
-      if (j0 > cj0) {
-        nk = compact_list(m.L, n, b0, m.T, m.wt);
-        unsigned long long* t = m.L; m.L = m.T; m.T = t;
-      }
-      // ... then merge in the runs of the panes that entered
-      if (j1 > cj1) {
-        const unsigned long long g0 = cb1;  // = pane_begin[cj1]
-        load_runs(q, m.L, nk, g0, b1);  // behind the kept entries
-        const int add = (int)(j1 - cj1);
-        if (tid == 0) m.bnd0[0] = 0u;
-        for (int r = tid; r <= add; r += blockDim.x)
-          m.bnd0[1 + r] = nk + (unsigned)((r == 0 ? g0 : r == add ? b1 : s.pane_begin[cj1 + r]) - g0);
-        __syncthreads();
-        unsigned long long* S = merge_runs<true>(m.L, m.T, m.bnd0, m.bnd1, add + 1, len);
-        if (S != m.L) { m.T = m.L; m.L = S; }
-      }
-    } else {  // full build: merge the window's runs
-      load_runs(q, m.T, 0u, b0, b1);
-      for (int r = tid; r <= nr; r += blockDim.x)
-        m.bnd0[r] = (unsigned)(s.pane_begin[j0 + r] - b0);
-      __syncthreads();
-      unsigned long long* S = merge_runs<true>(m.T, m.L, m.bnd0, m.bnd1, nr, len);
-      if (S != m.L) { m.T = m.L; m.L = S; }
-    }
-    have = true;
-    cj0 = j0;
-    cj1 = j1;
-    cb1 = b1;
-    n = len;
-    if (wi + 1 < wb) {  // the next window's state range (its panes have arrived by now)
-      nb0 = s.pane_begin[nj0];
-      nb1 = s.pane_begin[nj1];
+  const int lb = q.lb;
+  const unsigned long long L = it.na + it.nb;
+  const unsigned long long nch = (L + kEmC - 1) / kEmC;
+  if (tid == 0) sm.carry_valid = 0;
+  for (unsigned long long k0 = 0; k0 < nch; k0 += kEmT) {
+    const unsigned long long kn = nch - k0 < (unsigned long long)kEmT ? nch - k0 : kEmT;
+    __syncthreads();  // the previous batch of chunks no longer reads sm.split
+    for (unsigned long long t = tid; t <= kn; t += kEmT) {
+      const unsigned long long d = (k0 + t) * kEmC;
+      sm.split[t] = merge_split_g(it, d < L ? d : L, lb);
     }
     __syncthreads();
-    // the other buffer is free until the next window: it holds the key heads
-    if (WRITE)
-      acc += write_distinct<FLOAT, true>(q, m.L, len, wstart, out + acc,
-                                         reinterpret_cast<unsigned*>(m.T), m.wt);
-    else acc += count_distinct<true>(m.L, len, m.wt);
-  }
-  __syncthreads();
-  return acc;
-}
-
-// Rows of windows [wa, wb) without assembling them.  A window's rows are its
-// distinct keys; the group of key k in pane P is the first occurrence of k in
-// exactly the windows whose ids lie in [max(prev + 1, P - K + 1), P], prev the
-// last earlier pane holding k.  The CTA sweeps the range's panes in order
-// (pane by pane; keys within a pane are distinct) with a shared table of
-// (last pane, key) — entries older than any window still ahead are reused —
-// and adds, per group, the number of the range's windows in that id
-// interval.  Returns ~0 if the table overflowed (the caller then counts by
-// assembling the windows).
-__device__ unsigned long long count_range(const QueryDev& q, const Scratch& s, QCtl* c,
-                                          unsigned long long wa, unsigned long long wb,
-                                          unsigned cap, unsigned long long* tab, unsigned tab_n,
-                                          unsigned* s_fail) {
-  if (threadIdx.x == 0) *s_fail = 0u;
-  __syncthreads();
-  // global merge scratch the range's windows above `cap` entries will need
-  // (so that one retry can size the scratch for the whole emission)
-  unsigned long long need = 0;
-  unsigned big = 0;
-  for (unsigned long long wi = wa + threadIdx.x; wi < wb; wi += blockDim.x) {
-    const unsigned long long len = s.pane_begin[s.win_j1[wi]] - s.pane_begin[s.win_j0[wi]];
-    if (s.win_j1[wi] - s.win_j0[wi] > 1 && len > cap) need += 2ull * len;
-    if (2ull * len > tab_n) big = 1u;  // a window's keys might not fit the table
-  }
-  if (need) atomicAdd(&c->pool_need, need);
-  if (big) atomicOr(s_fail, 1u);
-  __syncthreads();
-  if (*s_fail) return ~0ull;  // count by assembling the windows instead
-  for (unsigned i = threadIdx.x; i < tab_n; i += blockDim.x) tab[i] = 0ull;  // pane ids are >= 1
-  const unsigned j_begin = s.win_j0[wa], j_end = s.win_j1[wb - 1];
-  const long long w_first = s.win_w[wa], w_last = s.win_w[wb - 1];
-  const long long* ww = s.win_w + wa;
-  const unsigned nw = (unsigned)(wb - wa);
-  // the range's window ids: consecutive (counts by arithmetic), else searched
-  // in shared memory when they fit, else in global memory
-  __shared__ unsigned s_ww[kWwStage];
-  const bool contig = w_last - w_first + 1 == (long long)nw;
-  const bool staged = !contig && nw <= kWwStage && w_last - w_first < (1ll << 32);
-  if (staged)
-    for (unsigned i = threadIdx.x; i < nw; i += blockDim.x) s_ww[i] = (unsigned)(ww[i] - w_first);
-  __syncthreads();
-  unsigned long long total = 0;
-  // one group (key of pane P): update the key's last pane in the table and add
-  // the range's windows in which this group is the key's first occurrence
-  auto group = [&](unsigned key, long long P) {
-    const unsigned long long nv = ((unsigned long long)P << 32) | key;
-    long long prev = LLONG_MIN;
-    unsigned h = (unsigned)(((unsigned long long)(key * 0x9E3779B1u) * tab_n) >> 32);
-    unsigned stale = 0xffffffffu;
-    unsigned long long stale_v = 0ull;
-    bool done = false;
-    for (unsigned probe = 0; probe < 256u && !done; ++probe) {
-      const unsigned long long e = *((volatile unsigned long long*)&tab[h]);
-      if (e != 0ull && (unsigned)e == key) {  // the key's entry: update its pane
-        if (atomicCAS(&tab[h], e, nv) == e) {
-          prev = (long long)(e >> 32);
-          done = true;
-        }
-        continue;  // changed under us: look again
-      }
-      if (e == 0ull) {  // the key is absent: take the first stale slot seen, else this one
-        if (stale != 0xffffffffu) {
-          if (atomicCAS(&tab[stale], stale_v, nv) == stale_v) {
-            done = true;
-          } else {
-            stale = 0xffffffffu;  // taken meanwhile: start over
-            h = (unsigned)(((unsigned long long)(key * 0x9E3779B1u) * tab_n) >> 32);
+    for (unsigned long long kk = 0; kk < kn; ++kk) {
+      const unsigned long long d0 = (k0 + kk) * kEmC;
+      const unsigned long long d1 = d0 + kEmC < L ? d0 + kEmC : L;
+      const unsigned long long a0 = sm.split[kk], a1 = sm.split[kk + 1];
+      const unsigned long long b0 = d0 - a0, b1 = d1 - a1;
+      const unsigned la = (unsigned)(a1 - a0), lbn = (unsigned)(b1 - b0);
+      for (unsigned i = tid; i < la; i += kEmT) sm.ga[i] = it.A[a0 + i].gkey;
+      for (unsigned i = tid; i < lbn; i += kEmT) sm.gb[i] = it.Bv[b0 + i].gkey;
+      __syncthreads();
+      Merged m;
+      m.n = 0;
+      const unsigned len = la + lbn, d = (unsigned)tid * kEmE;
+      if (d < len) {
+        unsigned i = merge_split_s(sm.ga, la, sm.gb, lbn, d, lb), j = d - i;
+#pragma unroll
+        for (int e = 0; e < kEmE; ++e) {
+          if (d + e < len) {
+            const bool ta = j >= lbn || (i < la && gkey_key(sm.ga[i], lb) <= gkey_key(sm.gb[j], lb));
+            const unsigned long long g = ta ? sm.ga[i] : sm.gb[j];
+            m.key[e] = gkey_key(g, lb);
+            m.pane[e] = gkey_pane(g, lb);
+            m.ia[e] = (unsigned)(a0 + i);
+            m.ib[e] = (unsigned)(b0 + j);
+            if (ta) ++i; else ++j;
+            m.n = e + 1;
           }
-        } else if (atomicCAS(&tab[h], 0ull, nv) == 0ull) {
-          done = true;
         }
-        continue;
+        sm.tkey[tid] = m.key[m.n - 1];
+        sm.tpane[tid] = m.pane[m.n - 1];
       }
-      if (stale == 0xffffffffu && (long long)(e >> 32) < P - q.k + 1) {
-        stale = h;  // no window still to come can contain that entry's pane
-        stale_v = e;
+      __syncthreads();
+      f(len, m);
+      // f ended with a barrier: the chunk's last entry becomes the carry
+      if (len > 0 && (unsigned)tid == (len - 1) / kEmE) {
+        sm.carry_key = m.key[m.n - 1];
+        sm.carry_pane = m.pane[m.n - 1];
+        sm.carry_valid = 1;
       }
-      h = h + 1 == tab_n ? 0u : h + 1;
     }
-    if (!done) {
-      atomicOr(s_fail, 1u);
-      return;
-    }
-    long long lo = prev == LLONG_MIN ? P - q.k + 1 : max(prev + 1, P - q.k + 1);
-    long long hi = P;
-    lo = max(lo, w_first);
-    hi = min(hi, w_last);
-    if (lo > hi) return;
-    if (contig) {
-      total += (unsigned long long)(hi - lo + 1);
-      return;
-    }
-    if (staged) {  // ids relative to w_first (their span is below 2^32)
-      const unsigned rl = (unsigned)(lo - w_first), rh = (unsigned)(hi - w_first);
-      unsigned a = 0, b = nw;  // first window with id >= lo
-      while (a < b) {
-        const unsigned m = (a + b) >> 1;
-        if (s_ww[m] < rl) a = m + 1;
-        else b = m;
-      }
-      unsigned c = a, d = nw;  // first window with id > hi
-      while (c < d) {
-        const unsigned m = (c + d) >> 1;
-        if (s_ww[m] <= rh) c = m + 1;
-        else d = m;
-      }
-      total += c - a;
-      return;
-    }
-    unsigned a = 0, b = nw;  // first window with id >= lo
-    while (a < b) {
-      const unsigned m = (a + b) >> 1;
-      if (ww[m] < lo) a = m + 1;
-      else b = m;
-    }
-    unsigned c = a, d = nw;  // first window with id > hi
-    while (c < d) {
-      const unsigned m = (c + d) >> 1;
-      if (ww[m] <= hi) c = m + 1;
-      else d = m;
-    }
-    total += c - a;
-  };
-  // Panes in order, one barrier per pane (its table updates before the next
-  // pane's lookups).  The next pane's bounds and this thread's first two keys
-  // of it are loaded while the current pane is processed.
-  const Grp* st = q.state;
-  const unsigned bd = blockDim.x;
-  long long nP = 0;
-  unsigned long long ng0 = 0, ng1 = 0;
-  unsigned nk0 = 0, nk1 = 0;
-  auto fetch = [&](unsigned jj) {
-    nP = (long long)s.pane_id[jj];
-    ng0 = s.pane_begin[jj];
-    ng1 = s.pane_begin[jj + 1];
-    const unsigned long long ga = ng0 + threadIdx.x, gb = ga + bd;
-    nk0 = ga < ng1 ? (unsigned)st[ga].gkey : 0u;
-    nk1 = gb < ng1 ? (unsigned)st[gb].gkey : 0u;
-  };
-  if (j_begin < j_end) fetch(j_begin);
-  for (unsigned j = j_begin; j < j_end; ++j) {
-    const long long P = nP;
-    const unsigned long long g0 = ng0, g1 = ng1;
-    const unsigned k0 = nk0, k1 = nk1;
-    if (j + 1 < j_end) fetch(j + 1);
-    const unsigned long long ga = g0 + threadIdx.x;
-    if (ga < g1) group(k0, P);
-    if (ga + bd < g1) group(k1, P);
-    for (unsigned long long g = ga + 2ull * bd; g < g1; g += bd) group((unsigned)st[g].gkey, P);
-    __syncthreads();
   }
-  __shared__ unsigned long long ctmp[33];
-  unsigned long long tot;
-  block_excl_scan(total, ctmp, &tot);
-  return *s_fail ? ~0ull : tot;
+  __syncthreads();
 }
 
-// Assembles the closed windows.  CTAs take ranges of consecutive windows in
-// ticket order; for each range: count its rows (pass 1), find the range's row
-// offset by the look-back, then write its rows (pass 2) in (window, key) order.
-// Dynamic shared memory: two padded list buffers of `cap` entries, then two
-// run-boundary arrays of k + 2 entries.
+// The entry before merged entry e of this thread (key, pane), if any.
+__device__ __forceinline__ bool prev_entry(const EmSmem& sm, const Merged& m, int e, unsigned* key,
+                                           unsigned long long* pane) {
+  if (e > 0) {
+    *key = m.key[e - 1];
+    *pane = m.pane[e - 1];
+    return true;
+  }
+  if (threadIdx.x > 0) {
+    *key = sm.tkey[threadIdx.x - 1];
+    *pane = sm.tpane[threadIdx.x - 1];
+    return true;
+  }
+  *key = sm.carry_key;
+  *pane = sm.carry_pane;
+  return sm.carry_valid != 0;
+}
+
+// Rows of each window of the item: a group is its key's first group in the
+// windows from max(previous pane of the key + 1, pane - K + 1) to its pane.
+__device__ void count_item(const QueryDev& q, const Item& it, EmSmem& sm) {
+  const int nw = (int)(it.whi - it.wlo + 1);
+  for (int i = threadIdx.x; i <= nw; i += kEmT) sm.cnt[i] = 0;
+  if (q.k == 1) {  // tumbling: one window, one pane, unique keys
+    __syncthreads();
+    if (threadIdx.x == 0) sm.cnt[0] = (long long)it.na;
+  } else {
+    for_merged_chunks(q, it, sm, [&](unsigned, const Merged& m) {
+      for (int e = 0; e < m.n; ++e) {
+        unsigned pk;
+        unsigned long long pp;
+        long long lo = (long long)m.pane[e] - q.k + 1;
+        if (prev_entry(sm, m, e, &pk, &pp) && pk == m.key[e]) {
+          const long long after = (long long)pp + 1;
+          lo = lo > after ? lo : after;
+        }
+        long long hi = (long long)m.pane[e];
+        lo = lo > it.wlo ? lo : it.wlo;
+        hi = hi < it.whi ? hi : it.whi;
+        if (lo <= hi) {
+          atomicAdd(reinterpret_cast<unsigned long long*>(&sm.cnt[lo - it.wlo]), 1ull);
+          atomicAdd(reinterpret_cast<unsigned long long*>(&sm.cnt[hi - it.wlo + 1]), ~0ull);
+        }
+      }
+      __syncthreads();
+    });
+    if (threadIdx.x == 0) {
+      long long acc = 0;
+      for (int i = 0; i < nw; ++i) {
+        acc += sm.cnt[i];
+        sm.cnt[i] = acc;
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long acc = 0;
+    for (int i = 0; i < nw; ++i) {
+      sm.woff[i] = acc;
+      acc += (unsigned long long)sm.cnt[i];
+    }
+    sm.total = acc;
+  }
+  __syncthreads();
+}
+
+// End (exclusive) of the run of key k in g[from, n): galloping, then binary search.
+__device__ unsigned long long run_end(const Grp* g, unsigned long long from, unsigned long long n,
+                                      unsigned k, int lb) {
+  if (from >= n || gkey_key(g[from].gkey, lb) != k) return from;
+  unsigned long long lo = from, step = 1;  // key(lo) == k
+  while (lo + step < n && gkey_key(g[lo + step].gkey, lb) == k) {
+    lo += step;
+    step <<= 1;
+  }
+  unsigned long long hi = lo + step < n ? lo + step : n;
+  while (hi - lo > 1) {
+    const unsigned long long mid = lo + ((hi - lo) >> 1);
+    if (gkey_key(g[mid].gkey, lb) == k) lo = mid;
+    else hi = mid;
+  }
+  return hi;
+}
+
+// Writes the item's rows from out[0]: rows of window i from out[woff[i]], in
+// key order.
 template <bool FLOAT>
-__global__ void __launch_bounds__(kEmitThreads, 1)
-    k_emit(const QueryDev q, const Scratch s, ResultRowDev* rows, unsigned cap,
-           unsigned long long rows_cap) {
-  extern __shared__ __align__(16) unsigned long long esm[];
-  const unsigned padded = cap + (cap >> 4) + 1;
-  __shared__ unsigned wt[33];
-  __shared__ unsigned long long s_ri, s_off;
-  __shared__ unsigned s_fail;
-  EmitSmem m;
-  m.L = esm;
-  m.T = esm + padded;
-  m.bnd0 = reinterpret_cast<unsigned*>(esm + 2ull * padded);
-  m.bnd1 = m.bnd0 + (q.k + 2);
-  m.wt = wt;
+__device__ void write_item(const QueryDev& q, const Item& it, EmSmem& sm, ResultRowDev* out) {
+  const int tid = threadIdx.x, w = tid >> 5;
+  const unsigned lane = lane_id(), lt = (1u << lane) - 1u;
+  const int lb = q.lb, K = q.k;
+  const int nw = (int)(it.whi - it.wlo + 1);
+  if (K == 1) {  // tumbling: the rows are the pane's groups, in key order
+    const long long wstart = (it.wlo - kPaneBias) * (long long)q.slide + q.base;
+    for (unsigned long long i = tid; i < it.na; i += kEmT) {
+      const Grp g = load_grp_v(it.A + i);
+      write_row<FLOAT>(q, out + i, wstart, gkey_key(g.gkey, lb), g.cnt, g.sum, g.mn, g.mx);
+    }
+    __syncthreads();
+    return;
+  }
+  for (int i = tid; i < nw; i += kEmT) sm.run[i] = 0ull;
+  for_merged_chunks(q, it, sm, [&](unsigned len, const Merged& m) {
+    // heads: the entries that start a key
+    unsigned nh_t = 0;
+    bool head[kEmE];
+#pragma unroll
+    for (int e = 0; e < kEmE; ++e) {
+      head[e] = false;
+      if (e < m.n) {
+        unsigned pk;
+        unsigned long long pp;
+        head[e] = !(prev_entry(sm, m, e, &pk, &pp) && pk == m.key[e]);
+        nh_t += head[e] ? 1u : 0u;
+      }
+    }
+    unsigned long long htot;
+    unsigned long long hpos = block_excl_scan((unsigned long long)nh_t, sm.tmp, &htot);
+#pragma unroll
+    for (int e = 0; e < kEmE; ++e) {
+      if (head[e]) {
+        sm.hk[hpos] = m.key[e];
+        sm.hia[hpos] = m.ia[e];
+        sm.hib[hpos] = m.ib[e];
+        ++hpos;
+      }
+    }
+    (void)len;
+    __syncthreads();
+    const unsigned nh = (unsigned)htot;
+    if (tid == 0 && nh > 0) {  // the last key may continue past the chunk
+      const unsigned k = sm.hk[nh - 1];
+      sm.hia[nh] = (unsigned)run_end(it.A, sm.hia[nh - 1], it.na, k, lb);
+      sm.hib[nh] = (unsigned)run_end(it.Bv, sm.hib[nh - 1], it.nb, k, lb);
+    }
+    __syncthreads();
+    for (unsigned r0 = 0; r0 < nh; r0 += kEmT) {
+      const unsigned h = r0 + (unsigned)tid;
+      const bool valid = h < nh;
+      unsigned key = 0u, ia = 0u, na_k = 0u, ib = 0u, nb_k = 0u;
+      unsigned long long mask = 0ull;
+      if (valid) {
+        key = sm.hk[h];
+        ia = sm.hia[h];
+        ib = sm.hib[h];
+        na_k = sm.hia[h + 1] - ia;
+        nb_k = sm.hib[h + 1] - ib;
+        for (unsigned e = 0; e < na_k; ++e)
+          mask |= pane_windows((long long)gkey_pane(it.A[ia + e].gkey, lb), K, it.wlo, it.whi);
+        for (unsigned e = 0; e < nb_k; ++e)
+          mask |= pane_windows((long long)gkey_pane(it.Bv[ib + e].gkey, lb), K, it.wlo, it.whi);
+      }
+      // rows of this warp per window, then their offsets over the warps
+      sm.wc[w][lane] = 0u;
+      sm.wc[w][lane + 32] = 0u;
+      const unsigned long long orm =
+          ((unsigned long long)__reduce_or_sync(kFull, (unsigned)(mask >> 32)) << 32) |
+          __reduce_or_sync(kFull, (unsigned)mask);
+      __syncwarp();
+      for (unsigned long long bits = orm; bits; bits &= bits - 1) {
+        const int i = __ffsll((long long)bits) - 1;
+        const unsigned bal = __ballot_sync(kFull, (mask >> i) & 1ull);
+        if (lane == 0) sm.wc[w][i] = (unsigned)__popc(bal);
+      }
+      __syncthreads();
+      for (int i = tid; i < nw; i += kEmT) {  // warp offsets inside window i
+        unsigned acc = (unsigned)sm.run[i];
+#pragma unroll
+        for (int ww = 0; ww < kEmWarps; ++ww) {
+          const unsigned t = sm.wc[ww][i];
+          sm.wc[ww][i] = acc;
+          acc += t;
+        }
+        sm.run[i] = acc;
+      }
+      __syncthreads();
+      // the rows: per window of the key, combine its groups in the window
+      const unsigned n_k = na_k + nb_k;
+      unsigned lo = 0u, hi = 0u;
+      for (unsigned long long bits = orm; bits; bits &= bits - 1) {
+        const int i = __ffsll((long long)bits) - 1;
+        const bool mine = (mask >> i) & 1ull;
+        const unsigned bal = __ballot_sync(kFull, mine);
+        if (!mine) continue;
+        const long long W = it.wlo + i;
+        auto entry = [&](unsigned e) -> const Grp* {
+          return e < na_k ? it.A + ia + e : it.Bv + ib + (e - na_k);
+        };
+        while (lo < n_k && (long long)gkey_pane(entry(lo)->gkey, lb) < W) ++lo;
+        if (hi < lo) hi = lo;
+        while (hi < n_k && (long long)gkey_pane(entry(hi)->gkey, lb) <= W + K - 1) ++hi;
+        if (lo >= hi) continue;  // cannot happen: the mask says a group lies in the window
+        const Grp g0 = load_grp_v(entry(lo));
+        long long cnt = g0.cnt;
+        unsigned long long isum = g0.sum;
+        double fsum = __longlong_as_double((long long)g0.sum);
+        unsigned mn = g0.mn, mx = g0.mx;
+        for (unsigned e = lo + 1; e < hi; ++e) {
+          const Grp g = load_grp_v(entry(e));
+          cnt += g.cnt;
+          mn = min(mn, g.mn);
+          mx = max(mx, g.mx);
+          if (FLOAT) fsum += __longlong_as_double((long long)g.sum);
+          else isum += g.sum;
+        }
+        const unsigned long long sb = FLOAT ? (unsigned long long)__double_as_longlong(fsum) : isum;
+        const unsigned long long pos =
+            sm.woff[i] + sm.wc[w][i] + (unsigned)__popc(bal & lt);
+        const long long wstart = (W - kPaneBias) * (long long)q.slide + q.base;
+        write_row<FLOAT>(q, out + pos, wstart, key, cnt, sb, mn, mx);
+      }
+      __syncthreads();
+    }
+  });
+}
+
+// Emits the closed windows.  CTAs take items in ticket order; for each item:
+// its rows per window (count_item), its row offset by the look-back, then the
+// rows (write_item).
+template <bool FLOAT>
+__global__ void __launch_bounds__(kEmT, 3)
+    k_emit(const QueryDev q, const Scratch s, ResultRowDev* rows, unsigned long long rows_cap) {
+  __shared__ EmSmem sm;
   QCtl* c = q.ctl;
   if (c->err & kErrNeedRetry) return;
-  const unsigned long long W = c->n_windows;
-  const unsigned long long per = (W + 4ull * gridDim.x - 1) / (4ull * gridDim.x);
-  const unsigned long long NR = per ? (W + per - 1) / per : 0;
+  const unsigned long long NI = c->n_items;
   const unsigned long long row_base = c->row_base;
   while (true) {
-    if (threadIdx.x == 0) s_ri = atomicAdd(&c->win_ticket, 1ull);
+    if (threadIdx.x == 0) sm.ri = atomicAdd(&c->item_ticket, 1ull);
     __syncthreads();
-    const unsigned long long ri = s_ri;
+    const unsigned long long ri = sm.ri;
     __syncthreads();
-    if (ri >= NR) break;
-    const unsigned long long wa = ri * per, wb = min(W, wa + per);
-    // the range's row count: by the pane sweep, else by assembling the windows
-    unsigned long long n = count_range(q, s, c, wa, wb, cap, esm, 2u * padded, &s_fail);
-    __syncthreads();
-    if (n == ~0ull) n = run_range<FLOAT, false>(q, s, c, wa, wb, cap, m, nullptr, &s_off);
+    if (ri >= NI) break;
+    const Item it = load_item(q, s, c, ri);
+    if (ri == 0 && (q.debug_flags & kDebugHoldFirstItem)) continue;  // never publishes
+    count_item(q, it, sm);
     if (threadIdx.x == 0) {
-      const unsigned long long off = range_lookback(s.win_stat, ri, n, c);
-      s_off = off;
+      const unsigned long long n = sm.total;
+      const unsigned long long off = item_lookback(s.item_stat, ri, n, c, q.lookback_ns);
+      sm.off = off;
       if (off != ~0ull) {
-        if (ri == NR - 1) c->rows_batch = off + n;
+        if (ri == NI - 1) c->rows_batch = off + n;
         if (row_base + off + n > rows_cap) atomicOr(&c->err, kErrRowsOverflow);
       }
     }
     __syncthreads();
-    const unsigned long long off = s_off;
+    const unsigned long long off = sm.off;
     __syncthreads();
-    if (off != ~0ull && row_base + off + n <= rows_cap && !(c->err & kErrPoolOverflow))
-      run_range<FLOAT, true>(q, s, c, wa, wb, cap, m, rows + row_base + off, &s_off);
+    if (off != ~0ull && row_base + off + sm.total <= rows_cap)
+      write_item<FLOAT>(q, it, sm, rows + row_base + off);
+    __syncthreads();
   }
 }
 
 // ---- carry the panes that stay open into the next batch's partial arrays --
 
+// Advances the cursor past the closed windows and finds where the groups that
+// may stay open start: the first block that holds panes >= the new cursor.
 __global__ void k_trim_prep(const QueryDev q, const Scratch s) {
   if (threadIdx.x != 0) return;
   QCtl* c = q.ctl;
   if (c->err & kErrNeedRetry) return;
   c->row_base += c->rows_batch;
   if (c->w_hi >= c->cursor) c->cursor = c->w_hi + 1;
-  // first pane that stays open: pane id > w_hi
-  const unsigned long long P = c->n_panes;
+  const unsigned long long bstar = (unsigned long long)c->cursor >> q.lb;
+  const unsigned long long P = c->n_blocks;
   unsigned long long lo = 0, hi = P;
   while (lo < hi) {
     const unsigned long long mid = (lo + hi) >> 1;
-    if ((long long)s.pane_id[mid] <= c->w_hi) lo = mid + 1; else hi = mid;
+    if ((unsigned long long)s.blk_id[mid] < bstar) lo = mid + 1; else hi = mid;
   }
-  const unsigned long long from = lo < P ? s.pane_begin[lo] : c->n_state;
-  c->trim_from = from;
-  c->carried = c->n_state - from;
-  c->n_parts = c->carried;
+  c->trim_from = lo < P ? s.blk_begin[lo] : c->n_state;
   c->or_mask = 0ull;
   c->and_mask = ~0ull;
 }
 
-__global__ void __launch_bounds__(256) k_trim_copy(const QueryDev q) {
+// Groups at or after trim_from whose pane is still open (pane >= cursor),
+// counted per chunk; then written, in order, to the front of the partial
+// arrays.
+__device__ __forceinline__ bool keep_group(const QueryDev& q, const QCtl* c, unsigned long long g) {
+  return (long long)gkey_pane(g, q.lb) >= c->cursor;
+}
+
+__global__ void __launch_bounds__(256) k_trim_count(const QueryDev q, const Scratch s) {
+  const QCtl* c = q.ctl;
+  if (c->err & kErrNeedRetry) return;
+  const unsigned long long from = c->trim_from, n = c->n_state - from;
+  unsigned long long lo, hi;
+  chunk_range(n, blockIdx.x, gridDim.x, &lo, &hi);
+  unsigned long long cnt = 0;
+  for (unsigned long long i = lo + threadIdx.x; i < hi; i += blockDim.x)
+    cnt += keep_group(q, c, q.state[from + i].gkey) ? 1ull : 0ull;
+  __shared__ unsigned long long tmp[33];
+  unsigned long long tot;
+  block_excl_scan(cnt, tmp, &tot);
+  if (threadIdx.x == 0) s.chunk[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(256) k_trim_scan(const QueryDev q, const Scratch s) {
   QCtl* c = q.ctl;
   if (c->err & kErrNeedRetry) return;
-  const unsigned long long from = c->trim_from, n = c->carried;
+  __shared__ unsigned long long tmp[33];
+  unsigned long long x[4], sum = 0;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int i = 4 * (int)threadIdx.x + u;
+    x[u] = i < kGrid ? s.chunk[i] : 0ull;
+    sum += x[u];
+  }
+  unsigned long long tot;
+  unsigned long long r = block_excl_scan(sum, tmp, &tot);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int i = 4 * (int)threadIdx.x + u;
+    if (i < kGrid) s.chunk[i] = r;
+    r += x[u];
+  }
+  if (threadIdx.x == 0) {
+    c->carried = tot;
+    c->n_parts = tot;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_trim_write(const QueryDev q, const Scratch s) {
+  QCtl* c = q.ctl;
+  if (c->err & kErrNeedRetry) return;
+  const unsigned long long from = c->trim_from, n = c->n_state - from;
+  unsigned long long lo, hi;
+  chunk_range(n, blockIdx.x, gridDim.x, &lo, &hi);
+  __shared__ unsigned long long tmp[33];
+  unsigned long long out = s.chunk[blockIdx.x];
   unsigned long long o_acc = 0ull, a_acc = ~0ull;
-  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
-       i += (unsigned long long)gridDim.x * blockDim.x) {
-    const Grp g = load_grp(q.state + from + i);
-    store_grp(q.parts + i, g.gkey, g.cnt, g.sum, g.mn, g.mx);
-    q.pkeys[i] = g.gkey;
-    o_acc |= g.gkey;
-    a_acc &= g.gkey;
+  for (unsigned long long i0 = lo; i0 < hi; i0 += blockDim.x) {
+    const unsigned long long i = i0 + threadIdx.x;
+    Grp g;
+    bool keep = false;
+    if (i < hi) {
+      g = load_grp(q.state + from + i);
+      keep = keep_group(q, c, g.gkey);
+    }
+    unsigned long long tot;
+    const unsigned long long r = block_excl_scan(keep ? 1ull : 0ull, tmp, &tot);
+    if (keep) {
+      store_grp(q.parts + out + r, g.gkey, g.cnt, g.sum, g.mn, g.mx);
+      q.pkeys[out + r] = g.gkey;
+      o_acc |= g.gkey;
+      a_acc &= g.gkey;
+    }
+    out += tot;
   }
   const unsigned olo = __reduce_or_sync(kFull, (unsigned)o_acc);
   const unsigned ohi = __reduce_or_sync(kFull, (unsigned)(o_acc >> 32));
@@ -915,19 +822,25 @@ __global__ void __launch_bounds__(256) k_trim_copy(const QueryDev q) {
   }
 }
 
-template <bool FLOAT>
-cudaError_t launch_emit_t(const QueryDev& q, const Scratch& s, ResultRowDev* rows, int grid,
-                          size_t smem, unsigned long long rows_cap, cudaStream_t st) {
-  // once per process (thread-safe static initialisation)
-  static const cudaError_t attr = cudaFuncSetAttribute(
-      k_emit<FLOAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEmitSmemMax);
-  if (attr != cudaSuccess) return attr;
-  k_emit<FLOAT><<<grid, kEmitThreads, smem, st>>>(q, s, rows, smem ? emit_cap(q.k) : 0u,
-                                                 rows_cap);
-  return cudaGetLastError();
+}  // namespace
+
+void set_block_shape(QueryDev* d) {
+  int lb = 0;
+  while ((1 << lb) < d->k) ++lb;
+  d->lb = lb;
+  d->nw = (1 << lb) < kMaxItemWindows ? (1 << lb) : kMaxItemWindows;
 }
 
-}  // namespace
+cudaError_t set_smem_limit(const void* fn, int bytes, unsigned long long* done_mask) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (__atomic_load_n(done_mask, __ATOMIC_ACQUIRE) & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) __atomic_fetch_or(done_mask, bit, __ATOMIC_ACQ_REL);
+  return e;
+}
 
 cudaError_t launch_batch_begin(SCtl* sctl, QCtl* const* ctls, int nq, cudaStream_t st) {
   QCtl* c[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -952,34 +865,36 @@ cudaError_t launch_watermark(SCtl* sctl, const QueryDev* qs, int nq, long long l
   return cudaGetLastError();
 }
 
-// ev4 (optional): events recorded before/after E1 and before/after E2.
+// ev4 (optional): events recorded before/after the item list and before/after
+// the row kernel.
 cudaError_t launch_emit(const QueryDev& q, const Scratch& s, ResultRowDev* rows,
                         unsigned long long rows_cap, int sms, cudaStream_t st, int* launches,
                         cudaEvent_t* ev4) {
+  if (ev4) record_event(ev4[0], st);
   k_emit_begin<<<1, 32, 0, st>>>(q.ctl);
-  k_win_count<<<kGrid, 256, 0, st>>>(q, s);
-  k_win_scan<<<1, 1024, 0, st>>>(q, s);
-  k_win_write<<<kGrid, 256, 0, st>>>(q, s);
-  // Tumbling windows (one pane each) need no merge buffers.
-  const size_t smem = q.k > 1 ? emit_smem(q.k) : 0;
-  const int grid = q.k > 1 ? sms : 4 * sms;
+  k_item_count<<<kGrid, 256, 0, st>>>(q, s);
+  k_item_scan<<<1, 1024, 0, st>>>(q, s);
+  k_item_write<<<kGrid, 256, 0, st>>>(q, s);
   if (ev4) {
-    record_event(ev4[0], st);
     record_event(ev4[1], st);
     record_event(ev4[2], st);
   }
-  cudaError_t e = q.value_is_float ? launch_emit_t<true>(q, s, rows, grid, smem, rows_cap, st)
-                                   : launch_emit_t<false>(q, s, rows, grid, smem, rows_cap, st);
+  const int grid = 3 * sms;
+  if (q.value_is_float) k_emit<true><<<grid, kEmT, 0, st>>>(q, s, rows, rows_cap);
+  else k_emit<false><<<grid, kEmT, 0, st>>>(q, s, rows, rows_cap);
   if (ev4) record_event(ev4[3], st);
   if (launches) *launches += 5;
-  return e;
+  return cudaGetLastError();
 }
 
 cudaError_t launch_trim(const QueryDev& q, const Scratch& s, int sms, cudaStream_t st,
                         int* launches) {
+  (void)sms;
   k_trim_prep<<<1, 32, 0, st>>>(q, s);
-  k_trim_copy<<<2 * sms, 256, 0, st>>>(q);
-  if (launches) *launches += 2;
+  k_trim_count<<<kGrid, 256, 0, st>>>(q, s);
+  k_trim_scan<<<1, 256, 0, st>>>(q, s);
+  k_trim_write<<<kGrid, 256, 0, st>>>(q, s);
+  if (launches) *launches += 4;
   return cudaGetLastError();
 }
 

@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(kK1Threads, K1Shape<ITEMS>::kCtasPerSm)
           } else {
             const unsigned long long prel = udiv_inv(u, Q.magic, Q.sh1, Q.sh2);
             if ((long long)prel < cursor) ++n_late;  // every window of this event was emitted
-            else g = (prel << 32) | key[i];
+            else g = make_gkey(prel, key[i], Q.lb);
           }
         }
         const unsigned enc = FLOAT ? enc_f32(__uint_as_float(val[i])) : enc_i32((int)val[i]);
@@ -445,10 +445,9 @@ __global__ void __launch_bounds__(kK1Threads, K1Shape<ITEMS>::kCtasPerSm)
 
 template <bool FLOAT, int ITEMS, bool WAGG>
 cudaError_t launch_k1_t(const K1Args& a, int grid, cudaStream_t st) {
-  // once per process and instantiation (thread-safe static initialisation)
-  static const cudaError_t attr =
-      cudaFuncSetAttribute(k1_fused<FLOAT, ITEMS, WAGG>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K1Shape<ITEMS>::kSmem);
+  static unsigned long long done = 0;  // devices whose limit is set
+  const cudaError_t attr = set_smem_limit(reinterpret_cast<const void*>(k1_fused<FLOAT, ITEMS, WAGG>),
+                                          (int)K1Shape<ITEMS>::kSmem, &done);
   if (attr != cudaSuccess) return attr;
   k1_fused<FLOAT, ITEMS, WAGG><<<grid, kK1Threads, K1Shape<ITEMS>::kSmem, st>>>(a);
   return cudaGetLastError();

@@ -6,7 +6,7 @@
 // sort of the 64-bit group keys (8-bit digits; digits that are equal in every
 // key are skipped, which the OR/AND masks gathered by the producers reveal),
 // then a reduce-by-key that combines equal (pane, key) groups, then the index
-// of distinct panes.  All sizes are read on the device, so the whole sequence
+// of distinct blocks.  All sizes are read on the device, so the whole sequence
 // launches without a host round trip.
 //
 // Chunked kernels use a fixed grid of kGrid CTAs, each owning one contiguous
@@ -511,49 +511,49 @@ __global__ void __launch_bounds__(256) k_rbk_long(const QueryDev q, const Scratc
   }
 }
 
-// ---- distinct panes of the window state ------------------------------------
+// ---- distinct blocks of the window state -----------------------------------
 
-// Pane ids never decrease along the sorted state and panes are runs of many
-// groups, so each thread finds the pane boundaries of its contiguous share of
+// Block ids never decrease along the sorted state and blocks are runs of many
+// groups, so each thread finds the block boundaries of its contiguous share of
 // a chunk by galloping and binary search instead of reading every group.
-__device__ __forceinline__ unsigned pane_of(const QueryDev& q, unsigned long long i) {
-  return (unsigned)(q.state[i].gkey >> 32);
+__device__ __forceinline__ unsigned block_of(const QueryDev& q, unsigned long long i) {
+  return (unsigned)gkey_block(q.state[i].gkey, q.lb);
 }
 
-// First index in (a, b) whose pane differs from p (the pane of a), else b.
-__device__ unsigned long long next_pane_change(const QueryDev& q, unsigned long long a,
-                                               unsigned long long b, unsigned p) {
-  unsigned long long lo = a, step = 1;  // pane(lo) == p
-  while (lo + step < b && pane_of(q, lo + step) == p) {
+// First index in (a, b) whose block differs from p (the block of a), else b.
+__device__ unsigned long long next_block_change(const QueryDev& q, unsigned long long a,
+                                                unsigned long long b, unsigned p) {
+  unsigned long long lo = a, step = 1;  // block(lo) == p
+  while (lo + step < b && block_of(q, lo + step) == p) {
     lo += step;
     step <<= 1;
   }
-  unsigned long long hi = lo + step < b ? lo + step : b;  // pane(hi) != p, or hi == b
+  unsigned long long hi = lo + step < b ? lo + step : b;  // block(hi) != p, or hi == b
   while (hi - lo > 1) {
     const unsigned long long mid = lo + ((hi - lo) >> 1);
-    if (pane_of(q, mid) == p) lo = mid;
+    if (block_of(q, mid) == p) lo = mid;
     else hi = mid;
   }
   return hi;
 }
 
-// Calls f(i, pane) for every first group of a pane in [a, b), in order.
+// Calls f(i, block) for every first group of a block in [a, b), in order.
 template <class F>
-__device__ void for_pane_heads(const QueryDev& q, unsigned long long a, unsigned long long b,
-                               F f) {
+__device__ void for_block_heads(const QueryDev& q, unsigned long long a, unsigned long long b,
+                                F f) {
   if (a >= b) return;
-  unsigned p = pane_of(q, a);
-  if (a == 0 || pane_of(q, a - 1) != p) f(a, p);
-  for (unsigned long long i = next_pane_change(q, a, b, p); i < b;
-       i = next_pane_change(q, i, b, p)) {
-    p = pane_of(q, i);
+  unsigned p = block_of(q, a);
+  if (a == 0 || block_of(q, a - 1) != p) f(a, p);
+  for (unsigned long long i = next_block_change(q, a, b, p); i < b;
+       i = next_block_change(q, i, b, p)) {
+    p = block_of(q, i);
     f(i, p);
   }
 }
 
 // This thread's share [*a, *b) of the block's chunk of the state.
-__device__ __forceinline__ void pane_share(unsigned long long n, unsigned long long* a,
-                                           unsigned long long* b) {
+__device__ __forceinline__ void thread_share(unsigned long long n, unsigned long long* a,
+                                             unsigned long long* b) {
   unsigned long long lo, hi;
   chunk_range(n, blockIdx.x, gridDim.x, &lo, &hi);
   const unsigned long long per = (hi - lo + blockDim.x - 1) / blockDim.x;
@@ -561,39 +561,41 @@ __device__ __forceinline__ void pane_share(unsigned long long n, unsigned long l
   *b = min(hi, *a + per);
 }
 
-__global__ void __launch_bounds__(256) k_pane_count(const QueryDev q, const Scratch s) {
+__global__ void __launch_bounds__(256) k_blk_count(const QueryDev q, const Scratch s) {
   unsigned long long a, b, cnt = 0;
-  pane_share(q.ctl->n_state, &a, &b);
-  for_pane_heads(q, a, b, [&](unsigned long long, unsigned) { ++cnt; });
+  thread_share(q.ctl->n_state, &a, &b);
+  for_block_heads(q, a, b, [&](unsigned long long, unsigned) { ++cnt; });
   __shared__ unsigned long long tmp[33];
   unsigned long long tot;
   block_excl_scan(cnt, tmp, &tot);
   if (threadIdx.x == 0) s.chunk[blockIdx.x] = tot;
 }
 
-__global__ void __launch_bounds__(256) k_pane_write(const QueryDev q, const Scratch s) {
+__global__ void __launch_bounds__(256) k_blk_write(const QueryDev q, const Scratch s) {
   const QCtl* c = q.ctl;
   const unsigned long long n = c->n_state;
   unsigned long long a, b, cnt = 0;
-  pane_share(n, &a, &b);
-  for_pane_heads(q, a, b, [&](unsigned long long, unsigned) { ++cnt; });
+  thread_share(n, &a, &b);
+  for_block_heads(q, a, b, [&](unsigned long long, unsigned) { ++cnt; });
   __shared__ unsigned long long tmp[33];
   unsigned long long tot;
   unsigned long long out = s.chunk[blockIdx.x] + block_excl_scan(cnt, tmp, &tot);
-  for_pane_heads(q, a, b, [&](unsigned long long i, unsigned p) {
-    s.pane_id[out] = p;
-    s.pane_begin[out] = i;
+  for_block_heads(q, a, b, [&](unsigned long long i, unsigned p) {
+    s.blk_id[out] = p;
+    s.blk_begin[out] = i;
     ++out;
   });
-  if (a < b && b == n) s.pane_begin[c->n_panes] = n;
+  if (a < b && b == n) s.blk_begin[c->n_blocks] = n;
+  if (n == 0 && blockIdx.x == 0 && threadIdx.x == 0) s.blk_begin[0] = 0;
 }
 
 }  // namespace
 
 cudaError_t launch_sort_reduce(const QueryDev& q, const Scratch& s, cudaStream_t st,
                                int* launches) {
-  static const cudaError_t attr = cudaFuncSetAttribute(
-      k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
+  static unsigned long long done = 0;  // devices whose limit is set
+  const cudaError_t attr =
+      set_smem_limit(reinterpret_cast<const void*>(k_sort_scatter), (int)kScatterSmem, &done);
   if (attr != cudaSuccess) return attr;
   int nl = 0;
   k_sort_plan<<<1, 32, 0, st>>>(q.ctl);
@@ -618,13 +620,13 @@ cudaError_t launch_sort_reduce(const QueryDev& q, const Scratch& s, cudaStream_t
   return cudaGetLastError();
 }
 
-// Index of distinct panes of q's window state (into the shared scratch; it
+// Index of distinct blocks of q's window state (into the shared scratch; it
 // must be rebuilt before every emission of q).
-cudaError_t launch_pane_index(const QueryDev& q, const Scratch& s, cudaStream_t st,
-                              int* launches) {
-  k_pane_count<<<kGrid, 256, 0, st>>>(q, s);
-  k_scan_chunks<<<1, 1024, 0, st>>>(s.chunk, kGrid, &q.ctl->n_panes);
-  k_pane_write<<<kGrid, 256, 0, st>>>(q, s);
+cudaError_t launch_block_index(const QueryDev& q, const Scratch& s, cudaStream_t st,
+                               int* launches) {
+  k_blk_count<<<kGrid, 256, 0, st>>>(q, s);
+  k_scan_chunks<<<1, 1024, 0, st>>>(s.chunk, kGrid, &q.ctl->n_blocks);
+  k_blk_write<<<kGrid, 256, 0, st>>>(q, s);
   if (launches) *launches += 3;
   return cudaGetLastError();
 }

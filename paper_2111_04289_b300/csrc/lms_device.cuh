@@ -19,6 +19,23 @@ __device__ __forceinline__ unsigned long long udiv_inv(unsigned long long n, uns
   return (t + ((n - t) >> sh1)) >> sh2;
 }
 
+// Group keys (see lms_internal.h): block-major, then key, then the pane's
+// position in its block of 2^lb panes.
+__device__ __forceinline__ unsigned long long make_gkey(unsigned long long pane_rel, unsigned key,
+                                                        int lb) {
+  const unsigned long long lo = (1ull << lb) - 1ull;
+  return ((pane_rel >> lb) << (32 + lb)) | ((unsigned long long)key << lb) | (pane_rel & lo);
+}
+__device__ __forceinline__ unsigned gkey_key(unsigned long long g, int lb) {
+  return (unsigned)(g >> lb);
+}
+__device__ __forceinline__ unsigned long long gkey_pane(unsigned long long g, int lb) {
+  return ((g >> (32 + lb)) << lb) | (g & ((1ull << lb) - 1ull));
+}
+__device__ __forceinline__ unsigned long long gkey_block(unsigned long long g, int lb) {
+  return g >> (32 + lb);
+}
+
 // Order-preserving uint32 images of int32 and float32 values, so that
 // unsigned atomicMin/atomicMax implement min/max.  The float image orders by
 // IEEE-754 totalOrder (-0.0 < +0.0).

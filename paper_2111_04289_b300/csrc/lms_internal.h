@@ -5,14 +5,21 @@
 //     time (pane p covers [p*slide, (p+1)*slide)).  A window of size K*slide is
 //     the union of K consecutive panes, so every event updates exactly one
 //     group, whatever K is; windows are assembled from panes at emission.
-//   * gkey = (pane_rel << 32) | key, pane_rel = pane - origin_pane + 2^31, so
-//     sorting gkeys as uint64 orders groups by (pane, key).
+//   * panes are numbered relative to the stream's origin, pane_rel = pane -
+//     origin_pane + 2^31 (< 2^32), and grouped into blocks of B = 2^lb panes,
+//     B the smallest power of two >= K.  The group key is
+//       gkey = (block << (32 + lb)) | (key << lb) | (pane_rel mod B),
+//     so sorting gkeys as uint64 orders groups by (block, key, pane): inside a
+//     block the state is key-major.  The windows starting in one block touch
+//     only that block and the next, so each of them is assembled from two
+//     key-sorted runs.  Tumbling windows have B = 1 (the (pane, key) order).
 //   * Groups are 32-byte records {gkey, cnt, sum, mn, mx} (Grp); min/max are
 //     stored order-preserving encoded as uint32 (see lms_device.cuh).  The
 //     partial groups' keys are also kept in a compact array for the sort.
 // Per micro-batch, the fused pass appends per-tile partial groups after the
 // carried state; a radix sort + reduce-by-key turns them into the sorted,
-// unique window state; closed windows are merged from their panes and emitted.
+// unique window state; closed windows are assembled from their blocks and
+// emitted.
 #pragma once
 
 #include <cstdint>
@@ -26,12 +33,18 @@ constexpr long long kPaneBias = 1ll << 31;  // pane_rel = pane - origin_pane + k
 
 // Error bits raised by kernels (QCtl::err).
 constexpr unsigned kErrPartsOverflow = 1u;   // partial-group buffer too small
-constexpr unsigned kErrWinOverflow = 2u;     // window list too small
+constexpr unsigned kErrItemOverflow = 2u;    // emission item list too small
 constexpr unsigned kErrRowsOverflow = 4u;    // result buffer too small
-constexpr unsigned kErrPoolOverflow = 8u;    // big-window merge scratch too small
 constexpr unsigned kErrProbe = 16u;          // shared hash probe bound hit (never expected)
-constexpr unsigned kErrLookback = 32u;       // a window's bounded look-back wait ran out
-constexpr unsigned kErrNeedRetry = kErrWinOverflow | kErrRowsOverflow | kErrPoolOverflow;
+constexpr unsigned kErrLookback = 32u;       // an item's bounded look-back wait ran out
+constexpr unsigned kErrNeedRetry = kErrItemOverflow | kErrRowsOverflow;
+
+// Windows per emission item (an item is a run of consecutive window ids that
+// start in one block).
+constexpr int kMaxItemWindows = 64;
+
+// Stream debug flags (lms_stream_config.debug_flags).
+constexpr unsigned kDebugHoldFirstItem = 1u;  // emission item 0 never publishes its row count
 
 // One (pane, key) group: a 32-byte record, so that a random gather of a group
 // touches one DRAM sector.
@@ -49,20 +62,17 @@ struct QCtl {
   unsigned long long or_mask;    // OR of all partial gkeys
   unsigned long long and_mask;   // AND of all partial gkeys
   unsigned long long n_state;    // unique groups in the window state
-  unsigned long long n_panes;    // distinct panes in the window state
-  unsigned long long n_windows;  // windows closed by this batch
+  unsigned long long n_blocks;   // distinct blocks in the window state
+  unsigned long long n_items;    // emission items of the windows closed by this batch
   long long cursor;              // first (relative) window id not yet closed
   long long w_hi;                // last (relative) window id closed by this batch
   unsigned long long late_rows;  // cumulative
   unsigned long long range_rows; // cumulative
   unsigned long long rows_batch; // rows emitted by this batch
   unsigned long long row_base;   // rows held in the device result buffer
-  unsigned long long pool_used;  // big-window scratch entries used (this emission)
-  unsigned long long pool_need;  // big-window scratch entries all closed windows need
   unsigned long long carried;    // groups carried into the next batch
-  unsigned long long big_windows;// windows merged through global scratch (this emission)
-  unsigned long long trim_from;  // first state index carried into the next batch
-  unsigned long long win_ticket; // next window to assemble (emission takes windows in order)
+  unsigned long long trim_from;  // first state index that may be carried into the next batch
+  unsigned long long item_ticket;// next emission item (CTAs take items in order)
   unsigned long long parts_at_sort; // partial groups the sort of this batch consumed
   unsigned long long n_long;     // long runs of equal keys left to the cooperative reduce
   unsigned int err;
@@ -99,6 +109,10 @@ struct QueryDev {
   long long base;              // origin_pane * slide
   long long origin_pane;
   int k;                       // size / slide
+  int lb;                      // log2 of the block size B (smallest power of two >= k)
+  int nw;                      // windows per emission item: min(B, kMaxItemWindows)
+  unsigned long long lookback_ns;  // bound of the emission's look-back wait
+  unsigned debug_flags;        // kDebug* bits (tests only)
   unsigned agg_mask;
   int qid;
   int value_is_float;
@@ -121,7 +135,7 @@ struct K1Args {
   QueryDev q[kMaxQueries];
 };
 
-// Scratch shared by the per-query pipelines: each query's sort/reduce, pane
+// Scratch shared by the per-query pipelines: each query's sort/reduce, block
 // index, emission and carry run back to back before the next query's start.
 struct Scratch {
   unsigned long long* keysA;
@@ -131,17 +145,14 @@ struct Scratch {
   unsigned long long cap;        // entries of keysA/B, valsA/B
   unsigned* hist;                // 256 * kGrid per-chunk digit counts, then 256 digit totals
   unsigned long long* chunk;     // kGrid (+1) per-chunk counts / offsets
-  unsigned* pane_id;             // [pane_cap]
-  unsigned long long* pane_begin;// [pane_cap + 1]
-  unsigned long long pane_cap;
-  long long* win_w;              // window list [win_cap]
-  unsigned* win_j0;
-  unsigned* win_j1;
-  unsigned long long* win_stat;  // look-back word per window: 0 = not ready,
+  unsigned* blk_id;              // distinct blocks of the state [blk_cap]
+  unsigned long long* blk_begin; // their first state index [blk_cap + 1]
+  unsigned long long blk_cap;
+  unsigned long long* item_c;    // emission items: window chunk c (windows [c*nw, c*nw + nw))
+  unsigned* item_j;              // index of the block that anchors the item
+  unsigned long long* item_stat; // look-back word per item: 0 = not ready,
                                  // 1<<62 | rows (own count), 2<<62 | rows (inclusive prefix)
-  unsigned long long win_cap;
-  unsigned long long* pool;      // big-window merge scratch (2 buffers per window)
-  unsigned long long pool_cap;   // entries
+  unsigned long long item_cap;
 };
 
 struct ResultRowDev {  // device image of lms_result_row (48 bytes)
@@ -168,8 +179,8 @@ cudaError_t launch_watermark(SCtl* sctl, const QueryDev* qs, int nq, long long l
                              cudaStream_t st);
 cudaError_t launch_sort_reduce(const QueryDev& q, const Scratch& s, cudaStream_t st,
                                int* launches);
-cudaError_t launch_pane_index(const QueryDev& q, const Scratch& s, cudaStream_t st,
-                              int* launches);
+cudaError_t launch_block_index(const QueryDev& q, const Scratch& s, cudaStream_t st,
+                               int* launches);
 cudaError_t launch_emit(const QueryDev& q, const Scratch& s, ResultRowDev* rows,
                         unsigned long long rows_cap, int sms, cudaStream_t st, int* launches,
                         cudaEvent_t* ev4);
@@ -199,6 +210,13 @@ inline cudaError_t record_event(cudaEvent_t e, cudaStream_t st) {
 
 // Fills filter_lo / filter_hi / filter_exact from filter_f.
 void set_float_filter(QueryDev* d);
+
+// Fills lb and nw from k.
+void set_block_shape(QueryDev* d);
+
+// Sets a kernel's dynamic shared-memory limit once per device (the attribute
+// belongs to the function's instance on the current device).
+cudaError_t set_smem_limit(const void* fn, int bytes, unsigned long long* done_mask);
 
 // Invariant division constants (Granlund & Montgomery 1994, unsigned, N=64).
 void udiv_constants(unsigned long long d, unsigned long long* magic, int* sh1, int* sh2);

@@ -6,15 +6,17 @@
 // device memory budget and forbids its guests from allocating, or an engine
 // that must not allocate on its serving path.  The stream API allocates (and
 // grows) its buffers; this entry point instead carves every intermediate
-// buffer of the hot path (partial groups, window state, sort buffers, pane
-// index, window list, big-window merge scratch, control blocks) out of one
+// buffer of the hot path (partial groups, window state, sort buffers, block
+// index, emission item list, control blocks) out of one
 // fixed array in device memory that the library declares at file scope.  The
 // caller passes the input columns and the output row buffer.
 //
-// The array (kStaticBytes, about 26 MiB) exists on every GPU that loads the
+// The array (kStaticBytes, about 17 MiB) exists on every GPU that loads the
 // library, for the life of the process.  Its device address is looked up with
 // cudaGetSymbolAddress once per device, with that device current, on the first
-// call made on that device; make that first call before any stream capture.
+// call made on that device.  Every call reads the batch's first event time
+// back to the host and waits for its stream, so no call may be made while a
+// stream is being captured into a CUDA graph.
 // Every call on a device shares the array and leaves its contents behind; each
 // call re-initialises what must start from zero (the control blocks).  Calls
 // are serialised by a process-wide lock and each one synchronises its stream
@@ -31,16 +33,15 @@ namespace lms {
 namespace {
 
 constexpr unsigned long long kStaticGroups = LMS_STATIC_MAX_ROWS;  // one group per row at most
-constexpr unsigned long long kStaticWindows = 1ull << 17;
-constexpr unsigned long long kStaticPool = 1ull << 20;  // big-window merge entries
+constexpr unsigned long long kStaticItems = 1ull << 17;  // emission items (runs of <= 64 windows)
 
 constexpr size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
   size_t sctl, qctl;
   size_t parts, pkeys, state;
-  size_t keysA, keysB, valsA, valsB, hist, chunk, pane_id, pane_begin;
-  size_t win_w, win_j0, win_j1, win_stat, pool, total;
+  size_t keysA, keysB, valsA, valsB, hist, chunk, blk_id, blk_begin;
+  size_t item_c, item_j, item_stat, total;
 };
 
 constexpr Layout make_layout() {
@@ -57,13 +58,11 @@ constexpr Layout make_layout() {
   L.valsB = o; o += al(4 * kStaticGroups);
   L.hist = o; o += al(4ull * (256 * kGrid + 256));
   L.chunk = o; o += al(8ull * (kGrid + 1));
-  L.pane_id = o; o += al(4 * (kStaticGroups + 1));
-  L.pane_begin = o; o += al(8 * (kStaticGroups + 1));
-  L.win_w = o; o += al(8 * kStaticWindows);
-  L.win_j0 = o; o += al(4 * kStaticWindows);
-  L.win_j1 = o; o += al(4 * kStaticWindows);
-  L.win_stat = o; o += al(8 * kStaticWindows);
-  L.pool = o; o += al(8 * kStaticPool);
+  L.blk_id = o; o += al(4 * (kStaticGroups + 1));
+  L.blk_begin = o; o += al(8 * (kStaticGroups + 1));
+  L.item_c = o; o += al(8 * kStaticItems);
+  L.item_j = o; o += al(4 * kStaticItems);
+  L.item_stat = o; o += al(8 * kStaticItems);
   L.total = o;
   return L;
 }
@@ -163,16 +162,13 @@ extern "C" lms_status lms_aggregate_batch_static(const lms_query_spec* q, int32_
   s.cap = kStaticGroups;
   s.hist = reinterpret_cast<unsigned*>(base + kL.hist);
   s.chunk = reinterpret_cast<unsigned long long*>(base + kL.chunk);
-  s.pane_id = reinterpret_cast<unsigned*>(base + kL.pane_id);
-  s.pane_begin = reinterpret_cast<unsigned long long*>(base + kL.pane_begin);
-  s.pane_cap = kStaticGroups;
-  s.win_w = reinterpret_cast<long long*>(base + kL.win_w);
-  s.win_j0 = reinterpret_cast<unsigned*>(base + kL.win_j0);
-  s.win_j1 = reinterpret_cast<unsigned*>(base + kL.win_j1);
-  s.win_stat = reinterpret_cast<unsigned long long*>(base + kL.win_stat);
-  s.win_cap = kStaticWindows;
-  s.pool = reinterpret_cast<unsigned long long*>(base + kL.pool);
-  s.pool_cap = kStaticPool;
+  s.blk_id = reinterpret_cast<unsigned*>(base + kL.blk_id);
+  s.blk_begin = reinterpret_cast<unsigned long long*>(base + kL.blk_begin);
+  s.blk_cap = kStaticGroups;
+  s.item_c = reinterpret_cast<unsigned long long*>(base + kL.item_c);
+  s.item_j = reinterpret_cast<unsigned*>(base + kL.item_j);
+  s.item_stat = reinterpret_cast<unsigned long long*>(base + kL.item_stat);
+  s.item_cap = kStaticItems;
 
   // ---- the query, with the batch's first row as event-time origin ----
   d.filter_col = q->filter_col;
@@ -184,11 +180,18 @@ extern "C" lms_status lms_aggregate_batch_static(const lms_query_spec* q, int32_
   udiv_constants(d.slide, &d.magic, &d.sh1, &d.sh2);
   d.size = size;
   d.k = (int)(size / slide);
+  set_block_shape(&d);
+  d.lookback_ns = 4000000000ull;
+  d.debug_flags = 0u;
   d.agg_mask = q->agg_mask ? q->agg_mask : LMS_AGG_ALL;
   d.qid = 0;
   d.value_is_float = value_type == LMS_VALUE_FLOAT32;
+  // the origin is read on the caller's stream, after whatever work of the
+  // caller's on that stream produced the columns
   long long origin = 0;
-  if (n_rows > 0 && cudaMemcpy(&origin, ts, sizeof(origin), cudaMemcpyDeviceToHost) != cudaSuccess)
+  if (n_rows > 0 &&
+      (cudaMemcpyAsync(&origin, ts, sizeof(origin), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+       cudaStreamSynchronize(st) != cudaSuccess))
     return LMS_ECUDA;
   d.origin_pane = floor_div_s(origin, slide);
   d.base = d.origin_pane * slide;
@@ -219,16 +222,16 @@ extern "C" lms_status lms_aggregate_batch_static(const lms_query_spec* q, int32_
   }
   if (launch_watermark(sctl, &d, 1, 0, 1, st) != cudaSuccess) return LMS_ECUDA;
   if (launch_sort_reduce(d, s, st, nullptr) != cudaSuccess) return LMS_ECUDA;
-  if (launch_pane_index(d, s, st, nullptr) != cudaSuccess) return LMS_ECUDA;
+  if (launch_block_index(d, s, st, nullptr) != cudaSuccess) return LMS_ECUDA;
   if (launch_emit(d, s, reinterpret_cast<ResultRowDev*>(rows), rows_cap, sms, st, nullptr,
                   nullptr) != cudaSuccess)
     return LMS_ECUDA;
   QCtl h{};
-  if (cudaStreamSynchronize(st) != cudaSuccess ||
-      cudaMemcpy(&h, d.ctl, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess)
+  if (cudaMemcpyAsync(&h, d.ctl, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
     return LMS_ECUDA;
   if (h.err & (kErrPartsOverflow | kErrProbe | kErrLookback)) return LMS_EDEVICE;
-  if (h.err & kErrNeedRetry) return LMS_ENOMEM;  // windows, merge scratch or rows_cap too small
+  if (h.err & kErrNeedRetry) return LMS_ENOMEM;  // item list or rows_cap too small
   *n_out = (size_t)h.rows_batch;
   return LMS_OK;
 }

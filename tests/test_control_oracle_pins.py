@@ -67,6 +67,37 @@ def test_eq9_recovers_exact_coefficients_and_matches_lstsq():
     np.testing.assert_allclose(beta, ref, rtol=1e-6)
 
 
+@pytest.mark.parametrize("case", [
+    # n = 2 (fewer than the three samples the three coefficients need)
+    dict(t=[1.0e5, 2.0e5], l=[30.0, 50.0], y=[100.0, 200.0], mean=150.0),
+    # constant throughput column: its coefficient is not identifiable
+    dict(t=[5.0e4] * 4, l=[10.0, 20.0, 30.0, 40.0], y=[10.0, 20.0, 30.0, 45.0], mean=26.25),
+    # constant latency column
+    dict(t=[1.0, 2.0, 3.0, 4.0, 5.0], l=[7.0] * 5, y=[3.0, 1.0, 4.0, 1.0, 5.0], mean=2.8),
+    # exactly collinear inputs: latency = 2 * throughput + 1
+    dict(t=[1.0, 2.0, 3.0, 4.0], l=[3.0, 5.0, 7.0, 9.0], y=[8.0, 6.0, 7.0, 5.0], mean=6.5),
+])
+def test_eq9_degenerate_inputs_fall_back_to_the_mean(case):
+    # Eq. 9 (Section III-E) needs three identifiable coefficients; with fewer
+    # than three samples, a constant input or collinear inputs the system is
+    # singular, and the reading used here answers with the intercept-only
+    # least-squares fit: b = (mean InfPT, 0, 0), whatever the targets.
+    for target in [(0.0, 0.0), (3.0e5, 100.0)]:
+        beta, pred = oc.regress_infpt(case["t"], case["l"], case["y"], *target)
+        np.testing.assert_array_equal(beta, [case["mean"], 0.0, 0.0])
+        assert pred == case["mean"]
+    # the intercept-only fit is what least squares gives on a column of ones
+    ones = np.ones((len(case["y"]), 1))
+    ref = np.linalg.lstsq(ones, np.asarray(case["y"]), rcond=None)[0][0]
+    assert ref == pytest.approx(case["mean"], rel=1e-15)
+
+
+def test_eq9_without_history_uses_the_initial_inflection_point():
+    beta, pred = oc.regress_infpt([], [], [], 1e5, 100.0)
+    np.testing.assert_array_equal(beta, [oc.INFPT0_BYTES, 0.0, 0.0])
+    assert pred == oc.INFPT0_BYTES == 150 * 1024
+
+
 def test_eqs_3_4_5_closed_forms():
     assert oc.avg_thput([1000, 3000], [100, 100]) == 20.0
     assert oc.max_lat([5, 30, 12], 7) == 37

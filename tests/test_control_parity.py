@@ -94,3 +94,19 @@ def test_eq9_matches_oracle():
     st, beta, pred = reg.fit(5.0, 7.0)
     rb, rp = oc.regress_infpt([5.0] * 10, [7.0] * 10, [1000.0 + k for k in range(10)], 5.0, 7.0)
     np.testing.assert_allclose(beta, rb)
+
+
+@pytest.mark.parametrize("t,l,y", [
+    ([1.0e5, 2.0e5], [30.0, 50.0], [100.0, 200.0]),                        # n = 2
+    ([5.0e4] * 4, [10.0, 20.0, 30.0, 40.0], [10.0, 20.0, 30.0, 45.0]),      # constant column
+    ([1.0, 2.0, 3.0, 4.0], [3.0, 5.0, 7.0, 9.0], [8.0, 6.0, 7.0, 5.0]),      # collinear
+])
+def test_eq9_degenerate_branch_matches_oracle(t, l, y):
+    reg = lm.Regressor(0)
+    for a, b, c in zip(t, l, y):
+        reg.add(a, b, c)
+    st, beta, pred = reg.fit(3.0e5, 100.0)
+    rb, rp = oc.regress_infpt(t, l, y, 3.0e5, 100.0)
+    assert st == (0 if len(y) >= 3 else -3)
+    np.testing.assert_array_equal(beta, rb)
+    assert pred == rp

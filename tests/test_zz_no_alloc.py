@@ -11,7 +11,7 @@ import pytest
 
 from paper_2111_04289_b300 import lmstream as lm
 from paper_2111_04289_b300 import synth
-from tests.engine_helpers import FLOAT_REL_TOL
+from tests.engine_helpers import FLOAT_REL_TOL, assert_rows_match, run_oracle
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -42,15 +42,34 @@ def _via_stream(b, spec):
     return rows
 
 
-def _via_static(b, spec):
+def _via_static(b, spec, side_stream=None):
     k = spec["size_ms"] // (spec["slide_ms"] or spec["size_ms"])
     cap = len(b) * k
-    out = torch.zeros(cap * 48, dtype=torch.uint8, device="cuda")
-    cols = [None if c is None else torch.from_numpy(np.ascontiguousarray(c)).cuda()
-            for c in (b.ts, b.key, b.value, b.type)]
-    n = lm.aggregate_batch_static(*cols, **spec, rows_ptr=out.data_ptr(), rows_cap=cap)
+    if side_stream is None:
+        out = torch.zeros(cap * 48, dtype=torch.uint8, device="cuda")
+        cols = [None if c is None else torch.from_numpy(np.ascontiguousarray(c)).cuda()
+                for c in (b.ts, b.key, b.value, b.type)]
+        n = lm.aggregate_batch_static(*cols, **spec, rows_ptr=out.data_ptr(), rows_cap=cap)
+    else:
+        # the columns are produced on a non-blocking side stream just before
+        # the call, which is given that stream: the call must read them after
+        # the copies that produce them
+        with torch.cuda.stream(side_stream):
+            out = torch.zeros(cap * 48, dtype=torch.uint8, device="cuda")
+            host = [None if c is None else torch.from_numpy(np.ascontiguousarray(c)).pin_memory()
+                    for c in (b.ts, b.key, b.value, b.type)]
+            cols = [None if c is None else c.to("cuda", non_blocking=True) for c in host]
+            n = lm.aggregate_batch_static(*cols, **spec, rows_ptr=out.data_ptr(), rows_cap=cap,
+                                          cuda_stream=side_stream.cuda_stream)
+        side_stream.synchronize()
     dt = lm.ROW_DTYPE_FLOAT if spec["value_type"] == "float32" else lm.ROW_DTYPE_INT
     return out[: n * 48].cpu().numpy().view(dt)
+
+
+def _oracle_rows(b, spec):
+    q = dict(size=spec["size_ms"], slide=spec["slide_ms"], col=spec["filter_col"],
+             op=spec["filter_op"], value=spec["filter_value"])
+    return run_oracle([b], [q], spec["value_type"] == "float32")[0][0]
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -59,6 +78,7 @@ def test_static_scratch_entry_point_matches_stream_api(name):
     for b in _batches(name):  # two calls in a row
         ref = _via_stream(b, spec)
         got = _via_static(b, spec)
+        assert_rows_match(got, _oracle_rows(b, spec), spec["value_type"] == "float32")
         assert len(got) == len(ref) > 0
         for f in ("window_start", "key", "count", "query_id"):
             np.testing.assert_array_equal(got[f], ref[f], err_msg=f)
@@ -70,6 +90,15 @@ def test_static_scratch_entry_point_matches_stream_api(name):
         else:
             for f in ("sum", "min", "max", "avg"):
                 np.testing.assert_array_equal(got[f], ref[f], err_msg=f)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_static_scratch_entry_point_on_a_non_blocking_stream(name):
+    spec = CASES[name]
+    side = torch.cuda.Stream()
+    for b in _batches(name):  # two calls in a row
+        got = _via_static(b, spec, side_stream=side)
+        assert_rows_match(got, _oracle_rows(b, spec), spec["value_type"] == "float32")
 
 
 def test_static_scratch_rejects_oversized_batch():
