@@ -291,27 +291,64 @@ constexpr int kEmT = 256;              // threads per CTA
 constexpr int kEmE = 4;                // merged entries per thread and chunk
 constexpr int kEmC = kEmT * kEmE;      // merged entries per chunk
 constexpr int kEmWarps = kEmT / 32;
+constexpr int kEmRows = 4096;          // row descriptors per round
 
+// Per-CTA state of the emission kernel (static shared memory); the staged
+// chunk and the round's row descriptors live in dynamic shared memory (EmDyn).
 struct EmSmem {
-  unsigned long long ga[kEmC];         // the chunk's gkeys from run A (block b)
-  unsigned long long gb[kEmC];         // ... and from run B (block b + 1)
-  unsigned hk[kEmC + 1];               // distinct keys starting in the chunk (heads)
-  unsigned hia[kEmC + 1];              // their first A / B entries (relative to the runs)
-  unsigned hib[kEmC + 1];
   unsigned long long split[kEmT + 1];  // merge-path A counts at chunk starts
-  long long cnt[kMaxItemWindows + 2];  // difference array, then rows per window
+  long long cnt[kMaxItemWindows + 2];  // rows per window
+  int wdiff[kEmWarps][kMaxItemWindows + 2];      // per-warp difference arrays of the count
   unsigned long long woff[kMaxItemWindows + 1];  // rows of the item before window i
-  unsigned wc[kEmWarps][kMaxItemWindows];        // per-warp rows of a round, then their offsets
-  unsigned long long run[kMaxItemWindows];       // rows of window i written by earlier rounds
-  unsigned tkey[kEmT];                 // each thread's last merged entry of the chunk
-  unsigned long long tpane[kEmT];
+  unsigned long long base[kMaxItemWindows];      // output row of descriptor 0 of window i
+  unsigned run[kMaxItemWindows];       // rows of window i written by earlier rounds
+  unsigned rb[kMaxItemWindows + 1];    // first descriptor of window i in the round
+  unsigned wc[kEmWarps][kMaxItemWindows];        // per-warp rows, then the warps' offsets
+  unsigned ball[kEmWarps][kMaxItemWindows];      // per-warp ballots of window i
   unsigned long long tmp[33];
-  unsigned carry_key;                  // the previous chunk's last entry
-  unsigned long long carry_pane;
+  unsigned long long carry_g;          // the previous chunk's last merged gkey
+  unsigned long long next_carry;
+  unsigned long long open_ia, open_ib; // global runs of the chunk's last key, if it continues
+  unsigned open_na;
+  unsigned open_kh;                    // round index of the key read from global memory, or ~0
   int carry_valid;
-  unsigned nh;
+  unsigned open_last;                  // the chunk's last key continues past the chunk
   unsigned long long ri, off, total;
 };
+
+// A chunk staged in shared memory as columns of its records (the A part, then
+// the B part), the merged order (record slot of each merged position), the
+// merged positions of the keys' first entries (heads), and the round's row
+// descriptors in output order: (key of the round << 6 | window), the first of
+// the key's groups in the window (a merged position, or for the key read from
+// global memory an index into its groups) and their number.
+struct EmDyn {
+  unsigned long long* gk;    // [kEmC] gkeys
+  long long* cnt;            // [kEmC]
+  unsigned long long* sum;   // [kEmC]
+  unsigned long long* mm;    // [kEmC] mn | mx << 32
+  unsigned short* mo;        // [kEmC]
+  unsigned short* hp;        // [kEmC + 1]
+  unsigned short* rows;      // [kEmRows]
+  unsigned* rln;             // [kEmRows] first group | number of groups << 16
+};
+constexpr size_t kEmDynBytes = (size_t)kEmC * (4 * 8 + 2) + (kEmC + 1) * 2 + 6 +
+                               (size_t)kEmRows * (4 + 2);
+
+__device__ __forceinline__ EmDyn em_dyn() {
+  extern __shared__ __align__(16) unsigned char em_smem[];
+  EmDyn d;
+  unsigned char* p = em_smem;
+  d.gk = reinterpret_cast<unsigned long long*>(p); p += (size_t)kEmC * 8;
+  d.cnt = reinterpret_cast<long long*>(p); p += (size_t)kEmC * 8;
+  d.sum = reinterpret_cast<unsigned long long*>(p); p += (size_t)kEmC * 8;
+  d.mm = reinterpret_cast<unsigned long long*>(p); p += (size_t)kEmC * 8;
+  d.mo = reinterpret_cast<unsigned short*>(p); p += (size_t)kEmC * 2;
+  d.hp = reinterpret_cast<unsigned short*>(p); p += (size_t)(kEmC + 1) * 2 + 6;
+  d.rln = reinterpret_cast<unsigned*>(p); p += (size_t)kEmRows * 4;
+  d.rows = reinterpret_cast<unsigned short*>(p);
+  return d;
+}
 
 struct Item {
   const Grp* A;               // run A: block b, key-major (may be empty)
@@ -352,8 +389,9 @@ __device__ __forceinline__ Item load_item(const QueryDev& q, const Scratch& s, c
   return it;
 }
 
-// Merge order of the two runs: by key; on equal keys run A first.  Number of
-// A entries among the first d merged entries (merge path, global memory).
+// Merge order of the two runs: by key; on equal keys run A first (its panes
+// are the earlier ones).  Number of A entries among the first d merged
+// entries (merge path, global memory).
 __device__ unsigned long long merge_split_g(const Item& it, unsigned long long d, int lb) {
   unsigned long long lo = d > it.nb ? d - it.nb : 0ull, hi = d < it.na ? d : it.na;
   while (lo < hi) {
@@ -364,14 +402,13 @@ __device__ unsigned long long merge_split_g(const Item& it, unsigned long long d
   return lo;
 }
 
-// The same within a chunk staged in shared memory.
-__device__ __forceinline__ unsigned merge_split_s(const unsigned long long* ga, unsigned la,
-                                                  const unsigned long long* gb, unsigned lbn,
-                                                  unsigned d, int lb) {
+// The same within a staged chunk: A part gk[0 .. la), B part gk[la .. la + lbn).
+__device__ __forceinline__ unsigned merge_split_s(const unsigned long long* gk, unsigned la,
+                                                  unsigned lbn, unsigned d, int lb) {
   unsigned lo = d > lbn ? d - lbn : 0u, hi = d < la ? d : la;
   while (lo < hi) {
     const unsigned mid = (lo + hi) >> 1;
-    if (gkey_key(ga[mid], lb) <= gkey_key(gb[d - 1 - mid], lb)) lo = mid + 1;
+    if (gkey_key(gk[mid], lb) <= gkey_key(gk[la + d - 1 - mid], lb)) lo = mid + 1;
     else hi = mid;
   }
   return lo;
@@ -389,21 +426,15 @@ __device__ __forceinline__ unsigned long long pane_windows(long long p, int k, l
   return m << (int)(lo - wlo);
 }
 
-// One merged chunk of an item: thread t receives entries t*E .. t*E + E - 1
-// of the chunk (key, pane, and the positions in A and B before the entry).
-struct Merged {
-  unsigned key[kEmE];
-  unsigned long long pane[kEmE];
-  unsigned ia[kEmE], ib[kEmE];
-  int n;
-};
-
-// Walks chunk by chunk over the merged runs of the item, calling
-// f(chunk_len, merged) with every thread's entries after a barrier that made
-// each thread's last entry visible in sm.tkey / sm.tpane; sm.carry_* holds the
-// previous chunk's last entry.  f must end with a barrier.
+// Walks chunk by chunk over the merged runs of the item.  Each chunk is
+// staged (records loaded with 16-byte vector loads; only the gkeys when
+// full == false) and merged into d.mo; then f(len, la, a0, b0, last) runs
+// with the chunk in shared memory (after a barrier) and must end with a
+// barrier.  sm.carry_g holds the previous chunk's last merged gkey (if
+// sm.carry_valid).
 template <class F>
-__device__ void for_merged_chunks(const QueryDev& q, const Item& it, EmSmem& sm, F f) {
+__device__ void for_merged_chunks(const QueryDev& q, const Item& it, EmSmem& sm, const EmDyn& d,
+                                  bool full, F f) {
   const int tid = threadIdx.x;
   const int lb = q.lb;
   const unsigned long long L = it.na + it.nb;
@@ -413,46 +444,55 @@ __device__ void for_merged_chunks(const QueryDev& q, const Item& it, EmSmem& sm,
     const unsigned long long kn = nch - k0 < (unsigned long long)kEmT ? nch - k0 : kEmT;
     __syncthreads();  // the previous batch of chunks no longer reads sm.split
     for (unsigned long long t = tid; t <= kn; t += kEmT) {
-      const unsigned long long d = (k0 + t) * kEmC;
-      sm.split[t] = merge_split_g(it, d < L ? d : L, lb);
+      const unsigned long long dd = (k0 + t) * kEmC;
+      sm.split[t] = merge_split_g(it, dd < L ? dd : L, lb);
     }
     __syncthreads();
     for (unsigned long long kk = 0; kk < kn; ++kk) {
       const unsigned long long d0 = (k0 + kk) * kEmC;
       const unsigned long long d1 = d0 + kEmC < L ? d0 + kEmC : L;
       const unsigned long long a0 = sm.split[kk], a1 = sm.split[kk + 1];
-      const unsigned long long b0 = d0 - a0, b1 = d1 - a1;
-      const unsigned la = (unsigned)(a1 - a0), lbn = (unsigned)(b1 - b0);
-      for (unsigned i = tid; i < la; i += kEmT) sm.ga[i] = it.A[a0 + i].gkey;
-      for (unsigned i = tid; i < lbn; i += kEmT) sm.gb[i] = it.Bv[b0 + i].gkey;
-      __syncthreads();
-      Merged m;
-      m.n = 0;
-      const unsigned len = la + lbn, d = (unsigned)tid * kEmE;
-      if (d < len) {
-        unsigned i = merge_split_s(sm.ga, la, sm.gb, lbn, d, lb), j = d - i;
-#pragma unroll
-        for (int e = 0; e < kEmE; ++e) {
-          if (d + e < len) {
-            const bool ta = j >= lbn || (i < la && gkey_key(sm.ga[i], lb) <= gkey_key(sm.gb[j], lb));
-            const unsigned long long g = ta ? sm.ga[i] : sm.gb[j];
-            m.key[e] = gkey_key(g, lb);
-            m.pane[e] = gkey_pane(g, lb);
-            m.ia[e] = (unsigned)(a0 + i);
-            m.ib[e] = (unsigned)(b0 + j);
-            if (ta) ++i; else ++j;
-            m.n = e + 1;
+      const unsigned long long b0 = d0 - a0;
+      const unsigned la = (unsigned)(a1 - a0), len = (unsigned)(d1 - d0);
+      if (full) {  // two 16-byte halves per record
+        for (unsigned h = tid; h < 2 * len; h += kEmT) {
+          const unsigned r = h >> 1;
+          const Grp* src = r < la ? it.A + a0 + r : it.Bv + b0 + (r - la);
+          const uint4 v = reinterpret_cast<const uint4*>(src)[h & 1];
+          const unsigned long long lo = ((unsigned long long)v.y << 32) | v.x;
+          const unsigned long long hi = ((unsigned long long)v.w << 32) | v.z;
+          if (h & 1) {
+            d.sum[r] = lo;
+            d.mm[r] = hi;
+          } else {
+            d.gk[r] = lo;
+            d.cnt[r] = (long long)hi;
           }
         }
-        sm.tkey[tid] = m.key[m.n - 1];
-        sm.tpane[tid] = m.pane[m.n - 1];
+      } else {
+        for (unsigned r = tid; r < len; r += kEmT)
+          d.gk[r] = r < la ? it.A[a0 + r].gkey : it.Bv[b0 + (r - la)].gkey;
       }
       __syncthreads();
-      f(len, m);
+      const unsigned x0 = (unsigned)tid * kEmE;
+      if (x0 < len) {
+        unsigned i = merge_split_s(d.gk, la, len - la, x0, lb), j = x0 - i;
+        const unsigned lbn = len - la;
+#pragma unroll
+        for (int e = 0; e < kEmE; ++e) {
+          if (x0 + e < len) {
+            const bool ta = j >= lbn || (i < la && gkey_key(d.gk[i], lb) <= gkey_key(d.gk[la + j], lb));
+            d.mo[x0 + e] = (unsigned short)(ta ? i : la + j);
+            if (ta) ++i; else ++j;
+          }
+        }
+      }
+      __syncthreads();
+      if (tid == 0) sm.next_carry = d.gk[d.mo[len - 1]];
+      f(len, la, a0, b0, d1 == L);
       // f ended with a barrier: the chunk's last entry becomes the carry
-      if (len > 0 && (unsigned)tid == (len - 1) / kEmE) {
-        sm.carry_key = m.key[m.n - 1];
-        sm.carry_pane = m.pane[m.n - 1];
+      if (tid == 0) {
+        sm.carry_g = sm.next_carry;
         sm.carry_valid = 1;
       }
     }
@@ -460,48 +500,51 @@ __device__ void for_merged_chunks(const QueryDev& q, const Item& it, EmSmem& sm,
   __syncthreads();
 }
 
-// The entry before merged entry e of this thread (key, pane), if any.
-__device__ __forceinline__ bool prev_entry(const EmSmem& sm, const Merged& m, int e, unsigned* key,
-                                           unsigned long long* pane) {
-  if (e > 0) {
-    *key = m.key[e - 1];
-    *pane = m.pane[e - 1];
+// gkey of the merged entry before position x of the staged chunk, if any.
+__device__ __forceinline__ bool prev_gkey(const EmSmem& sm, const EmDyn& d, unsigned x,
+                                          unsigned long long* g) {
+  if (x > 0) {
+    *g = d.gk[d.mo[x - 1]];
     return true;
   }
-  if (threadIdx.x > 0) {
-    *key = sm.tkey[threadIdx.x - 1];
-    *pane = sm.tpane[threadIdx.x - 1];
-    return true;
-  }
-  *key = sm.carry_key;
-  *pane = sm.carry_pane;
+  *g = sm.carry_g;
   return sm.carry_valid != 0;
 }
 
 // Rows of each window of the item: a group is its key's first group in the
 // windows from max(previous pane of the key + 1, pane - K + 1) to its pane.
-__device__ void count_item(const QueryDev& q, const Item& it, EmSmem& sm) {
+__device__ void count_item(const QueryDev& q, const Item& it, EmSmem& sm, const EmDyn& d) {
   const int nw = (int)(it.whi - it.wlo + 1);
+  const int lb = q.lb;
   for (int i = threadIdx.x; i <= nw; i += kEmT) sm.cnt[i] = 0;
+  for (int i = threadIdx.x; i < kEmWarps * (kMaxItemWindows + 2); i += kEmT)
+    (&sm.wdiff[0][0])[i] = 0;
   if (q.k == 1) {  // tumbling: one window, one pane, unique keys
     __syncthreads();
     if (threadIdx.x == 0) sm.cnt[0] = (long long)it.na;
   } else {
-    for_merged_chunks(q, it, sm, [&](unsigned, const Merged& m) {
-      for (int e = 0; e < m.n; ++e) {
-        unsigned pk;
-        unsigned long long pp;
-        long long lo = (long long)m.pane[e] - q.k + 1;
-        if (prev_entry(sm, m, e, &pk, &pp) && pk == m.key[e]) {
-          const long long after = (long long)pp + 1;
+    for_merged_chunks(q, it, sm, d, false, [&](unsigned len, unsigned, unsigned long long,
+                                               unsigned long long, bool) {
+      const unsigned x0 = threadIdx.x * kEmE;
+#pragma unroll
+      for (int e = 0; e < kEmE; ++e) {
+        const unsigned x = x0 + e;
+        if (x >= len) break;
+        const unsigned long long g = d.gk[d.mo[x]];
+        const long long p = (long long)gkey_pane(g, lb);
+        long long lo = p - q.k + 1;
+        unsigned long long pg;
+        if (prev_gkey(sm, d, x, &pg) && gkey_key(pg, lb) == gkey_key(g, lb)) {
+          const long long after = (long long)gkey_pane(pg, lb) + 1;
           lo = lo > after ? lo : after;
         }
-        long long hi = (long long)m.pane[e];
+        long long hi = p;
         lo = lo > it.wlo ? lo : it.wlo;
         hi = hi < it.whi ? hi : it.whi;
         if (lo <= hi) {
-          atomicAdd(reinterpret_cast<unsigned long long*>(&sm.cnt[lo - it.wlo]), 1ull);
-          atomicAdd(reinterpret_cast<unsigned long long*>(&sm.cnt[hi - it.wlo + 1]), ~0ull);
+          int* wd = sm.wdiff[threadIdx.x >> 5];
+          atomicAdd(&wd[lo - it.wlo], 1);
+          atomicAdd(&wd[hi - it.wlo + 1], -1);
         }
       }
       __syncthreads();
@@ -509,7 +552,8 @@ __device__ void count_item(const QueryDev& q, const Item& it, EmSmem& sm) {
     if (threadIdx.x == 0) {
       long long acc = 0;
       for (int i = 0; i < nw; ++i) {
-        acc += sm.cnt[i];
+#pragma unroll
+        for (int ww = 0; ww < kEmWarps; ++ww) acc += sm.wdiff[ww][i];
         sm.cnt[i] = acc;
       }
     }
@@ -544,10 +588,22 @@ __device__ unsigned long long run_end(const Grp* g, unsigned long long from, uns
   return hi;
 }
 
+// gkey of group e (pane order) of a key whose first group is at merged
+// position x0: staged, or in global memory for the chunk's last key when it
+// continues past the chunk (A groups from open_ia, then B groups from open_ib).
+__device__ __forceinline__ unsigned long long key_gkey(const EmSmem& sm, const EmDyn& d,
+                                                       const Item& it, bool glob, unsigned x0,
+                                                       unsigned e) {
+  if (!glob) return d.gk[d.mo[x0 + e]];
+  return e < sm.open_na ? it.A[sm.open_ia + e].gkey : it.Bv[sm.open_ib + (e - sm.open_na)].gkey;
+}
 // Writes the item's rows from out[0]: rows of window i from out[woff[i]], in
-// key order.
+// key order.  Per chunk, rounds of up to kEmT keys (one per thread): each key's
+// windows as a bit mask, the warps' ballots per window, then row descriptors
+// laid out in output order, then one row per thread over the descriptors.
 template <bool FLOAT>
-__device__ void write_item(const QueryDev& q, const Item& it, EmSmem& sm, ResultRowDev* out) {
+__device__ void write_item(const QueryDev& q, const Item& it, EmSmem& sm, const EmDyn& d,
+                           ResultRowDev* out) {
   const int tid = threadIdx.x, w = tid >> 5;
   const unsigned lane = lane_id(), lt = (1u << lane) - 1u;
   const int lb = q.lb, K = q.k;
@@ -561,104 +617,187 @@ __device__ void write_item(const QueryDev& q, const Item& it, EmSmem& sm, Result
     __syncthreads();
     return;
   }
-  for (int i = tid; i < nw; i += kEmT) sm.run[i] = 0ull;
-  for_merged_chunks(q, it, sm, [&](unsigned len, const Merged& m) {
-    // heads: the entries that start a key
+  // keys per round: one per thread, and at most kEmRows rows
+  const unsigned kpr = kEmRows / nw < (unsigned)kEmT ? (unsigned)(kEmRows / nw) : (unsigned)kEmT;
+  for (int i = tid; i < nw; i += kEmT) sm.run[i] = 0u;
+  for_merged_chunks(q, it, sm, d, true, [&](unsigned len, unsigned la, unsigned long long a0,
+                                            unsigned long long b0, bool last_chunk) {
+    // heads: the merged positions that start a key
     unsigned nh_t = 0;
     bool head[kEmE];
+    const unsigned x0 = (unsigned)tid * kEmE;
 #pragma unroll
     for (int e = 0; e < kEmE; ++e) {
       head[e] = false;
-      if (e < m.n) {
-        unsigned pk;
-        unsigned long long pp;
-        head[e] = !(prev_entry(sm, m, e, &pk, &pp) && pk == m.key[e]);
+      const unsigned x = x0 + e;
+      if (x < len) {
+        unsigned long long pg;
+        head[e] = !(prev_gkey(sm, d, x, &pg) &&
+                    gkey_key(pg, lb) == gkey_key(d.gk[d.mo[x]], lb));
         nh_t += head[e] ? 1u : 0u;
       }
     }
     unsigned long long htot;
     unsigned long long hpos = block_excl_scan((unsigned long long)nh_t, sm.tmp, &htot);
 #pragma unroll
-    for (int e = 0; e < kEmE; ++e) {
-      if (head[e]) {
-        sm.hk[hpos] = m.key[e];
-        sm.hia[hpos] = m.ia[e];
-        sm.hib[hpos] = m.ib[e];
-        ++hpos;
-      }
-    }
-    (void)len;
-    __syncthreads();
+    for (int e = 0; e < kEmE; ++e)
+      if (head[e]) d.hp[hpos++] = (unsigned short)(x0 + e);
     const unsigned nh = (unsigned)htot;
-    if (tid == 0 && nh > 0) {  // the last key may continue past the chunk
-      const unsigned k = sm.hk[nh - 1];
-      sm.hia[nh] = (unsigned)run_end(it.A, sm.hia[nh - 1], it.na, k, lb);
-      sm.hib[nh] = (unsigned)run_end(it.Bv, sm.hib[nh - 1], it.nb, k, lb);
+    if (tid == 0) {
+      d.hp[nh] = (unsigned short)len;
+      // does the chunk's last key continue in the next chunk?  Then its
+      // groups are read from global memory: A from open_ia, then B from open_ib.
+      unsigned open_n = 0u;
+      if (!last_chunk && nh > 0) {
+        const unsigned long long a1 = a0 + la, b1 = b0 + (len - la);
+        const unsigned k = gkey_key(d.gk[d.mo[len - 1]], lb);
+        if ((a1 < it.na && gkey_key(it.A[a1].gkey, lb) == k) ||
+            (b1 < it.nb && gkey_key(it.Bv[b1].gkey, lb) == k)) {
+          const unsigned hx = d.hp[nh - 1], slot = d.mo[hx];
+          unsigned long long ia, ib;
+          if (slot < la) {  // its first group is from A: hx - slot B groups precede it
+            ia = a0 + slot;
+            ib = b0 + (hx - slot);
+          } else {
+            ib = b0 + (slot - la);
+            ia = a0 + (hx - (slot - la));
+          }
+          sm.open_ia = ia;
+          sm.open_ib = ib;
+          sm.open_na = (unsigned)(run_end(it.A, ia, it.na, k, lb) - ia);
+          open_n = sm.open_na + (unsigned)(run_end(it.Bv, ib, it.nb, k, lb) - ib);
+        }
+      }
+      sm.open_last = open_n;
     }
     __syncthreads();
-    for (unsigned r0 = 0; r0 < nh; r0 += kEmT) {
+    for (unsigned r0 = 0; r0 < nh; r0 += kpr) {
+      // phase 1: this thread's key of the round and the item windows holding it
       const unsigned h = r0 + (unsigned)tid;
-      const bool valid = h < nh;
-      unsigned key = 0u, ia = 0u, na_k = 0u, ib = 0u, nb_k = 0u;
+      const bool valid = (unsigned)tid < kpr && h < nh;
+      const bool glob = valid && h + 1 == nh && sm.open_last != 0u;
+      unsigned n = 0u, hx = 0u;
       unsigned long long mask = 0ull;
+      long long pc0 = 0, pc1 = 0, pc2 = 0, pc3 = 0;  // the first four panes of the key
       if (valid) {
-        key = sm.hk[h];
-        ia = sm.hia[h];
-        ib = sm.hib[h];
-        na_k = sm.hia[h + 1] - ia;
-        nb_k = sm.hib[h + 1] - ib;
-        for (unsigned e = 0; e < na_k; ++e)
-          mask |= pane_windows((long long)gkey_pane(it.A[ia + e].gkey, lb), K, it.wlo, it.whi);
-        for (unsigned e = 0; e < nb_k; ++e)
-          mask |= pane_windows((long long)gkey_pane(it.Bv[ib + e].gkey, lb), K, it.wlo, it.whi);
+        hx = d.hp[h];
+        n = glob ? sm.open_last : d.hp[h + 1] - hx;
+        for (unsigned e = 0; e < n; ++e) {
+          const long long p = (long long)gkey_pane(key_gkey(sm, d, it, glob, hx, e), lb);
+          pc0 = e == 0 ? p : pc0;
+          pc1 = e == 1 ? p : pc1;
+          pc2 = e == 2 ? p : pc2;
+          pc3 = e == 3 ? p : pc3;
+          mask |= pane_windows(p, K, it.wlo, it.whi);
+        }
       }
-      // rows of this warp per window, then their offsets over the warps
-      sm.wc[w][lane] = 0u;
-      sm.wc[w][lane + 32] = 0u;
+      if (tid == 0) sm.open_kh = sm.open_last != 0u && nh - 1 - r0 < kpr ? nh - 1 - r0 : ~0u;
       const unsigned long long orm =
           ((unsigned long long)__reduce_or_sync(kFull, (unsigned)(mask >> 32)) << 32) |
           __reduce_or_sync(kFull, (unsigned)mask);
+      for (int i = lane; i < nw; i += 32) sm.wc[w][i] = 0u;
       __syncwarp();
       for (unsigned long long bits = orm; bits; bits &= bits - 1) {
         const int i = __ffsll((long long)bits) - 1;
         const unsigned bal = __ballot_sync(kFull, (mask >> i) & 1ull);
-        if (lane == 0) sm.wc[w][i] = (unsigned)__popc(bal);
-      }
-      __syncthreads();
-      for (int i = tid; i < nw; i += kEmT) {  // warp offsets inside window i
-        unsigned acc = (unsigned)sm.run[i];
-#pragma unroll
-        for (int ww = 0; ww < kEmWarps; ++ww) {
-          const unsigned t = sm.wc[ww][i];
-          sm.wc[ww][i] = acc;
-          acc += t;
+        if (lane == 0) {
+          sm.ball[w][i] = bal;
+          sm.wc[w][i] = (unsigned)__popc(bal);
         }
-        sm.run[i] = acc;
       }
       __syncthreads();
-      // the rows: per window of the key, combine its groups in the window
-      const unsigned n_k = na_k + nb_k;
-      unsigned lo = 0u, hi = 0u;
-      for (unsigned long long bits = orm; bits; bits &= bits - 1) {
-        const int i = __ffsll((long long)bits) - 1;
-        const bool mine = (mask >> i) & 1ull;
-        const unsigned bal = __ballot_sync(kFull, mine);
-        if (!mine) continue;
-        const long long W = it.wlo + i;
-        auto entry = [&](unsigned e) -> const Grp* {
-          return e < na_k ? it.A + ia + e : it.Bv + ib + (e - na_k);
+      // offsets: warps inside each window, windows inside the round
+      if (tid < 32) {
+        unsigned tot_i[2] = {0u, 0u};
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int i = tid + 32 * u;
+          if (i < nw) {
+            unsigned acc = 0;
+#pragma unroll
+            for (int ww = 0; ww < kEmWarps; ++ww) {
+              const unsigned t = sm.wc[ww][i];
+              sm.wc[ww][i] = acc;
+              acc += t;
+            }
+            tot_i[u] = acc;
+          }
+        }
+        // exclusive scan of the per-window totals (windows tid and tid + 32)
+        unsigned inc0 = tot_i[0], inc1 = tot_i[1];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const unsigned y0 = __shfl_up_sync(kFull, inc0, o), y1 = __shfl_up_sync(kFull, inc1, o);
+          if ((int)tid >= o) {
+            inc0 += y0;
+            inc1 += y1;
+          }
+        }
+        const unsigned tot0 = __shfl_sync(kFull, inc0, 31);
+        const unsigned e0 = inc0 - tot_i[0], e1 = tot0 + inc1 - tot_i[1];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int i = tid + 32 * u;
+          if (i < nw) {
+            const unsigned rb = u == 0 ? e0 : e1;
+            sm.rb[i] = rb;
+#pragma unroll
+            for (int ww = 0; ww < kEmWarps; ++ww) sm.wc[ww][i] += rb;
+            sm.base[i] = sm.woff[i] + sm.run[i] - rb;
+            sm.run[i] += tot_i[u];
+          }
+        }
+        const unsigned tot1 = __shfl_sync(kFull, inc1, 31);
+        if (tid == 0) sm.rb[nw] = tot0 + tot1;
+      }
+      __syncthreads();
+      // phase 2: each thread lays out its key's rows in output order: the
+      // window, and the first of its groups in the window and their number
+      {
+        unsigned lo = 0u, hi = 0u;
+        auto pane_at = [&](unsigned e) -> long long {
+          if (e < 4) return e == 0 ? pc0 : e == 1 ? pc1 : e == 2 ? pc2 : pc3;
+          return (long long)gkey_pane(key_gkey(sm, d, it, glob, hx, e), lb);
         };
-        while (lo < n_k && (long long)gkey_pane(entry(lo)->gkey, lb) < W) ++lo;
-        if (hi < lo) hi = lo;
-        while (hi < n_k && (long long)gkey_pane(entry(hi)->gkey, lb) <= W + K - 1) ++hi;
-        if (lo >= hi) continue;  // cannot happen: the mask says a group lies in the window
-        const Grp g0 = load_grp_v(entry(lo));
+        for (unsigned long long bits = mask; bits; bits &= bits - 1) {
+          const int i = __ffsll((long long)bits) - 1;
+          const long long W = it.wlo + i;
+          while (lo < n && pane_at(lo) < W) ++lo;
+          if (hi < lo) hi = lo;
+          while (hi < n && pane_at(hi) <= W + K - 1) ++hi;
+          const unsigned pos = sm.wc[w][i] + (unsigned)__popc(sm.ball[w][i] & lt);
+          d.rows[pos] = (unsigned short)((tid << 6) | i);
+          d.rln[pos] = (glob ? lo : hx + lo) | ((hi - lo) << 16);
+        }
+      }
+      __syncthreads();
+      // phase 3: one row per thread, two rows' inputs loaded before either is
+      // combined and written
+      const unsigned R = sm.rb[nw];
+      const unsigned okh = sm.open_kh;
+      auto group_at = [&](bool glob_key, unsigned x) -> Grp {
+        if (glob_key)
+          return load_grp_v(x < sm.open_na ? it.A + sm.open_ia + x
+                                           : it.Bv + sm.open_ib + (x - sm.open_na));
+        const unsigned slot = d.mo[x];
+        Grp g;
+        g.gkey = d.gk[slot];
+        g.cnt = d.cnt[slot];
+        g.sum = d.sum[slot];
+        const unsigned long long m = d.mm[slot];
+        g.mn = (unsigned)m;
+        g.mx = (unsigned)(m >> 32);
+        return g;
+      };
+      auto finish = [&](unsigned r, unsigned desc, unsigned x, unsigned nn, const Grp& g0) {
+        const unsigned kh = desc >> 6, i = desc & 63u;
+        const bool kg = kh == okh;
         long long cnt = g0.cnt;
         unsigned long long isum = g0.sum;
         double fsum = __longlong_as_double((long long)g0.sum);
         unsigned mn = g0.mn, mx = g0.mx;
-        for (unsigned e = lo + 1; e < hi; ++e) {
-          const Grp g = load_grp_v(entry(e));
+        for (unsigned e = 1; e < nn; ++e) {
+          const Grp g = group_at(kg, x + e);
           cnt += g.cnt;
           mn = min(mn, g.mn);
           mx = max(mx, g.mx);
@@ -666,10 +805,20 @@ __device__ void write_item(const QueryDev& q, const Item& it, EmSmem& sm, Result
           else isum += g.sum;
         }
         const unsigned long long sb = FLOAT ? (unsigned long long)__double_as_longlong(fsum) : isum;
-        const unsigned long long pos =
-            sm.woff[i] + sm.wc[w][i] + (unsigned)__popc(bal & lt);
-        const long long wstart = (W - kPaneBias) * (long long)q.slide + q.base;
-        write_row<FLOAT>(q, out + pos, wstart, key, cnt, sb, mn, mx);
+        const long long wstart = (it.wlo + (long long)i - kPaneBias) * (long long)q.slide + q.base;
+        write_row<FLOAT>(q, out + sm.base[i] + r, wstart, gkey_key(g0.gkey, lb), cnt, sb, mn, mx);
+      };
+      for (unsigned r = tid; r < R; r += 2 * kEmT) {
+        const unsigned r2 = r + kEmT;
+        const bool two = r2 < R;
+        const unsigned desc1 = d.rows[r], ln1 = d.rln[r];
+        const unsigned desc2 = two ? d.rows[r2] : desc1, ln2 = two ? d.rln[r2] : ln1;
+        const unsigned x1 = ln1 & 0xffffu, n1 = ln1 >> 16, x2 = ln2 & 0xffffu, n2 = ln2 >> 16;
+        if (n1 == 0u || (two && n2 == 0u)) continue;  // cannot happen: a row has >= 1 group
+        const Grp g1 = group_at((desc1 >> 6) == okh, x1);
+        const Grp g2 = group_at((desc2 >> 6) == okh, x2);
+        finish(r, desc1, x1, n1, g1);
+        if (two) finish(r2, desc2, x2, n2, g2);
       }
       __syncthreads();
     }
@@ -683,6 +832,7 @@ template <bool FLOAT>
 __global__ void __launch_bounds__(kEmT, 3)
     k_emit(const QueryDev q, const Scratch s, ResultRowDev* rows, unsigned long long rows_cap) {
   __shared__ EmSmem sm;
+  const EmDyn d = em_dyn();
   QCtl* c = q.ctl;
   if (c->err & kErrNeedRetry) return;
   const unsigned long long NI = c->n_items;
@@ -695,7 +845,7 @@ __global__ void __launch_bounds__(kEmT, 3)
     if (ri >= NI) break;
     const Item it = load_item(q, s, c, ri);
     if (ri == 0 && (q.debug_flags & kDebugHoldFirstItem)) continue;  // never publishes
-    count_item(q, it, sm);
+    count_item(q, it, sm, d);
     if (threadIdx.x == 0) {
       const unsigned long long n = sm.total;
       const unsigned long long off = item_lookback(s.item_stat, ri, n, c, q.lookback_ns);
@@ -709,7 +859,7 @@ __global__ void __launch_bounds__(kEmT, 3)
     const unsigned long long off = sm.off;
     __syncthreads();
     if (off != ~0ull && row_base + off + sm.total <= rows_cap)
-      write_item<FLOAT>(q, it, sm, rows + row_base + off);
+      write_item<FLOAT>(q, it, sm, d, rows + row_base + off);
     __syncthreads();
   }
 }
@@ -879,9 +1029,14 @@ cudaError_t launch_emit(const QueryDev& q, const Scratch& s, ResultRowDev* rows,
     record_event(ev4[1], st);
     record_event(ev4[2], st);
   }
+  static unsigned long long done_f = 0, done_i = 0;  // devices whose limit is set
+  cudaError_t e = q.value_is_float
+                      ? set_smem_limit(reinterpret_cast<const void*>(k_emit<true>), (int)kEmDynBytes, &done_f)
+                      : set_smem_limit(reinterpret_cast<const void*>(k_emit<false>), (int)kEmDynBytes, &done_i);
+  if (e != cudaSuccess) return e;
   const int grid = 3 * sms;
-  if (q.value_is_float) k_emit<true><<<grid, kEmT, 0, st>>>(q, s, rows, rows_cap);
-  else k_emit<false><<<grid, kEmT, 0, st>>>(q, s, rows, rows_cap);
+  if (q.value_is_float) k_emit<true><<<grid, kEmT, kEmDynBytes, st>>>(q, s, rows, rows_cap);
+  else k_emit<false><<<grid, kEmT, kEmDynBytes, st>>>(q, s, rows, rows_cap);
   if (ev4) record_event(ev4[3], st);
   if (launches) *launches += 5;
   return cudaGetLastError();
