@@ -88,6 +88,10 @@ typedef int32_t lms_status;
 
 /* Batch flags. */
 #define LMS_BATCH_EOS 1u /* end of stream: emit every remaining window */
+#define LMS_INGEST_STABLE 2u /* lms_ingest: the host columns are pinned and stay unchanged until
+                                the lms_push_ingested that covers them returns, so the library
+                                copies them to the device directly instead of through its own
+                                pinned ring */
 
 /* origin_ts value that means "the first row of the first pushed batch". */
 #define LMS_ORIGIN_AUTO INT64_MIN
@@ -243,8 +247,9 @@ lms_status lms_results_device(lms_stream *s, int32_t query_id, const lms_result_
                               size_t *n);
 
 /* Grows the stream's buffers now so that a push of n_rows rows (from host
- * memory if host_input is 1) allocates nothing.  Queries must be registered.
- * LMS_ENOMEM if that exceeds state_cap_bytes or the device. */
+ * memory if host_input is 1; through the ingest ring if host_input is 2)
+ * allocates nothing.  Queries must be registered.  LMS_ENOMEM if that exceeds
+ * state_cap_bytes or the device. */
 lms_status lms_stream_reserve(lms_stream *s, int64_t n_rows, int32_t host_input);
 
 /* Device bytes a push of n_rows rows (from host memory if host_input is 1)
@@ -267,6 +272,29 @@ lms_status lms_stream_admissible_rows(lms_stream *s, int32_t host_input, int64_t
 
 /* Drops query_id's unpolled rows (e.g. after consuming them on the device). */
 lms_status lms_results_discard(lms_stream *s, int32_t query_id);
+
+/* ---- ingest ring: arriving data goes to the device while it is buffered ----
+ *
+ * The paper's micro-batches are built from datasets that arrive and wait in a
+ * buffer until ConstructMicroBatch (Alg. 1, Section III-C) admits them; the
+ * buffering phase takes 13-93 % of the time (Table IV).  lms_ingest takes one
+ * arriving dataset (host columns, b->memory = LMS_MEM_HOST): it copies the
+ * rows into a pinned host ring that the library owns (unless b->flags holds
+ * LMS_INGEST_STABLE) and enqueues their host-to-device copy into a device
+ * ring on a side stream, then returns; the caller may reuse its buffers at
+ * once (with LMS_INGEST_STABLE: once the covering lms_push_ingested returns).
+ * The copy runs while the data waits and while earlier micro-batches compute.
+ * lms_push_ingested then processes the oldest n_rows ingested rows as one
+ * micro-batch exactly as push_microbatch would (flags: LMS_BATCH_EOS): the
+ * compute stream waits only for the copies still in flight.  Both rings grow
+ * on demand (device memory counts against state_cap_bytes).  While ingested
+ * rows are pending, push_microbatch returns LMS_EINVAL.  Errors: LMS_EINVAL
+ * for bad arguments or n_rows above the rows pending; LMS_ENOMEM if a ring
+ * cannot grow; LMS_ECLOSED after end of stream. */
+lms_status lms_ingest(lms_stream *s, const lms_batch *b);
+lms_status lms_push_ingested(lms_stream *s, int64_t n_rows, uint32_t flags);
+/* Rows ingested and not yet pushed. */
+lms_status lms_ingest_pending(lms_stream *s, int64_t *n_rows);
 
 /* ---- control plane: dynamic micro-batching and per-operation planning ---- */
 
@@ -400,6 +428,12 @@ typedef struct lms_serve_backend {
   double (*process)(void *ctx, const lms_serve_chunk *chunks, int32_t n_chunks, int64_t n_events,
                     lms_serve_batch *rec);
   int64_t (*admissible_rows)(void *ctx);
+  /* optional: called with each tick (j_begin = 0, j_end = n_total) when it
+   * becomes visible, before any micro-batch that holds it is processed; an
+   * ingest step that runs beside the loop (its wall time is reported as
+   * arrive_ms and does not advance the clock).  Returns 0, or < 0 to stop the
+   * run with LMS_EDEVICE. */
+  int32_t (*arrive)(void *ctx, const lms_serve_chunk *tick);
 } lms_serve_backend;
 
 typedef struct lms_serve_config {
@@ -430,6 +464,7 @@ typedef struct lms_serve_result {
   int64_t max_backlog_events;
   double decide_ms;          /* wall time of all admission decisions */
   double observe_ms;         /* wall time the observer blocked the loop */
+  double arrive_ms;          /* wall time of the backend's arrive() calls (not on the clock) */
 } lms_serve_result;
 
 /* Called after every micro-batch with its record (for example to train a
@@ -466,6 +501,8 @@ lms_status lms_serve_run(const lms_serve_config *cfg, const int64_t *tick_counts
  * buffers for the largest admissible batch. */
 #define LMS_SERVE_KEEP_ROWS 1
 #define LMS_SERVE_DEVICE_INPUT 2
+#define LMS_SERVE_INGEST 4 /* host columns sent to the device as ticks arrive (lms_ingest), each
+                              micro-batch pushed with lms_push_ingested (arrive() is set) */
 typedef struct lms_serve_gpu lms_serve_gpu;
 lms_status lms_serve_gpu_create(const lms_stream_config *cfg, const lms_query_spec *qs,
                                 int32_t nq, uint64_t seed, uint32_t n_keys, double zipf_s,
@@ -672,11 +709,6 @@ lms_status lms_aggregate_batch_static(const lms_query_spec *q, int32_t value_typ
  * stream with this value type and number of queries (process-wide; 1 below
  * 2^15 rows), or 0 while it is still timing the variants of that size class. */
 int32_t lms_k1_tuned_variant(int32_t value_type, int32_t n_queries, int64_t rows);
-
-/* Floor division helper the kernels use for window ids, exposed so that host
- * tests can check it: returns n / d for d >= 1 computed by the invariant
- * multiply-and-shift method of Granlund & Montgomery (1994). */
-uint64_t lms_udiv_invariant(uint64_t n, uint64_t d);
 
 #ifdef __cplusplus
 }

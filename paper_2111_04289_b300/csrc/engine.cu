@@ -14,11 +14,14 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <deque>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/lmstream.h"
+#include "../../include/lmstream_testing.h"
 #include "lms_internal.h"
 
 namespace lms {
@@ -108,6 +111,28 @@ struct lms_stream {
   unsigned char* in_type = nullptr;
   unsigned long long dev_bytes = 0;
   std::vector<std::pair<void*, size_t>> allocs;
+  // ingest ring (lms_ingest / lms_push_ingested): rows [ring_head, ring_tail)
+  // (absolute counters; row r lives at r mod ring_cap) in device memory, and
+  // in pinned host memory for rows the library copied on the host
+  cudaStream_t ist = nullptr;           // side stream of the ring's host-to-device copies
+  unsigned long long ring_cap = 0, ring_head = 0, ring_tail = 0;
+  long long* r_ts = nullptr;
+  unsigned* r_key = nullptr;
+  unsigned* r_val = nullptr;
+  unsigned char* r_type = nullptr;
+  long long* h_ts = nullptr;
+  unsigned* h_key = nullptr;
+  unsigned* h_val = nullptr;
+  unsigned char* h_type = nullptr;
+  unsigned long long pinned_bytes = 0;
+  struct Copy {
+    unsigned long long end;  // rows before this absolute index are copied once ev completes
+    cudaEvent_t ev;
+  };
+  std::deque<Copy> copies;
+  std::vector<cudaEvent_t> free_events;
+  long long ring_first_ts = 0;          // ts of the first row ever ingested
+  bool ring_first_set = false;
   cudaEvent_t ev[8] = {};
   cudaEvent_t tev[2] = {};  // around the fused pass while the autotuner samples
   cudaEvent_t qev[kMaxQueries][6] = {};  // E1, E2, sort/reduce
@@ -456,58 +481,121 @@ lms_status query_register(lms_stream* s, const lms_query_spec* q, int32_t* query
   return LMS_OK;
 }
 
-lms_status push_microbatch(lms_stream* s, const lms_batch* b) {
-  if (!s || !b) return LMS_EINVAL;
-  std::lock_guard<std::mutex> lk(s->mu);
-  if (s->latched != LMS_OK) return s->latched;
-  if (s->eos_seen) return fail(s, LMS_ECLOSED, "stream already ended");
-  if (s->qs.empty()) return fail(s, LMS_EINVAL, "no query registered");
-  const long long n = b->n_rows;
-  if (n < 0) return fail(s, LMS_EINVAL, "n_rows < 0");
-  if (n > 0 && (!b->ts || !b->key || !b->value || (s->cfg.has_type && !b->type)))
-    return fail(s, LMS_EINVAL, "missing column pointer");
-  if (b->memory != LMS_MEM_HOST && b->memory != LMS_MEM_DEVICE)
-    return fail(s, LMS_EINVAL, "bad memory kind");
-  const auto t0 = std::chrono::steady_clock::now();
-  LMS_CK(cudaSetDevice(s->cfg.device));
-  const int eos = (b->flags & LMS_BATCH_EOS) ? 1 : 0;
-  if (!s->origin_set) {
-    if (s->cfg.origin_ts != LMS_ORIGIN_AUTO) {
-      set_origin(s, s->cfg.origin_ts);
-    } else if (n > 0) {
-      long long first = 0;
-      if (b->memory == LMS_MEM_HOST) first = (long long)b->ts[0];
-      else {
-        LMS_CK(cudaMemcpyAsync(&first, b->ts, sizeof(long long), cudaMemcpyDeviceToHost, s->st));
-        LMS_CK(cudaStreamSynchronize(s->st));
-      }
-      set_origin(s, first);
-    } else {
-      set_origin(s, 0);
-    }
+}  // extern "C"
+
+namespace {
+
+// One contiguous piece of a micro-batch's columns in device memory.
+struct InSeg {
+  const long long* ts;
+  const unsigned* key;
+  const void* val;
+  const unsigned char* typ;
+  long long n;
+};
+
+// Copies `bytes` on the host, with up to 8 threads for large copies.
+void par_memcpy(void* dst, const void* src, size_t bytes) {
+  constexpr size_t kPiece = 16u << 20;
+  if (bytes < 2 * kPiece) {
+    std::memcpy(dst, src, bytes);
+    return;
   }
-  // capacities: parts hold the carried groups plus at most one group per row
-  unsigned long long need = 0;
-  for (QueryHost& q : s->qs) need = std::max(need, q.carried + (unsigned long long)n);
-  lms_status r = ensure_group_capacity(s, need + 1);
-  if (r != LMS_OK) return r;
+  const size_t hw = std::max(1u, std::thread::hardware_concurrency());
+  const size_t nt = std::min<size_t>(std::min<size_t>(8, hw), bytes / kPiece);
+  const size_t per = (bytes + nt - 1) / nt;
+  std::vector<std::thread> th;
+  for (size_t t = 1; t < nt; ++t) {
+    const size_t a = t * per;
+    if (a >= bytes) break;
+    const size_t len = std::min(per, bytes - a);
+    th.emplace_back([=] { std::memcpy(static_cast<char*>(dst) + a, static_cast<const char*>(src) + a, len); });
+  }
+  std::memcpy(dst, src, std::min(per, bytes));
+  for (std::thread& x : th) x.join();
+}
+
+// Grows the ingest ring to at least `need` rows: new device and pinned
+// rings, the rows held moved to their front (after every copy in flight).
+lms_status ensure_ring(lms_stream* s, unsigned long long need) {
+  if (s->ring_cap >= need) return LMS_OK;
+  const unsigned long long nc = round_cap(need + need / 2);
+  LMS_CK(cudaStreamSynchronize(s->ist));
+  LMS_CK(cudaStreamSynchronize(s->st));
+  void *d_ts, *d_key, *d_val, *d_type = nullptr;
+  lms_status r;
+  if ((r = dalloc(s, &d_ts, nc * 8)) != LMS_OK || (r = dalloc(s, &d_key, nc * 4)) != LMS_OK ||
+      (r = dalloc(s, &d_val, nc * 4)) != LMS_OK ||
+      (s->cfg.has_type && (r = dalloc(s, &d_type, nc)) != LMS_OK))
+    return r;
+  void *p_ts = nullptr, *p_key = nullptr, *p_val = nullptr, *p_type = nullptr;
+  if (cudaHostAlloc(&p_ts, nc * 8, cudaHostAllocDefault) != cudaSuccess ||
+      cudaHostAlloc(&p_key, nc * 4, cudaHostAllocDefault) != cudaSuccess ||
+      cudaHostAlloc(&p_val, nc * 4, cudaHostAllocDefault) != cudaSuccess ||
+      (s->cfg.has_type && cudaHostAlloc(&p_type, nc, cudaHostAllocDefault) != cudaSuccess)) {
+    cudaGetLastError();
+    cudaFreeHost(p_ts);
+    cudaFreeHost(p_key);
+    cudaFreeHost(p_val);
+    cudaFreeHost(p_type);
+    return fail(s, LMS_ENOMEM, "cudaHostAlloc: pinned ingest ring");
+  }
+  // move the rows held, [head, tail), to rows [0, tail - head) of the new ring
+  const unsigned long long held = s->ring_tail - s->ring_head;
+  for (unsigned long long done = 0; done < held;) {
+    const unsigned long long pos = (s->ring_head + done) % s->ring_cap;
+    const unsigned long long m = std::min(held - done, s->ring_cap - pos);
+    LMS_CK(cudaMemcpyAsync(static_cast<long long*>(d_ts) + done, s->r_ts + pos, m * 8,
+                           cudaMemcpyDeviceToDevice, s->st));
+    LMS_CK(cudaMemcpyAsync(static_cast<unsigned*>(d_key) + done, s->r_key + pos, m * 4,
+                           cudaMemcpyDeviceToDevice, s->st));
+    LMS_CK(cudaMemcpyAsync(static_cast<unsigned*>(d_val) + done, s->r_val + pos, m * 4,
+                           cudaMemcpyDeviceToDevice, s->st));
+    if (d_type)
+      LMS_CK(cudaMemcpyAsync(static_cast<unsigned char*>(d_type) + done, s->r_type + pos, m,
+                             cudaMemcpyDeviceToDevice, s->st));
+    done += m;
+  }
+  LMS_CK(cudaStreamSynchronize(s->st));
+  dfree(s, s->r_ts);
+  dfree(s, s->r_key);
+  dfree(s, s->r_val);
+  dfree(s, s->r_type);
+  cudaFreeHost(s->h_ts);
+  cudaFreeHost(s->h_key);
+  cudaFreeHost(s->h_val);
+  cudaFreeHost(s->h_type);
+  s->r_ts = static_cast<long long*>(d_ts);
+  s->r_key = static_cast<unsigned*>(d_key);
+  s->r_val = static_cast<unsigned*>(d_val);
+  s->r_type = static_cast<unsigned char*>(d_type);
+  s->h_ts = static_cast<long long*>(p_ts);
+  s->h_key = static_cast<unsigned*>(p_key);
+  s->h_val = static_cast<unsigned*>(p_val);
+  s->h_type = static_cast<unsigned char*>(p_type);
+  s->pinned_bytes = nc * (8 + 4 + 4 + (s->cfg.has_type ? 1 : 0));
+  for (const lms_stream::Copy& c : s->copies) s->free_events.push_back(c.ev);
+  s->copies.clear();
+  s->ring_tail = held;
+  s->ring_head = 0;
+  s->ring_cap = nc;
+  return LMS_OK;
+}
+
+// Sets the event-time origin from the first row of the first pushed batch.
+void origin_from(lms_stream* s, bool have_row, long long first_ts) {
+  if (s->origin_set) return;
+  if (s->cfg.origin_ts != LMS_ORIGIN_AUTO) set_origin(s, s->cfg.origin_ts);
+  else set_origin(s, have_row ? first_ts : 0);
+}
+
+// The hot path of one micro-batch of n rows whose columns are the device
+// segments seg[0 .. nseg) (their copy, if any, is already enqueued on s->st
+// after s->ev[0]); group buffers must hold the carried groups plus n.
+lms_status run_batch(lms_stream* s, const InSeg* seg, int nseg, long long n, int eos,
+                     std::chrono::steady_clock::time_point t0) {
   const bool timing = s->cfg.enable_timing != 0;
-  const long long* ts = reinterpret_cast<const long long*>(b->ts);
-  const unsigned* key = b->key;
-  const void* val = b->value;
-  const unsigned char* typ = s->cfg.has_type ? b->type : nullptr;
-  if (timing) LMS_CK(cudaEventRecord(s->ev[0], s->st));
-  if (n > 0 && b->memory == LMS_MEM_HOST) {
-    if ((r = ensure_input(s, (unsigned long long)n)) != LMS_OK) return r;
-    LMS_CK(cudaMemcpyAsync(s->in_ts, b->ts, n * 8, cudaMemcpyHostToDevice, s->st));
-    LMS_CK(cudaMemcpyAsync(s->in_key, b->key, n * 4, cudaMemcpyHostToDevice, s->st));
-    LMS_CK(cudaMemcpyAsync(s->in_val, b->value, n * 4, cudaMemcpyHostToDevice, s->st));
-    if (typ) LMS_CK(cudaMemcpyAsync(s->in_type, b->type, n, cudaMemcpyHostToDevice, s->st));
-    ts = s->in_ts;
-    key = s->in_key;
-    val = s->in_val;
-    if (typ) typ = s->in_type;
-  }
+  lms_status r = LMS_OK;
   if (timing) LMS_CK(cudaEventRecord(s->ev[5], s->st));
   int launches = 0;
   int variant = 1;
@@ -519,24 +607,27 @@ lms_status push_microbatch(lms_stream* s, const lms_batch* b) {
   ++launches;
   if (timing) LMS_CK(cudaEventRecord(s->ev[1], s->st));
   if (n > 0) {
-    K1Args a{};
-    a.ts = ts;
-    a.key = key;
-    a.value = val;
-    a.type = typ;
-    a.n = n;
-    a.nq = nq;
-    a.value_is_float = s->cfg.value_type == LMS_VALUE_FLOAT32;
-    a.sctl = s->sctl;
-    for (int i = 0; i < nq; ++i) a.q[i] = s->qs[i].dev;
     variant = pick_k1_variant(s, n, &tuning);
-    const long long ntiles = (n + k1_tile_events(variant) - 1) / k1_tile_events(variant);
-    const int grid = (int)std::min<long long>(ntiles, k1_max_grid(s->cfg.device, variant, 0));
     if (tuning) LMS_CK(cudaEventRecord(s->tev[0], s->st));
-    LMS_CK(launch_k1(a, variant, grid, s->st));
+    for (int g = 0; g < nseg; ++g) {  // one fused pass per contiguous piece of the batch
+      if (seg[g].n == 0) continue;
+      K1Args a{};
+      a.ts = seg[g].ts;
+      a.key = seg[g].key;
+      a.value = seg[g].val;
+      a.type = seg[g].typ;
+      a.n = seg[g].n;
+      a.nq = nq;
+      a.value_is_float = s->cfg.value_type == LMS_VALUE_FLOAT32;
+      a.sctl = s->sctl;
+      for (int i = 0; i < nq; ++i) a.q[i] = s->qs[i].dev;
+      const long long ntiles = (a.n + k1_tile_events(variant) - 1) / k1_tile_events(variant);
+      const int grid = (int)std::min<long long>(ntiles, k1_max_grid(s->cfg.device, variant, 0));
+      LMS_CK(launch_k1(a, variant, grid, s->st));
+      ++launches;
+      ++s->stats.k1_launches;
+    }
     if (tuning) LMS_CK(cudaEventRecord(s->tev[1], s->st));
-    ++launches;
-    ++s->stats.k1_launches;
     s->stats.k1_tile_events = (uint64_t)k1_tile_events(variant);
   }
   if (timing) LMS_CK(cudaEventRecord(s->ev[2], s->st));
@@ -699,6 +790,170 @@ lms_status push_microbatch(lms_stream* s, const lms_batch* b) {
   return LMS_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+lms_status push_microbatch(lms_stream* s, const lms_batch* b) {
+  if (!s || !b) return LMS_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->latched != LMS_OK) return s->latched;
+  if (s->eos_seen) return fail(s, LMS_ECLOSED, "stream already ended");
+  if (s->qs.empty()) return fail(s, LMS_EINVAL, "no query registered");
+  const long long n = b->n_rows;
+  if (n < 0) return fail(s, LMS_EINVAL, "n_rows < 0");
+  if (n > 0 && (!b->ts || !b->key || !b->value || (s->cfg.has_type && !b->type)))
+    return fail(s, LMS_EINVAL, "missing column pointer");
+  if (b->memory != LMS_MEM_HOST && b->memory != LMS_MEM_DEVICE)
+    return fail(s, LMS_EINVAL, "bad memory kind");
+  if (s->ring_tail != s->ring_head)
+    return fail(s, LMS_EINVAL, "ingested rows pending: push them with lms_push_ingested first");
+  const auto t0 = std::chrono::steady_clock::now();
+  LMS_CK(cudaSetDevice(s->cfg.device));
+  const int eos = (b->flags & LMS_BATCH_EOS) ? 1 : 0;
+  if (!s->origin_set) {
+    long long first = 0;
+    if (n > 0 && s->cfg.origin_ts == LMS_ORIGIN_AUTO) {
+      if (b->memory == LMS_MEM_HOST) first = (long long)b->ts[0];
+      else {
+        LMS_CK(cudaMemcpyAsync(&first, b->ts, sizeof(long long), cudaMemcpyDeviceToHost, s->st));
+        LMS_CK(cudaStreamSynchronize(s->st));
+      }
+    }
+    origin_from(s, n > 0, first);
+  }
+  // capacities: parts hold the carried groups plus at most one group per row
+  unsigned long long need = 0;
+  for (QueryHost& q : s->qs) need = std::max(need, q.carried + (unsigned long long)n);
+  lms_status r = ensure_group_capacity(s, need + 1);
+  if (r != LMS_OK) return r;
+  const bool timing = s->cfg.enable_timing != 0;
+  InSeg seg{reinterpret_cast<const long long*>(b->ts), b->key, b->value,
+            s->cfg.has_type ? b->type : nullptr, n};
+  if (timing) LMS_CK(cudaEventRecord(s->ev[0], s->st));
+  if (n > 0 && b->memory == LMS_MEM_HOST) {
+    if ((r = ensure_input(s, (unsigned long long)n)) != LMS_OK) return r;
+    LMS_CK(cudaMemcpyAsync(s->in_ts, b->ts, n * 8, cudaMemcpyHostToDevice, s->st));
+    LMS_CK(cudaMemcpyAsync(s->in_key, b->key, n * 4, cudaMemcpyHostToDevice, s->st));
+    LMS_CK(cudaMemcpyAsync(s->in_val, b->value, n * 4, cudaMemcpyHostToDevice, s->st));
+    if (seg.typ) LMS_CK(cudaMemcpyAsync(s->in_type, b->type, n, cudaMemcpyHostToDevice, s->st));
+    seg = InSeg{s->in_ts, s->in_key, s->in_val, seg.typ ? s->in_type : nullptr, n};
+  }
+  return run_batch(s, &seg, 1, n, eos, t0);
+}
+
+lms_status lms_ingest(lms_stream* s, const lms_batch* b) {
+  if (!s || !b) return LMS_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->latched != LMS_OK) return s->latched;
+  if (s->eos_seen) return fail(s, LMS_ECLOSED, "stream already ended");
+  if (s->qs.empty()) return fail(s, LMS_EINVAL, "no query registered");
+  const long long n = b->n_rows;
+  if (n < 0) return fail(s, LMS_EINVAL, "n_rows < 0");
+  if (b->memory != LMS_MEM_HOST) return fail(s, LMS_EINVAL, "lms_ingest takes host columns");
+  if (n == 0) return LMS_OK;
+  if (!b->ts || !b->key || !b->value || (s->cfg.has_type && !b->type))
+    return fail(s, LMS_EINVAL, "missing column pointer");
+  LMS_CK(cudaSetDevice(s->cfg.device));
+  if (!s->ist) LMS_CK(cudaStreamCreateWithFlags(&s->ist, cudaStreamNonBlocking));
+  lms_status r = ensure_ring(s, s->ring_tail - s->ring_head + (unsigned long long)n);
+  if (r != LMS_OK) return r;
+  if (!s->ring_first_set) {
+    s->ring_first_ts = (long long)b->ts[0];
+    s->ring_first_set = true;
+  }
+  const bool stable = (b->flags & LMS_INGEST_STABLE) != 0;
+  const bool typ = s->cfg.has_type;
+  unsigned long long pos = s->ring_tail % s->ring_cap, done = 0;
+  while (done < (unsigned long long)n) {
+    const unsigned long long m = std::min((unsigned long long)n - done, s->ring_cap - pos);
+    const void* src_ts = b->ts + done;
+    const void* src_key = b->key + done;
+    const void* src_val = static_cast<const unsigned*>(b->value) + done;
+    const void* src_type = typ ? b->type + done : nullptr;
+    if (!stable) {  // into the library's pinned ring first: the caller may reuse its buffers
+      par_memcpy(s->h_ts + pos, src_ts, m * 8);
+      par_memcpy(s->h_key + pos, src_key, m * 4);
+      par_memcpy(s->h_val + pos, src_val, m * 4);
+      if (typ) par_memcpy(s->h_type + pos, src_type, m);
+      src_ts = s->h_ts + pos;
+      src_key = s->h_key + pos;
+      src_val = s->h_val + pos;
+      src_type = typ ? s->h_type + pos : nullptr;
+    }
+    LMS_CK(cudaMemcpyAsync(s->r_ts + pos, src_ts, m * 8, cudaMemcpyHostToDevice, s->ist));
+    LMS_CK(cudaMemcpyAsync(s->r_key + pos, src_key, m * 4, cudaMemcpyHostToDevice, s->ist));
+    LMS_CK(cudaMemcpyAsync(s->r_val + pos, src_val, m * 4, cudaMemcpyHostToDevice, s->ist));
+    if (typ) LMS_CK(cudaMemcpyAsync(s->r_type + pos, src_type, m, cudaMemcpyHostToDevice, s->ist));
+    done += m;
+    pos = 0;
+  }
+  cudaEvent_t ev = nullptr;
+  if (!s->free_events.empty()) {
+    ev = s->free_events.back();
+    s->free_events.pop_back();
+  } else {
+    LMS_CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  }
+  LMS_CK(cudaEventRecord(ev, s->ist));
+  s->ring_tail += (unsigned long long)n;
+  s->copies.push_back({s->ring_tail, ev});
+  return LMS_OK;
+}
+
+lms_status lms_push_ingested(lms_stream* s, int64_t n_rows, uint32_t flags) {
+  if (!s) return LMS_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->latched != LMS_OK) return s->latched;
+  if (s->eos_seen) return fail(s, LMS_ECLOSED, "stream already ended");
+  if (s->qs.empty()) return fail(s, LMS_EINVAL, "no query registered");
+  if (n_rows < 0 || (unsigned long long)n_rows > s->ring_tail - s->ring_head)
+    return fail(s, LMS_EINVAL, "n_rows exceeds the rows ingested and not yet pushed");
+  const auto t0 = std::chrono::steady_clock::now();
+  LMS_CK(cudaSetDevice(s->cfg.device));
+  const long long n = n_rows;
+  const int eos = (flags & LMS_BATCH_EOS) ? 1 : 0;
+  origin_from(s, s->ring_first_set, s->ring_first_ts);
+  unsigned long long need = 0;
+  for (QueryHost& q : s->qs) need = std::max(need, q.carried + (unsigned long long)n);
+  lms_status r = ensure_group_capacity(s, need + 1);
+  if (r != LMS_OK) return r;
+  if (s->cfg.enable_timing) LMS_CK(cudaEventRecord(s->ev[0], s->st));
+  InSeg seg[2];
+  int nseg = 0;
+  if (n > 0) {
+    // the compute stream waits for the copies of the batch's rows
+    const unsigned long long end = s->ring_head + (unsigned long long)n;
+    for (const lms_stream::Copy& c : s->copies) {
+      LMS_CK(cudaStreamWaitEvent(s->st, c.ev, 0));
+      if (c.end >= end) break;
+    }
+    const unsigned long long pos = s->ring_head % s->ring_cap;
+    const unsigned long long m = std::min((unsigned long long)n, s->ring_cap - pos);
+    const bool typ = s->cfg.has_type;
+    seg[nseg++] = InSeg{s->r_ts + pos, s->r_key + pos, s->r_val + pos, typ ? s->r_type + pos : nullptr,
+                        (long long)m};
+    if ((unsigned long long)n > m)
+      seg[nseg++] = InSeg{s->r_ts, s->r_key, s->r_val, typ ? s->r_type : nullptr, n - (long long)m};
+  }
+  r = run_batch(s, seg, nseg, n, eos, t0);
+  if (r == LMS_OK) {
+    s->ring_head += (unsigned long long)n;
+    while (!s->copies.empty() && s->copies.front().end <= s->ring_head) {
+      s->free_events.push_back(s->copies.front().ev);
+      s->copies.pop_front();
+    }
+  }
+  return r;
+}
+
+lms_status lms_ingest_pending(lms_stream* s, int64_t* n_rows) {
+  if (!s || !n_rows) return LMS_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  *n_rows = (int64_t)(s->ring_tail - s->ring_head);
+  return LMS_OK;
+}
+
 lms_status poll_results(lms_stream* s, int32_t query_id, lms_result_row* out, size_t cap,
                         size_t* n_out, int32_t timeout_ms) {
   (void)timeout_ms;  // results are complete when push_microbatch returns
@@ -772,7 +1027,11 @@ lms_status lms_stream_reserve(lms_stream* s, int64_t n_rows, int32_t host_input)
   unsigned long long need = 0;
   for (QueryHost& q : s->qs) need = std::max(need, q.carried + (unsigned long long)n_rows);
   lms_status r = ensure_group_capacity(s, need + 1);
-  if (r == LMS_OK && host_input) r = ensure_input(s, (unsigned long long)n_rows);
+  if (r == LMS_OK && host_input == 1) r = ensure_input(s, (unsigned long long)n_rows);
+  if (r == LMS_OK && host_input == 2) {
+    if (!s->ist) LMS_CK(cudaStreamCreateWithFlags(&s->ist, cudaStreamNonBlocking));
+    r = ensure_ring(s, (unsigned long long)n_rows);
+  }
   if (r == LMS_OK) LMS_CK(cudaStreamSynchronize(s->st));
   return r;
 }
@@ -852,6 +1111,14 @@ lms_status stream_close(lms_stream* s) {
     std::lock_guard<std::mutex> lk(s->mu);
     cudaSetDevice(s->cfg.device);
     if (s->st) cudaStreamSynchronize(s->st);
+    if (s->ist) cudaStreamSynchronize(s->ist);
+    for (const lms_stream::Copy& c : s->copies) cudaEventDestroy(c.ev);
+    for (cudaEvent_t e : s->free_events) cudaEventDestroy(e);
+    cudaFreeHost(s->h_ts);
+    cudaFreeHost(s->h_key);
+    cudaFreeHost(s->h_val);
+    cudaFreeHost(s->h_type);
+    if (s->ist) cudaStreamDestroy(s->ist);
     for (auto& a : s->allocs) cudaFree(a.first);
     s->allocs.clear();
     for (GraphSlot& g : s->graphs)

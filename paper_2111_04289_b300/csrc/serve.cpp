@@ -122,17 +122,29 @@ extern "C" lms_status lms_serve_run(const lms_serve_config* cfg, const int64_t* 
   lms_status status = LMS_OK;
   std::vector<double> arr, bytes;
   std::vector<lms_serve_chunk> chunks;
+  double arrive_total = 0.0;
 
   for (;;) {
     while (tick < n_ticks && (double)(tick + 1) * poll <= now + 1e-9) {
       const int64_t c = tick_counts[tick];
       if (c > 0) {
         pending.push_back({(double)tick * poll, poll, c, 0, c, first, false});
+        if (be->arrive) {
+          const auto a0 = std::chrono::steady_clock::now();
+          const lms_serve_chunk tc{(double)tick * poll, poll, c, 0, c, first};
+          const int32_t ar = be->arrive(be->ctx, &tc);
+          arrive_total += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - a0).count();
+          if (ar < 0) {
+            status = LMS_EDEVICE;
+            break;
+          }
+        }
         pend_events += c;
         first += c;
       }
       ++tick;
     }
+    if (status != LMS_OK) break;
     const bool all_arrived = tick == n_ticks;
     max_backlog = std::max(max_backlog, pend_events);
     if (pending.empty()) {
@@ -282,6 +294,7 @@ extern "C" lms_status lms_serve_run(const lms_serve_config* cfg, const int64_t* 
   r.max_backlog_events = max_backlog;
   r.decide_ms = decide_total;
   r.observe_ms = observe_total;
+  r.arrive_ms = arrive_total;
   if (processed > 0) {
     r.p50_ms = kth(segs, (int64_t)std::ceil(0.5 * (double)processed));
     r.p_hi_ms = kth(segs, std::max<int64_t>(1, (int64_t)std::ceil(qhi * (double)processed)));

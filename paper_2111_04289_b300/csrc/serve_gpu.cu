@@ -9,7 +9,12 @@
 // host-to-device copy is inside the measured time) followed by poll_results of
 // every emitted row into pinned host memory.  In device mode the columns are
 // already in HBM (push reads them in place) and the rows are still polled to
-// the host.  The processing time is the wall time of push + polls.
+// the host.  In ingest mode the columns are in pinned host memory too, but
+// every tick is handed to lms_ingest when it arrives (its ts written into a
+// pinned ts pool indexed like the key/value pool), so its host-to-device copy
+// runs on the stream's side stream while the data waits for admission; each
+// micro-batch is then lms_push_ingested + polls.  The processing time is the
+// wall time of push + polls.
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -30,6 +35,10 @@ struct lms_serve_gpu {
   int dev = 0;
   int sms = 148;
   bool device_input = false;
+  bool ingest = false;
+  long long* ts_pool = nullptr;   // ingest mode: pinned ts of event c at c mod kPool
+  long long* m_ts_pool = nullptr; // its device-side address
+  long long ingested = 0, pushed = 0;
   cudaStream_t gen_st = nullptr;
   unsigned long long seed = 0;
   unsigned n_keys = 0;
@@ -68,6 +77,7 @@ void destroy(lms_serve_gpu* g) {
   free_col(g, g->ts);
   free_col(g, g->key);
   free_col(g, g->val);
+  cudaFreeHost(g->ts_pool);
   cudaFreeHost(g->h_chunks);
   cudaFreeHost(g->h_rows);
   delete g;
@@ -109,23 +119,55 @@ lms_status make_batch(lms_serve_gpu* g, const lms_serve_chunk* chunks, int32_t n
   return LMS_OK;
 }
 
+// Ingest mode: a tick became visible; its ts go to the ts pool (not measured)
+// and its rows to lms_ingest.
+int32_t arrive(void* ctx, const lms_serve_chunk* t) {
+  lms_serve_gpu* g = static_cast<lms_serve_gpu*>(ctx);
+  const long long n = t->j_end - t->j_begin;
+  // rows ingested and not pushed must keep their ts pool slots
+  if (n <= 0 || n > g->max_rows || g->ingested + n - g->pushed > kPool) return -1;
+  const long long pos = (t->first_event + t->j_begin) % kPool;
+  if (cudaSetDevice(g->dev) != cudaSuccess) return -1;
+  g->h_chunks[0] = {t->t0_ms, t->width_ms, t->n_total, t->j_begin, t->first_event, 0};
+  if (cudaMemcpyAsync(g->d_chunks, g->h_chunks, sizeof(GenChunk), cudaMemcpyHostToDevice,
+                      g->gen_st) != cudaSuccess ||
+      launch_gen_ts(g->d_chunks, 1, n, g->m_ts_pool + pos, g->sms, g->gen_st) != cudaSuccess ||
+      cudaStreamSynchronize(g->gen_st) != cudaSuccess)
+    return -1;
+  lms_batch b{};
+  b.n_rows = n;
+  b.ts = reinterpret_cast<const int64_t*>(g->ts_pool + pos);
+  b.key = g->key + pos;
+  b.value = g->val + pos;
+  b.memory = LMS_MEM_HOST;
+  b.flags = LMS_INGEST_STABLE;
+  if (lms_ingest(g->s, &b) != LMS_OK) return -1;
+  g->ingested += n;
+  return 0;
+}
+
 double process(void* ctx, const lms_serve_chunk* chunks, int32_t n_chunks, int64_t n_events,
                lms_serve_batch* rec) {
   lms_serve_gpu* g = static_cast<lms_serve_gpu*>(ctx);
   long long off = 0;
-  // make the batch (not measured)
-  if (make_batch(g, chunks, n_chunks, n_events, &off) != LMS_OK) return -1.0;
+  // make the batch (not measured; in ingest mode its rows are already ingested)
+  if (!g->ingest && make_batch(g, chunks, n_chunks, n_events, &off) != LMS_OK) return -1.0;
   lms_stats before{}, after{};
   lms_stream_stats(g->s, &before);
   // process it as a client would: push, then poll every row to the host
   const auto t0 = std::chrono::steady_clock::now();
-  lms_batch b{};
-  b.n_rows = n_events;
-  b.ts = reinterpret_cast<const int64_t*>(g->ts);
-  b.key = g->key + off;
-  b.value = g->val + off;
-  b.memory = g->device_input ? LMS_MEM_DEVICE : LMS_MEM_HOST;
-  if (push_microbatch(g->s, &b) != LMS_OK) return -1.0;
+  if (g->ingest) {
+    if (lms_push_ingested(g->s, n_events, 0u) != LMS_OK) return -1.0;
+    g->pushed += n_events;
+  } else {
+    lms_batch b{};
+    b.n_rows = n_events;
+    b.ts = reinterpret_cast<const int64_t*>(g->ts);
+    b.key = g->key + off;
+    b.value = g->val + off;
+    b.memory = g->device_input ? LMS_MEM_DEVICE : LMS_MEM_HOST;
+    if (push_microbatch(g->s, &b) != LMS_OK) return -1.0;
+  }
   unsigned long long rows = 0;
   for (int q = 0; q < g->nq; ++q) {
     for (;;) {
@@ -181,6 +223,7 @@ lms_status lms_serve_gpu_create(const lms_stream_config* cfg, const lms_query_sp
   g->nq = nq;
   g->keep_rows = (flags & LMS_SERVE_KEEP_ROWS) != 0;
   g->device_input = (flags & LMS_SERVE_DEVICE_INPUT) != 0;
+  g->ingest = !g->device_input && (flags & LMS_SERVE_INGEST) != 0;
   g->kept.resize(nq);
   lms_status r = stream_open(cfg, &g->s);
   if (r != LMS_OK) {
@@ -215,6 +258,7 @@ lms_status lms_serve_gpu_create(const lms_stream_config* cfg, const lms_query_sp
       alloc_col(g, (void**)&g->ts, 8 * n) != cudaSuccess ||
       alloc_col(g, (void**)&g->key, 4 * np) != cudaSuccess ||
       alloc_col(g, (void**)&g->val, 4 * np) != cudaSuccess ||
+      (g->ingest && cudaHostAlloc((void**)&g->ts_pool, 8 * np, cudaHostAllocMapped) != cudaSuccess) ||
       cudaHostAlloc(&g->h_rows, sizeof(lms_result_row) * g->rows_cap, cudaHostAllocDefault) !=
           cudaSuccess) {
     cudaGetLastError();
@@ -227,7 +271,8 @@ lms_status lms_serve_gpu_create(const lms_stream_config* cfg, const lms_query_sp
   if (!g->device_input &&
       (cudaHostGetDevicePointer((void**)&g->m_ts, g->ts, 0) != cudaSuccess ||
        cudaHostGetDevicePointer((void**)&m_key, g->key, 0) != cudaSuccess ||
-       cudaHostGetDevicePointer((void**)&m_val, g->val, 0) != cudaSuccess)) {
+       cudaHostGetDevicePointer((void**)&m_val, g->val, 0) != cudaSuccess ||
+       (g->ingest && cudaHostGetDevicePointer((void**)&g->m_ts_pool, g->ts_pool, 0) != cudaSuccess))) {
     cudaGetLastError();
     destroy(g);
     return LMS_ECUDA;
@@ -296,7 +341,15 @@ lms_status lms_serve_gpu_create(const lms_stream_config* cfg, const lms_query_sp
     int64_t adm = -1;
     if (wr == LMS_OK) wr = lms_stream_admissible_rows(g->s, g->device_input ? 0 : 1, &adm);
     const int64_t res = (adm < 0 || adm > max_batch_rows) ? max_batch_rows : adm;
-    if (wr == LMS_OK) wr = lms_stream_reserve(g->s, res, g->device_input ? 0 : 1);
+    if (wr == LMS_OK) wr = lms_stream_reserve(g->s, res, g->device_input ? 0 : g->ingest ? 2 : 1);
+    // the chunk table of one tick (arrive() in ingest mode)
+    if (wr == LMS_OK && g->chunk_cap < 1) {
+      if (cudaMalloc(&g->d_chunks, sizeof(GenChunk) * 2) != cudaSuccess ||
+          cudaHostAlloc(&g->h_chunks, sizeof(GenChunk) * 2, cudaHostAllocDefault) != cudaSuccess)
+        wr = LMS_ENOMEM;
+      else
+        g->chunk_cap = 2;
+    }
     if (wr != LMS_OK) {
       destroy(g);
       return wr;
@@ -311,6 +364,7 @@ lms_status lms_serve_gpu_backend(lms_serve_gpu* g, lms_serve_backend* out) {
   out->ctx = g;
   out->process = process;
   out->admissible_rows = admissible;
+  out->arrive = g->ingest ? arrive : nullptr;
   return LMS_OK;
 }
 

@@ -26,6 +26,7 @@ OPS = {"none": 0, "eq": 1, "ne": 2, "lt": 3, "le": 4, "gt": 5, "ge": 6}
 AGG_COUNT, AGG_SUM, AGG_MIN, AGG_MAX, AGG_AVG, AGG_ALL = 1, 2, 4, 8, 16, 31
 MEM_HOST, MEM_DEVICE = 0, 1
 BATCH_EOS = 1
+INGEST_STABLE = 2
 GRAPH_DEFAULT, GRAPH_OFF, GRAPH_ON = 0, 1, 2
 ORIGIN_AUTO = -(2 ** 63)
 
@@ -99,7 +100,8 @@ EXPORTED_SYMBOLS = ("stream_open", "query_register", "push_microbatch", "poll_re
                     "lms_serve_gpu_device_input", "lms_stream_push_bytes",
                     "lms_stream_device_bytes", "lms_server_create", "lms_server_submit",
                     "lms_server_wait", "lms_server_forget", "lms_server_get_stats",
-                    "lms_server_destroy", "lms_server_create_ops", "lms_k1_tuned_variant")
+                    "lms_server_destroy", "lms_server_create_ops", "lms_k1_tuned_variant",
+                    "lms_ingest", "lms_push_ingested", "lms_ingest_pending")
 ADMIT_PAPER, ADMIT_GUARDED = 0, 1
 QOPS = {"aggregation": 0, "filter": 1, "shuffle": 2, "project": 3, "join": 4, "expand": 5,
         "scan": 6, "sort": 7}
@@ -156,7 +158,7 @@ SERVE_ADMISSIBLE = ctypes.CFUNCTYPE(ctypes.c_int64, ctypes.c_void_p)
 
 class ServeBackend(ctypes.Structure):
     _fields_ = [("ctx", ctypes.c_void_p), ("process", ctypes.c_void_p),
-                ("admissible_rows", ctypes.c_void_p)]
+                ("admissible_rows", ctypes.c_void_p), ("arrive", ctypes.c_void_p)]
 
 
 class ServeConfig(ctypes.Structure):
@@ -176,7 +178,8 @@ class ServeResult(ctypes.Structure):
                 ("p50_ms", ctypes.c_double), ("p_hi_ms", ctypes.c_double),
                 ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
                 ("events_per_s", ctypes.c_double), ("max_backlog_events", ctypes.c_int64),
-                ("decide_ms", ctypes.c_double), ("observe_ms", ctypes.c_double)]
+                ("decide_ms", ctypes.c_double), ("observe_ms", ctypes.c_double),
+                ("arrive_ms", ctypes.c_double)]
 STATIC_MAX_ROWS = 131072
 
 _lib = None
@@ -219,6 +222,12 @@ def load(build_if_missing: bool = True):
     lib.lms_results_discard.argtypes = [P, ctypes.c_int32]
     lib.lms_udiv_invariant.restype = ctypes.c_uint64
     lib.lms_udiv_invariant.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+    lib.lms_ingest.restype = ctypes.c_int32
+    lib.lms_ingest.argtypes = [P, P]
+    lib.lms_push_ingested.restype = ctypes.c_int32
+    lib.lms_push_ingested.argtypes = [P, ctypes.c_int64, ctypes.c_uint32]
+    lib.lms_ingest_pending.restype = ctypes.c_int32
+    lib.lms_ingest_pending.argtypes = [P, P]
     lib.lms_aggregate_batch_static.restype = ctypes.c_int32
     lib.lms_aggregate_batch_static.argtypes = [
         ctypes.POINTER(QuerySpec), ctypes.c_int32, P, P, P, P, ctypes.c_int64, P, P,
@@ -382,6 +391,7 @@ class Stream:
         self.has_type = bool(has_type)
         self.row_dtype = ROW_DTYPE_FLOAT if self.is_float else ROW_DTYPE_INT
         self.queries = []
+        self._ingest_keep = []
 
     def _check(self, st: int, what: str):
         if st != LMS_OK:
@@ -429,6 +439,34 @@ class Stream:
         del keep
         self._check(st, "push_microbatch")
         return int(b.n_rows)
+
+    def ingest(self, ts, key, value, type_=None, stable: bool = False) -> int:
+        """lms_ingest of one arriving dataset (host numpy arrays or pinned torch
+        tensors); with stable=True the columns must stay unchanged until the
+        push_ingested that covers them returns."""
+        b, keep = self.make_batch(ts, key, value, type_)
+        if b.memory != MEM_HOST:
+            raise ValueError("lms_ingest takes host columns")
+        b.flags = INGEST_STABLE if stable else 0
+        st = self._lib.lms_ingest(self._h, ctypes.byref(b))
+        if stable:
+            self._ingest_keep.append(keep)
+        del keep
+        self._check(st, "lms_ingest")
+        return int(b.n_rows)
+
+    def push_ingested(self, n_rows: int, eos: bool = False) -> int:
+        """lms_push_ingested: the oldest n_rows ingested rows as one micro-batch."""
+        st = self._lib.lms_push_ingested(self._h, int(n_rows), BATCH_EOS if eos else 0)
+        self._check(st, "lms_push_ingested")
+        if self.ingest_pending() == 0:
+            self._ingest_keep = []
+        return int(n_rows)
+
+    def ingest_pending(self) -> int:
+        n = ctypes.c_int64()
+        self._check(self._lib.lms_ingest_pending(self._h, ctypes.byref(n)), "lms_ingest_pending")
+        return n.value
 
     def poll(self, qid: int, max_rows: Optional[int] = None) -> np.ndarray:
         """All (or up to max_rows) pending rows of query qid, oldest first."""
@@ -682,7 +720,7 @@ class ServeGpu:
     def __init__(self, queries, *, seed: int, n_keys: int = 1_000_000, zipf_s: float = 1.1,
                  max_batch_rows: int = 1 << 24, state_cap_bytes: int = 0,
                  enable_timing: bool = True, keep_rows: bool = False, device_input: bool = False,
-                 device: int = 0):
+                 ingest: bool = False, device: int = 0):
         self._lib = load()
         cfg = StreamConfig(device=device, value_type=VALUE_FLOAT32, has_type=0,
                            enable_timing=int(enable_timing), allowed_lateness_ms=0,
@@ -693,7 +731,8 @@ class ServeGpu:
         h = ctypes.c_void_p()
         st = self._lib.lms_serve_gpu_create(ctypes.byref(cfg), specs, len(queries), int(seed),
                                             int(n_keys), float(zipf_s), int(max_batch_rows),
-                                            (1 if keep_rows else 0) | (2 if device_input else 0),
+                                            (1 if keep_rows else 0) | (2 if device_input else 0)
+                                            | (4 if ingest else 0),
                                             ctypes.byref(h))
         if st != LMS_OK:
             raise LmsError(st, "lms_serve_gpu_create")

@@ -18,8 +18,11 @@ HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))
 
 
 def _declared_functions():
-    src = open(HEADER).read()
+    inc = os.path.dirname(HEADER)
+    src = "\n".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc))
+                    if f.endswith(".h"))
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"#ifdef __cplusplus.*?#endif", "", src, flags=re.S)  # extern "C" { and }
     src = re.sub(r"\{[^{}]*\}", "{}", src)  # struct bodies (function-pointer members)
     src = "\n".join(l for l in src.splitlines() if not l.lstrip().startswith("typedef"))
     names = re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*([a-z_0-9]+)\s*\(", src, flags=re.M)

@@ -76,13 +76,17 @@ def test_generator_definition_and_split_invariance():
     g.close()
 
 
-@pytest.mark.parametrize("policy,device_input", [(lm.POLICY_ANALYTIC, False),
-                                                 (lm.POLICY_FIXED_SIZE, False),
-                                                 (lm.POLICY_ANALYTIC, True)])
-def test_serving_rows_match_oracle(policy, device_input):
+@pytest.mark.parametrize("policy,device_input,ingest", [(lm.POLICY_ANALYTIC, False, False),
+                                                        (lm.POLICY_FIXED_SIZE, False, False),
+                                                        (lm.POLICY_ANALYTIC, True, False),
+                                                        (lm.POLICY_ANALYTIC, False, True),
+                                                        (lm.POLICY_FIXED_SIZE, False, True)])
+def test_serving_rows_match_oracle(policy, device_input, ingest):
+    """Ingest mode: ticks go to the device through the ingest ring as they
+    arrive (overlapped with buffering and compute); the rows must not change."""
     ticks = np.random.default_rng(3).poisson(np.linspace(500, 6000, 260)).astype(np.int64)
     g = lm.ServeGpu(QUERIES, seed=11, n_keys=20_000, max_batch_rows=1 << 18, keep_rows=True,
-                    device_input=device_input)
+                    device_input=device_input, ingest=ingest)
     res, log = lm.serve_run(ticks, poll_ms=10.0, policy=policy, bound_ms=60.0,
                             backend=g.backend(), fixed_rows=17_000)
     assert res["processed_events"] == ticks.sum() and res["completed"] == 1
