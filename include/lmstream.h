@@ -366,6 +366,48 @@ void lms_regressor_add(lms_regressor *r, double thput, double lat, double infpt)
 lms_status lms_regressor_fit(lms_regressor *r, double target_thput, double target_lat,
                              double *beta3, double *infpt);
 
+/* ---- per-operation variant choice (Alg. 2 and Eq. 9 re-read) -------------
+ *
+ * The engine runs every operation on the GPU, so MapDevice's choice between a
+ * CPU and a GPU implementation of an operation (Alg. 2, Eqs. 6-8) is re-read
+ * as the choice between two implementations of the fused pass: variant 1
+ * (1024-event tiles, two CTAs per SM; the paper's CPU side: its cost grows
+ * with the partition) and variant 2 (2048-event tiles; the GPU side).  A
+ * chooser is asked before every fused pass and, if it installs an observer,
+ * told the pass's measured time afterwards. */
+typedef int32_t (*lms_variant_chooser)(void *ctx, int64_t rows, int32_t n_queries);
+typedef void (*lms_variant_observer)(void *ctx, int64_t rows, int32_t variant, double ms);
+/* Installs (or with NULL removes) the chooser of s's fused-pass variant; it
+ * takes precedence over cfg.k1_variant and the timing autotuner.  Results do
+ * not depend on the variant. */
+lms_status lms_stream_set_variant_chooser(lms_stream *s, lms_variant_chooser choose,
+                                          lms_variant_observer observe, void *ctx);
+
+/* The analytic chooser: Alg. 2 over the one-operation chain (Aggregation,
+ * Table II base cost 1.0, transition base cost 0.1) with Part = batch bytes /
+ * partitions (bytes_per_row each) and the current inflection point.  Each
+ * variant is first tried `explore` times.  After each pass: the observed
+ * inflection point is where the two variants' fitted costs (ms = c rows^b,
+ * least squares on logs over each variant's latest 16 passes) cross, kept
+ * within [1/2 smallest, 2 x largest] size seen; Eq. 9 is refitted on
+ * (throughput = rows/ms, latency = ms, observed InfPT) over the last
+ * history_len passes (0 = all) and evaluated at the targets (the largest
+ * throughput seen, the mean latency) to give the next inflection point.
+ * choose / observe have the chooser / observer signatures (ctx = the
+ * chooser).  predict: a variant's fitted cost in ms at `rows` (< 0 if not
+ * fitted yet).  state: the inflection point (bytes per partition) and the
+ * picks of variants 1 and 2. */
+typedef struct lms_variant_analytic lms_variant_analytic;
+lms_variant_analytic *lms_variant_analytic_create(int32_t partitions, double bytes_per_row,
+                                                  double infpt0_bytes, int32_t history_len,
+                                                  int32_t explore);
+void lms_variant_analytic_destroy(lms_variant_analytic *v);
+int32_t lms_variant_analytic_choose(void *ctx, int64_t rows, int32_t n_queries);
+void lms_variant_analytic_observe(void *ctx, int64_t rows, int32_t variant, double ms);
+double lms_variant_analytic_predict(const lms_variant_analytic *v, int64_t rows, int32_t variant);
+void lms_variant_analytic_state(const lms_variant_analytic *v, double *infpt_bytes,
+                                int64_t *picks);
+
 /* Keeps only the first n_keep datasets of the micro-batch Alg. 1 just admitted
  * (the caller re-offers the others as new datasets at its next poll); when
  * last_bytes > 0 it replaces the size of the last kept dataset (a dataset that
@@ -563,6 +605,8 @@ lms_status lms_mlp_train(lms_mlp *m, const float *x, const float *t, int32_t n, 
 #define LMS_OP_EMIT 3  /* window assembly, emission and carry */
 #define LMS_OP_HOST 4  /* the rest of the processing time (launches, syncs, result copies) */
 #define LMS_N_OPS 5
+/* The fused pass run as variant v (1 or 2), for the learned variant chooser. */
+#define LMS_OP_K1_VARIANT(v) (4 + (v))
 
 /* The model's eight input features of operator `op` of a micro-batch:
  * log2(1+rows)/32, log2(1+carried state groups)/32, log2(key cardinality)/32,
@@ -607,6 +651,31 @@ double lms_learned_predict(void *learned, double batch_bytes, int32_t n_datasets
 /* Judge's moving errors and how often each estimate answered. */
 void lms_learned_stats(const lms_learned *l, double *err_net, double *err_eq5, int64_t *uses_net,
                        int64_t *uses_eq5);
+
+/* Learned chooser of the fused pass's variant (see lms_variant_analytic): the
+ * network m predicts ln(us) of the pass for each variant from the features of
+ * lms_cost_features (rows, no carried groups, the stream's key cardinality,
+ * selectivity, panes per window and queries, span 0, operator
+ * LMS_OP_K1_VARIANT(v)); it picks the variant of the smaller prediction, and
+ * every 16th pick the other one, so both stay measured.  The analytic chooser
+ * `judge` (owned by the caller) answers while the network is untrained or
+ * while its moving |ln(predicted / measured)| error is the larger of the two;
+ * it also sees every measurement.  Measured passes become training samples
+ * (a ring of LMS_MLP_MAX_BATCH); fit() trains on them, and with online
+ * refitting on, observe() does so every refit_every passes.  choose / observe
+ * have the chooser / observer signatures (ctx = the learned chooser). */
+typedef struct lms_variant_learned lms_variant_learned;
+lms_variant_learned *lms_variant_learned_create(lms_mlp *m, lms_variant_analytic *judge,
+                                                double key_card, double selectivity,
+                                                double panes_per_window, double n_queries);
+void lms_variant_learned_destroy(lms_variant_learned *v);
+void lms_variant_learned_set_online(lms_variant_learned *v, int32_t refit_every,
+                                    int32_t refit_steps, float lr);
+lms_status lms_variant_learned_fit(lms_variant_learned *v, int32_t steps, float lr, float *loss);
+int32_t lms_variant_learned_choose(void *ctx, int64_t rows, int32_t n_queries);
+void lms_variant_learned_observe(void *ctx, int64_t rows, int32_t variant, double ms);
+void lms_variant_learned_stats(const lms_variant_learned *v, double *err_net, double *err_an,
+                               int64_t *uses_net, int64_t *uses_an, int64_t *picks);
 
 /* ---- continuous batching across streams --------------------------------
  *

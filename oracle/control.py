@@ -190,3 +190,72 @@ def regress_infpt(thput: Sequence[float], lat: Sequence[float], infpt: Sequence[
             beta = np.array([float(y.mean() - b12[0] * t.mean() - b12[1] * l.mean()),
                              float(b12[0]), float(b12[1])])
     return beta, float(beta[0] + beta[1] * target_thput + beta[2] * target_lat)
+
+
+class VariantAnalytic:
+    """Alg. 2 re-read as the choice between the fused pass's two variants, with
+    Eq. 9 refitting the inflection point (the reading is the engine's; the
+    paper places operations on a CPU or a GPU).
+
+    Variant 1 takes the place of the CPU in Eqs. 6-8 and variant 2 that of the
+    GPU; Part = batch bytes / partitions.  Each variant is first tried
+    `explore` times (the less sampled one first).  After a pass of `rows` rows
+    taking `ms`: each variant's cost is fitted as ln ms = a + b ln rows over
+    its latest `window` passes (least squares); where the two fits cross (kept
+    within [1/2 smallest, 2 x largest] size seen; the far end on the cheaper
+    side if they do not cross there) is the observed inflection point, in bytes
+    per partition; Eq. 9 is refitted on (rows/ms, ms, observed InfPT) and
+    evaluated at (largest throughput seen, mean latency) for the next pass."""
+
+    def __init__(self, partitions: int, bytes_per_row: float, infpt0: float = INFPT0_BYTES,
+                 history: int = 0, explore: int = 2, window: int = 16):
+        self.partitions, self.bpr, self.infpt = partitions, float(bytes_per_row), float(infpt0)
+        self.history, self.explore, self.window = history, explore, window
+        self.obs = {1: [], 2: []}  # (ln rows, ln ms)
+        self.hist = []  # (throughput, latency, observed InfPT)
+        self.max_thput, self.sum_lat, self.n = 0.0, 0.0, 0
+        self.picks = {1: 0, 2: 0}
+
+    def choose(self, rows: int) -> int:
+        if len(self.obs[1]) < self.explore or len(self.obs[2]) < self.explore:
+            pick = 1 if len(self.obs[1]) <= len(self.obs[2]) else 2
+        else:
+            plan = map_device(["aggregation"], max(rows, 1) * self.bpr, self.partitions,
+                              self.infpt)
+            pick = 1 if plan[0][0] == "CPU" else 2
+        self.picks[pick] += 1
+        return pick
+
+    def _fit(self, v):
+        o = self.obs[v]
+        x = np.array([p[0] for p in o])
+        if len(o) < 2 or np.sum((x - x.mean()) ** 2) <= 1e-12:
+            return None
+        b, a = np.polyfit(x, np.array([p[1] for p in o]), 1)  # ln ms = a + b ln rows
+        return a, b
+
+    def predict(self, rows: int, v: int) -> float:
+        f = self._fit(v)
+        return -1.0 if f is None else float(np.exp(f[0] + f[1] * np.log(rows)))
+
+    def observe(self, rows: int, v: int, ms: float) -> None:
+        self.obs[v].append((np.log(rows), np.log(ms)))
+        self.obs[v] = self.obs[v][-self.window:]
+        self.max_thput = max(self.max_thput, rows / ms)
+        self.sum_lat += ms
+        self.n += 1
+        f1, f2 = self._fit(1), self._fit(2)
+        if f1 is None or f2 is None:
+            return
+        xs = [p[0] for v_ in (1, 2) for p in self.obs[v_]]
+        lo, hi = min(xs) - np.log(2.0), max(xs) + np.log(2.0)
+        (a1, b1), (a2, b2) = f1, f2
+        x = (a1 - a2) / (b2 - b1) if b1 != b2 else (hi if a1 < a2 else lo)
+        if x < lo or x > hi:
+            x = hi if a1 + b1 * hi < a2 + b2 * hi else lo
+        self.hist.append((rows / ms, ms, float(np.exp(x)) * self.bpr / self.partitions))
+        h = self.hist[-self.history:] if self.history else self.hist
+        _, inf = regress_infpt([p[0] for p in h], [p[1] for p in h], [p[2] for p in h],
+                               self.max_thput, self.sum_lat / self.n)
+        if inf > 0:
+            self.infpt = inf

@@ -10,6 +10,17 @@
 // target (policy PAPER is Alg. 1 as printed); Eq. 9 is solved on centred
 // inputs and falls back to (mean InfPT, 0, 0) with fewer than 3 samples, a
 // constant input, or collinear inputs (1 - r^2 below 1e-12).
+//
+// The engine runs every operation on the GPU, so Alg. 2's CPU/GPU choice is
+// re-read as the choice between the fused pass's two tile shapes: variant 1
+// (1024-event tiles, two CTAs per SM; its cost grows with the partition like
+// Eq. 6's CPU cost) and variant 2 (2048-event tiles; fewer partial groups per
+// event, its relative cost falls with the partition like Eq. 7's GPU cost).
+// Part = batch bytes / partitions (the SMs).  The inflection point where the
+// two cost the same is refitted after every batch by Eq. 9 on (throughput,
+// latency, observed InfPT) samples, where the observed InfPT is the crossover
+// of the two variants' measured costs (power laws ms = c rows^b fitted by
+// least squares on logs over their latest samples).
 #include <algorithm>
 #include <cmath>
 #include <deque>
@@ -45,6 +56,19 @@ struct lms_admission {
 struct lms_regressor {
   int history = 0;
   std::deque<double> thp, lat, inf;
+};
+
+struct lms_variant_analytic {
+  int partitions = 148;
+  double bpr = 16.0;            // bytes per row
+  double infpt = 150.0 * 1024;  // inflection point, bytes per partition
+  lms_regressor* reg = nullptr;
+  int window = 16;              // samples per variant in its cost fit
+  int explore = 2;              // each variant is tried this many times first
+  std::deque<double> lr[2], lm[2];  // ln rows, ln ms of variants 1 and 2
+  double max_thput = 0.0, sum_lat = 0.0;
+  long long n_obs = 0;
+  long long picks[2] = {0, 0};
 };
 
 extern "C" {
@@ -170,6 +194,129 @@ lms_status lms_map_device(const int32_t* ops, int32_t n_ops, double batch_bytes,
     if (gpu_cost) gpu_cost[o] = gpu;
   }
   return LMS_OK;
+}
+
+namespace {
+
+// ln ms = a + b ln rows over the samples of one variant (least squares);
+// false without two distinct sizes.
+bool power_fit(const std::deque<double>& x, const std::deque<double>& y, double* a, double* b) {
+  const size_t n = x.size();
+  if (n < 2) return false;
+  double mx = 0, my = 0;
+  for (size_t k = 0; k < n; ++k) {
+    mx += x[k];
+    my += y[k];
+  }
+  mx /= (double)n;
+  my /= (double)n;
+  double sxx = 0, sxy = 0;
+  for (size_t k = 0; k < n; ++k) {
+    sxx += (x[k] - mx) * (x[k] - mx);
+    sxy += (x[k] - mx) * (y[k] - my);
+  }
+  if (!(sxx > 1e-12)) return false;
+  *b = sxy / sxx;
+  *a = my - *b * mx;
+  return true;
+}
+
+}  // namespace
+
+lms_variant_analytic* lms_variant_analytic_create(int32_t partitions, double bytes_per_row,
+                                                  double infpt0_bytes, int32_t history_len,
+                                                  int32_t explore) {
+  if (partitions < 1 || !(bytes_per_row > 0) || !(infpt0_bytes > 0) || history_len < 0 ||
+      explore < 0)
+    return nullptr;
+  lms_variant_analytic* v = new lms_variant_analytic();
+  v->partitions = partitions;
+  v->bpr = bytes_per_row;
+  v->infpt = infpt0_bytes;
+  v->explore = explore;
+  v->reg = lms_regressor_create(history_len);
+  return v;
+}
+
+void lms_variant_analytic_destroy(lms_variant_analytic* v) {
+  if (!v) return;
+  lms_regressor_destroy(v->reg);
+  delete v;
+}
+
+int32_t lms_variant_analytic_choose(void* ctx, int64_t rows, int32_t n_queries) {
+  lms_variant_analytic* v = static_cast<lms_variant_analytic*>(ctx);
+  (void)n_queries;
+  int32_t pick;
+  if ((int)v->lr[0].size() < v->explore || (int)v->lr[1].size() < v->explore) {
+    pick = v->lr[0].size() <= v->lr[1].size() ? 1 : 2;  // explore: the less sampled variant
+  } else {
+    // Alg. 2 over the one-operation chain (Aggregation): variant 1 stands
+    // where the paper puts the CPU, variant 2 where it puts the GPU
+    const int32_t op = LMS_QOP_AGGREGATION;
+    int32_t dev = 0;
+    const double bytes = (double)std::max<int64_t>(rows, 1) * v->bpr;
+    if (lms_map_device(&op, 1, bytes, v->partitions, v->infpt, 0.1, &dev, nullptr, nullptr) !=
+        LMS_OK)
+      dev = 0;
+    pick = dev == 1 ? 1 : 2;
+  }
+  ++v->picks[pick - 1];
+  return pick;
+}
+
+void lms_variant_analytic_observe(void* ctx, int64_t rows, int32_t variant, double ms) {
+  lms_variant_analytic* v = static_cast<lms_variant_analytic*>(ctx);
+  if (!v || rows < 1 || !(ms > 0) || (variant != 1 && variant != 2)) return;
+  const int i = variant - 1;
+  v->lr[i].push_back(std::log((double)rows));
+  v->lm[i].push_back(std::log(ms));
+  if ((int)v->lr[i].size() > v->window) {
+    v->lr[i].pop_front();
+    v->lm[i].pop_front();
+  }
+  const double thput = (double)rows / ms, lat = ms;
+  v->max_thput = std::max(v->max_thput, thput);
+  v->sum_lat += lat;
+  ++v->n_obs;
+  double a1, b1, a2, b2;
+  if (!power_fit(v->lr[0], v->lm[0], &a1, &b1) || !power_fit(v->lr[1], v->lm[1], &a2, &b2)) return;
+  // observed InfPT: where the two fits cross, kept within the sizes seen (a
+  // factor 2 beyond them when one variant is the cheaper one throughout)
+  double lo = 1e300, hi = -1e300;
+  for (int k = 0; k < 2; ++k)
+    for (double x : v->lr[k]) {
+      lo = std::min(lo, x);
+      hi = std::max(hi, x);
+    }
+  lo -= std::log(2.0);
+  hi += std::log(2.0);
+  double x;
+  if (b1 != b2) x = (a1 - a2) / (b2 - b1);
+  else x = a1 < a2 ? hi : lo;
+  if (x < lo || x > hi) x = (a1 + b1 * hi < a2 + b2 * hi) ? hi : lo;
+  const double obs = std::exp(x) * v->bpr / (double)v->partitions;
+  lms_regressor_add(v->reg, thput, lat, obs);
+  double beta[3], inf = 0.0;
+  lms_regressor_fit(v->reg, v->max_thput, v->sum_lat / (double)v->n_obs, beta, &inf);
+  if (inf > 0) v->infpt = inf;
+}
+
+double lms_variant_analytic_predict(const lms_variant_analytic* v, int64_t rows, int32_t variant) {
+  if (!v || rows < 1 || (variant != 1 && variant != 2)) return -1.0;
+  double a, b;
+  if (!power_fit(v->lr[variant - 1], v->lm[variant - 1], &a, &b)) return -1.0;
+  return std::exp(a + b * std::log((double)rows));
+}
+
+void lms_variant_analytic_state(const lms_variant_analytic* v, double* infpt_bytes,
+                                int64_t* picks) {
+  if (!v) return;
+  if (infpt_bytes) *infpt_bytes = v->infpt;
+  if (picks) {
+    picks[0] = v->picks[0];
+    picks[1] = v->picks[1];
+  }
 }
 
 lms_regressor* lms_regressor_create(int32_t history_len) {

@@ -138,6 +138,10 @@ struct lms_stream {
   cudaEvent_t qev[kMaxQueries][6] = {};  // E1, E2, sort/reduce
   lms_stats stats{};
   long long wm = LLONG_MIN;
+  // fused-pass variant chooser installed by lms_stream_set_variant_chooser
+  lms_variant_chooser vc = nullptr;
+  lms_variant_observer vo = nullptr;
+  void* vctx = nullptr;
 };
 
 namespace {
@@ -323,6 +327,10 @@ Tune& tune_slot(const lms_stream* s, long long n) {
 
 int pick_k1_variant(lms_stream* s, long long n, bool* tuning) {
   *tuning = false;
+  if (s->vc) {
+    const int v = s->vc(s->vctx, n, (int32_t)s->qs.size());
+    return (v >= 1 && v <= 4) ? v : 1;
+  }
   if (s->cfg.k1_variant >= 1 && s->cfg.k1_variant <= 4) return s->cfg.k1_variant;
   if (n < (1ll << 15)) return 1;
   std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -599,7 +607,7 @@ lms_status run_batch(lms_stream* s, const InSeg* seg, int nseg, long long n, int
   if (timing) LMS_CK(cudaEventRecord(s->ev[5], s->st));
   int launches = 0;
   int variant = 1;
-  bool tuning = false;
+  bool tuning = false, timed_k1 = false;
   QCtl* ctls[kMaxQueries];
   const int nq = (int)s->qs.size();
   for (int i = 0; i < nq; ++i) ctls[i] = s->qs[i].dev.ctl;
@@ -608,7 +616,8 @@ lms_status run_batch(lms_stream* s, const InSeg* seg, int nseg, long long n, int
   if (timing) LMS_CK(cudaEventRecord(s->ev[1], s->st));
   if (n > 0) {
     variant = pick_k1_variant(s, n, &tuning);
-    if (tuning) LMS_CK(cudaEventRecord(s->tev[0], s->st));
+    timed_k1 = tuning || s->vo != nullptr;
+    if (timed_k1) LMS_CK(cudaEventRecord(s->tev[0], s->st));
     for (int g = 0; g < nseg; ++g) {  // one fused pass per contiguous piece of the batch
       if (seg[g].n == 0) continue;
       K1Args a{};
@@ -627,7 +636,7 @@ lms_status run_batch(lms_stream* s, const InSeg* seg, int nseg, long long n, int
       ++launches;
       ++s->stats.k1_launches;
     }
-    if (tuning) LMS_CK(cudaEventRecord(s->tev[1], s->st));
+    if (timed_k1) LMS_CK(cudaEventRecord(s->tev[1], s->st));
     s->stats.k1_tile_events = (uint64_t)k1_tile_events(variant);
   }
   if (timing) LMS_CK(cudaEventRecord(s->ev[2], s->st));
@@ -701,9 +710,13 @@ lms_status run_batch(lms_stream* s, const InSeg* seg, int nseg, long long n, int
   }
   std::vector<QCtl> hc(nq);
   if ((r = read_ctls(s, hc.data())) != LMS_OK) return r;
-  if (tuning) {
+  if (timed_k1) {
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, s->tev[0], s->tev[1]) == cudaSuccess) record_k1_sample(s, n, variant, ms);
+    if (cudaEventElapsedTime(&ms, s->tev[0], s->tev[1]) == cudaSuccess) {
+      if (tuning) record_k1_sample(s, n, variant, ms);
+      if (s->vo) s->vo(s->vctx, n, variant, (double)ms);
+    }
+    cudaGetLastError();
   }
   // retry emission for queries whose buffers were too small
   bool retried = false;
@@ -1004,6 +1017,16 @@ lms_status lms_results_discard(lms_stream* s, int32_t query_id) {
   const unsigned long long zero = 0;
   LMS_CK(cudaMemcpyAsync(&q.dev.ctl->row_base, &zero, sizeof(zero), cudaMemcpyHostToDevice, s->st));
   LMS_CK(cudaStreamSynchronize(s->st));
+  return LMS_OK;
+}
+
+lms_status lms_stream_set_variant_chooser(lms_stream* s, lms_variant_chooser choose,
+                                          lms_variant_observer observe, void* ctx) {
+  if (!s) return LMS_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->vc = choose;
+  s->vo = observe;
+  s->vctx = ctx;
   return LMS_OK;
 }
 

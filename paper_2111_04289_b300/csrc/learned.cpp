@@ -35,6 +35,25 @@ struct lms_learned {
   bool host_input = true;  // the batches' columns come from host memory (H2D is an operator)
 };
 
+// Learned chooser of the fused pass's variant: the network predicts the pass's
+// time for each variant (operator code LMS_OP_K1_VARIANT(v)); the analytic
+// chooser (Alg. 2 around the Eq. 9 inflection point) is the fallback and the
+// judge, exactly as Eq. 5 is for the batch-time predictor.
+struct lms_variant_learned {
+  lms_mlp* m = nullptr;
+  lms_variant_analytic* an = nullptr;
+  double key_card = 1, selectivity = 1, panes = 1, nq = 1;
+  std::vector<float> x, t;
+  int count = 0, head = 0;
+  bool trained = false;
+  int refit_every = 0, refit_steps = 0;
+  float lr = 1e-3f;
+  long long obs = 0, choices = 0;
+  double err_net = 0.0, err_an = 0.0;
+  long long judged = 0, uses_net = 0, uses_an = 0;
+  long long picks[2] = {0, 0};
+};
+
 namespace {
 
 // Sum over the operators (no H2D when the input is already on the device) of
@@ -56,12 +75,22 @@ double net_predict_ms(lms_learned* l, double rows, double carried, double span_p
   return us * 1e-3;
 }
 
-void push_sample(lms_learned* l, const float* x, float t) {
+template <class L>
+void push_sample(L* l, const float* x, float t) {
   const int cap = LMS_MLP_MAX_BATCH;
   std::copy(x, x + LMS_MLP_INPUTS, l->x.begin() + (size_t)l->head * LMS_MLP_INPUTS);
   l->t[l->head] = t;
   l->head = (l->head + 1) % cap;
   l->count = std::min(l->count + 1, cap);
+}
+
+// The network's fused-pass time of `variant` for `rows` rows, ms (< 0 on error).
+double net_variant_ms(lms_variant_learned* v, double rows, int variant) {
+  float x[LMS_MLP_INPUTS], y = 0.f;
+  lms_cost_features(rows, 0.0, v->key_card, v->selectivity, v->panes, v->nq, 0.0,
+                    LMS_OP_K1_VARIANT(variant), x);
+  if (lms_mlp_forward(v->m, x, 1, &y) != LMS_OK) return -1.0;
+  return std::exp((double)y) * 1e-3;
 }
 
 float log_us(double ms) { return (float)std::log(std::max(1.0, ms * 1e3)); }
@@ -214,6 +243,101 @@ double lms_learned_predict(void* ctx, double batch_bytes, int32_t n_datasets) {
   }
   ++l->uses_net;
   return p;
+}
+
+lms_variant_learned* lms_variant_learned_create(lms_mlp* m, lms_variant_analytic* judge,
+                                                double key_card, double selectivity,
+                                                double panes_per_window, double n_queries) {
+  if (!m || !judge) return nullptr;
+  lms_variant_learned* v = new lms_variant_learned();
+  v->m = m;
+  v->an = judge;
+  v->key_card = key_card;
+  v->selectivity = selectivity;
+  v->panes = panes_per_window;
+  v->nq = n_queries;
+  v->x.assign((size_t)LMS_MLP_MAX_BATCH * LMS_MLP_INPUTS, 0.f);
+  v->t.assign(LMS_MLP_MAX_BATCH, 0.f);
+  return v;
+}
+
+void lms_variant_learned_destroy(lms_variant_learned* v) { delete v; }
+
+void lms_variant_learned_set_online(lms_variant_learned* v, int32_t refit_every,
+                                    int32_t refit_steps, float lr) {
+  if (!v) return;
+  v->refit_every = std::max(0, refit_every);
+  v->refit_steps = std::max(0, refit_steps);
+  v->lr = lr > 0 ? lr : 1e-3f;
+}
+
+lms_status lms_variant_learned_fit(lms_variant_learned* v, int32_t steps, float lr, float* loss) {
+  if (!v || steps < 0) return LMS_EINVAL;
+  if (v->count == 0) return LMS_EAGAIN;
+  const lms_status r =
+      lms_mlp_train(v->m, v->x.data(), v->t.data(), v->count, steps, lr, nullptr, loss);
+  if (r == LMS_OK && steps > 0) v->trained = true;
+  return r;
+}
+
+int32_t lms_variant_learned_choose(void* ctx, int64_t rows, int32_t n_queries) {
+  lms_variant_learned* v = static_cast<lms_variant_learned*>(ctx);
+  ++v->choices;
+  // the analytic recommendation (it also explores both variants first)
+  const int32_t an_pick = lms_variant_analytic_choose(v->an, rows, n_queries);
+  int32_t pick = an_pick;
+  const bool net_ok = v->trained && !(v->judged >= 5 && v->err_net > v->err_an);
+  if (net_ok) {
+    const double p1 = net_variant_ms(v, (double)rows, 1), p2 = net_variant_ms(v, (double)rows, 2);
+    if (p1 > 0 && p2 > 0) {
+      pick = p1 <= p2 ? 1 : 2;
+      if (v->choices % 16 == 0) pick = 3 - pick;  // keep measuring the other variant
+      ++v->uses_net;
+    } else {
+      ++v->uses_an;
+    }
+  } else {
+    ++v->uses_an;
+  }
+  ++v->picks[pick - 1];
+  return pick;
+}
+
+void lms_variant_learned_observe(void* ctx, int64_t rows, int32_t variant, double ms) {
+  lms_variant_learned* v = static_cast<lms_variant_learned*>(ctx);
+  if (!v || rows < 1 || !(ms > 0) || (variant != 1 && variant != 2)) return;
+  // judge both models on this pass before either learns from it
+  if (v->trained) {
+    const double pn = net_variant_ms(v, (double)rows, variant);
+    const double pa = lms_variant_analytic_predict(v->an, rows, variant);
+    if (pn > 0 && pa > 0) {
+      const double a = v->judged < 10 ? 1.0 / (double)(v->judged + 1) : 0.1;
+      v->err_net += a * (std::fabs(std::log(pn / ms)) - v->err_net);
+      v->err_an += a * (std::fabs(std::log(pa / ms)) - v->err_an);
+      ++v->judged;
+    }
+  }
+  lms_variant_analytic_observe(v->an, rows, variant, ms);
+  float x[LMS_MLP_INPUTS];
+  lms_cost_features((double)rows, 0.0, v->key_card, v->selectivity, v->panes, v->nq, 0.0,
+                    LMS_OP_K1_VARIANT(variant), x);
+  push_sample(v, x, log_us(ms));
+  ++v->obs;
+  if (v->refit_every > 0 && v->refit_steps > 0 && v->obs % v->refit_every == 0)
+    lms_variant_learned_fit(v, v->refit_steps, v->lr, nullptr);
+}
+
+void lms_variant_learned_stats(const lms_variant_learned* v, double* err_net, double* err_an,
+                               int64_t* uses_net, int64_t* uses_an, int64_t* picks) {
+  if (!v) return;
+  if (err_net) *err_net = v->err_net;
+  if (err_an) *err_an = v->err_an;
+  if (uses_net) *uses_net = v->uses_net;
+  if (uses_an) *uses_an = v->uses_an;
+  if (picks) {
+    picks[0] = v->picks[0];
+    picks[1] = v->picks[1];
+  }
 }
 
 }  // extern "C"

@@ -101,7 +101,14 @@ EXPORTED_SYMBOLS = ("stream_open", "query_register", "push_microbatch", "poll_re
                     "lms_stream_device_bytes", "lms_server_create", "lms_server_submit",
                     "lms_server_wait", "lms_server_forget", "lms_server_get_stats",
                     "lms_server_destroy", "lms_server_create_ops", "lms_k1_tuned_variant",
-                    "lms_ingest", "lms_push_ingested", "lms_ingest_pending")
+                    "lms_ingest", "lms_push_ingested", "lms_ingest_pending",
+                    "lms_stream_set_variant_chooser", "lms_variant_analytic_create",
+                    "lms_variant_analytic_destroy", "lms_variant_analytic_choose",
+                    "lms_variant_analytic_observe", "lms_variant_analytic_predict",
+                    "lms_variant_analytic_state", "lms_variant_learned_create",
+                    "lms_variant_learned_destroy", "lms_variant_learned_set_online",
+                    "lms_variant_learned_fit", "lms_variant_learned_choose",
+                    "lms_variant_learned_observe", "lms_variant_learned_stats")
 ADMIT_PAPER, ADMIT_GUARDED = 0, 1
 QOPS = {"aggregation": 0, "filter": 1, "shuffle": 2, "project": 3, "join": 4, "expand": 5,
         "scan": 6, "sort": 7}
@@ -228,6 +235,30 @@ def load(build_if_missing: bool = True):
     lib.lms_push_ingested.argtypes = [P, ctypes.c_int64, ctypes.c_uint32]
     lib.lms_ingest_pending.restype = ctypes.c_int32
     lib.lms_ingest_pending.argtypes = [P, P]
+    lib.lms_stream_set_variant_chooser.restype = ctypes.c_int32
+    lib.lms_stream_set_variant_chooser.argtypes = [P, P, P, P]
+    lib.lms_variant_analytic_create.restype = P
+    lib.lms_variant_analytic_create.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                                ctypes.c_int32, ctypes.c_int32]
+    lib.lms_variant_analytic_destroy.argtypes = [P]
+    lib.lms_variant_analytic_choose.restype = ctypes.c_int32
+    lib.lms_variant_analytic_choose.argtypes = [P, ctypes.c_int64, ctypes.c_int32]
+    lib.lms_variant_analytic_observe.argtypes = [P, ctypes.c_int64, ctypes.c_int32, ctypes.c_double]
+    lib.lms_variant_analytic_predict.restype = ctypes.c_double
+    lib.lms_variant_analytic_predict.argtypes = [P, ctypes.c_int64, ctypes.c_int32]
+    lib.lms_variant_analytic_state.argtypes = [P, P, P]
+    lib.lms_variant_learned_create.restype = P
+    lib.lms_variant_learned_create.argtypes = [P, P, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_double, ctypes.c_double]
+    lib.lms_variant_learned_destroy.argtypes = [P]
+    lib.lms_variant_learned_set_online.argtypes = [P, ctypes.c_int32, ctypes.c_int32,
+                                                   ctypes.c_float]
+    lib.lms_variant_learned_fit.restype = ctypes.c_int32
+    lib.lms_variant_learned_fit.argtypes = [P, ctypes.c_int32, ctypes.c_float, P]
+    lib.lms_variant_learned_choose.restype = ctypes.c_int32
+    lib.lms_variant_learned_choose.argtypes = [P, ctypes.c_int64, ctypes.c_int32]
+    lib.lms_variant_learned_observe.argtypes = [P, ctypes.c_int64, ctypes.c_int32, ctypes.c_double]
+    lib.lms_variant_learned_stats.argtypes = [P, P, P, P, P, P]
     lib.lms_aggregate_batch_static.restype = ctypes.c_int32
     lib.lms_aggregate_batch_static.argtypes = [
         ctypes.POINTER(QuerySpec), ctypes.c_int32, P, P, P, P, ctypes.c_int64, P, P,
@@ -468,6 +499,14 @@ class Stream:
         self._check(self._lib.lms_ingest_pending(self._h, ctypes.byref(n)), "lms_ingest_pending")
         return n.value
 
+    def set_variant_chooser(self, chooser) -> None:
+        """Installs a VariantAnalytic / VariantLearned (or None) as the chooser of
+        the fused pass's variant."""
+        self._chooser = chooser
+        hooks = (None, None, None) if chooser is None else chooser.hooks()
+        self._check(self._lib.lms_stream_set_variant_chooser(self._h, *hooks),
+                    "lms_stream_set_variant_chooser")
+
     def poll(self, qid: int, max_rows: Optional[int] = None) -> np.ndarray:
         """All (or up to max_rows) pending rows of query qid, oldest first."""
         avail = self.pending(qid)
@@ -567,6 +606,99 @@ def aggregate_batch_static(ts, key, value, type_=None, *, value_type: str, size_
     if st != LMS_OK:
         raise LmsError(st, "lms_aggregate_batch_static")
     return n.value
+
+
+class VariantAnalytic:
+    """lms_variant_analytic: Alg. 2 + Eq. 9 chooser of the fused pass's variant."""
+
+    def __init__(self, partitions: int = 148, bytes_per_row: float = 16.0,
+                 infpt0: float = 150 * 1024, history: int = 0, explore: int = 2):
+        self._lib = load()
+        self._h = self._lib.lms_variant_analytic_create(int(partitions), float(bytes_per_row),
+                                                        float(infpt0), int(history), int(explore))
+        if not self._h:
+            raise LmsError(LMS_EINVAL, "lms_variant_analytic_create")
+
+    def choose(self, rows: int, n_queries: int = 1) -> int:
+        return int(self._lib.lms_variant_analytic_choose(self._h, int(rows), int(n_queries)))
+
+    def observe(self, rows: int, variant: int, ms: float) -> None:
+        self._lib.lms_variant_analytic_observe(self._h, int(rows), int(variant), float(ms))
+
+    def predict(self, rows: int, variant: int) -> float:
+        return float(self._lib.lms_variant_analytic_predict(self._h, int(rows), int(variant)))
+
+    def state(self) -> dict:
+        inf = ctypes.c_double()
+        picks = (ctypes.c_int64 * 2)()
+        self._lib.lms_variant_analytic_state(self._h, ctypes.byref(inf), picks)
+        return {"infpt_bytes": inf.value, "picks": [picks[0], picks[1]]}
+
+    def hooks(self):
+        lib = self._lib
+        return (ctypes.cast(lib.lms_variant_analytic_choose, ctypes.c_void_p).value,
+                ctypes.cast(lib.lms_variant_analytic_observe, ctypes.c_void_p).value, self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lms_variant_analytic_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class VariantLearned:
+    """lms_variant_learned: the network's chooser of the fused pass's variant,
+    with a VariantAnalytic as fallback and judge."""
+
+    def __init__(self, mlp, judge: VariantAnalytic, *, key_card, selectivity, panes, n_queries):
+        self._lib = load()
+        self.judge = judge
+        self._h = self._lib.lms_variant_learned_create(mlp.handle, judge._h, float(key_card),
+                                                       float(selectivity), float(panes),
+                                                       float(n_queries))
+        if not self._h:
+            raise LmsError(LMS_EINVAL, "lms_variant_learned_create")
+
+    def set_online(self, refit_every: int, refit_steps: int, lr: float = 1e-3):
+        self._lib.lms_variant_learned_set_online(self._h, int(refit_every), int(refit_steps),
+                                                 float(lr))
+
+    def fit(self, steps: int, lr: float = 1e-3) -> float:
+        loss = ctypes.c_float()
+        st = self._lib.lms_variant_learned_fit(self._h, int(steps), float(lr), ctypes.byref(loss))
+        if st not in (LMS_OK, LMS_EAGAIN):
+            raise LmsError(st, "lms_variant_learned_fit")
+        return float(loss.value)
+
+    def stats(self) -> dict:
+        en, ea = ctypes.c_double(), ctypes.c_double()
+        un, ua = ctypes.c_int64(), ctypes.c_int64()
+        picks = (ctypes.c_int64 * 2)()
+        self._lib.lms_variant_learned_stats(self._h, ctypes.byref(en), ctypes.byref(ea),
+                                            ctypes.byref(un), ctypes.byref(ua), picks)
+        return {"err_net": en.value, "err_analytic": ea.value, "uses_net": un.value,
+                "uses_analytic": ua.value, "picks": [picks[0], picks[1]]}
+
+    def hooks(self):
+        lib = self._lib
+        return (ctypes.cast(lib.lms_variant_learned_choose, ctypes.c_void_p).value,
+                ctypes.cast(lib.lms_variant_learned_observe, ctypes.c_void_p).value, self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lms_variant_learned_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Admission:

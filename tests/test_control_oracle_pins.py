@@ -167,3 +167,49 @@ def test_fig4_scenario_slide_time_bounds_latency():
     lm = _simulate("lmstream")
     assert len(trig) > 10 and min(trig) > 3000.0
     assert len(lm) > 10 and max(lm) < 3000.0
+
+
+def test_variant_choice_threshold_of_alg2_on_one_operation():
+    """One Aggregation (base cost 1) with r = Part / InfPT: Eq. 6 gives r for
+    variant 1, Eq. 7 1/r for variant 2, and Eq. 8's transition 0.1 r is charged
+    to variant 2 (the chain's first operation): variant 1 iff 1/r + 0.1 r > r,
+    i.e. r < sqrt(1 / 0.9)."""
+    infpt, parts, bpr = 150 * 1024, 148, 16.0
+    v = oc.VariantAnalytic(parts, bpr, infpt, explore=0)
+    r_star = np.sqrt(1 / 0.9)
+    for r in (0.01, 0.5, 1.0, 1.05, 1.06, 2.0, 50.0):
+        rows = int(round(r * infpt * parts / bpr))
+        r_act = rows * bpr / parts / infpt
+        assert v.choose(rows) == (1 if r_act < r_star else 2), r
+
+
+def test_variant_crossover_of_exact_power_laws():
+    """Exact costs ms_v = c_v rows^b_v: the fits are exact, the observed
+    inflection point is their crossing (c1/c2)^(1/(b2 - b1)) rows, and Eq. 9 on a
+    constant target returns it."""
+    parts, bpr = 148, 16.0
+    c1, b1, c2, b2 = 2e-6, 1.0, 4e-3, 0.55
+    cross = (c1 / c2) ** (1.0 / (b2 - b1))  # ~2.2e7 rows
+    v = oc.VariantAnalytic(parts, bpr, explore=2)
+    # the extreme sizes first, so that every fit's range holds the crossing
+    for rows in [1 << 20, 1 << 26, 1 << 22, 1 << 24, 3 << 20, 5 << 22]:
+        for var, c, b in ((1, c1, b1), (2, c2, b2)):
+            v.observe(rows, var, c * rows ** b)
+    assert v.infpt == pytest.approx(cross * bpr / parts, rel=1e-9)
+    assert v.predict(1 << 23, 2) == pytest.approx(c2 * (1 << 23) ** b2, rel=1e-9)
+    # below the crossing variant 1 is cheaper, above it variant 2
+    assert v.choose(int(cross / 4)) == 1 and v.choose(int(cross * 4)) == 2
+
+
+def test_variant_without_crossing_takes_the_far_end():
+    """Variant 1 cheaper at every size seen: the observed inflection point is
+    twice the largest size seen so far (Eq. 9 over the last sample only, so the
+    inflection point is that sample), and variant 1 stays chosen."""
+    parts, bpr = 148, 16.0
+    v = oc.VariantAnalytic(parts, bpr, explore=2, history=1)
+    sizes = [1 << 16, 1 << 18, 1 << 20]
+    for rows in sizes:
+        v.observe(rows, 1, 1e-6 * rows)
+        v.observe(rows, 2, 3e-6 * rows)
+    assert v.infpt == pytest.approx(2 * max(sizes) * bpr / parts, rel=1e-9)
+    assert all(v.choose(r) == 1 for r in sizes)

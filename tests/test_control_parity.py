@@ -110,3 +110,28 @@ def test_eq9_degenerate_branch_matches_oracle(t, l, y):
     assert st == (0 if len(y) >= 3 else -3)
     np.testing.assert_array_equal(beta, rb)
     assert pred == rp
+
+
+def test_variant_analytic_chooser_matches_oracle():
+    """The engine's analytic variant chooser against the oracle's on noisy
+    power-law pass times: the same picks and the same inflection point after
+    every pass."""
+    rng = np.random.default_rng(21)
+    eng = lm.VariantAnalytic(148, 16.0, 150 * 1024, history=12, explore=2)
+    orc = oc.VariantAnalytic(148, 16.0, 150 * 1024, history=12, explore=2)
+    for k in range(120):
+        rows = int(2 ** rng.uniform(12, 26))
+        pe, po = eng.choose(rows), orc.choose(rows)
+        assert pe == po, k
+        c, b = (2e-6, 1.0) if pe == 1 else (4e-3, 0.55)
+        ms = c * rows ** b * float(np.exp(rng.normal(0, 0.05)))
+        eng.observe(rows, pe, ms)
+        orc.observe(rows, pe, ms)
+        assert eng.state()["infpt_bytes"] == pytest.approx(orc.infpt, rel=1e-9), k
+        for v in (1, 2):
+            pe_, po_ = eng.predict(rows, v), orc.predict(rows, v)
+            assert (pe_ < 0) == (po_ < 0)
+            if po_ > 0:
+                assert pe_ == pytest.approx(po_, rel=1e-9)
+    assert eng.state()["picks"] == [orc.picks[1], orc.picks[2]]
+    eng.close()
