@@ -28,6 +28,8 @@ _lib = None
 # the engine's public header because both follow the same query description).
 COL_TS, COL_KEY, COL_VALUE, COL_TYPE = 0, 1, 2, 3
 OP_NONE, OP_EQ, OP_NE, OP_LT, OP_LE, OP_GT, OP_GE = 0, 1, 2, 3, 4, 5, 6
+# Aggregates a HAVING or ORDER BY refers to.
+AGGS = {"count": 1, "sum": 2, "min": 3, "max": 4, "avg": 5}
 
 ROW_DTYPE = np.dtype(
     [
@@ -92,6 +94,11 @@ def _load():
         lib.oracle_late_rows.argtypes = [ctypes.c_void_p, ctypes.c_int]
         lib.oracle_open_groups.restype = ctypes.c_int64
         lib.oracle_open_groups.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        lib.oracle_set_post.restype = ctypes.c_int
+        lib.oracle_set_post.argtypes = [
+            ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, ctypes.c_int, ctypes.c_int,
+            ctypes.c_double, ctypes.c_int, ctypes.c_int,
+        ]
         lib.oracle_row_size.restype = ctypes.c_int64
         assert lib.oracle_row_size() == ROW_DTYPE.itemsize
         _lib = lib
@@ -127,6 +134,18 @@ class WindowAggOracle:
         if q < 0:
             raise ValueError("invalid window: size must be a positive multiple of slide")
         return q
+
+    def set_post(self, qid: int, group_mask: int = 0xFFFFFFFF, having=None, order_by=None):
+        """Post-aggregation of query qid: group by key & group_mask; having =
+        (agg, op, value) keeps rows with (double)agg OP value; order_by =
+        (agg, descending) sorts each window's rows by the aggregate (ties in key
+        order).  agg: one of AGGS."""
+        ha, ho, hv = (0, OP_NONE, 0.0) if having is None else (AGGS[having[0]], having[1],
+                                                               float(having[2]))
+        oa, od = (0, 0) if order_by is None else (AGGS[order_by[0]], int(bool(order_by[1])))
+        if self._lib.oracle_set_post(self._h, int(qid), int(group_mask) & 0xFFFFFFFF, ha, int(ho),
+                                     hv, oa, od) != 0:
+            raise ValueError("bad post-aggregation")
 
     def push(self, ts, key, value, type_=None, eos: bool = False):
         ts = np.ascontiguousarray(ts, dtype=np.int64)

@@ -28,6 +28,16 @@
 //      the batch, filtered or not, - allowed_lateness).  Every group whose
 //      window end is <= watermark is emitted, in (window start, key) order, with
 //      avg = (double)sum / count, and deleted.  End of stream emits everything.
+//   6. post-aggregation (Table III: LR2S's HAVING, CM1's ORDER BY, the
+//      multi-column GROUP BY of LR2S), per query and optional:
+//      * GROUP BY a subset of the key's packed fields: the group key is
+//        key & group_mask (the bits of the selected fields);
+//      * HAVING agg OP c: an emitted row is kept iff (double)agg OP c (the
+//        same IEEE comparison as the filter), agg one of count, sum, min,
+//        max, avg;
+//      * ORDER BY agg: the rows of each window come out sorted by the
+//        aggregate's value (ascending, or descending), equal values in key
+//        order (a stable sort of the key-ordered rows).
 // Parity pins for this file live in tests/test_oracle_pins.py (brute force per
 // window on tiny streams, invariants, special cases that reduce to numpy
 // group-by routines, hand-worked fixtures).
@@ -35,6 +45,7 @@
 #include <cstdint>
 #include <cstring>
 #include <cstdlib>
+#include <algorithm>
 #include <map>
 #include <utility>
 #include <vector>
@@ -68,6 +79,10 @@ struct OracleQuery {
   double filter_f = 0.0;
   int64_t size = 1;
   int64_t slide = 1;
+  uint32_t group_mask = 0xffffffffu;
+  int having_agg = 0, having_op = OP_NONE;
+  double having_value = 0.0;
+  int order_agg = 0, order_desc = 0;
   // Per (window start, key) group.
   struct Agg {
     int64_t count = 0;
@@ -137,7 +152,31 @@ struct Oracle {
   std::vector<OracleQuery> queries;
 };
 
+// The value of aggregate `agg` (1 count, 2 sum, 3 min, 4 max, 5 avg) of a row.
+double agg_value(const Oracle& o, const OracleRow& r, int agg) {
+  switch (agg) {
+    case 1: return (double)r.count;
+    case 2: return o.value_is_float ? r.sum_f : (double)r.sum_i;
+    case 3: return o.value_is_float ? (double)r.min_f : (double)r.min_i;
+    case 4: return o.value_is_float ? (double)r.max_f : (double)r.max_i;
+    default: return r.avg;
+  }
+}
+
+// Sorts the rows of one window, out[from ..], by the ORDER BY aggregate.
+void order_window(const Oracle& o, const OracleQuery& q, std::vector<OracleRow>& out,
+                  size_t from) {
+  std::stable_sort(out.begin() + (long)from, out.end(),
+                   [&](const OracleRow& x, const OracleRow& y) {
+                     const double a = agg_value(o, x, q.order_agg), b = agg_value(o, y, q.order_agg);
+                     return q.order_desc ? a > b : a < b;
+                   });
+}
+
 void emit_closed(Oracle& o, OracleQuery& q, bool all) {
+  size_t win_from = q.out.size();
+  int64_t win_start = 0;
+  bool have_win = false;
   auto it = q.groups.begin();
   while (it != q.groups.end()) {
     int64_t start = it->first.first;
@@ -160,9 +199,18 @@ void emit_closed(Oracle& o, OracleQuery& q, bool all) {
       r.max_i = a.max_i;
       r.avg = (double)a.sum_i / (double)a.count;
     }
-    q.out.push_back(r);
     it = q.groups.erase(it);
+    if (q.having_agg && !compare_f(q.having_op, agg_value(o, r, q.having_agg), q.having_value))
+      continue;
+    if (q.order_agg && (!have_win || start != win_start)) {
+      if (have_win) order_window(o, q, q.out, win_from);
+      win_from = q.out.size();
+      win_start = start;
+      have_win = true;
+    }
+    q.out.push_back(r);
   }
+  if (q.order_agg && have_win) order_window(o, q, q.out, win_from);
 }
 
 }  // namespace
@@ -218,12 +266,13 @@ int oracle_push(void* h, int64_t n, const int64_t* ts, const uint32_t* key,
       if (!pass) continue;
       // 2-4. every window containing ts that is still open
       const int64_t w0 = floor_div(ts[e], q.slide);
+      const uint32_t gk = key[e] & q.group_mask;
       bool any_open = false;
       for (int64_t k = 0; k < K; ++k) {
         const int64_t start = (w0 - k) * q.slide;
         if (o->have_wm && start + q.size <= o->wm) continue;  // already emitted
         any_open = true;
-        OracleQuery::Agg& a = q.groups[std::make_pair(start, key[e])];
+        OracleQuery::Agg& a = q.groups[std::make_pair(start, gk)];
         if (o->value_is_float) {
           const float v = vf[e];
           if (a.count == 0) {
@@ -265,6 +314,24 @@ int oracle_push(void* h, int64_t n, const int64_t* ts, const uint32_t* key,
     else if (o->have_wm)
       emit_closed(*o, q, false);
   }
+  return 0;
+}
+
+// Post-aggregation of query qid (see item 6 above): group_mask, HAVING (agg
+// 0 = none) and ORDER BY (agg 0 = none).  Must precede the first push.
+int oracle_set_post(void* h, int qid, uint32_t group_mask, int having_agg, int having_op,
+                    double having_value, int order_agg, int order_desc) {
+  Oracle* o = static_cast<Oracle*>(h);
+  if (qid < 0 || qid >= (int)o->queries.size() || having_agg < 0 || having_agg > 5 ||
+      order_agg < 0 || order_agg > 5)
+    return -1;
+  OracleQuery& q = o->queries[qid];
+  q.group_mask = group_mask;
+  q.having_agg = having_agg;
+  q.having_op = having_op;
+  q.having_value = having_value;
+  q.order_agg = order_agg;
+  q.order_desc = order_desc;
   return 0;
 }
 

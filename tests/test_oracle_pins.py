@@ -272,3 +272,94 @@ def test_emission_respects_watermark():
     o.push(np.zeros(0, np.int64), np.zeros(0, np.uint32), np.zeros(0, np.int32), None, eos=True)
     rows = o.take_rows(qid)
     assert np.all(rows["window_end"] > wm)
+
+
+# --------------------------------------------------------------------------- #
+# post-aggregation: GROUP BY packed key fields, HAVING, ORDER BY (Table III)
+# --------------------------------------------------------------------------- #
+
+def _brute_groups(ts, key, val, size, slide, mask):
+    """{(window start, key & mask): (count, sum, min, max)} from the events."""
+    K = size // slide
+    out = {}
+    for t, k, v in zip(ts.tolist(), (key & np.uint32(mask)).tolist(), val.tolist()):
+        w0 = t // slide
+        for j in range(K):
+            g = ((w0 - j) * slide, k)
+            c, s, mn, mx = out.get(g, (0, 0, None, None))
+            out[g] = (c + 1, s + v, v if mn is None else min(mn, v), v if mx is None else max(mx, v))
+    return out
+
+
+def _three_field_stream(seed, n=3000):
+    """Key = highway (4 bits) | direction (1 bit) << 4 | segment (7 bits) << 5,
+    int speeds 0..120 (the LR2S query's shape)."""
+    rng = np.random.default_rng(seed)
+    hw, dr, sg = rng.integers(0, 3, n), rng.integers(0, 2, n), rng.integers(0, 20, n)
+    key = (hw | (dr << 4) | (sg << 5)).astype(np.uint32)
+    ts = np.sort(rng.integers(0, 9000, n)).astype(np.int64)
+    val = rng.integers(0, 121, n).astype(np.int32)
+    return ts, key, val
+
+
+@pytest.mark.parametrize("mask", [0xFFFFFFFF, 0b11111, 0b111111100000, 0b1111])
+def test_group_by_key_fields_equals_brute_force(mask):
+    ts, key, val = _three_field_stream(5)
+    o = wa.WindowAggOracle(False, 0)
+    q = o.add_query(size_ms=3000, slide_ms=1000)
+    o.set_post(q, group_mask=mask)
+    o.push(ts, key, val, None, eos=True)
+    rows = o.take_rows(q)
+    exp = _brute_groups(ts, key, val, 3000, 1000, mask)
+    assert len(rows) == len(exp)
+    assert all(int(r["key"]) & ~mask & 0xFFFFFFFF == 0 for r in rows)
+    for r in rows:
+        c, s, mn, mx = exp[(int(r["window_start"]), int(r["key"]))]
+        assert (int(r["count"]), int(r["sum_i"]), int(r["min_i"]), int(r["max_i"])) == (c, s, mn, mx)
+
+
+@pytest.mark.parametrize("having", [("avg", wa.OP_LT, 40.0), ("count", wa.OP_GE, 30),
+                                    ("max", wa.OP_EQ, 120), ("sum", wa.OP_NE, 0)])
+def test_having_keeps_the_rows_whose_aggregate_passes(having):
+    """LR2S: ... GROUPBY (highway, direction, segment) HAVING avgSpeed < 40."""
+    ts, key, val = _three_field_stream(6)
+    o = wa.WindowAggOracle(False, 0)
+    q = o.add_query(size_ms=3000, slide_ms=1000)
+    o.set_post(q, group_mask=0b111111111111, having=having)
+    o.push(ts, key, val, None, eos=True)
+    rows = o.take_rows(q)
+    agg, op, c = having
+    pick = {"count": 0, "sum": 1, "min": 2, "max": 3}
+    test = {wa.OP_LT: np.less, wa.OP_GE: np.greater_equal, wa.OP_EQ: np.equal,
+            wa.OP_NE: np.not_equal}[op]
+    exp = sorted(g for g, a in _brute_groups(ts, key, val, 3000, 1000, 0xFFF).items()
+                 if test(a[1] / a[0] if agg == "avg" else a[pick[agg]], c))
+    assert [(int(r["window_start"]), int(r["key"])) for r in rows] == exp
+
+
+@pytest.mark.parametrize("agg,desc", [("sum", False), ("sum", True), ("count", True),
+                                      ("min", False)])
+def test_order_by_sorts_each_window_by_the_aggregate(agg, desc):
+    """CM1: ... GROUPBY category ORDERBY SUM(cpu): per window, rows sorted by
+    the aggregate, equal values in key order (numpy.lexsort on (key, value))."""
+    rng = np.random.default_rng(7)
+    n = 4000
+    ts = np.sort(rng.integers(0, 20_000, n)).astype(np.int64)
+    key = rng.integers(0, 30, n).astype(np.uint32)
+    val = rng.integers(0, 5, n).astype(np.int32)  # many equal aggregates
+    o = wa.WindowAggOracle(False, 0)
+    q = o.add_query(size_ms=6000, slide_ms=2000)
+    o.set_post(q, order_by=(agg, desc))
+    o.push(ts[: n // 2], key[: n // 2], val[: n // 2], None)
+    o.push(ts[n // 2:], key[n // 2:], val[n // 2:], None, eos=True)
+    rows = o.take_rows(q)
+    exp = _brute_groups(ts, key, val, 6000, 2000, 0xFFFFFFFF)
+    pick = {"count": 0, "sum": 1, "min": 2, "max": 3}[agg]
+    starts = sorted({g[0] for g in exp})
+    expected = []
+    for w in starts:
+        ks = np.array(sorted(k for (s, k) in exp if s == w), dtype=np.int64)
+        vs = np.array([exp[(w, int(k))][pick] for k in ks], dtype=np.int64)
+        order = np.lexsort((ks, -vs if desc else vs))
+        expected += [(w, int(k)) for k in ks[order]]
+    assert [(int(r["window_start"]), int(r["key"])) for r in rows] == expected
