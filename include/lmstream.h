@@ -117,7 +117,10 @@ typedef struct lms_stream_config {
                                   earlier windows, us; 0 = 4 s.  When it runs out the push
                                   returns LMS_EDEVICE (latched) instead of waiting longer. */
   uint32_t debug_flags;        /* LMS_DEBUG_*: test hooks, 0 in normal use */
-  int32_t reserved[4];
+  uint32_t key_fields;         /* the key column as up to four packed fields: byte f holds the
+                                  bit width of field f (field 0 in the lowest bits); 0 = one
+                                  32-bit field.  Widths must sum to <= 32. */
+  int32_t reserved[3];
 } lms_stream_config;
 
 /* debug_flags.  HOLD_FIRST_ITEM: the first group of closed windows never
@@ -141,8 +144,26 @@ typedef struct lms_query_spec {
   int64_t window_slide_ms;/* 0 or == size: tumbling; else size % slide == 0 and
                              size/slide <= 4096 (sliding) */
   uint32_t agg_mask;      /* LMS_AGG_* bits; 0 means LMS_AGG_ALL */
-  int32_t reserved;
+  uint32_t group_fields;  /* GROUP BY the key fields whose bits are set (of the stream's
+                             key_fields, bit f = field f); 0 = the whole key.  A row's key
+                             holds the selected fields in place, the others zero. */
+  int32_t having_agg;     /* HAVING: LMS_POST_* aggregate, 0 = none */
+  int32_t having_op;      /* LMS_OP_*: a row is kept iff (double)agg OP having_value */
+  double having_value;
+  int32_t order_agg;      /* ORDER BY: LMS_POST_* aggregate, 0 = none (rows in key order) */
+  int32_t order_desc;     /* 1: descending; equal values keep key order either way */
 } lms_query_spec;
+
+/* Aggregates HAVING and ORDER BY refer to (Table III: LR2S's HAVING
+ * avgSpeed < 40.0, CM1's ORDER BY SUM(cpu)).  ORDER BY sorts each window's
+ * rows in device shared memory: a window may then hold at most
+ * LMS_ORDER_MAX_ROWS rows (push returns LMS_EINVAL otherwise). */
+#define LMS_POST_COUNT 1
+#define LMS_POST_SUM 2
+#define LMS_POST_MIN 3
+#define LMS_POST_MAX 4
+#define LMS_POST_AVG 5
+#define LMS_ORDER_MAX_ROWS 16384
 
 typedef struct lms_batch {
   int64_t n_rows;       /* rows in the batch (>= 0) */
@@ -763,6 +784,9 @@ lms_status lms_server_destroy(lms_server *sv);
  * calls share the array and leave their data in it; each call first resets the
  * parts that must start from zero.  Calls are serialised inside the library;
  * other work touching the array concurrently would race.
+ *
+ * The query's post-aggregation fields (group_fields, having_agg, order_agg)
+ * must be 0.
  *
  * Errors: LMS_EINVAL for a bad argument or n_rows > LMS_STATIC_MAX_ROWS;
  * LMS_ENOMEM if the emission items (runs of up to 64 consecutive closed

@@ -65,6 +65,7 @@ struct QueryHost {
   QueryDev dev{};
   unsigned long long cap = 0;  // group capacity of parts/state
   ResultRowDev* rows = nullptr;
+  ResultRowDev* rows_tmp = nullptr;   // scratch rows of HAVING / ORDER BY (same capacity)
   unsigned long long rows_cap = 0;
   unsigned long long rows_read = 0;   // rows already handed out by poll
   unsigned long long row_base = 0;    // rows in the device buffer (mirror)
@@ -266,6 +267,9 @@ lms_status ensure_rows(lms_stream* s, QueryHost& q, unsigned long long need) {
   const unsigned long long nc = round_cap(need + need / 4);
   lms_status r = dgrow(s, &q.rows, q.rows_cap, nc, q.row_base);
   if (r != LMS_OK) return r;
+  if (q.dev.having_agg || q.dev.order_agg) {
+    if ((r = dgrow(s, &q.rows_tmp, q.rows_cap, nc, 0)) != LMS_OK) return r;
+  }
   q.rows_cap = nc;
   return LMS_OK;
 }
@@ -389,6 +393,11 @@ lms_status stream_open(const lms_stream_config* cfg, lms_stream** out) {
   if (cfg->value_type != LMS_VALUE_INT32 && cfg->value_type != LMS_VALUE_FLOAT32) return LMS_EINVAL;
   if (cfg->allowed_lateness_ms < 0 || cfg->max_batch_rows < 0) return LMS_EINVAL;
   if (cfg->graph_mode < LMS_GRAPH_DEFAULT || cfg->graph_mode > LMS_GRAPH_ON) return LMS_EINVAL;
+  {
+    unsigned bits = 0;
+    for (int f = 0; f < 4; ++f) bits += (cfg->key_fields >> (8 * f)) & 0xffu;
+    if (bits > 32) return LMS_EINVAL;
+  }
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
     cudaGetLastError();
@@ -456,6 +465,25 @@ lms_status query_register(lms_stream* s, const lms_query_spec* q, int32_t* query
   if (q->filter_col < LMS_COL_TS || q->filter_col > LMS_COL_TYPE || q->filter_op < LMS_OP_NONE ||
       q->filter_op > LMS_OP_GE)
     return fail(s, LMS_EINVAL, "filter: bad column or operator");
+  if (q->having_agg < 0 || q->having_agg > LMS_POST_AVG || q->having_op < LMS_OP_NONE ||
+      q->having_op > LMS_OP_GE || q->order_agg < 0 || q->order_agg > LMS_POST_AVG)
+    return fail(s, LMS_EINVAL, "HAVING / ORDER BY: bad aggregate or operator");
+  // GROUP BY fields: the mask of the selected fields' bits
+  unsigned key_mask = 0xffffffffu;
+  if (q->group_fields) {
+    const unsigned kf = s->cfg.key_fields;
+    unsigned shift = 0;
+    key_mask = 0u;
+    for (int f = 0; f < 4; ++f) {
+      const unsigned w = (kf >> (8 * f)) & 0xffu;
+      if ((q->group_fields >> f) & 1u) {
+        if (w == 0) return fail(s, LMS_EINVAL, "GROUP BY: field not declared in key_fields");
+        key_mask |= (w >= 32 ? 0xffffffffu : ((1u << w) - 1u)) << shift;
+      }
+      shift += w;
+    }
+    if (q->group_fields >> 4) return fail(s, LMS_EINVAL, "GROUP BY: at most four key fields");
+  }
   QueryHost h;
   h.spec = *q;
   h.size = size;
@@ -475,6 +503,12 @@ lms_status query_register(lms_stream* s, const lms_query_spec* q, int32_t* query
   d.lookback_ns = s->cfg.lookback_limit_us > 0 ? 1000ull * (unsigned long long)s->cfg.lookback_limit_us
                                                : 4000000000ull;
   d.debug_flags = s->cfg.debug_flags;
+  d.key_mask = key_mask;
+  d.having_agg = q->having_agg;
+  d.having_op = q->having_op;
+  d.having_value = q->having_value;
+  d.order_agg = q->order_agg;
+  d.order_desc = q->order_desc ? 1 : 0;
   d.agg_mask = q->agg_mask ? q->agg_mask : LMS_AGG_ALL;
   d.qid = (int)s->qs.size();
   d.value_is_float = s->cfg.value_type == LMS_VALUE_FLOAT32;
@@ -665,6 +699,8 @@ lms_status run_batch(lms_stream* s, const InSeg* seg, int nseg, long long n, int
       if ((e = launch_emit(q.dev, s->scr, q.rows, q.rows_cap, s->sms, s->st, nl,
                            timing ? s->qev[i] : nullptr)) != cudaSuccess)
         break;
+      if ((e = launch_post(q.dev, s->scr, q.rows, q.rows_tmp, s->sms, s->st, nl)) != cudaSuccess)
+        break;
       e = launch_trim(q.dev, s->scr, s->sms, s->st, nl);
     }
     if (e == cudaSuccess && timing) e = record_event(s->ev[4], s->st);
@@ -732,12 +768,15 @@ lms_status run_batch(lms_stream* s, const InSeg* seg, int nseg, long long n, int
       LMS_CK(launch_block_index(q.dev, s->scr, s->st, &launches));
       LMS_CK(launch_emit(q.dev, s->scr, q.rows, q.rows_cap, s->sms, s->st, &launches,
                          nullptr));
+      LMS_CK(launch_post(q.dev, s->scr, q.rows, q.rows_tmp, s->sms, s->st, &launches));
       LMS_CK(launch_trim(q.dev, s->scr, s->sms, s->st, &launches));
       if ((r = read_ctls(s, hc.data())) != LMS_OK) return r;
       retried = true;
     }
     if (hc[i].err & kErrNeedRetry)
       return fail(s, LMS_ENOMEM, "emission buffers could not be grown enough");
+    if (hc[i].err & kErrOrderBy)
+      return fail(s, LMS_EINVAL, "ORDER BY: a window holds more than LMS_ORDER_MAX_ROWS rows");
     if (hc[i].err & (kErrPartsOverflow | kErrProbe | kErrLookback)) {
       s->latched = LMS_EDEVICE;
       return fail(s, LMS_EDEVICE, "internal device error flag raised by a kernel");

@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(kK1Threads, K1Shape<ITEMS>::kCtasPerSm)
           } else {
             const unsigned long long prel = udiv_inv(u, Q.magic, Q.sh1, Q.sh2);
             if ((long long)prel < cursor) ++n_late;  // every window of this event was emitted
-            else g = make_gkey(prel, key[i], Q.lb);
+            else g = make_gkey(prel, key[i] & Q.key_mask, Q.lb);
           }
         }
         const unsigned enc = FLOAT ? enc_f32(__uint_as_float(val[i])) : enc_i32((int)val[i]);

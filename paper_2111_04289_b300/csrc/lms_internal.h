@@ -37,7 +37,11 @@ constexpr unsigned kErrItemOverflow = 2u;    // emission item list too small
 constexpr unsigned kErrRowsOverflow = 4u;    // result buffer too small
 constexpr unsigned kErrProbe = 16u;          // shared hash probe bound hit (never expected)
 constexpr unsigned kErrLookback = 32u;       // an item's bounded look-back wait ran out
+constexpr unsigned kErrOrderBy = 64u;        // ORDER BY: a window holds more than kOrderMax rows
 constexpr unsigned kErrNeedRetry = kErrItemOverflow | kErrRowsOverflow;
+
+// Largest window ORDER BY sorts (in shared memory).
+constexpr int kOrderMax = 16384;
 
 // Windows per emission item (an item is a run of consecutive window ids that
 // start in one block).
@@ -73,6 +77,7 @@ struct QCtl {
   unsigned long long carried;    // groups carried into the next batch
   unsigned long long trim_from;  // first state index that may be carried into the next batch
   unsigned long long item_ticket;// next emission item (CTAs take items in order)
+  unsigned long long rows_kept;  // rows HAVING kept of this batch's
   unsigned long long parts_at_sort; // partial groups the sort of this batch consumed
   unsigned long long n_long;     // long runs of equal keys left to the cooperative reduce
   unsigned int err;
@@ -113,6 +118,10 @@ struct QueryDev {
   int nw;                      // windows per emission item: min(B, kMaxItemWindows)
   unsigned long long lookback_ns;  // bound of the emission's look-back wait
   unsigned debug_flags;        // kDebug* bits (tests only)
+  unsigned key_mask;           // GROUP BY: the bits of the key's selected fields
+  int having_agg, having_op;   // HAVING agg OP having_value (agg 0: none)
+  double having_value;
+  int order_agg, order_desc;   // ORDER BY agg (0: none), descending
   unsigned agg_mask;
   int qid;
   int value_is_float;
@@ -186,6 +195,10 @@ cudaError_t launch_emit(const QueryDev& q, const Scratch& s, ResultRowDev* rows,
                         cudaEvent_t* ev4);
 cudaError_t launch_trim(const QueryDev& q, const Scratch& s, int sms, cudaStream_t st,
                         int* launches);
+// HAVING and ORDER BY over the rows the emission just wrote (tmp_rows: a
+// scratch row buffer as large as rows).
+cudaError_t launch_post(const QueryDev& q, const Scratch& s, ResultRowDev* rows,
+                        ResultRowDev* tmp_rows, int sms, cudaStream_t st, int* launches);
 
 // Synthetic load generator of the serving backend (kernels_gen.cu).
 struct GenChunk {

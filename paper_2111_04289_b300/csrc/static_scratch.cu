@@ -136,6 +136,7 @@ extern "C" lms_status lms_aggregate_batch_static(const lms_query_spec* q, int32_
   if (q->filter_col < LMS_COL_TS || q->filter_col > LMS_COL_TYPE || q->filter_op < LMS_OP_NONE ||
       q->filter_op > LMS_OP_GE)
     return LMS_EINVAL;
+  if (q->group_fields || q->having_agg || q->order_agg) return LMS_EINVAL;  // not offered here
 
   std::lock_guard<std::mutex> lk(g_mu);
   int dev = 0;
@@ -183,6 +184,7 @@ extern "C" lms_status lms_aggregate_batch_static(const lms_query_spec* q, int32_
   set_block_shape(&d);
   d.lookback_ns = 4000000000ull;
   d.debug_flags = 0u;
+  d.key_mask = 0xffffffffu;
   d.agg_mask = q->agg_mask ? q->agg_mask : LMS_AGG_ALL;
   d.qid = 0;
   d.value_is_float = value_type == LMS_VALUE_FLOAT32;

@@ -46,7 +46,8 @@ class StreamConfig(ctypes.Structure):
                 ("state_cap_bytes", ctypes.c_uint64), ("cuda_stream", ctypes.c_void_p),
                 ("origin_ts", ctypes.c_int64), ("k1_variant", ctypes.c_int32),
                 ("graph_mode", ctypes.c_int32), ("lookback_limit_us", ctypes.c_int32),
-                ("debug_flags", ctypes.c_uint32), ("reserved", ctypes.c_int32 * 4)]
+                ("debug_flags", ctypes.c_uint32), ("key_fields", ctypes.c_uint32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 DEBUG_HOLD_FIRST_ITEM = 1
@@ -56,7 +57,14 @@ class QuerySpec(ctypes.Structure):
     _fields_ = [("filter_col", ctypes.c_int32), ("filter_op", ctypes.c_int32),
                 ("filter_i", ctypes.c_int64), ("filter_f", ctypes.c_double),
                 ("window_size_ms", ctypes.c_int64), ("window_slide_ms", ctypes.c_int64),
-                ("agg_mask", ctypes.c_uint32), ("reserved", ctypes.c_int32)]
+                ("agg_mask", ctypes.c_uint32), ("group_fields", ctypes.c_uint32),
+                ("having_agg", ctypes.c_int32), ("having_op", ctypes.c_int32),
+                ("having_value", ctypes.c_double), ("order_agg", ctypes.c_int32),
+                ("order_desc", ctypes.c_int32)]
+
+
+POST_AGGS = {"count": 1, "sum": 2, "min": 3, "max": 4, "avg": 5}
+ORDER_MAX_ROWS = 16384
 
 
 class BatchC(ctypes.Structure):
@@ -396,7 +404,7 @@ class Stream:
                  allowed_lateness_ms: int = 0, max_batch_rows: int = 0, state_cap_bytes: int = 0,
                  cuda_stream: Optional[int] = None, origin_ts: Optional[int] = None,
                  enable_timing: bool = False, k1_variant: int = 0, graph_mode: int = 0,
-                 lookback_limit_us: int = 0, debug_flags: int = 0):
+                 lookback_limit_us: int = 0, debug_flags: int = 0, key_fields=None):
         self._lib = load()
         self.value_type = value_type
         self.is_float = value_type == "float32"
@@ -414,6 +422,8 @@ class Stream:
         cfg.graph_mode = int(graph_mode)
         cfg.lookback_limit_us = int(lookback_limit_us)
         cfg.debug_flags = int(debug_flags)
+        # key_fields: bit widths of up to four packed key fields (field 0 lowest)
+        cfg.key_fields = sum(int(w) << (8 * f) for f, w in enumerate(key_fields or ()))
         h = ctypes.c_void_p()
         st = self._lib.stream_open(ctypes.byref(cfg), ctypes.byref(h))
         if st != LMS_OK:
@@ -430,7 +440,11 @@ class Stream:
             raise LmsError(st, f"{what}: {msg.decode() if msg else ''}")
 
     def register_query(self, size_ms: int, slide_ms: int = 0, filter_col: str = "ts",
-                       filter_op: str = "none", filter_value=0, agg_mask: int = AGG_ALL) -> int:
+                       filter_op: str = "none", filter_value=0, agg_mask: int = AGG_ALL,
+                       group_fields: int = 0, having=None, order_by=None) -> int:
+        """having = (agg, op, value): keep rows with (double)agg OP value;
+        order_by = (agg, descending): each window's rows sorted by agg (ties in
+        key order); group_fields: bit mask of the stream's key fields."""
         q = QuerySpec()
         q.filter_col = COLS[filter_col]
         q.filter_op = OPS[filter_op]
@@ -441,6 +455,12 @@ class Stream:
         q.window_size_ms = int(size_ms)
         q.window_slide_ms = int(slide_ms)
         q.agg_mask = int(agg_mask)
+        q.group_fields = int(group_fields)
+        if having is not None:
+            q.having_agg, q.having_op, q.having_value = (POST_AGGS[having[0]], OPS[having[1]],
+                                                         float(having[2]))
+        if order_by is not None:
+            q.order_agg, q.order_desc = POST_AGGS[order_by[0]], int(bool(order_by[1]))
         qid = ctypes.c_int32()
         self._check(self._lib.query_register(self._h, ctypes.byref(q), ctypes.byref(qid)),
                     "query_register")
