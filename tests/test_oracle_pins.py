@@ -363,3 +363,59 @@ def test_order_by_sorts_each_window_by_the_aggregate(agg, desc):
         order = np.lexsort((ks, -vs if desc else vs))
         expected += [(w, int(k)) for k in ks[order]]
     assert [(int(r["window_start"]), int(r["key"])) for r in rows] == expected
+
+
+# --------------------------------------------------------------------------- #
+# windowed equi-join (LR1S / LR1T of Table III): explicit pair enumeration
+# --------------------------------------------------------------------------- #
+
+@pytest.mark.parametrize("size,slide", [(100, 100), (90, 30)])
+def test_window_join_equals_enumerated_pairs(size, slide):
+    from oracle import join as oj
+    rng = np.random.default_rng(11)
+    n = 300
+    ts = np.sort(rng.integers(0, 400, n)).astype(np.int64)
+    key = rng.integers(0, 12, n).astype(np.uint32)
+    val = rng.integers(-5, 50, n).astype(np.int32)
+    typ = rng.integers(0, 2, n).astype(np.uint8)
+    left = (wa.COL_TYPE, wa.OP_EQ, 0, 0.0)
+    right = (wa.COL_TYPE, wa.OP_EQ, 1, 0.0)
+    o = oj.WindowJoinOracle(False, size, slide, left, right)
+    rows = np.concatenate([o.push(ts[:150], key[:150], val[:150], typ[:150]),
+                           o.push(ts[150:], key[150:], val[150:], typ[150:], eos=True)])
+    o.close()
+    # every window any event lies in; every (left, right) event pair with equal keys
+    K = size // slide
+    exp = {}
+    for a in range(n):
+        if typ[a] != 0:
+            continue
+        for b in range(n):
+            if typ[b] != 1 or key[a] != key[b]:
+                continue
+            wa_ = {(ts[a] // slide - j) * slide for j in range(K)}
+            wb_ = {(ts[b] // slide - j) * slide for j in range(K)}
+            for w in wa_ & wb_:  # both events in window w
+                p, sl, sr = exp.get((w, int(key[a])), (0, 0, 0))
+                exp[(w, int(key[a]))] = (p + 1, sl + int(val[a]), sr + int(val[b]))
+    assert len(rows) == len(exp) > 0
+    for r in rows:
+        p, sl, sr = exp[(int(r["window_start"]), int(r["key"]))]
+        assert int(r["pairs"]) == p
+        # per-pair sums: sum of l.value over pairs = left_sum * right_count
+        assert r["left_sum"] * r["right_count"] == sl and r["right_sum"] * r["left_count"] == sr
+    keys = [(int(r["window_start"]), int(r["key"])) for r in rows]
+    assert keys == sorted(keys)
+
+
+def test_self_join_pairs_are_squared_counts():
+    """LR1: a stream joined with itself on vehicle: pairs = count^2 per window."""
+    from oracle import join as oj
+    b = synth.TinyIntStream(seed=12, card=15).next_batch(2000)
+    allrows = (wa.COL_TS, wa.OP_NONE, 0, 0.0)
+    o = oj.WindowJoinOracle(False, 3000, 1000, allrows, allrows)
+    rows = o.push(b.ts, b.key, b.value, b.type, eos=True)
+    o.close()
+    assert len(rows) > 0
+    assert np.array_equal(rows["pairs"], rows["left_count"] ** 2)
+    assert np.array_equal(rows["left_count"], rows["right_count"])
