@@ -231,6 +231,54 @@ lms_status stream_open(const lms_stream_config *cfg, lms_stream **out);
  * window or filter is invalid. */
 lms_status query_register(lms_stream *s, const lms_query_spec *q, int32_t *query_id);
 
+/* ---- windowed equi-join of two streams -------------------------------------
+ *
+ * Table III's LR1S / LR1T join a windowed stream with a stream on vehicle
+ * (Join: Table II, base cost 0.9).  Here the two sides are the rows of the
+ * stream that pass a left and a right predicate (a type column can tell two
+ * streams apart; for a self-join both predicates may be LMS_OP_NONE).  For
+ * every window (as for queries: [start, start + size), sliding by slide,
+ * emitted once the watermark passes its end) the join's result is the
+ * multiset of pairs (l, r) of the window's left and right rows with equal
+ * keys.  It is reported in factored form, one lms_join_row per (window, key)
+ * present on both sides, in (window_start, key) order: pairs = left_count *
+ * right_count, with both sides' counts and value sums (every aggregate over
+ * the pairs that separates per side follows, e.g. the sum of the left values
+ * over all pairs is left_sum * right_count).  The pairs are not listed one by
+ * one: with Zipf-distributed keys their number grows with the square of a hot
+ * key's count.  Each side runs as an aggregation query of the stream, so a
+ * join takes two of the stream's eight query slots (their ids are not
+ * returned and cannot be polled); register joins before the first push. */
+typedef struct lms_join_spec {
+  int64_t window_size_ms;  /* > 0 */
+  int64_t window_slide_ms; /* 0 or == size: tumbling; else as for queries */
+  int32_t left_col, left_op;   /* left side predicate: LMS_COL_*, LMS_OP_* */
+  int64_t left_i;
+  double left_f;
+  int32_t right_col, right_op; /* right side predicate */
+  int64_t right_i;
+  double right_f;
+} lms_join_spec;
+
+typedef struct lms_join_row { /* 56 bytes */
+  int64_t window_start;
+  int64_t pairs;        /* left_count * right_count */
+  int64_t left_count;
+  int64_t right_count;
+  union { int64_t i; double f; } left_sum;  /* integer for an INT32 stream */
+  union { int64_t i; double f; } right_sum;
+  uint32_t key;
+  uint32_t join_id;
+} lms_join_row;
+
+/* Registers a join; *join_id receives 0, 1, ... (at most 4 joins).  LMS_EINVAL
+ * for a bad window or predicate, or when fewer than two query slots remain. */
+lms_status lms_join_register(lms_stream *s, const lms_join_spec *j, int32_t *join_id);
+/* Copies up to cap of the join's rows, oldest first, into out (host) and
+ * removes them; LMS_EAGAIN if there are none. */
+lms_status lms_join_poll(lms_stream *s, int32_t join_id, lms_join_row *out, size_t cap,
+                         size_t *n_out);
+
 /* Processes one micro-batch (the paper's processing phase, Section III-A)
  * through every registered query and emits the windows it closes.  Returns
  * when the results are ready to poll.  Columns are read from host or device

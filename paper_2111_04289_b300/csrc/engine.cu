@@ -73,6 +73,15 @@ struct QueryHost {
   unsigned long long n_state = 0;
   unsigned long long late_rows = 0, range_rows = 0;
   unsigned long long rows_emitted = 0;
+  bool hidden = false;  // a side of a join (its rows feed the join, not the caller)
+};
+
+struct JoinHost {
+  lms_join_spec spec{};
+  int ql = 0, qr = 0;  // the side queries
+  JCtl* jc = nullptr;
+  JoinRowDev* rows = nullptr;
+  unsigned long long cap = 0, row_base = 0, rows_read = 0, rows_emitted = 0;
 };
 
 }  // namespace
@@ -104,6 +113,7 @@ struct lms_stream {
   SCtl* sctl = nullptr;
   QCtl* qctl = nullptr;  // device array [kMaxQueries]
   std::vector<QueryHost> qs;
+  std::vector<JoinHost> joins;
   Scratch scr{};
   unsigned long long in_cap = 0;
   long long* in_ts = nullptr;
@@ -452,9 +462,11 @@ lms_status stream_open(const lms_stream_config* cfg, lms_stream** out) {
   return LMS_OK;
 }
 
-lms_status query_register(lms_stream* s, const lms_query_spec* q, int32_t* query_id) {
-  if (!s || !q || !query_id) return LMS_EINVAL;
-  std::lock_guard<std::mutex> lk(s->mu);
+}  // extern "C"
+
+namespace {
+
+lms_status register_query(lms_stream* s, const lms_query_spec* q, bool hidden, int32_t* query_id) {
   if (s->stats.batches > 0) return fail(s, LMS_EINVAL, "queries must be registered before the first push");
   if ((int)s->qs.size() >= kMaxQueries) return fail(s, LMS_EINVAL, "at most 8 queries per stream");
   const long long size = q->window_size_ms;
@@ -518,8 +530,108 @@ lms_status query_register(lms_stream* s, const lms_query_spec* q, int32_t* query
   c.cursor = 0;
   if (cudaMemcpy(d.ctl, &c, sizeof(c), cudaMemcpyHostToDevice) != cudaSuccess)
     return cuda_fail(s, cudaGetLastError(), "cudaMemcpy(ctl)");
+  h.hidden = hidden;
   s->qs.push_back(h);
   *query_id = d.qid;
+  return LMS_OK;
+}
+
+lms_status ensure_join_rows(lms_stream* s, JoinHost& j, unsigned long long need) {
+  if (j.cap >= need) return LMS_OK;
+  const unsigned long long nc = round_cap(need + need / 4);
+  lms_status r = dgrow(s, &j.rows, j.cap, nc, j.row_base);
+  if (r != LMS_OK) return r;
+  j.cap = nc;
+  return LMS_OK;
+}
+
+JoinArgs join_args(lms_stream* s, int i) {
+  JoinHost& j = s->joins[i];
+  JoinArgs a{};
+  a.lrows = s->qs[j.ql].rows;
+  a.lc = s->qs[j.ql].dev.ctl;
+  a.rrows = s->qs[j.qr].rows;
+  a.rc = s->qs[j.qr].dev.ctl;
+  a.out = j.rows;
+  a.cap = j.cap;
+  a.jc = j.jc;
+  a.jid = i;
+  return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+lms_status query_register(lms_stream* s, const lms_query_spec* q, int32_t* query_id) {
+  if (!s || !q || !query_id) return LMS_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  return register_query(s, q, false, query_id);
+}
+
+lms_status lms_join_register(lms_stream* s, const lms_join_spec* j, int32_t* join_id) {
+  if (!s || !j || !join_id) return LMS_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->stats.batches > 0) return fail(s, LMS_EINVAL, "joins must be registered before the first push");
+  if (s->joins.size() >= 4) return fail(s, LMS_EINVAL, "at most 4 joins per stream");
+  if ((int)s->qs.size() + 2 > kMaxQueries)
+    return fail(s, LMS_EINVAL, "a join needs two of the stream's 8 query slots");
+  lms_query_spec side{};
+  side.window_size_ms = j->window_size_ms;
+  side.window_slide_ms = j->window_slide_ms;
+  side.agg_mask = LMS_AGG_COUNT | LMS_AGG_SUM;
+  JoinHost jh;
+  jh.spec = *j;
+  lms_status r;
+  side.filter_col = j->left_col;
+  side.filter_op = j->left_op;
+  side.filter_i = j->left_i;
+  side.filter_f = j->left_f;
+  if ((r = register_query(s, &side, true, &jh.ql)) != LMS_OK) return r;
+  side.filter_col = j->right_col;
+  side.filter_op = j->right_op;
+  side.filter_i = j->right_i;
+  side.filter_f = j->right_f;
+  if ((r = register_query(s, &side, true, &jh.qr)) != LMS_OK) {
+    s->qs.pop_back();
+    return r;
+  }
+  void* p = nullptr;
+  if ((r = dalloc(s, &p, sizeof(JCtl))) != LMS_OK) return r;
+  jh.jc = static_cast<JCtl*>(p);
+  const JCtl z{};
+  if (cudaMemcpy(jh.jc, &z, sizeof(z), cudaMemcpyHostToDevice) != cudaSuccess)
+    return cuda_fail(s, cudaGetLastError(), "cudaMemcpy(join ctl)");
+  s->joins.push_back(jh);
+  if ((r = ensure_join_rows(s, s->joins.back(), 4096)) != LMS_OK) return r;
+  *join_id = (int32_t)s->joins.size() - 1;
+  return LMS_OK;
+}
+
+lms_status lms_join_poll(lms_stream* s, int32_t join_id, lms_join_row* out, size_t cap,
+                         size_t* n_out) {
+  if (!s || !n_out || (cap && !out)) return LMS_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->latched != LMS_OK) return s->latched;
+  if (join_id < 0 || join_id >= (int)s->joins.size()) return fail(s, LMS_EINVAL, "bad join id");
+  JoinHost& j = s->joins[join_id];
+  const unsigned long long avail = j.row_base - j.rows_read;
+  if (avail == 0) return LMS_EAGAIN;
+  const unsigned long long m = std::min<unsigned long long>(avail, cap);
+  if (m) {
+    LMS_CK(cudaMemcpyAsync(out, j.rows + j.rows_read, m * sizeof(lms_join_row),
+                           cudaMemcpyDeviceToHost, s->st));
+    LMS_CK(cudaStreamSynchronize(s->st));
+  }
+  j.rows_read += m;
+  if (j.rows_read == j.row_base) {
+    j.rows_read = 0;
+    j.row_base = 0;
+    const unsigned long long zero = 0;
+    LMS_CK(cudaMemcpyAsync(&j.jc->row_base, &zero, sizeof(zero), cudaMemcpyHostToDevice, s->st));
+    LMS_CK(cudaStreamSynchronize(s->st));
+  }
+  *n_out = (size_t)m;
   return LMS_OK;
 }
 
@@ -680,6 +792,8 @@ lms_status run_batch(lms_stream* s, const InSeg* seg, int nseg, long long n, int
   if ((r = ensure_items(s, 1024)) != LMS_OK) return r;
   for (QueryHost& q : s->qs)
     if ((r = ensure_rows(s, q, q.row_base + 4096)) != LMS_OK) return r;
+  for (JoinHost& j : s->joins)
+    if ((r = ensure_join_rows(s, j, j.row_base + 4096)) != LMS_OK) return r;
   // (Timing events inside the tail are recorded as external event nodes so that
   // a replayed graph still records them.)
   // The rest of the batch's work — watermark, then per query (back to back:
@@ -703,6 +817,8 @@ lms_status run_batch(lms_stream* s, const InSeg* seg, int nseg, long long n, int
         break;
       e = launch_trim(q.dev, s->scr, s->sms, s->st, nl);
     }
+    for (size_t i = 0; i < s->joins.size() && e == cudaSuccess; ++i)
+      e = launch_join(join_args(s, (int)i), s->scr, true, s->st, nl);
     if (e == cudaSuccess && timing) e = record_event(s->ev[4], s->st);
     return e;
   };
@@ -782,6 +898,26 @@ lms_status run_batch(lms_stream* s, const InSeg* seg, int nseg, long long n, int
       return fail(s, LMS_EDEVICE, "internal device error flag raised by a kernel");
     }
   }
+  // joins whose sides were retried, or whose row buffer was too small
+  for (size_t i = 0; i < s->joins.size(); ++i) {
+    JoinHost& j = s->joins[i];
+    for (int attempt = 0;; ++attempt) {
+      JCtl jh{};
+      LMS_CK(cudaMemcpyAsync(&jh, j.jc, sizeof(jh), cudaMemcpyDeviceToHost, s->st));
+      LMS_CK(cudaStreamSynchronize(s->st));
+      if (!(jh.err & kJoinPendingBit)) {
+        j.rows_emitted += jh.rows_batch;
+        j.row_base = jh.row_base;
+        break;
+      }
+      if (attempt >= 4) return fail(s, LMS_ENOMEM, "join rows: the buffer could not be grown enough");
+      if (jh.err & kJoinOverflowBit) {
+        if ((r = ensure_join_rows(s, j, jh.row_base + jh.rows_batch)) != LMS_OK) return r;
+      }
+      LMS_CK(launch_join(join_args(s, (int)i), s->scr, false, s->st, &launches));
+    }
+  }
+  if (!s->joins.empty() && (r = read_ctls(s, hc.data())) != LMS_OK) return r;
   SCtl hs{};
   LMS_CK(cudaMemcpyAsync(&hs, s->sctl, sizeof(hs), cudaMemcpyDeviceToHost, s->st));
   LMS_CK(cudaStreamSynchronize(s->st));
@@ -799,7 +935,7 @@ lms_status run_batch(lms_stream* s, const InSeg* seg, int nseg, long long n, int
     q.range_rows = hc[i].range_rows;
     late += q.late_rows;
     range += q.range_rows;
-    rows += q.rows_emitted;
+    if (!q.hidden) rows += q.rows_emitted;
     groups += q.carried;
   }
   if (timing) {
@@ -1012,7 +1148,8 @@ lms_status poll_results(lms_stream* s, int32_t query_id, lms_result_row* out, si
   if (!s || !n_out || (cap && !out)) return LMS_EINVAL;
   std::lock_guard<std::mutex> lk(s->mu);
   if (s->latched != LMS_OK) return s->latched;
-  if (query_id < 0 || query_id >= (int)s->qs.size()) return fail(s, LMS_EINVAL, "bad query id");
+  if (query_id < 0 || query_id >= (int)s->qs.size() || s->qs[query_id].hidden)
+    return fail(s, LMS_EINVAL, "bad query id");
   QueryHost& q = s->qs[query_id];
   const unsigned long long avail = q.row_base - q.rows_read;
   if (avail == 0) return LMS_EAGAIN;
@@ -1039,7 +1176,8 @@ lms_status lms_results_device(lms_stream* s, int32_t query_id, const lms_result_
                               size_t* n) {
   if (!s || !rows || !n) return LMS_EINVAL;
   std::lock_guard<std::mutex> lk(s->mu);
-  if (query_id < 0 || query_id >= (int)s->qs.size()) return fail(s, LMS_EINVAL, "bad query id");
+  if (query_id < 0 || query_id >= (int)s->qs.size() || s->qs[query_id].hidden)
+    return fail(s, LMS_EINVAL, "bad query id");
   QueryHost& q = s->qs[query_id];
   *rows = reinterpret_cast<const lms_result_row*>(q.rows + q.rows_read);
   *n = (size_t)(q.row_base - q.rows_read);
@@ -1049,7 +1187,8 @@ lms_status lms_results_device(lms_stream* s, int32_t query_id, const lms_result_
 lms_status lms_results_discard(lms_stream* s, int32_t query_id) {
   if (!s) return LMS_EINVAL;
   std::lock_guard<std::mutex> lk(s->mu);
-  if (query_id < 0 || query_id >= (int)s->qs.size()) return fail(s, LMS_EINVAL, "bad query id");
+  if (query_id < 0 || query_id >= (int)s->qs.size() || s->qs[query_id].hidden)
+    return fail(s, LMS_EINVAL, "bad query id");
   QueryHost& q = s->qs[query_id];
   q.rows_read = 0;
   q.row_base = 0;

@@ -178,6 +178,37 @@ struct ResultRowDev {  // device image of lms_result_row (48 bytes)
 constexpr int kGrid = 592;         // CTAs of the chunked (count/scan/write) kernels: 4 per SM
 constexpr int kChunkThreads = 256;
 
+// Windowed equi-join: device image of lms_join_row (56 bytes), its control
+// block, and what the join kernels read.
+struct JoinRowDev {
+  long long window_start;
+  long long pairs;
+  long long left_count;
+  long long right_count;
+  unsigned long long left_sum;   // int64 or the bits of a double
+  unsigned long long right_sum;
+  unsigned key;
+  unsigned jid;
+};
+struct JCtl {
+  unsigned long long rows_batch;  // join rows of this batch
+  unsigned long long row_base;    // join rows held in the device buffer
+  unsigned err;                   // pending / overflow bits
+  unsigned pad;
+};
+struct JoinArgs {
+  const ResultRowDev* lrows;  // the left side's (hidden query's) rows
+  QCtl* lc;
+  const ResultRowDev* rrows;
+  QCtl* rc;
+  JoinRowDev* out;
+  unsigned long long cap;
+  JCtl* jc;
+  int jid;
+  int pad;
+};
+constexpr unsigned kJoinPendingBit = 1u, kJoinOverflowBit = 2u;
+
 // ---- launch wrappers (kernels_*.cu) -------------------------------------
 // All enqueue on `st` and return the launch error.
 cudaError_t launch_batch_begin(SCtl* sctl, QCtl* const* ctls, int nq, cudaStream_t st);
@@ -194,6 +225,9 @@ cudaError_t launch_emit(const QueryDev& q, const Scratch& s, ResultRowDev* rows,
                         unsigned long long rows_cap, int sms, cudaStream_t st, int* launches,
                         cudaEvent_t* ev4);
 cudaError_t launch_trim(const QueryDev& q, const Scratch& s, int sms, cudaStream_t st,
+                        int* launches);
+// The join of this batch's rows of both sides (begin: mark it pending first).
+cudaError_t launch_join(const JoinArgs& a, const Scratch& s, bool begin, cudaStream_t st,
                         int* launches);
 // HAVING and ORDER BY over the rows the emission just wrote (tmp_rows: a
 // scratch row buffer as large as rows).

@@ -67,6 +67,23 @@ POST_AGGS = {"count": 1, "sum": 2, "min": 3, "max": 4, "avg": 5}
 ORDER_MAX_ROWS = 16384
 
 
+class JoinSpec(ctypes.Structure):
+    _fields_ = [("window_size_ms", ctypes.c_int64), ("window_slide_ms", ctypes.c_int64),
+                ("left_col", ctypes.c_int32), ("left_op", ctypes.c_int32),
+                ("left_i", ctypes.c_int64), ("left_f", ctypes.c_double),
+                ("right_col", ctypes.c_int32), ("right_op", ctypes.c_int32),
+                ("right_i", ctypes.c_int64), ("right_f", ctypes.c_double)]
+
+
+JOIN_ROW_DTYPE_INT = np.dtype([("window_start", "<i8"), ("pairs", "<i8"), ("left_count", "<i8"),
+                               ("right_count", "<i8"), ("left_sum", "<i8"), ("right_sum", "<i8"),
+                               ("key", "<u4"), ("join_id", "<u4")])
+JOIN_ROW_DTYPE_FLOAT = np.dtype([("window_start", "<i8"), ("pairs", "<i8"),
+                                 ("left_count", "<i8"), ("right_count", "<i8"),
+                                 ("left_sum", "<f8"), ("right_sum", "<f8"), ("key", "<u4"),
+                                 ("join_id", "<u4")])
+
+
 class BatchC(ctypes.Structure):
     _fields_ = [("n_rows", ctypes.c_int64), ("ts", ctypes.c_void_p), ("key", ctypes.c_void_p),
                 ("value", ctypes.c_void_p), ("type", ctypes.c_void_p),
@@ -116,7 +133,8 @@ EXPORTED_SYMBOLS = ("stream_open", "query_register", "push_microbatch", "poll_re
                     "lms_variant_analytic_state", "lms_variant_learned_create",
                     "lms_variant_learned_destroy", "lms_variant_learned_set_online",
                     "lms_variant_learned_fit", "lms_variant_learned_choose",
-                    "lms_variant_learned_observe", "lms_variant_learned_stats")
+                    "lms_variant_learned_observe", "lms_variant_learned_stats",
+                    "lms_join_register", "lms_join_poll")
 ADMIT_PAPER, ADMIT_GUARDED = 0, 1
 QOPS = {"aggregation": 0, "filter": 1, "shuffle": 2, "project": 3, "join": 4, "expand": 5,
         "scan": 6, "sort": 7}
@@ -243,6 +261,10 @@ def load(build_if_missing: bool = True):
     lib.lms_push_ingested.argtypes = [P, ctypes.c_int64, ctypes.c_uint32]
     lib.lms_ingest_pending.restype = ctypes.c_int32
     lib.lms_ingest_pending.argtypes = [P, P]
+    lib.lms_join_register.restype = ctypes.c_int32
+    lib.lms_join_register.argtypes = [P, P, P]
+    lib.lms_join_poll.restype = ctypes.c_int32
+    lib.lms_join_poll.argtypes = [P, ctypes.c_int32, P, ctypes.c_size_t, P]
     lib.lms_stream_set_variant_chooser.restype = ctypes.c_int32
     lib.lms_stream_set_variant_chooser.argtypes = [P, P, P, P]
     lib.lms_variant_analytic_create.restype = P
@@ -518,6 +540,40 @@ class Stream:
         n = ctypes.c_int64()
         self._check(self._lib.lms_ingest_pending(self._h, ctypes.byref(n)), "lms_ingest_pending")
         return n.value
+
+    def register_join(self, size_ms: int, slide_ms: int = 0, left=("ts", "none", 0),
+                      right=("ts", "none", 0)) -> int:
+        """lms_join_register: left / right = (column, op, value) side predicates."""
+        j = JoinSpec()
+        j.window_size_ms, j.window_slide_ms = int(size_ms), int(slide_ms)
+        for side, (col, op, v) in (("left", left), ("right", right)):
+            setattr(j, side + "_col", COLS[col])
+            setattr(j, side + "_op", OPS[op])
+            if col == "value" and self.is_float:
+                setattr(j, side + "_f", float(v))
+            else:
+                setattr(j, side + "_i", int(v))
+        jid = ctypes.c_int32()
+        self._check(self._lib.lms_join_register(self._h, ctypes.byref(j), ctypes.byref(jid)),
+                    "lms_join_register")
+        return jid.value
+
+    def poll_join(self, join_id: int, chunk: int = 1 << 20) -> np.ndarray:
+        """All pending rows of a join (lms_join_poll), oldest first."""
+        dt = JOIN_ROW_DTYPE_FLOAT if self.is_float else JOIN_ROW_DTYPE_INT
+        parts = []
+        while True:
+            out = np.zeros(chunk, dtype=dt)
+            got = ctypes.c_size_t()
+            st = self._lib.lms_join_poll(self._h, int(join_id), out.ctypes.data, chunk,
+                                         ctypes.byref(got))
+            if st == LMS_EAGAIN:
+                break
+            self._check(st, "lms_join_poll")
+            parts.append(out[: got.value])
+            if got.value < chunk:
+                break
+        return np.concatenate(parts) if parts else np.zeros(0, dtype=dt)
 
     def set_variant_chooser(self, chooser) -> None:
         """Installs a VariantAnalytic / VariantLearned (or None) as the chooser of
