@@ -365,6 +365,75 @@ lms_status lms_push_ingested(lms_stream *s, int64_t n_rows, uint32_t flags);
 /* Rows ingested and not yet pushed. */
 lms_status lms_ingest_pending(lms_stream *s, int64_t *n_rows);
 
+/* ---- key sharding across devices (one stream per device) ----
+ *
+ * A group (window, key) depends only on the rows of its key, so the key space
+ * can be split over G streams, one per GPU, each owning the keys with
+ * lms_shard_of(key, key_mask, G) == its index (the "Shuffling" operation of
+ * Table II, done on the host before the copy to the device).  Every shard
+ * stream must be opened with the same configuration and an explicit event-time
+ * origin (lms_stream_config.origin_ts or lms_stream_set_origin), register the
+ * same queries and joins in the same order, and be pushed once per global
+ * micro-batch (an empty shard included) after lms_stream_set_batch_max_ts with
+ * the global batch's max event time: then every shard advances the same
+ * watermark (Section II-A's event-time windows close on the max event time
+ * seen) and closes the same windows.  The union of the shards' rows of a
+ * window is the single stream's; rows of one window are ordered by key (or by
+ * the ORDER BY aggregate, equal values in key order) on each shard.
+ *
+ * key_mask selects the key bits every query of the stream groups by (the
+ * fields common to all GROUP BYs; 0xffffffff without GROUP BY): rows whose
+ * masked keys are equal land on one shard. */
+
+/* Shard of a key: h = fmix32(key & key_mask) (MurmurHash3's 32-bit finaliser:
+ * h ^= h >> 16; h *= 0x85ebca6b; h ^= h >> 13; h *= 0xc2b2ae35; h ^= h >> 16),
+ * then (h * n_shards) >> 32 (multiply-shift range reduction).  n_shards >= 1. */
+uint32_t lms_shard_of(uint32_t key, uint32_t key_mask, int32_t n_shards);
+
+/* Splits the host batch `in` (n_rows rows, host columns) by lms_shard_of into
+ * caller-owned host columns of in->n_rows rows each: shard g's rows, in their
+ * input order, are rows [offsets[g], offsets[g+1]) of ts_out/key_out/value_out
+ * (and type_out, which may be NULL when in->type is NULL); offsets has
+ * n_shards + 1 entries.  *max_ts (may be NULL) receives the batch's max event
+ * time (INT64_MIN if it is empty): the watermark hint for every shard.  Large
+ * batches are split by up to 8 host threads.  Errors: LMS_EINVAL for NULL
+ * pointers, n_shards < 1 or device columns. */
+lms_status lms_shard_split(const lms_batch *in, uint32_t key_mask, int32_t n_shards,
+                           int64_t *ts_out, uint32_t *key_out, uint32_t *value_out,
+                           uint8_t *type_out, int64_t *offsets, int64_t *max_ts);
+
+/* The next push (push_microbatch or lms_push_ingested) treats its batch's max
+ * event time as at least ts (a watermark hint: the max over all shards of a
+ * global micro-batch).  It applies to one push only, which then advances the
+ * watermark even when it carries no rows. */
+lms_status lms_stream_set_batch_max_ts(lms_stream *s, int64_t ts);
+
+/* Fixes the event-time origin (what origin_ts of the configuration does)
+ * before the first push; LMS_EINVAL once it is set. */
+lms_status lms_stream_set_origin(lms_stream *s, int64_t origin_ts);
+
+/* ---- snapshot / resume of a stream's device state ----
+ *
+ * Between pushes a stream's state is: its configuration and queries, the
+ * event-time origin and watermark, every query's carried partial groups of
+ * still-open panes (32 bytes each) and control block, and the rows not yet
+ * polled (queries and joins).  lms_stream_snapshot writes all of it into a
+ * host buffer (the state flushing / checkpoint step that follows each
+ * micro-batch in Section III-E's processing cycle); lms_stream_restore opens a
+ * new stream on `device` (-1: the snapshot's) in exactly that state, so that
+ * pushing the rest of the input gives the rows the original stream would have.
+ * The format is the library's own: a header with a magic and a version, then
+ * per query and per join its spec, control block and arrays.  Not saved: the
+ * cuda_stream of the configuration (the restored stream creates its own), a
+ * variant chooser, the fused-pass autotuner's timings.  Snapshot: with buf
+ * NULL only *size is set; LMS_EINVAL if cap < *size or ingested rows are
+ * pending.  Restore: LMS_EINVAL for a buffer that is not a snapshot of this
+ * library's format; LMS_ENOMEM / LMS_ECUDA as stream_open. */
+lms_status lms_stream_snapshot(lms_stream *s, void *buf, size_t cap, size_t *size);
+/* The stream's configuration (origin_ts as set, cuda_stream as in use). */
+lms_status lms_stream_get_config(lms_stream *s, lms_stream_config *out);
+lms_status lms_stream_restore(const void *buf, size_t size, int32_t device, lms_stream **out);
+
 /* ---- control plane: dynamic micro-batching and per-operation planning ---- */
 
 /* Alg. 1 policies.  PAPER: ConstructMicroBatch as printed (decides only when

@@ -45,10 +45,10 @@ class WindowJoinOracle:
         self.ql = self.o.add_query(left[0], left[1], left[2], left[3], size_ms, slide_ms)
         self.qr = self.o.add_query(right[0], right[1], right[2], right[3], size_ms, slide_ms)
 
-    def push(self, ts, key, value, type_=None, eos=False) -> np.ndarray:
+    def push(self, ts, key, value, type_=None, eos=False, ts_floor=None) -> np.ndarray:
         """Feeds one micro-batch; returns the join rows of the windows it closed,
-        ordered by (window start, key)."""
-        self.o.push(ts, key, value, type_, eos=eos)
+        ordered by (window start, key).  ts_floor: as WindowAggOracle.push."""
+        self.o.push(ts, key, value, type_, eos=eos, ts_floor=ts_floor)
         lrows, rrows = self.o.take_rows(self.ql), self.o.take_rows(self.qr)
         right = {(int(r["window_start"]), int(r["key"])): r for r in rrows}
         out = []

@@ -84,6 +84,11 @@ def _load():
             ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
         ]
+        lib.oracle_push_floor.restype = ctypes.c_int
+        lib.oracle_push_floor.argtypes = [
+            ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64,
+        ]
         lib.oracle_pending_rows.restype = ctypes.c_int64
         lib.oracle_pending_rows.argtypes = [ctypes.c_void_p, ctypes.c_int]
         lib.oracle_take_rows.restype = ctypes.c_int64
@@ -147,7 +152,9 @@ class WindowAggOracle:
                                      hv, oa, od) != 0:
             raise ValueError("bad post-aggregation")
 
-    def push(self, ts, key, value, type_=None, eos: bool = False):
+    def push(self, ts, key, value, type_=None, eos: bool = False, ts_floor=None):
+        """One micro-batch; ts_floor: a lower bound of the batch's max event
+        time (the whole micro-batch's, when this stream holds one key shard)."""
         ts = np.ascontiguousarray(ts, dtype=np.int64)
         key = np.ascontiguousarray(key, dtype=np.uint32)
         value = np.ascontiguousarray(
@@ -160,9 +167,9 @@ class WindowAggOracle:
             type_ = np.ascontiguousarray(type_, dtype=np.uint8)
             assert type_.shape[0] == n
             tp = type_.ctypes.data
-        self._lib.oracle_push(
+        self._lib.oracle_push_floor(
             self._h, n, ts.ctypes.data, key.ctypes.data, value.ctypes.data, tp,
-            int(bool(eos)),
+            int(bool(eos)), -(1 << 63) if ts_floor is None else int(ts_floor),
         )
 
     def take_rows(self, qid: int) -> np.ndarray:

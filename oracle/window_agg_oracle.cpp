@@ -25,7 +25,9 @@
 //      int32 values, sequential double for float32 values), min/max by value;
 //      float min/max follow IEEE-754 totalOrder (-0.0 < +0.0).
 //   5. after the micro-batch: watermark = max(watermark, max ts of all rows of
-//      the batch, filtered or not, - allowed_lateness).  Every group whose
+//      the batch, filtered or not, - allowed_lateness); a caller may raise the
+//      batch's max ts to a floor (oracle_push_floor: when the stream holds one
+//      key shard of a micro-batch, the max is the whole batch's).  Every group whose
 //      window end is <= watermark is emitted, in (window start, key) order, with
 //      avg = (double)sum / count, and deleted.  End of stream emits everything.
 //   6. post-aggregation (Table III: LR2S's HAVING, CM1's ORDER BY, the
@@ -242,9 +244,12 @@ int oracle_add_query(void* h, int filter_col, int filter_op, int64_t filter_i,
 }
 
 // Feeds one micro-batch, event by event, then advances the watermark and emits.
-// `value` points at int32 or float32 values; `type` may be NULL.
-int oracle_push(void* h, int64_t n, const int64_t* ts, const uint32_t* key,
-                const void* value, const uint8_t* type, int eos) {
+// `value` points at int32 or float32 values; `type` may be NULL.  ts_floor is
+// INT64_MIN, or a lower bound of the batch's max event time: the max over a
+// micro-batch whose rows were split by key over several streams, each of
+// which must advance the watermark the whole batch advances.
+int oracle_push_floor(void* h, int64_t n, const int64_t* ts, const uint32_t* key,
+                      const void* value, const uint8_t* type, int eos, int64_t ts_floor) {
   Oracle* o = static_cast<Oracle*>(h);
   const int32_t* vi = static_cast<const int32_t*>(value);
   const float* vf = static_cast<const float*>(value);
@@ -299,10 +304,10 @@ int oracle_push(void* h, int64_t n, const int64_t* ts, const uint32_t* key,
       if (!any_open) q.late_rows += 1;
     }
   }
-  // 5. watermark over every arriving row, then emission
-  if (n > 0) {
-    int64_t mx = ts[0];
-    for (int64_t e = 1; e < n; ++e)
+  // 5. watermark over every arriving row (and the floor), then emission
+  if (n > 0 || ts_floor != INT64_MIN) {
+    int64_t mx = ts_floor;
+    for (int64_t e = 0; e < n; ++e)
       if (ts[e] > mx) mx = ts[e];
     const int64_t cand = mx - o->lateness;
     if (!o->have_wm || cand > o->wm) o->wm = cand;
@@ -315,6 +320,11 @@ int oracle_push(void* h, int64_t n, const int64_t* ts, const uint32_t* key,
       emit_closed(*o, q, false);
   }
   return 0;
+}
+
+int oracle_push(void* h, int64_t n, const int64_t* ts, const uint32_t* key,
+                const void* value, const uint8_t* type, int eos) {
+  return oracle_push_floor(h, n, ts, key, value, type, eos, INT64_MIN);
 }
 
 // Post-aggregation of query qid (see item 6 above): group_mask, HAVING (agg

@@ -149,6 +149,9 @@ struct lms_stream {
   cudaEvent_t qev[kMaxQueries][6] = {};  // E1, E2, sort/reduce
   lms_stats stats{};
   long long wm = LLONG_MIN;
+  // watermark hint for the next push (lms_stream_set_batch_max_ts)
+  long long ts_hint = 0;
+  bool ts_hint_set = false;
   // fused-pass variant chooser installed by lms_stream_set_variant_chooser
   lms_variant_chooser vc = nullptr;
   lms_variant_observer vo = nullptr;
@@ -757,7 +760,8 @@ lms_status run_batch(lms_stream* s, const InSeg* seg, int nseg, long long n, int
   QCtl* ctls[kMaxQueries];
   const int nq = (int)s->qs.size();
   for (int i = 0; i < nq; ++i) ctls[i] = s->qs[i].dev.ctl;
-  LMS_CK(launch_batch_begin(s->sctl, ctls, nq, s->st));
+  LMS_CK(launch_batch_begin(s->sctl, ctls, nq, s->ts_hint_set ? s->ts_hint : LLONG_MIN, s->st));
+  s->ts_hint_set = false;
   ++launches;
   if (timing) LMS_CK(cudaEventRecord(s->ev[1], s->st));
   if (n > 0) {
@@ -1304,6 +1308,23 @@ lms_status lms_stream_admissible_rows(lms_stream* s, int32_t host_input, int64_t
   return LMS_OK;
 }
 
+lms_status lms_stream_set_batch_max_ts(lms_stream* s, int64_t ts) {
+  if (!s) return LMS_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->ts_hint = (long long)ts;
+  s->ts_hint_set = true;
+  return LMS_OK;
+}
+
+lms_status lms_stream_set_origin(lms_stream* s, int64_t origin_ts) {
+  if (!s) return LMS_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->origin_set || s->stats.batches > 0 || s->ring_first_set)
+    return fail(s, LMS_EINVAL, "the event-time origin is already set");
+  s->cfg.origin_ts = (long long)origin_ts;
+  return LMS_OK;
+}
+
 const char* lms_last_error(lms_stream* s) { return s ? s->err.c_str() : "null stream"; }
 
 lms_status stream_close(lms_stream* s) {
@@ -1334,6 +1355,290 @@ lms_status stream_close(lms_stream* s) {
     if (s->own_stream && s->st) cudaStreamDestroy(s->st);
   }
   delete s;
+  return LMS_OK;
+}
+
+}  // extern "C"
+
+// ---- snapshot / resume -------------------------------------------------------
+
+namespace {
+
+constexpr char kSnapMagic[8] = {'L', 'M', 'S', 'S', 'N', 'A', 'P', '\0'};
+constexpr uint32_t kSnapVersion = 1;
+
+struct SnapHead {
+  char magic[8];
+  uint32_t version;
+  uint32_t cfg_bytes, spec_bytes, join_spec_bytes, ctl_bytes, jctl_bytes, grp_bytes, row_bytes;
+  uint32_t nq, nj;
+  int32_t origin_set, eos_seen;
+  int64_t origin_ts, wm;
+  SCtl sctl;
+  lms_stats stats;
+  lms_stream_config cfg;
+};
+struct SnapQuery {
+  lms_query_spec spec;
+  int32_t hidden, pad;
+  QCtl ctl;
+  uint64_t groups, rows, rows_emitted;
+};
+struct SnapJoin {
+  lms_join_spec spec;
+  int32_t ql, qr;
+  JCtl ctl;
+  uint64_t rows, rows_emitted;
+};
+
+// Bounded writer/reader over a host buffer.
+struct SnapOut {
+  unsigned char* p;
+  size_t cap, off;
+  unsigned char* take(size_t n) {
+    unsigned char* r = (p && off + n <= cap) ? p + off : nullptr;
+    off += n;
+    return r;
+  }
+};
+struct SnapIn {
+  const unsigned char* p;
+  size_t size, off;
+  const unsigned char* take(size_t n) {
+    if (n > size - off) return nullptr;
+    const unsigned char* r = p + off;
+    off += n;
+    return r;
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+lms_status lms_stream_snapshot(lms_stream* s, void* buf, size_t cap, size_t* size) {
+  if (!s || !size) return LMS_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->latched != LMS_OK) return s->latched;
+  if (s->ring_tail != s->ring_head)
+    return fail(s, LMS_EINVAL, "snapshot: ingested rows are pending");
+  LMS_CK(cudaSetDevice(s->cfg.device));
+  const int nq = (int)s->qs.size(), nj = (int)s->joins.size();
+  std::vector<QCtl> hc((size_t)nq);
+  std::vector<JCtl> jc((size_t)nj);
+  SCtl hs{};
+  if (nq) LMS_CK(cudaMemcpyAsync(hc.data(), s->qctl, sizeof(QCtl) * nq, cudaMemcpyDeviceToHost, s->st));
+  for (int j = 0; j < nj; ++j)
+    LMS_CK(cudaMemcpyAsync(&jc[j], s->joins[j].jc, sizeof(JCtl), cudaMemcpyDeviceToHost, s->st));
+  LMS_CK(cudaMemcpyAsync(&hs, s->sctl, sizeof(hs), cudaMemcpyDeviceToHost, s->st));
+  LMS_CK(cudaStreamSynchronize(s->st));
+  size_t need = sizeof(SnapHead);
+  for (int i = 0; i < nq; ++i)
+    need += sizeof(SnapQuery) + hc[i].carried * sizeof(Grp) +
+            (s->qs[i].row_base - s->qs[i].rows_read) * sizeof(ResultRowDev);
+  for (int j = 0; j < nj; ++j)
+    need += sizeof(SnapJoin) + (s->joins[j].row_base - s->joins[j].rows_read) * sizeof(JoinRowDev);
+  *size = need;
+  if (!buf) return LMS_OK;
+  if (cap < need) return fail(s, LMS_EINVAL, "snapshot: buffer too small");
+  SnapOut o{static_cast<unsigned char*>(buf), cap, 0};
+  SnapHead h{};
+  std::memcpy(h.magic, kSnapMagic, sizeof(kSnapMagic));
+  h.version = kSnapVersion;
+  h.cfg_bytes = sizeof(lms_stream_config);
+  h.spec_bytes = sizeof(lms_query_spec);
+  h.join_spec_bytes = sizeof(lms_join_spec);
+  h.ctl_bytes = sizeof(QCtl);
+  h.jctl_bytes = sizeof(JCtl);
+  h.grp_bytes = sizeof(Grp);
+  h.row_bytes = sizeof(ResultRowDev);
+  h.nq = (uint32_t)nq;
+  h.nj = (uint32_t)nj;
+  h.origin_set = s->origin_set ? 1 : 0;
+  h.eos_seen = s->eos_seen ? 1 : 0;
+  h.origin_ts = s->origin_ts;
+  h.wm = s->wm;
+  h.sctl = hs;
+  h.stats = s->stats;
+  h.cfg = s->cfg;
+  h.cfg.cuda_stream = nullptr;
+  std::memcpy(o.take(sizeof(h)), &h, sizeof(h));
+  for (int i = 0; i < nq; ++i) {
+    const QueryHost& q = s->qs[i];
+    SnapQuery sq{};
+    sq.spec = q.spec;
+    sq.hidden = q.hidden ? 1 : 0;
+    sq.ctl = hc[i];
+    sq.groups = hc[i].carried;
+    sq.rows = q.row_base - q.rows_read;
+    sq.rows_emitted = q.rows_emitted;
+    sq.ctl.row_base = sq.rows;
+    std::memcpy(o.take(sizeof(sq)), &sq, sizeof(sq));
+    if (sq.groups)
+      LMS_CK(cudaMemcpyAsync(o.take(sq.groups * sizeof(Grp)), q.dev.parts, sq.groups * sizeof(Grp),
+                             cudaMemcpyDeviceToHost, s->st));
+    if (sq.rows)
+      LMS_CK(cudaMemcpyAsync(o.take(sq.rows * sizeof(ResultRowDev)), q.rows + q.rows_read,
+                             sq.rows * sizeof(ResultRowDev), cudaMemcpyDeviceToHost, s->st));
+  }
+  for (int j = 0; j < nj; ++j) {
+    const JoinHost& jh = s->joins[j];
+    SnapJoin sj{};
+    sj.spec = jh.spec;
+    sj.ql = jh.ql;
+    sj.qr = jh.qr;
+    sj.ctl = jc[j];
+    sj.rows = jh.row_base - jh.rows_read;
+    sj.rows_emitted = jh.rows_emitted;
+    sj.ctl.row_base = sj.rows;
+    std::memcpy(o.take(sizeof(sj)), &sj, sizeof(sj));
+    if (sj.rows)
+      LMS_CK(cudaMemcpyAsync(o.take(sj.rows * sizeof(JoinRowDev)), jh.rows + jh.rows_read,
+                             sj.rows * sizeof(JoinRowDev), cudaMemcpyDeviceToHost, s->st));
+  }
+  LMS_CK(cudaStreamSynchronize(s->st));
+  return LMS_OK;
+}
+
+lms_status lms_stream_get_config(lms_stream* s, lms_stream_config* out) {
+  if (!s || !out) return LMS_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  *out = s->cfg;
+  if (s->origin_set) out->origin_ts = s->origin_ts;
+  out->cuda_stream = s->st;
+  return LMS_OK;
+}
+
+lms_status lms_stream_restore(const void* buf, size_t size, int32_t device, lms_stream** out) {
+  if (!buf || !out) return LMS_EINVAL;
+  *out = nullptr;
+  SnapIn in{static_cast<const unsigned char*>(buf), size, 0};
+  const unsigned char* hp = in.take(sizeof(SnapHead));
+  if (!hp) return LMS_EINVAL;
+  SnapHead h;
+  std::memcpy(&h, hp, sizeof(h));
+  if (std::memcmp(h.magic, kSnapMagic, sizeof(kSnapMagic)) != 0 || h.version != kSnapVersion ||
+      h.cfg_bytes != sizeof(lms_stream_config) || h.spec_bytes != sizeof(lms_query_spec) ||
+      h.join_spec_bytes != sizeof(lms_join_spec) || h.ctl_bytes != sizeof(QCtl) ||
+      h.jctl_bytes != sizeof(JCtl) || h.grp_bytes != sizeof(Grp) ||
+      h.row_bytes != sizeof(ResultRowDev) || h.nq > (uint32_t)kMaxQueries || h.nj > 4)
+    return LMS_EINVAL;
+  // walk the buffer once to find every record (and check that it is complete)
+  std::vector<SnapQuery> sq(h.nq);
+  std::vector<const unsigned char*> q_groups(h.nq), q_rows(h.nq);
+  for (uint32_t i = 0; i < h.nq; ++i) {
+    const unsigned char* p = in.take(sizeof(SnapQuery));
+    if (!p) return LMS_EINVAL;
+    std::memcpy(&sq[i], p, sizeof(SnapQuery));
+    if (sq[i].groups > (1ull << 40) || sq[i].rows > (1ull << 40)) return LMS_EINVAL;
+    q_groups[i] = in.take(sq[i].groups * sizeof(Grp));
+    q_rows[i] = in.take(sq[i].rows * sizeof(ResultRowDev));
+    if ((sq[i].groups && !q_groups[i]) || (sq[i].rows && !q_rows[i])) return LMS_EINVAL;
+  }
+  std::vector<SnapJoin> sj(h.nj);
+  std::vector<const unsigned char*> j_rows(h.nj);
+  for (uint32_t j = 0; j < h.nj; ++j) {
+    const unsigned char* p = in.take(sizeof(SnapJoin));
+    if (!p) return LMS_EINVAL;
+    std::memcpy(&sj[j], p, sizeof(SnapJoin));
+    if (sj[j].rows > (1ull << 40) || sj[j].ql < 0 || sj[j].qr != sj[j].ql + 1 ||
+        sj[j].qr >= (int32_t)h.nq)
+      return LMS_EINVAL;
+    j_rows[j] = in.take(sj[j].rows * sizeof(JoinRowDev));
+    if (sj[j].rows && !j_rows[j]) return LMS_EINVAL;
+  }
+  if (in.off != size) return LMS_EINVAL;
+  lms_stream_config cfg = h.cfg;
+  cfg.cuda_stream = nullptr;
+  if (device >= 0) cfg.device = device;
+  lms_stream* s = nullptr;
+  lms_status r = stream_open(&cfg, &s);
+  if (r != LMS_OK) return r;
+  auto bail = [&](lms_status code) {
+    stream_close(s);
+    return code;
+  };
+  // registrations in their original order: a join's two hidden side queries
+  // are consecutive and created by registering the join
+  for (uint32_t i = 0; i < h.nq; ++i) {
+    int jfound = -1;
+    for (uint32_t j = 0; j < h.nj; ++j)
+      if (sj[j].ql == (int32_t)i) jfound = (int)j;
+    int32_t id = -1;
+    if (jfound >= 0) {
+      if (!sq[i].hidden || !sq[i + 1].hidden) return bail(LMS_EINVAL);
+      if ((r = lms_join_register(s, &sj[jfound].spec, &id)) != LMS_OK) return bail(r);
+      if (id != jfound || s->joins[id].ql != (int)i) return bail(LMS_EINVAL);
+      ++i;
+    } else {
+      if (sq[i].hidden) return bail(LMS_EINVAL);
+      if ((r = query_register(s, &sq[i].spec, &id)) != LMS_OK) return bail(r);
+      if (id != (int32_t)i) return bail(LMS_EINVAL);
+    }
+  }
+  if ((int)s->joins.size() != (int)h.nj) return bail(LMS_EINVAL);
+  // (s is not visible to any other thread yet; the copies below run on s->st,
+  // after the registrations' own copies have completed)
+  if (cudaSetDevice(s->cfg.device) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+    return bail(LMS_ECUDA);
+  if (h.origin_set) set_origin(s, h.origin_ts);
+  s->eos_seen = h.eos_seen != 0;
+  s->wm = h.wm;
+  unsigned long long need = 0;
+  for (uint32_t i = 0; i < h.nq; ++i) need = std::max<unsigned long long>(need, sq[i].groups);
+  if ((r = ensure_group_capacity(s, need + 1)) != LMS_OK) return bail(r);
+  std::vector<unsigned long long> gk;
+  for (uint32_t i = 0; i < h.nq; ++i) {
+    QueryHost& q = s->qs[i];
+    const SnapQuery& x = sq[i];
+    if ((r = ensure_rows(s, q, x.rows + 4096)) != LMS_OK) return bail(r);
+    if (x.groups) {
+      gk.resize(x.groups);
+      for (unsigned long long g = 0; g < x.groups; ++g)
+        std::memcpy(&gk[g], q_groups[i] + g * sizeof(Grp), sizeof(unsigned long long));
+      if (cudaMemcpyAsync(q.dev.parts, q_groups[i], x.groups * sizeof(Grp),
+                          cudaMemcpyHostToDevice, s->st) != cudaSuccess ||
+          cudaMemcpyAsync(q.dev.pkeys, gk.data(), x.groups * 8, cudaMemcpyHostToDevice,
+                          s->st) != cudaSuccess)
+        return bail(LMS_ECUDA);
+    }
+    if (x.rows && cudaMemcpyAsync(q.rows, q_rows[i], x.rows * sizeof(ResultRowDev),
+                                  cudaMemcpyHostToDevice, s->st) != cudaSuccess)
+      return bail(LMS_ECUDA);
+    QCtl c = x.ctl;
+    c.err = 0u;
+    if (cudaMemcpyAsync(q.dev.ctl, &c, sizeof(c), cudaMemcpyHostToDevice, s->st) != cudaSuccess)
+      return bail(LMS_ECUDA);
+    q.row_base = x.rows;
+    q.rows_read = 0;
+    q.carried = x.groups;
+    q.n_state = c.n_state;
+    q.late_rows = c.late_rows;
+    q.range_rows = c.range_rows;
+    q.rows_emitted = x.rows_emitted;
+  }
+  for (uint32_t j = 0; j < h.nj; ++j) {
+    JoinHost& jh = s->joins[j];
+    const SnapJoin& x = sj[j];
+    if ((r = ensure_join_rows(s, jh, x.rows + 4096)) != LMS_OK) return bail(r);
+    if (x.rows && cudaMemcpyAsync(jh.rows, j_rows[j], x.rows * sizeof(JoinRowDev),
+                                  cudaMemcpyHostToDevice, s->st) != cudaSuccess)
+      return bail(LMS_ECUDA);
+    JCtl c = x.ctl;
+    c.err = 0u;
+    if (cudaMemcpyAsync(jh.jc, &c, sizeof(c), cudaMemcpyHostToDevice, s->st) != cudaSuccess)
+      return bail(LMS_ECUDA);
+    jh.row_base = x.rows;
+    jh.rows_read = 0;
+    jh.rows_emitted = x.rows_emitted;
+  }
+  SCtl sc = h.sctl;
+  sc.batch_max_ts = LLONG_MIN;
+  if (cudaMemcpyAsync(s->sctl, &sc, sizeof(sc), cudaMemcpyHostToDevice, s->st) != cudaSuccess)
+    return bail(LMS_ECUDA);
+  s->stats = h.stats;
+  if (cudaStreamSynchronize(s->st) != cudaSuccess) return bail(LMS_ECUDA);
+  *out = s;
   return LMS_OK;
 }
 

@@ -39,10 +39,10 @@ __device__ __forceinline__ long long floor_div_ll(long long a, long long b) {
   return q;
 }
 
-__global__ void k_batch_begin(SCtl* sc, QCtl* c0, QCtl* c1, QCtl* c2, QCtl* c3, QCtl* c4,
-                              QCtl* c5, QCtl* c6, QCtl* c7) {
+__global__ void k_batch_begin(SCtl* sc, long long ts_floor, QCtl* c0, QCtl* c1, QCtl* c2,
+                              QCtl* c3, QCtl* c4, QCtl* c5, QCtl* c6, QCtl* c7) {
   if (threadIdx.x != 0) return;
-  sc->batch_max_ts = LLONG_MIN;
+  sc->batch_max_ts = ts_floor;  // LLONG_MIN, or a watermark hint for the batch
   QCtl* cs[8] = {c0, c1, c2, c3, c4, c5, c6, c7};
   for (int i = 0; i < 8; ++i)
     if (cs[i]) cs[i]->err = 0u;
@@ -992,10 +992,11 @@ cudaError_t set_smem_limit(const void* fn, int bytes, unsigned long long* done_m
   return e;
 }
 
-cudaError_t launch_batch_begin(SCtl* sctl, QCtl* const* ctls, int nq, cudaStream_t st) {
+cudaError_t launch_batch_begin(SCtl* sctl, QCtl* const* ctls, int nq, long long ts_floor,
+                               cudaStream_t st) {
   QCtl* c[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   for (int i = 0; i < nq && i < 8; ++i) c[i] = ctls[i];
-  k_batch_begin<<<1, 32, 0, st>>>(sctl, c[0], c[1], c[2], c[3], c[4], c[5], c[6], c[7]);
+  k_batch_begin<<<1, 32, 0, st>>>(sctl, ts_floor, c[0], c[1], c[2], c[3], c[4], c[5], c[6], c[7]);
   return cudaGetLastError();
 }
 

@@ -211,7 +211,10 @@ constexpr unsigned kJoinPendingBit = 1u, kJoinOverflowBit = 2u;
 
 // ---- launch wrappers (kernels_*.cu) -------------------------------------
 // All enqueue on `st` and return the launch error.
-cudaError_t launch_batch_begin(SCtl* sctl, QCtl* const* ctls, int nq, cudaStream_t st);
+// ts_floor: LLONG_MIN, or a lower bound of the batch's max event time (a
+// watermark hint, lms_stream_set_batch_max_ts).
+cudaError_t launch_batch_begin(SCtl* sctl, QCtl* const* ctls, int nq, long long ts_floor,
+                               cudaStream_t st);
 cudaError_t launch_k1(const K1Args& a, int variant, int grid, cudaStream_t st);
 int k1_max_grid(int device, int variant, int value_is_float);
 int k1_tile_events(int variant);

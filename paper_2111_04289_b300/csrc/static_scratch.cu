@@ -206,7 +206,7 @@ extern "C" lms_status lms_aggregate_batch_static(const lms_query_spec* q, int32_
 
   // ---- the hot path, end of stream: every window is emitted ----
   QCtl* ctls[1] = {d.ctl};
-  if (launch_batch_begin(sctl, ctls, 1, st) != cudaSuccess) return LMS_ECUDA;
+  if (launch_batch_begin(sctl, ctls, 1, LLONG_MIN, st) != cudaSuccess) return LMS_ECUDA;
   if (n_rows > 0) {
     K1Args a{};
     a.ts = reinterpret_cast<const long long*>(ts);

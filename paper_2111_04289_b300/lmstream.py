@@ -134,7 +134,9 @@ EXPORTED_SYMBOLS = ("stream_open", "query_register", "push_microbatch", "poll_re
                     "lms_variant_learned_destroy", "lms_variant_learned_set_online",
                     "lms_variant_learned_fit", "lms_variant_learned_choose",
                     "lms_variant_learned_observe", "lms_variant_learned_stats",
-                    "lms_join_register", "lms_join_poll")
+                    "lms_join_register", "lms_join_poll", "lms_shard_of", "lms_shard_split",
+                    "lms_stream_set_batch_max_ts", "lms_stream_set_origin",
+                    "lms_stream_snapshot", "lms_stream_restore", "lms_stream_get_config")
 ADMIT_PAPER, ADMIT_GUARDED = 0, 1
 QOPS = {"aggregation": 0, "filter": 1, "shuffle": 2, "project": 3, "join": 4, "expand": 5,
         "scan": 6, "sort": 7}
@@ -267,6 +269,20 @@ def load(build_if_missing: bool = True):
     lib.lms_join_poll.argtypes = [P, ctypes.c_int32, P, ctypes.c_size_t, P]
     lib.lms_stream_set_variant_chooser.restype = ctypes.c_int32
     lib.lms_stream_set_variant_chooser.argtypes = [P, P, P, P]
+    lib.lms_shard_of.restype = ctypes.c_uint32
+    lib.lms_shard_of.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int32]
+    lib.lms_shard_split.restype = ctypes.c_int32
+    lib.lms_shard_split.argtypes = [P, ctypes.c_uint32, ctypes.c_int32, P, P, P, P, P, P]
+    lib.lms_stream_set_batch_max_ts.restype = ctypes.c_int32
+    lib.lms_stream_set_batch_max_ts.argtypes = [P, ctypes.c_int64]
+    lib.lms_stream_set_origin.restype = ctypes.c_int32
+    lib.lms_stream_set_origin.argtypes = [P, ctypes.c_int64]
+    lib.lms_stream_snapshot.restype = ctypes.c_int32
+    lib.lms_stream_snapshot.argtypes = [P, P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
+    lib.lms_stream_restore.restype = ctypes.c_int32
+    lib.lms_stream_restore.argtypes = [P, ctypes.c_size_t, ctypes.c_int32, ctypes.POINTER(P)]
+    lib.lms_stream_get_config.restype = ctypes.c_int32
+    lib.lms_stream_get_config.argtypes = [P, ctypes.POINTER(StreamConfig)]
     lib.lms_variant_analytic_create.restype = P
     lib.lms_variant_analytic_create.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                                                 ctypes.c_int32, ctypes.c_int32]
@@ -574,6 +590,47 @@ class Stream:
             if got.value < chunk:
                 break
         return np.concatenate(parts) if parts else np.zeros(0, dtype=dt)
+
+    def set_batch_max_ts(self, ts: int) -> None:
+        """Watermark hint for the next push (lms_stream_set_batch_max_ts)."""
+        self._check(self._lib.lms_stream_set_batch_max_ts(self._h, int(ts)),
+                    "lms_stream_set_batch_max_ts")
+
+    def set_origin(self, origin_ts: int) -> None:
+        self._check(self._lib.lms_stream_set_origin(self._h, int(origin_ts)),
+                    "lms_stream_set_origin")
+
+    def snapshot(self) -> bytes:
+        """lms_stream_snapshot: the stream's state as bytes."""
+        n = ctypes.c_size_t()
+        self._check(self._lib.lms_stream_snapshot(self._h, None, 0, ctypes.byref(n)),
+                    "lms_stream_snapshot")
+        buf = ctypes.create_string_buffer(max(1, n.value))
+        self._check(self._lib.lms_stream_snapshot(self._h, buf, n.value, ctypes.byref(n)),
+                    "lms_stream_snapshot")
+        return buf.raw[: n.value]
+
+    @classmethod
+    def restore(cls, blob: bytes, device: int = -1) -> "Stream":
+        """lms_stream_restore: a new stream in the state a snapshot holds."""
+        lib = load()
+        h = ctypes.c_void_p()
+        buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+        st = lib.lms_stream_restore(buf, len(blob), int(device), ctypes.byref(h))
+        if st != LMS_OK:
+            raise LmsError(st, "lms_stream_restore failed")
+        self = cls.__new__(cls)
+        self._lib = lib
+        self._h = h
+        cfg = StreamConfig()
+        self._check(lib.lms_stream_get_config(h, ctypes.byref(cfg)), "lms_stream_get_config")
+        self.value_type = "float32" if cfg.value_type == VALUE_FLOAT32 else "int32"
+        self.is_float = cfg.value_type == VALUE_FLOAT32
+        self.has_type = bool(cfg.has_type)
+        self.row_dtype = ROW_DTYPE_FLOAT if self.is_float else ROW_DTYPE_INT
+        self.queries = []
+        self._ingest_keep = []
+        return self
 
     def set_variant_chooser(self, chooser) -> None:
         """Installs a VariantAnalytic / VariantLearned (or None) as the chooser of
