@@ -195,10 +195,12 @@ __device__ __forceinline__ double recip_small(unsigned n) {
   return __longlong_as_double(((long long)(e0 + 896) << 52) + m);
 }
 
+// The last two 16-byte parts of a row (sum, avg | key, min, max, query id);
+// the first is (window_start, count).
 template <bool FLOAT>
-__device__ __forceinline__ void write_row(const QueryDev& q, ResultRowDev* out, long long wstart,
-                                          unsigned key, long long cnt, unsigned long long sbits,
-                                          unsigned mn, unsigned mx) {
+__device__ __forceinline__ void row_parts(const QueryDev& q, unsigned key, long long cnt,
+                                          unsigned long long sbits, unsigned mn, unsigned mx,
+                                          uint4* p1, uint4* p2) {
   // avg = sum / count; counts of 1 and powers of two need no division (the
   // product with an exact power of two is the correctly rounded quotient).
   const double sd = FLOAT ? __longlong_as_double((long long)sbits) : (double)(long long)sbits;
@@ -231,15 +233,29 @@ __device__ __forceinline__ void write_row(const QueryDev& q, ResultRowDev* out, 
   unsigned mnv = 0u, mxv = 0u;
   if (q.agg_mask & 4u) mnv = FLOAT ? dec_f32_bits(mn) : (unsigned)dec_i32(mn);
   if (q.agg_mask & 8u) mxv = FLOAT ? dec_f32_bits(mx) : (unsigned)dec_i32(mx);
-  // rows are written once and read only by the host: streaming stores, so
-  // that they do not displace the state groups the next items read
+  const unsigned long long ab = (unsigned long long)__double_as_longlong(avg);
+  *p1 = make_uint4((unsigned)sbits, (unsigned)(sbits >> 32), (unsigned)ab, (unsigned)(ab >> 32));
+  *p2 = make_uint4(key, mnv, mxv, (unsigned)q.qid);
+}
+
+// Rows are written once and read only by the host: streaming stores, so that
+// they do not displace the state groups the next items read.
+__device__ __forceinline__ void store_row(ResultRowDev* out, long long wstart, long long cnt,
+                                          const uint4& p1, const uint4& p2) {
   uint4* o = reinterpret_cast<uint4*>(out);
   __stcs(o, make_uint4((unsigned)wstart, (unsigned)((unsigned long long)wstart >> 32),
                        (unsigned)cnt, (unsigned)((unsigned long long)cnt >> 32)));
-  const unsigned long long ab = (unsigned long long)__double_as_longlong(avg);
-  __stcs(o + 1,
-         make_uint4((unsigned)sbits, (unsigned)(sbits >> 32), (unsigned)ab, (unsigned)(ab >> 32)));
-  __stcs(o + 2, make_uint4(key, mnv, mxv, (unsigned)q.qid));
+  __stcs(o + 1, p1);
+  __stcs(o + 2, p2);
+}
+
+template <bool FLOAT>
+__device__ __forceinline__ void write_row(const QueryDev& q, ResultRowDev* out, long long wstart,
+                                          unsigned key, long long cnt, unsigned long long sbits,
+                                          unsigned mn, unsigned mx) {
+  uint4 p1, p2;
+  row_parts<FLOAT>(q, key, cnt, sbits, mn, mx, &p1, &p2);
+  store_row(out, wstart, cnt, p1, p2);
 }
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -297,6 +313,7 @@ constexpr int kEmRows = 4096;          // row descriptors per round
 // chunk and the round's row descriptors live in dynamic shared memory (EmDyn).
 struct EmSmem {
   unsigned long long split[kEmT + 1];  // merge-path A counts at chunk starts
+  unsigned long long split_b[kEmT + 1];// B counts at chunk starts (key-aligned chunks)
   long long cnt[kMaxItemWindows + 2];  // rows per window
   int wdiff[kEmWarps][kMaxItemWindows + 2];      // per-warp difference arrays of the count
   unsigned long long woff[kMaxItemWindows + 1];  // rows of the item before window i
@@ -329,11 +346,15 @@ struct EmDyn {
   unsigned long long* mm;    // [kEmC] mn | mx << 32
   unsigned short* mo;        // [kEmC]
   unsigned short* hp;        // [kEmC + 1]
-  unsigned short* rows;      // [kEmRows]
-  unsigned* rln;             // [kEmRows] first group | number of groups << 16
+  unsigned* kw;              // [kEmC] per key of the chunk: its panes (relative to the
+                             // item's block) as bits (pane-word path)
+  unsigned* rln;             // [kEmRows] first group | number of groups << 16 (general path)
+  unsigned short* rows;      // [kEmRows] (general path)
 };
-constexpr size_t kEmDynBytes = (size_t)kEmC * (4 * 8 + 2) + (kEmC + 1) * 2 + 6 +
-                               (size_t)kEmRows * (4 + 2);
+// Dynamic shared memory of the pane-word path (no row descriptors) and of the
+// general path.
+constexpr size_t kEmDynBytesPW = (size_t)kEmC * (4 * 8 + 2) + (kEmC + 1) * 2 + 6 + (size_t)kEmC * 4;
+constexpr size_t kEmDynBytes = kEmDynBytesPW + (size_t)kEmRows * (4 + 2);
 
 __device__ __forceinline__ EmDyn em_dyn() {
   extern __shared__ __align__(16) unsigned char em_smem[];
@@ -345,6 +366,7 @@ __device__ __forceinline__ EmDyn em_dyn() {
   d.mm = reinterpret_cast<unsigned long long*>(p); p += (size_t)kEmC * 8;
   d.mo = reinterpret_cast<unsigned short*>(p); p += (size_t)kEmC * 2;
   d.hp = reinterpret_cast<unsigned short*>(p); p += (size_t)(kEmC + 1) * 2 + 6;
+  d.kw = reinterpret_cast<unsigned*>(p); p += (size_t)kEmC * 4;
   d.rln = reinterpret_cast<unsigned*>(p); p += (size_t)kEmRows * 4;
   d.rows = reinterpret_cast<unsigned short*>(p);
   return d;
@@ -426,34 +448,61 @@ __device__ __forceinline__ unsigned long long pane_windows(long long p, int k, l
   return m << (int)(lo - wlo);
 }
 
+// First index of key k in g[lo, hi) (g is key-ordered there).
+__device__ __forceinline__ unsigned long long key_lower_bound(const Grp* g, unsigned long long lo,
+                                                              unsigned long long hi, unsigned k,
+                                                              int lb) {
+  while (lo < hi) {
+    const unsigned long long mid = (lo + hi) >> 1;
+    if (gkey_key(g[mid].gkey, lb) < k) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
 // Walks chunk by chunk over the merged runs of the item.  Each chunk is
 // staged (records loaded with 16-byte vector loads; only the gkeys when
 // full == false) and merged into d.mo; then f(len, la, a0, b0, last) runs
 // with the chunk in shared memory (after a barrier) and must end with a
 // barrier.  sm.carry_g holds the previous chunk's last merged gkey (if
-// sm.carry_valid).
+// sm.carry_valid).  With key_aligned (only for 2B <= 32), chunks nominally
+// hold kEmC - 32 entries and every boundary is moved back to the first group
+// of the key there, so that no key straddles two chunks: a key has fewer than
+// 2B <= 32 groups before a boundary, so a chunk stays within kEmC entries.
 template <class F>
 __device__ void for_merged_chunks(const QueryDev& q, const Item& it, EmSmem& sm, const EmDyn& d,
-                                  bool full, F f) {
+                                  bool full, F f, bool key_aligned = false) {
   const int tid = threadIdx.x;
   const int lb = q.lb;
   const unsigned long long L = it.na + it.nb;
-  const unsigned long long nch = (L + kEmC - 1) / kEmC;
+  const unsigned long long C = key_aligned ? (unsigned long long)(kEmC - 32) : (unsigned long long)kEmC;
+  const unsigned long long nch = (L + C - 1) / C;
   if (tid == 0) sm.carry_valid = 0;
   for (unsigned long long k0 = 0; k0 < nch; k0 += kEmT) {
     const unsigned long long kn = nch - k0 < (unsigned long long)kEmT ? nch - k0 : kEmT;
     __syncthreads();  // the previous batch of chunks no longer reads sm.split
     for (unsigned long long t = tid; t <= kn; t += kEmT) {
-      const unsigned long long dd = (k0 + t) * kEmC;
-      sm.split[t] = merge_split_g(it, dd < L ? dd : L, lb);
+      const unsigned long long dd = (k0 + t) * C < L ? (k0 + t) * C : L;
+      unsigned long long a = merge_split_g(it, dd, lb), b = dd - a;
+      if (key_aligned && dd > 0 && dd < L) {
+        // the key of merged entry dd starts at (lower bound in A, lower bound in B)
+        const unsigned ka = a < it.na ? gkey_key(it.A[a].gkey, lb) : 0xffffffffu;
+        const unsigned kb = b < it.nb ? gkey_key(it.Bv[b].gkey, lb) : 0xffffffffu;
+        const bool from_a = a < it.na && (b >= it.nb || ka <= kb);
+        const unsigned k = from_a ? ka : kb;
+        const unsigned long long span = 1ull << lb;  // groups of one key in one run
+        a = key_lower_bound(it.A, a > span ? a - span : 0ull, a, k, lb);
+        b = key_lower_bound(it.Bv, b > span ? b - span : 0ull, b, k, lb);
+      }
+      sm.split[t] = a;
+      sm.split_b[t] = b;
     }
     __syncthreads();
     for (unsigned long long kk = 0; kk < kn; ++kk) {
-      const unsigned long long d0 = (k0 + kk) * kEmC;
-      const unsigned long long d1 = d0 + kEmC < L ? d0 + kEmC : L;
       const unsigned long long a0 = sm.split[kk], a1 = sm.split[kk + 1];
-      const unsigned long long b0 = d0 - a0;
-      const unsigned la = (unsigned)(a1 - a0), len = (unsigned)(d1 - d0);
+      const unsigned long long b0 = sm.split_b[kk], b1 = sm.split_b[kk + 1];
+      const unsigned long long d1 = a1 + b1;
+      const unsigned la = (unsigned)(a1 - a0), len = (unsigned)(a1 - a0 + b1 - b0);
       if (full) {  // two 16-byte halves per record
         for (unsigned h = tid; h < 2 * len; h += kEmT) {
           const unsigned r = h >> 1;
@@ -825,11 +874,173 @@ __device__ void write_item(const QueryDev& q, const Item& it, EmSmem& sm, const 
   });
 }
 
+// The pane-word path of write_item, for items whose two blocks span 2B <= 32
+// panes (K <= 16).  Chunks are key-aligned, so every key of a chunk is whole
+// in shared memory.  Every merged entry ORs the bit of its pane (relative to
+// the item's block b) into its key's word; a key's windows are then the word
+// dilated by K (a window whose first pane is r, relative to block b, holds
+// the key iff a bit of [r, r + K) is set), and the groups of its row in that
+// window are the set bits of [r, r + K): the first is the number of set bits
+// below r (the key's groups are in pane order), their number the set bits in
+// the range.  Per round of up to kEmT keys (one per thread): the warps'
+// ballots per window and one prefix over the warps give every row its output
+// position; then each warp writes its own keys' rows window by window (the
+// lanes whose key is in the window write consecutive rows), with no row
+// descriptors and no barrier between the warps' rows.
+template <bool FLOAT>
+__device__ void write_item_pw(const QueryDev& q, const Item& it, EmSmem& sm, const EmDyn& d,
+                              ResultRowDev* out) {
+  const int tid = threadIdx.x, w = tid >> 5;
+  const unsigned lane = lane_id(), lt = (1u << lane) - 1u;
+  const int lb = q.lb, K = q.k;
+  const int nw = (int)(it.whi - it.wlo + 1);
+  if (K == 1) {  // tumbling: the rows are the pane's groups, in key order
+    const long long wstart = (it.wlo - kPaneBias) * (long long)q.slide + q.base;
+    for (unsigned long long i = tid; i < it.na; i += kEmT) {
+      const Grp g = load_grp_v(it.A + i);
+      write_row<FLOAT>(q, out + i, wstart, gkey_key(g.gkey, lb), g.cnt, g.sum, g.mn, g.mx);
+    }
+    __syncthreads();
+    return;
+  }
+  const unsigned long long blk = (unsigned long long)it.wlo >> lb;  // the item's block b
+  const int wrel0 = (int)(it.wlo - (long long)(blk << lb));         // wlo relative to block b
+  const unsigned long long wmask = nw >= 64 ? ~0ull : ((1ull << nw) - 1ull);
+  const unsigned long long kmask = (1ull << K) - 1ull;
+  const long long wstart0 = (it.wlo - kPaneBias) * (long long)q.slide + q.base;
+  for (int i = tid; i < nw; i += kEmT) sm.run[i] = 0u;
+  for_merged_chunks(q, it, sm, d, true, [&](unsigned len, unsigned, unsigned long long,
+                                            unsigned long long, bool) {
+    // heads (a chunk starts with one) and each entry's key index
+    unsigned nh_t = 0;
+    bool head[kEmE];
+    const unsigned x0 = (unsigned)tid * kEmE;
+#pragma unroll
+    for (int e = 0; e < kEmE; ++e) {
+      const unsigned x = x0 + e;
+      head[e] = x < len && (x == 0 || gkey_key(d.gk[d.mo[x - 1]], lb) != gkey_key(d.gk[d.mo[x]], lb));
+      nh_t += head[e] ? 1u : 0u;
+    }
+    unsigned long long htot;
+    unsigned long long hpos = block_excl_scan((unsigned long long)nh_t, sm.tmp, &htot);
+    unsigned ki = (unsigned)hpos;  // key index + 1 of the current entry
+#pragma unroll
+    for (int e = 0; e < kEmE; ++e)
+      if (head[e]) d.hp[hpos++] = (unsigned short)(x0 + e);
+    const unsigned nh = (unsigned)htot;
+    for (unsigned k = tid; k < nh; k += kEmT) d.kw[k] = 0u;
+    if (tid == 0) d.hp[nh] = (unsigned short)len;
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < kEmE; ++e) {
+      const unsigned x = x0 + e;
+      if (x < len) {
+        ki += head[e] ? 1u : 0u;
+        const unsigned long long g = d.gk[d.mo[x]];
+        const unsigned rel =
+            (unsigned)(g & ((1ull << lb) - 1ull)) | ((unsigned)(gkey_block(g, lb) - blk) << lb);
+        atomicOr(&d.kw[ki - 1], 1u << rel);
+      }
+    }
+    __syncthreads();
+    for (unsigned r0 = 0; r0 < nh; r0 += kEmT) {
+      const unsigned h = r0 + (unsigned)tid;
+      unsigned hx = 0u;
+      unsigned long long word = 0ull, mask = 0ull;
+      if (h < nh) {
+        hx = d.hp[h];
+        word = d.kw[h];
+        unsigned long long dl = word;  // dilation by K: bit r set iff a bit of [r, r + K) is
+        int span = 1;
+        while (2 * span <= K) {
+          dl |= dl >> span;
+          span <<= 1;
+        }
+        if (span < K) dl |= dl >> (K - span);
+        mask = (dl >> wrel0) & wmask;
+      }
+      const unsigned long long orm =
+          ((unsigned long long)__reduce_or_sync(kFull, (unsigned)(mask >> 32)) << 32) |
+          __reduce_or_sync(kFull, (unsigned)mask);
+      for (int i = lane; i < nw; i += 32) sm.wc[w][i] = 0u;
+      __syncwarp();
+      for (unsigned long long bits = orm; bits; bits &= bits - 1) {
+        const int i = __ffsll((long long)bits) - 1;
+        const unsigned bal = __ballot_sync(kFull, (mask >> i) & 1ull);
+        if (lane == 0) sm.wc[w][i] = (unsigned)__popc(bal);
+      }
+      __syncthreads();
+      // output offsets: warps inside each window, after the rows of the
+      // window's earlier rounds
+      if (tid < 32) {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int i = tid + 32 * u;
+          if (i < nw) {
+            unsigned acc = (unsigned)sm.woff[i] + sm.run[i];
+#pragma unroll
+            for (int ww = 0; ww < kEmWarps; ++ww) {
+              const unsigned t = sm.wc[ww][i];
+              sm.wc[ww][i] = acc;
+              acc += t;
+            }
+            sm.run[i] = acc - (unsigned)sm.woff[i];
+          }
+        }
+      }
+      __syncthreads();
+      // this warp's rows, window by window; consecutive windows of a key often
+      // hold the same groups, so the row's aggregate parts are kept for the
+      // last (first group, number of groups) and only recomputed on a change
+      const unsigned key = gkey_key(d.gk[d.mo[hx]], lb);
+      unsigned cx = ~0u, cn = 0u;
+      long long ccnt = 0;
+      uint4 p1 = make_uint4(0u, 0u, 0u, 0u), p2 = p1;
+      for (unsigned long long bits = orm; bits; bits &= bits - 1) {
+        const int i = __ffsll((long long)bits) - 1;
+        const bool in = (mask >> i) & 1ull;
+        const unsigned bal = __ballot_sync(kFull, in);
+        if (!in) continue;
+        const int r = wrel0 + i;  // the window's first pane, relative to block b
+        const unsigned x = hx + (unsigned)__popcll(word & ((1ull << r) - 1ull));
+        const unsigned nn = (unsigned)__popcll(word & (kmask << r));
+        if (x != cx || nn != cn) {
+          unsigned slot = d.mo[x];
+          long long cnt = d.cnt[slot];
+          unsigned long long isum = d.sum[slot];
+          double fsum = __longlong_as_double((long long)isum);
+          unsigned long long m = d.mm[slot];
+          unsigned mn = (unsigned)m, mx = (unsigned)(m >> 32);
+          for (unsigned e = 1; e < nn; ++e) {
+            slot = d.mo[x + e];
+            cnt += d.cnt[slot];
+            const unsigned long long sv = d.sum[slot];
+            if (FLOAT) fsum += __longlong_as_double((long long)sv);
+            else isum += sv;
+            m = d.mm[slot];
+            mn = min(mn, (unsigned)m);
+            mx = max(mx, (unsigned)(m >> 32));
+          }
+          const unsigned long long sb =
+              FLOAT ? (unsigned long long)__double_as_longlong(fsum) : isum;
+          row_parts<FLOAT>(q, key, cnt, sb, mn, mx, &p1, &p2);
+          ccnt = cnt;
+          cx = x;
+          cn = nn;
+        }
+        const unsigned pos = sm.wc[w][i] + (unsigned)__popc(bal & lt);
+        store_row(out + pos, wstart0 + (long long)i * (long long)q.slide, ccnt, p1, p2);
+      }
+    }
+    __syncthreads();
+  }, true);
+}
+
 // Emits the closed windows.  CTAs take items in ticket order; for each item:
 // its rows per window (count_item), its row offset by the look-back, then the
 // rows (write_item).
-template <bool FLOAT>
-__global__ void __launch_bounds__(kEmT, 3)
+template <bool FLOAT, bool PW>
+__global__ void __launch_bounds__(kEmT, PW ? 4 : 3)
     k_emit(const QueryDev q, const Scratch s, ResultRowDev* rows, unsigned long long rows_cap) {
   __shared__ EmSmem sm;
   const EmDyn d = em_dyn();
@@ -858,8 +1069,10 @@ __global__ void __launch_bounds__(kEmT, 3)
     __syncthreads();
     const unsigned long long off = sm.off;
     __syncthreads();
-    if (off != ~0ull && row_base + off + sm.total <= rows_cap)
-      write_item<FLOAT>(q, it, sm, d, rows + row_base + off);
+    if (off != ~0ull && row_base + off + sm.total <= rows_cap) {
+      if (PW) write_item_pw<FLOAT>(q, it, sm, d, rows + row_base + off);
+      else write_item<FLOAT>(q, it, sm, d, rows + row_base + off);
+    }
     __syncthreads();
   }
 }
@@ -1030,14 +1243,27 @@ cudaError_t launch_emit(const QueryDev& q, const Scratch& s, ResultRowDev* rows,
     record_event(ev4[1], st);
     record_event(ev4[2], st);
   }
-  static unsigned long long done_f = 0, done_i = 0;  // devices whose limit is set
-  cudaError_t e = q.value_is_float
-                      ? set_smem_limit(reinterpret_cast<const void*>(k_emit<true>), (int)kEmDynBytes, &done_f)
-                      : set_smem_limit(reinterpret_cast<const void*>(k_emit<false>), (int)kEmDynBytes, &done_i);
+  // devices whose smem limit is set, per kernel
+  static unsigned long long done[4] = {0, 0, 0, 0};
+  const bool pw = (2 << q.lb) <= 32;
+  const void* fn = q.value_is_float
+                       ? (pw ? reinterpret_cast<const void*>(k_emit<true, true>)
+                             : reinterpret_cast<const void*>(k_emit<true, false>))
+                       : (pw ? reinterpret_cast<const void*>(k_emit<false, true>)
+                             : reinterpret_cast<const void*>(k_emit<false, false>));
+  const size_t dyn = pw ? kEmDynBytesPW : kEmDynBytes;
+  cudaError_t e = set_smem_limit(fn, (int)dyn, &done[(q.value_is_float ? 2 : 0) + (pw ? 1 : 0)]);
   if (e != cudaSuccess) return e;
-  const int grid = 3 * sms;
-  if (q.value_is_float) k_emit<true><<<grid, kEmT, kEmDynBytes, st>>>(q, s, rows, rows_cap);
-  else k_emit<false><<<grid, kEmT, kEmDynBytes, st>>>(q, s, rows, rows_cap);
+  // resident CTAs per SM: four on the pane-word path (64 registers, 54 KB of
+  // shared memory), three on the general one (its row descriptors need more)
+  const int grid = (pw ? 4 : 3) * sms;
+  if (q.value_is_float) {
+    if (pw) k_emit<true, true><<<grid, kEmT, dyn, st>>>(q, s, rows, rows_cap);
+    else k_emit<true, false><<<grid, kEmT, dyn, st>>>(q, s, rows, rows_cap);
+  } else {
+    if (pw) k_emit<false, true><<<grid, kEmT, dyn, st>>>(q, s, rows, rows_cap);
+    else k_emit<false, false><<<grid, kEmT, dyn, st>>>(q, s, rows, rows_cap);
+  }
   if (ev4) record_event(ev4[3], st);
   if (launches) *launches += 5;
   return cudaGetLastError();
