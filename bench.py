@@ -448,6 +448,63 @@ def run_profile_serving(args):
     return 0
 
 
+def run_profile_carry(args):
+    """Per-batch cost against the open state: `--profile-batches` micro-batches
+    of `--profile-events` events arriving at 2e8 events/s (ts spread evenly over
+    the batch's span), key Zipf(1.1) over 1M keys, the serving query (sliding
+    60 s / 5 s), columns generated in HBM per batch.  Prints, every 50 batches
+    and at the end, the carried groups and the mean per-batch k1 / sort-merge-
+    reduce / emission times (CUDA events) of the last 50 batches."""
+    import torch
+
+    from paper_2111_04289_b300 import lmstream as lm
+    from paper_2111_04289_b300 import synth
+
+    dev = torch.device("cuda", 0)
+    n, nb = args.profile_events, args.profile_batches
+    span_ms = max(1, round(n / 2e8 * 1e3))
+    g = torch.Generator(device=dev)
+    g.manual_seed(synth.BASE_SEED + 43)
+    w = torch.arange(1, 1_000_001, dtype=torch.float64, device=dev) ** -1.1
+    cdf = torch.cumsum(w, 0)
+    cdf = cdf / cdf[-1]
+    # the engine runs on the (non-default) torch stream that generates each
+    # batch, so a batch's columns are complete before the fused pass reads them
+    cs = torch.cuda.Stream(dev)
+    s = lm.Stream("float32", enable_timing=True, k1_variant=1, cuda_stream=cs.cuda_stream)
+    qid = s.register_query(WINDOW_SIZE_MS, WINDOW_SLIDE_MS, "value", "gt", FILTER_GT)
+    rows, last = [], s.stats()
+    t0 = 0
+    torch.cuda.synchronize()
+    for b in range(nb):
+        with torch.cuda.stream(cs):
+            ts = t0 + (torch.arange(n, device=dev, dtype=torch.int64) * span_ms) // n
+            key = torch.searchsorted(cdf, torch.rand(n, generator=g, device=dev, dtype=torch.float64),
+                                     right=True).clamp_(max=999_999).to(torch.int32)
+            val = torch.exp(torch.randn(n, generator=g, device=dev, dtype=torch.float32))
+            t0 += span_ms
+            cs.synchronize()
+            w0 = time.perf_counter()
+            s.push(ts, key, val)
+            wall = (time.perf_counter() - w0) * 1e3
+            s.discard(qid)
+            st = s.stats()
+            rows.append({k: st[k] - last[k] for k in ("k1_ms", "sort_ms", "emit_ms")})
+            rows[-1]["push_wall_ms"] = wall
+            rows[-1]["carried"] = st["state_groups"]
+            last = st
+            if (b + 1) % 50 == 0 or b + 1 == nb:
+                tail = rows[-50:]
+                print(json.dumps({"profile_carry": {
+                    "batches": b + 1, "events_per_batch": n, "event_time_s": t0 / 1e3,
+                    "carried_groups": rows[-1]["carried"],
+                    "mean_ms_last50": {k: round(sum(r[k] for r in tail) / len(tail), 4)
+                                       for k in ("k1_ms", "sort_ms", "emit_ms",
+                                                 "push_wall_ms")}}}), flush=True)
+    s.close()
+    return 0
+
+
 def max_over_ranks(dist, torch, x, device):
     """Largest x over the ranks: a job's timed region lasts as long as its
     slowest rank's."""
@@ -674,6 +731,8 @@ def main():
     ap.add_argument("--fixed-triggers", type=lambda x: [float(v) for v in x.split(",")],
                     default=[25.0, 50.0])
     ap.add_argument("--ref-duration-ms", type=float, default=20_000.0)
+    ap.add_argument("--profile-carry", action="store_true",
+                    help="per-batch sort/merge cost against a growing open state, then exit")
     ap.add_argument("--profile-serving", action="store_true",
                     help="run a fixed serving-like load for a profiler and exit")
     ap.add_argument("--profile-events", type=int, default=20_000_000)
@@ -685,6 +744,8 @@ def main():
         print("note: warmup < 3 is below the timing rules", file=sys.stderr)
     if args.profile_serving:
         sys.exit(run_profile_serving(args))
+    if args.profile_carry:
+        sys.exit(run_profile_carry(args))
     sys.exit(run_reference(args) if args.impl == "reference" else run_ours(args))
 
 

@@ -113,20 +113,13 @@ typedef struct lms_stream_config {
                                   tiles (two CTAs per SM); 2 = 2048-event tiles (one CTA per SM);
                                   3 / 4 = 1 / 2 with warp aggregation of equal group keys */
   int32_t graph_mode;          /* LMS_GRAPH_*: replay the per-batch launch sequence from a CUDA graph */
-  int32_t lookback_limit_us;   /* bound of the emission's device-side wait for the row counts of
-                                  earlier windows, us; 0 = 4 s.  When it runs out the push
-                                  returns LMS_EDEVICE (latched) instead of waiting longer. */
-  uint32_t debug_flags;        /* LMS_DEBUG_*: test hooks, 0 in normal use */
+  int32_t reserved0;           /* 0 */
+  uint32_t reserved1;          /* 0 */
   uint32_t key_fields;         /* the key column as up to four packed fields: byte f holds the
                                   bit width of field f (field 0 in the lowest bits); 0 = one
                                   32-bit field.  Widths must sum to <= 32. */
   int32_t reserved[3];
 } lms_stream_config;
-
-/* debug_flags.  HOLD_FIRST_ITEM: the first group of closed windows never
- * publishes its row count, so the emission's bounded wait runs out (a test of
- * the failure path; the push returns LMS_EDEVICE). */
-#define LMS_DEBUG_HOLD_FIRST_ITEM 1u
 
 /* graph_mode.  Everything a push launches after the fused pass reads its sizes
  * on the device, so the sequence is captured once into a CUDA graph and
@@ -891,7 +884,7 @@ lms_status lms_server_destroy(lms_server *sv);
  * rows[0 .. rows_cap); *n_out receives their number.  The first row's ts is
  * the event-time origin.  Returns when the rows are written.
  *
- * Every intermediate buffer lives in one fixed array of about 17 MiB that the
+ * Every intermediate buffer lives in one fixed array of about 31 MiB that the
  * library declares in device memory: it is present on every GPU that loads the
  * library until the process exits, and this function calls no cudaMalloc,
  * cudaFree or other allocating routine.  The first call on a device looks the
@@ -906,10 +899,10 @@ lms_status lms_server_destroy(lms_server *sv);
  * must be 0.
  *
  * Errors: LMS_EINVAL for a bad argument or n_rows > LMS_STATIC_MAX_ROWS;
- * LMS_ENOMEM if the emission items (runs of up to 64 consecutive closed
- * windows; at most 131072) or the rows do not fit (rows_cap >= n_rows *
- * size/slide always suffices); LMS_ECUDA for a CUDA failure; LMS_EDEVICE for
- * an internal kernel flag. */
+ * LMS_ENOMEM if the emission units (runs of up to 64 consecutive closed
+ * windows, cut into pieces of about 32K state groups; at most 32768) or the
+ * rows do not fit (rows_cap >= n_rows * size/slide always suffices);
+ * LMS_ECUDA for a CUDA failure; LMS_EDEVICE for an internal kernel flag. */
 lms_status lms_aggregate_batch_static(const lms_query_spec *q, int32_t value_type,
                                       const int64_t *ts, const uint32_t *key, const void *value,
                                       const uint8_t *type, int64_t n_rows, void *cuda_stream,

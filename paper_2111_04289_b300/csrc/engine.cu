@@ -271,6 +271,8 @@ lms_status ensure_items(lms_stream* s, unsigned long long need) {
   if ((r = dgrow(s, &sc.item_c, sc.item_cap, nc, 0)) != LMS_OK) return r;
   if ((r = dgrow(s, &sc.item_j, sc.item_cap, nc, 0)) != LMS_OK) return r;
   if ((r = dgrow(s, &sc.item_stat, sc.item_cap, nc, 0)) != LMS_OK) return r;
+  if ((r = dgrow(s, &sc.unit_off, sc.item_cap * kMaxItemWindows, nc * kMaxItemWindows, 0)) != LMS_OK)
+    return r;
   sc.item_cap = nc;
   return LMS_OK;
 }
@@ -515,9 +517,6 @@ lms_status register_query(lms_stream* s, const lms_query_spec* q, bool hidden, i
   d.size = size;
   d.k = h.k;
   set_block_shape(&d);
-  d.lookback_ns = s->cfg.lookback_limit_us > 0 ? 1000ull * (unsigned long long)s->cfg.lookback_limit_us
-                                               : 4000000000ull;
-  d.debug_flags = s->cfg.debug_flags;
   d.key_mask = key_mask;
   d.having_agg = q->having_agg;
   d.having_op = q->having_op;
@@ -897,7 +896,7 @@ lms_status run_batch(lms_stream* s, const InSeg* seg, int nseg, long long n, int
       return fail(s, LMS_ENOMEM, "emission buffers could not be grown enough");
     if (hc[i].err & kErrOrderBy)
       return fail(s, LMS_EINVAL, "ORDER BY: a window holds more than LMS_ORDER_MAX_ROWS rows");
-    if (hc[i].err & (kErrPartsOverflow | kErrProbe | kErrLookback)) {
+    if (hc[i].err & (kErrPartsOverflow | kErrProbe)) {
       s->latched = LMS_EDEVICE;
       return fail(s, LMS_EDEVICE, "internal device error flag raised by a kernel");
     }
@@ -1258,7 +1257,7 @@ lms_status lms_stream_push_bytes(lms_stream* s, int64_t n_rows, int32_t host_inp
   }
   // emission buffers a first push allocates (later growth follows the rows
   // a batch emits and is not predicted here)
-  if (s->scr.item_cap == 0) total += 1024ull * (8 + 4 + 8);
+  if (s->scr.item_cap == 0) total += 1024ull * (8 + 4 + 8 + 8 * kMaxItemWindows);
   for (const QueryHost& q : s->qs)
     if (q.rows_cap == 0) total += round_cap(4096 + 4096 / 4) * sizeof(lms_result_row);
   *bytes = total;

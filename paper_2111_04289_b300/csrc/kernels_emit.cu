@@ -11,21 +11,23 @@
 // (lms_internal.h).  Closed windows are emitted by "items": an item is a run
 // of up to 64 consecutive window ids that start in one block b, so every
 // window of the item covers panes of blocks b and b + 1 only.  Both blocks
-// are key-major runs of the state; the CTA that takes an item merges the two
-// runs by key (merge path, chunks of 1024 entries through shared memory) and
-// gives each distinct key to one thread.  The thread walks the key's groups
-// (in pane order) once to find the windows of the item that hold the key (a
-// 64-bit mask), and the warp's ballots over the masks give every row its rank
-// among the window's keys, so the rows of one window and one warp land at
-// consecutive positions; then the thread combines, for each of its windows,
-// the groups whose pane lies in the window and writes the row.  Each group is
-// read by the threads of at most two items (instead of once per window that
-// holds it), and no per-window key list is built.
+// are key-major runs of the state; merged by key (merge path) they give every
+// key's groups of the item in pane order.  An item's merged runs are cut at
+// key boundaries into units of about 32K entries, and every unit is one CTA's
+// work: it stages its merged entries chunk by chunk in shared memory, finds
+// for each distinct key the windows of the item that hold it (a bit mask over
+// the item's windows) and writes the key's row of each such window, combining
+// the key's groups whose pane lies in the window.  Warp ballots over the masks
+// give every row its rank among the window's keys, so the rows of one window
+// and one warp land at consecutive positions.  Each group is read by the
+// units of at most two items (instead of once per window that holds it).
 //
-// An item's row count is found first (the same merge; each group is the key's
-// first group in the windows between its previous pane + 1 and its own pane,
-// added to a difference array over the item's windows), then the item's row
-// offset comes from a decoupled look-back over the items before it.
+// The output positions come first: k_emit_count finds every unit's rows per
+// window (the same merge; each group is the key's first group in the windows
+// between its previous pane + 1 and its own pane, added to a difference array
+// over the item's windows), one exclusive scan over those counts laid out in
+// (item, window, unit) order gives every (unit, window) its first output row,
+// and k_emit_write writes the rows.  No CTA waits on another.
 #include <climits>
 
 #include "lms_device.cuh"
@@ -91,7 +93,125 @@ __global__ void k_emit_begin(QCtl* c) {
   c->rows_batch = 0ull;
   c->n_items = 0ull;
   c->item_ticket = 0ull;
+  c->unit_ticket = 0ull;
   c->err &= ~kErrNeedRetry;
+}
+
+struct Item {
+  const Grp* A;               // run A: block b, key-major (may be empty)
+  unsigned long long na;
+  const Grp* Bv;              // run B: block b + 1 (empty if the item's windows do not reach it)
+  unsigned long long nb;
+  long long wlo, whi;         // the item's closed windows (relative ids, inclusive)
+  // the unit of the item (key-aligned range of its merged runs) one CTA takes
+  unsigned long long a_lo, b_lo, a_hi, b_hi;  // A / B entries before the unit's start / end
+  unsigned sub, nsub;         // the unit's index in the item, the item's units
+};
+
+// The runs of the item of window chunk cc anchored at block index ja.
+__device__ __forceinline__ Item load_item(const QueryDev& q, const Scratch& s, const QCtl* c,
+                                          long long cc, unsigned long long ja) {
+  Item it;
+  const unsigned long long nblk = c->n_blocks;
+  const long long w0 = cc * q.nw;
+  const unsigned long long b = (unsigned long long)w0 >> q.lb;
+  it.wlo = w0 > c->cursor ? w0 : c->cursor;
+  it.whi = w0 + q.nw - 1 < c->w_hi ? w0 + q.nw - 1 : c->w_hi;
+  unsigned long long jb = ja;
+  it.A = q.state;
+  it.na = 0;
+  if (ja < nblk && s.blk_id[ja] == b) {
+    const unsigned long long a0 = s.blk_begin[ja];
+    it.A = q.state + a0;
+    it.na = s.blk_begin[ja + 1] - a0;
+    jb = ja + 1;
+  }
+  it.Bv = q.state;
+  it.nb = 0;
+  const long long last_pane = it.whi + q.k - 1;
+  if (q.k > 1 && jb < nblk && s.blk_id[jb] == b + 1 &&
+      last_pane >= (long long)((b + 1) << q.lb)) {
+    const unsigned long long b0 = s.blk_begin[jb];
+    it.Bv = q.state + b0;
+    it.nb = s.blk_begin[jb + 1] - b0;
+  }
+  it.a_lo = it.b_lo = 0;
+  it.a_hi = it.na;
+  it.b_hi = it.nb;
+  it.sub = 0;
+  it.nsub = 1;
+  return it;
+}
+
+// Merged entries per unit: an item's merged runs are cut into units of about
+// this many entries (at key boundaries), each taken by one CTA, so that a few
+// closed windows over a large state still spread over the whole GPU.
+constexpr unsigned long long kUnitEntries = 32768;
+
+__device__ __forceinline__ unsigned item_units(const Item& it) {
+  const unsigned long long L = it.na + it.nb;
+  return L == 0 ? 1u : (unsigned)((L + kUnitEntries - 1) / kUnitEntries);
+}
+
+// Merge order of the two runs: by key; on equal keys run A first (its panes
+// are the earlier ones).  Number of A entries among the first d merged
+// entries (merge path, global memory).
+__device__ unsigned long long merge_split_g(const Item& it, unsigned long long d, int lb) {
+  unsigned long long lo = d > it.nb ? d - it.nb : 0ull, hi = d < it.na ? d : it.na;
+  while (lo < hi) {
+    const unsigned long long mid = (lo + hi) >> 1;
+    if (gkey_key(it.A[mid].gkey, lb) <= gkey_key(it.Bv[d - 1 - mid].gkey, lb)) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// First index of key k in g[lo, hi) (g is key-ordered there).
+__device__ __forceinline__ unsigned long long key_lower_bound(const Grp* g, unsigned long long lo,
+                                                              unsigned long long hi, unsigned k,
+                                                              int lb) {
+  while (lo < hi) {
+    const unsigned long long mid = (lo + hi) >> 1;
+    if (gkey_key(g[mid].gkey, lb) < k) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Key-aligned merge split at merged position d: (A entries, B entries) before
+// the first group of the key of merged entry d (d itself at 0 and L).  A key
+// has at most B groups in each run, so the lower bounds search that far back.
+__device__ __forceinline__ void aligned_split(const Item& it, unsigned long long d, int lb,
+                                              unsigned long long* pa, unsigned long long* pb) {
+  unsigned long long a = merge_split_g(it, d, lb), b = d - a;
+  if (d > 0 && d < it.na + it.nb) {
+    const unsigned ka = a < it.na ? gkey_key(it.A[a].gkey, lb) : 0xffffffffu;
+    const unsigned kb = b < it.nb ? gkey_key(it.Bv[b].gkey, lb) : 0xffffffffu;
+    const bool from_a = a < it.na && (b >= it.nb || ka <= kb);
+    const unsigned k = from_a ? ka : kb;
+    const unsigned long long span = 1ull << lb;
+    a = key_lower_bound(it.A, a > span ? a - span : 0ull, a, k, lb);
+    b = key_lower_bound(it.Bv, b > span ? b - span : 0ull, b, k, lb);
+  }
+  *pa = a;
+  *pb = b;
+}
+
+// Unit u of the emission: its item's runs and its key-aligned range.
+__device__ __forceinline__ Item load_unit(const QueryDev& q, const Scratch& s, const QCtl* c,
+                                          unsigned long long u) {
+  Item it = load_item(q, s, c, (long long)s.item_c[u], s.item_j[u]);
+  const unsigned long long st = s.item_stat[u];
+  it.sub = (unsigned)st;
+  it.nsub = (unsigned)(st >> 32);
+  const unsigned long long L = it.na + it.nb;
+  if (it.nsub > 1) {
+    const unsigned long long d0 = (unsigned long long)it.sub * kUnitEntries;
+    const unsigned long long d1 = it.sub + 1 < it.nsub ? d0 + kUnitEntries : L;
+    aligned_split(it, d0 < L ? d0 : L, q.lb, &it.a_lo, &it.b_lo);
+    aligned_split(it, d1 < L ? d1 : L, q.lb, &it.a_hi, &it.b_hi);
+  }
+  return it;
 }
 
 // ---- emission items ----------------------------------------------------------
@@ -119,16 +239,25 @@ __device__ __forceinline__ void block_items(const QueryDev& q, const Scratch& s,
   *hi = b < ch ? b : ch;
 }
 
+// Units of the items anchored at block index j.
+__device__ __forceinline__ unsigned long long block_units(const QueryDev& q, const Scratch& s,
+                                                          const QCtl* c, unsigned long long j) {
+  long long a, b;
+  block_items(q, s, c, j, &a, &b);
+  unsigned long long n = 0;
+  for (long long cc = a; cc <= b; ++cc) n += item_units(load_item(q, s, c, cc, j));
+  return n;
+}
+
+// The unit list (the "items" of the scratch): per item, item_units() units
+// in order, each recorded as (window chunk, anchor block, sub | nsub << 32).
 __global__ void __launch_bounds__(256) k_item_count(const QueryDev q, const Scratch s) {
   const QCtl* c = q.ctl;
   unsigned long long lo, hi;
   chunk_range(c->n_blocks, blockIdx.x, gridDim.x, &lo, &hi);
   unsigned long long cnt = 0;
-  for (unsigned long long j = lo + threadIdx.x; j < hi; j += blockDim.x) {
-    long long a, b;
-    block_items(q, s, c, j, &a, &b);
-    if (b >= a) cnt += (unsigned long long)(b - a + 1);
-  }
+  for (unsigned long long j = lo + threadIdx.x; j < hi; j += blockDim.x)
+    cnt += block_units(q, s, c, j);
   __shared__ unsigned long long tmp[33];
   unsigned long long tot;
   block_excl_scan(cnt, tmp, &tot);
@@ -158,15 +287,72 @@ __global__ void __launch_bounds__(256) k_item_write(const QueryDev q, const Scra
     const unsigned long long j = j0 + threadIdx.x;
     long long a = 1, b = 0;
     if (j < hi) block_items(q, s, c, j, &a, &b);
-    const unsigned long long cnt = b >= a ? (unsigned long long)(b - a + 1) : 0ull;
+    const unsigned long long cnt = j < hi ? block_units(q, s, c, j) : 0ull;
     unsigned long long tot;
-    const unsigned long long r = block_excl_scan(cnt, tmp, &tot);
-    for (unsigned long long t = 0; t < cnt; ++t) {
-      s.item_c[out + r + t] = (unsigned long long)(a + (long long)t);
-      s.item_j[out + r + t] = (unsigned)j;
-      s.item_stat[out + r + t] = 0ull;
+    unsigned long long o = out + block_excl_scan(cnt, tmp, &tot);
+    for (long long cc = a; cc <= b; ++cc) {
+      const unsigned nsub = item_units(load_item(q, s, c, cc, j));
+      for (unsigned t = 0; t < nsub; ++t, ++o) {
+        s.item_c[o] = (unsigned long long)cc;
+        s.item_j[o] = (unsigned)j;
+        s.item_stat[o] = (unsigned long long)t | ((unsigned long long)nsub << 32);
+      }
     }
     out += tot;
+  }
+}
+
+// ---- unit row counts -> output offsets ------------------------------------------
+//
+// Rows come out in (window, key) order: within an item, window i's rows are
+// the rows of its units in unit order.  Unit u = (item, sub) writes its
+// per-window counts to the item's slice of s.unit_off, at [u0 * nw + i * nsub
+// + sub] (u0: the item's first unit, nw: the query's windows per item), so
+// that one exclusive scan over the whole array, in index order, gives every
+// (unit, window) its output row.
+
+__global__ void __launch_bounds__(256) k_uoff_sum(const QueryDev q, const Scratch s) {
+  const QCtl* c = q.ctl;
+  if (c->err & kErrNeedRetry) return;
+  unsigned long long lo, hi;
+  chunk_range(c->n_items * (unsigned long long)q.nw, blockIdx.x, gridDim.x, &lo, &hi);
+  unsigned long long acc = 0;
+  for (unsigned long long i = lo + threadIdx.x; i < hi; i += blockDim.x) acc += s.unit_off[i];
+  __shared__ unsigned long long tmp[33];
+  unsigned long long tot;
+  block_excl_scan(acc, tmp, &tot);
+  if (threadIdx.x == 0) s.chunk[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_uoff_scan(const QueryDev q, const Scratch s,
+                                                    unsigned long long rows_cap) {
+  QCtl* c = q.ctl;
+  if (c->err & kErrNeedRetry) return;
+  __shared__ unsigned long long tmp[33];
+  const unsigned long long v = (int)threadIdx.x < kGrid ? s.chunk[threadIdx.x] : 0ull;
+  unsigned long long tot;
+  const unsigned long long r = block_excl_scan(v, tmp, &tot);
+  if ((int)threadIdx.x < kGrid) s.chunk[threadIdx.x] = r;
+  if (threadIdx.x == 0) {
+    c->rows_batch = tot;
+    if (c->row_base + tot > rows_cap) atomicOr(&c->err, kErrRowsOverflow);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_uoff_write(const QueryDev q, const Scratch s) {
+  const QCtl* c = q.ctl;
+  if (c->err & kErrNeedRetry) return;
+  unsigned long long lo, hi;
+  chunk_range(c->n_items * (unsigned long long)q.nw, blockIdx.x, gridDim.x, &lo, &hi);
+  __shared__ unsigned long long tmp[33];
+  unsigned long long run = s.chunk[blockIdx.x];
+  for (unsigned long long i0 = lo; i0 < hi; i0 += blockDim.x) {
+    const unsigned long long i = i0 + threadIdx.x;
+    const unsigned long long v = i < hi ? s.unit_off[i] : 0ull;
+    unsigned long long tot;
+    const unsigned long long r = block_excl_scan(v, tmp, &tot);
+    if (i < hi) s.unit_off[i] = run + r;
+    run += tot;
   }
 }
 
@@ -258,49 +444,6 @@ __device__ __forceinline__ void write_row(const QueryDev& q, ResultRowDev* out, 
   store_row(out, wstart, cnt, p1, p2);
 }
 
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Decoupled look-back over the items before `ri` (items are taken in ticket
-// order, so every predecessor is already running or done).  Publishes this
-// item's row count, waits (bounded by limit_ns) for the predecessors' counts
-// and returns the exclusive prefix, or ~0 after setting kErrLookback.
-__device__ unsigned long long item_lookback(unsigned long long* stat, unsigned long long ri,
-                                            unsigned long long n, QCtl* c,
-                                            unsigned long long limit_ns) {
-  constexpr unsigned long long kAgg = 1ull << 62, kPre = 2ull << 62, kVal = kAgg - 1;
-  volatile unsigned long long* vs = stat;
-  if (ri == 0) {
-    vs[0] = kPre | n;
-    return 0ull;
-  }
-  vs[ri] = kAgg | n;
-  unsigned long long acc = 0;
-  long long p = (long long)ri - 1;
-  const unsigned long long t0 = global_ns();
-  unsigned spins = 0;
-  while (p >= 0) {
-    const unsigned long long v = vs[p];
-    if ((v >> 62) == 0) {
-      if ((++spins & 63u) == 0 && global_ns() - t0 > limit_ns) {
-        atomicOr(&c->err, kErrLookback);
-        return ~0ull;
-      }
-      __nanosleep(128);
-      continue;
-    }
-    acc += v & kVal;
-    if ((v >> 62) == 2) break;
-    --p;
-  }
-  __threadfence();
-  vs[ri] = kPre | (acc + n);
-  return acc;
-}
-
 // ---- assembly of an item's windows -------------------------------------------
 
 constexpr int kEmT = 256;              // threads per CTA
@@ -372,58 +515,6 @@ __device__ __forceinline__ EmDyn em_dyn() {
   return d;
 }
 
-struct Item {
-  const Grp* A;               // run A: block b, key-major (may be empty)
-  unsigned long long na;
-  const Grp* Bv;              // run B: block b + 1 (empty if the item's windows do not reach it)
-  unsigned long long nb;
-  long long wlo, whi;         // the item's closed windows (relative ids, inclusive)
-};
-
-__device__ __forceinline__ Item load_item(const QueryDev& q, const Scratch& s, const QCtl* c,
-                                          unsigned long long ii) {
-  Item it;
-  const long long cc = (long long)s.item_c[ii];
-  const unsigned long long ja = s.item_j[ii];
-  const unsigned long long nblk = c->n_blocks;
-  const long long w0 = cc * q.nw;
-  const unsigned long long b = (unsigned long long)w0 >> q.lb;
-  it.wlo = w0 > c->cursor ? w0 : c->cursor;
-  it.whi = w0 + q.nw - 1 < c->w_hi ? w0 + q.nw - 1 : c->w_hi;
-  unsigned long long jb = ja;
-  it.A = q.state;
-  it.na = 0;
-  if (ja < nblk && s.blk_id[ja] == b) {
-    const unsigned long long a0 = s.blk_begin[ja];
-    it.A = q.state + a0;
-    it.na = s.blk_begin[ja + 1] - a0;
-    jb = ja + 1;
-  }
-  it.Bv = q.state;
-  it.nb = 0;
-  const long long last_pane = it.whi + q.k - 1;
-  if (q.k > 1 && jb < nblk && s.blk_id[jb] == b + 1 &&
-      last_pane >= (long long)((b + 1) << q.lb)) {
-    const unsigned long long b0 = s.blk_begin[jb];
-    it.Bv = q.state + b0;
-    it.nb = s.blk_begin[jb + 1] - b0;
-  }
-  return it;
-}
-
-// Merge order of the two runs: by key; on equal keys run A first (its panes
-// are the earlier ones).  Number of A entries among the first d merged
-// entries (merge path, global memory).
-__device__ unsigned long long merge_split_g(const Item& it, unsigned long long d, int lb) {
-  unsigned long long lo = d > it.nb ? d - it.nb : 0ull, hi = d < it.na ? d : it.na;
-  while (lo < hi) {
-    const unsigned long long mid = (lo + hi) >> 1;
-    if (gkey_key(it.A[mid].gkey, lb) <= gkey_key(it.Bv[d - 1 - mid].gkey, lb)) lo = mid + 1;
-    else hi = mid;
-  }
-  return lo;
-}
-
 // The same within a staged chunk: A part gk[0 .. la), B part gk[la .. la + lbn).
 __device__ __forceinline__ unsigned merge_split_s(const unsigned long long* gk, unsigned la,
                                                   unsigned lbn, unsigned d, int lb) {
@@ -448,18 +539,6 @@ __device__ __forceinline__ unsigned long long pane_windows(long long p, int k, l
   return m << (int)(lo - wlo);
 }
 
-// First index of key k in g[lo, hi) (g is key-ordered there).
-__device__ __forceinline__ unsigned long long key_lower_bound(const Grp* g, unsigned long long lo,
-                                                              unsigned long long hi, unsigned k,
-                                                              int lb) {
-  while (lo < hi) {
-    const unsigned long long mid = (lo + hi) >> 1;
-    if (gkey_key(g[mid].gkey, lb) < k) lo = mid + 1;
-    else hi = mid;
-  }
-  return lo;
-}
-
 // Walks chunk by chunk over the merged runs of the item.  Each chunk is
 // staged (records loaded with 16-byte vector loads; only the gkeys when
 // full == false) and merged into d.mo; then f(len, la, a0, b0, last) runs
@@ -474,7 +553,9 @@ __device__ void for_merged_chunks(const QueryDev& q, const Item& it, EmSmem& sm,
                                   bool full, F f, bool key_aligned = false) {
   const int tid = threadIdx.x;
   const int lb = q.lb;
-  const unsigned long long L = it.na + it.nb;
+  // the unit's merged range [D0, D1) (it starts and ends at key boundaries)
+  const unsigned long long D0 = it.a_lo + it.b_lo, D1 = it.a_hi + it.b_hi;
+  const unsigned long long L = D1 - D0;
   const unsigned long long C = key_aligned ? (unsigned long long)(kEmC - 32) : (unsigned long long)kEmC;
   const unsigned long long nch = (L + C - 1) / C;
   if (tid == 0) sm.carry_valid = 0;
@@ -482,17 +563,19 @@ __device__ void for_merged_chunks(const QueryDev& q, const Item& it, EmSmem& sm,
     const unsigned long long kn = nch - k0 < (unsigned long long)kEmT ? nch - k0 : kEmT;
     __syncthreads();  // the previous batch of chunks no longer reads sm.split
     for (unsigned long long t = tid; t <= kn; t += kEmT) {
-      const unsigned long long dd = (k0 + t) * C < L ? (k0 + t) * C : L;
-      unsigned long long a = merge_split_g(it, dd, lb), b = dd - a;
-      if (key_aligned && dd > 0 && dd < L) {
-        // the key of merged entry dd starts at (lower bound in A, lower bound in B)
-        const unsigned ka = a < it.na ? gkey_key(it.A[a].gkey, lb) : 0xffffffffu;
-        const unsigned kb = b < it.nb ? gkey_key(it.Bv[b].gkey, lb) : 0xffffffffu;
-        const bool from_a = a < it.na && (b >= it.nb || ka <= kb);
-        const unsigned k = from_a ? ka : kb;
-        const unsigned long long span = 1ull << lb;  // groups of one key in one run
-        a = key_lower_bound(it.A, a > span ? a - span : 0ull, a, k, lb);
-        b = key_lower_bound(it.Bv, b > span ? b - span : 0ull, b, k, lb);
+      const unsigned long long off = (k0 + t) * C < L ? (k0 + t) * C : L;
+      unsigned long long a, b;
+      if (off == 0) {
+        a = it.a_lo;
+        b = it.b_lo;
+      } else if (off == L) {
+        a = it.a_hi;
+        b = it.b_hi;
+      } else if (key_aligned) {
+        aligned_split(it, D0 + off, lb, &a, &b);
+      } else {
+        a = merge_split_g(it, D0 + off, lb);
+        b = D0 + off - a;
       }
       sm.split[t] = a;
       sm.split_b[t] = b;
@@ -538,7 +621,7 @@ __device__ void for_merged_chunks(const QueryDev& q, const Item& it, EmSmem& sm,
       }
       __syncthreads();
       if (tid == 0) sm.next_carry = d.gk[d.mo[len - 1]];
-      f(len, la, a0, b0, d1 == L);
+      f(len, la, a0, b0, d1 == D1);
       // f ended with a barrier: the chunk's last entry becomes the carry
       if (tid == 0) {
         sm.carry_g = sm.next_carry;
@@ -570,7 +653,7 @@ __device__ void count_item(const QueryDev& q, const Item& it, EmSmem& sm, const 
     (&sm.wdiff[0][0])[i] = 0;
   if (q.k == 1) {  // tumbling: one window, one pane, unique keys
     __syncthreads();
-    if (threadIdx.x == 0) sm.cnt[0] = (long long)it.na;
+    if (threadIdx.x == 0) sm.cnt[0] = (long long)(it.a_hi - it.a_lo);
   } else {
     for_merged_chunks(q, it, sm, d, false, [&](unsigned len, unsigned, unsigned long long,
                                                unsigned long long, bool) {
@@ -657,11 +740,12 @@ __device__ void write_item(const QueryDev& q, const Item& it, EmSmem& sm, const 
   const unsigned lane = lane_id(), lt = (1u << lane) - 1u;
   const int lb = q.lb, K = q.k;
   const int nw = (int)(it.whi - it.wlo + 1);
-  if (K == 1) {  // tumbling: the rows are the pane's groups, in key order
+  if (K == 1) {  // tumbling: the unit's rows are its groups of the pane, in key order
     const long long wstart = (it.wlo - kPaneBias) * (long long)q.slide + q.base;
-    for (unsigned long long i = tid; i < it.na; i += kEmT) {
+    for (unsigned long long i = it.a_lo + tid; i < it.a_hi; i += kEmT) {
       const Grp g = load_grp_v(it.A + i);
-      write_row<FLOAT>(q, out + i, wstart, gkey_key(g.gkey, lb), g.cnt, g.sum, g.mn, g.mx);
+      write_row<FLOAT>(q, out + sm.woff[0] + (i - it.a_lo), wstart, gkey_key(g.gkey, lb), g.cnt,
+                       g.sum, g.mn, g.mx);
     }
     __syncthreads();
     return;
@@ -894,11 +978,12 @@ __device__ void write_item_pw(const QueryDev& q, const Item& it, EmSmem& sm, con
   const unsigned lane = lane_id(), lt = (1u << lane) - 1u;
   const int lb = q.lb, K = q.k;
   const int nw = (int)(it.whi - it.wlo + 1);
-  if (K == 1) {  // tumbling: the rows are the pane's groups, in key order
+  if (K == 1) {  // tumbling: the unit's rows are its groups of the pane, in key order
     const long long wstart = (it.wlo - kPaneBias) * (long long)q.slide + q.base;
-    for (unsigned long long i = tid; i < it.na; i += kEmT) {
+    for (unsigned long long i = it.a_lo + tid; i < it.a_hi; i += kEmT) {
       const Grp g = load_grp_v(it.A + i);
-      write_row<FLOAT>(q, out + i, wstart, gkey_key(g.gkey, lb), g.cnt, g.sum, g.mn, g.mx);
+      write_row<FLOAT>(q, out + sm.woff[0] + (i - it.a_lo), wstart, gkey_key(g.gkey, lb), g.cnt,
+                       g.sum, g.mn, g.mx);
     }
     __syncthreads();
     return;
@@ -1036,43 +1121,57 @@ __device__ void write_item_pw(const QueryDev& q, const Item& it, EmSmem& sm, con
   }, true);
 }
 
-// Emits the closed windows.  CTAs take items in ticket order; for each item:
-// its rows per window (count_item), its row offset by the look-back, then the
-// rows (write_item).
-template <bool FLOAT, bool PW>
-__global__ void __launch_bounds__(kEmT, PW ? 4 : 3)
-    k_emit(const QueryDev q, const Scratch s, ResultRowDev* rows, unsigned long long rows_cap) {
+// Emission, in two kernels over the units (CTAs take units by ticket, so the
+// units of a large item spread over all SMs):
+//   k_emit_count: each unit's rows per window (count_item), stored at the
+//     unit's slots of s.unit_off;
+//   (k_uoff_*: the exclusive scan of s.unit_off, in output order)
+//   k_emit_write: each unit's rows, window i's from its scanned slot.
+// Neither kernel waits on another CTA.
+__global__ void __launch_bounds__(kEmT, 4) k_emit_count(const QueryDev q, const Scratch s) {
   __shared__ EmSmem sm;
   const EmDyn d = em_dyn();
   QCtl* c = q.ctl;
   if (c->err & kErrNeedRetry) return;
   const unsigned long long NI = c->n_items;
-  const unsigned long long row_base = c->row_base;
   while (true) {
     if (threadIdx.x == 0) sm.ri = atomicAdd(&c->item_ticket, 1ull);
     __syncthreads();
-    const unsigned long long ri = sm.ri;
+    const unsigned long long u = sm.ri;
     __syncthreads();
-    if (ri >= NI) break;
-    const Item it = load_item(q, s, c, ri);
-    if (ri == 0 && (q.debug_flags & kDebugHoldFirstItem)) continue;  // never publishes
+    if (u >= NI) break;
+    const Item it = load_unit(q, s, c, u);
     count_item(q, it, sm, d);
-    if (threadIdx.x == 0) {
-      const unsigned long long n = sm.total;
-      const unsigned long long off = item_lookback(s.item_stat, ri, n, c, q.lookback_ns);
-      sm.off = off;
-      if (off != ~0ull) {
-        if (ri == NI - 1) c->rows_batch = off + n;
-        if (row_base + off + n > rows_cap) atomicOr(&c->err, kErrRowsOverflow);
-      }
-    }
+    const int nw = (int)(it.whi - it.wlo + 1);
+    unsigned long long* slot = s.unit_off + (u - it.sub) * (unsigned long long)q.nw + it.sub;
+    for (int i = threadIdx.x; i < q.nw; i += kEmT)
+      slot[(unsigned long long)i * it.nsub] = i < nw ? (unsigned long long)sm.cnt[i] : 0ull;
     __syncthreads();
-    const unsigned long long off = sm.off;
+  }
+}
+
+template <bool FLOAT, bool PW>
+__global__ void __launch_bounds__(kEmT, PW ? 4 : 3)
+    k_emit_write(const QueryDev q, const Scratch s, ResultRowDev* rows) {
+  __shared__ EmSmem sm;
+  const EmDyn d = em_dyn();
+  QCtl* c = q.ctl;
+  if (c->err & kErrNeedRetry) return;
+  const unsigned long long NI = c->n_items;
+  ResultRowDev* out = rows + c->row_base;
+  while (true) {
+    if (threadIdx.x == 0) sm.ri = atomicAdd(&c->unit_ticket, 1ull);
     __syncthreads();
-    if (off != ~0ull && row_base + off + sm.total <= rows_cap) {
-      if (PW) write_item_pw<FLOAT>(q, it, sm, d, rows + row_base + off);
-      else write_item<FLOAT>(q, it, sm, d, rows + row_base + off);
-    }
+    const unsigned long long u = sm.ri;
+    __syncthreads();
+    if (u >= NI) break;
+    const Item it = load_unit(q, s, c, u);
+    const int nw = (int)(it.whi - it.wlo + 1);
+    const unsigned long long* slot = s.unit_off + (u - it.sub) * (unsigned long long)q.nw + it.sub;
+    for (int i = threadIdx.x; i < nw; i += kEmT) sm.woff[i] = slot[(unsigned long long)i * it.nsub];
+    __syncthreads();
+    if (PW) write_item_pw<FLOAT>(q, it, sm, d, out);
+    else write_item<FLOAT>(q, it, sm, d, out);
     __syncthreads();
   }
 }
@@ -1087,14 +1186,15 @@ __global__ void k_trim_prep(const QueryDev q, const Scratch s) {
   if (c->err & kErrNeedRetry) return;
   c->row_base += c->rows_batch;
   if (c->w_hi >= c->cursor) c->cursor = c->w_hi + 1;
+  // the first state group of a block >= the cursor's (a binary search over the
+  // state: it is sorted by gkey, whose top bits are the block)
   const unsigned long long bstar = (unsigned long long)c->cursor >> q.lb;
-  const unsigned long long P = c->n_blocks;
-  unsigned long long lo = 0, hi = P;
+  unsigned long long lo = 0, hi = c->n_state;
   while (lo < hi) {
     const unsigned long long mid = (lo + hi) >> 1;
-    if ((unsigned long long)s.blk_id[mid] < bstar) lo = mid + 1; else hi = mid;
+    if (gkey_block(q.state[mid].gkey, q.lb) < bstar) lo = mid + 1; else hi = mid;
   }
-  c->trim_from = lo < P ? s.blk_begin[lo] : c->n_state;
+  c->trim_from = lo;
   c->or_mask = 0ull;
   c->and_mask = ~0ull;
 }
@@ -1239,33 +1339,41 @@ cudaError_t launch_emit(const QueryDev& q, const Scratch& s, ResultRowDev* rows,
   k_item_count<<<kGrid, 256, 0, st>>>(q, s);
   k_item_scan<<<1, 1024, 0, st>>>(q, s);
   k_item_write<<<kGrid, 256, 0, st>>>(q, s);
+  // devices whose smem limit is set, per kernel
+  static unsigned long long done[5] = {0, 0, 0, 0, 0};
+  cudaError_t e = set_smem_limit(reinterpret_cast<const void*>(k_emit_count), (int)kEmDynBytesPW,
+                                 &done[4]);
+  if (e != cudaSuccess) return e;
+  k_emit_count<<<4 * sms, kEmT, kEmDynBytesPW, st>>>(q, s);
+  const int g = kGrid;
+  k_uoff_sum<<<g, 256, 0, st>>>(q, s);
+  k_uoff_scan<<<1, 1024, 0, st>>>(q, s, rows_cap);
+  k_uoff_write<<<g, 256, 0, st>>>(q, s);
   if (ev4) {
     record_event(ev4[1], st);
     record_event(ev4[2], st);
   }
-  // devices whose smem limit is set, per kernel
-  static unsigned long long done[4] = {0, 0, 0, 0};
   const bool pw = (2 << q.lb) <= 32;
   const void* fn = q.value_is_float
-                       ? (pw ? reinterpret_cast<const void*>(k_emit<true, true>)
-                             : reinterpret_cast<const void*>(k_emit<true, false>))
-                       : (pw ? reinterpret_cast<const void*>(k_emit<false, true>)
-                             : reinterpret_cast<const void*>(k_emit<false, false>));
+                       ? (pw ? reinterpret_cast<const void*>(k_emit_write<true, true>)
+                             : reinterpret_cast<const void*>(k_emit_write<true, false>))
+                       : (pw ? reinterpret_cast<const void*>(k_emit_write<false, true>)
+                             : reinterpret_cast<const void*>(k_emit_write<false, false>));
   const size_t dyn = pw ? kEmDynBytesPW : kEmDynBytes;
-  cudaError_t e = set_smem_limit(fn, (int)dyn, &done[(q.value_is_float ? 2 : 0) + (pw ? 1 : 0)]);
+  e = set_smem_limit(fn, (int)dyn, &done[(q.value_is_float ? 2 : 0) + (pw ? 1 : 0)]);
   if (e != cudaSuccess) return e;
   // resident CTAs per SM: four on the pane-word path (64 registers, 54 KB of
   // shared memory), three on the general one (its row descriptors need more)
   const int grid = (pw ? 4 : 3) * sms;
   if (q.value_is_float) {
-    if (pw) k_emit<true, true><<<grid, kEmT, dyn, st>>>(q, s, rows, rows_cap);
-    else k_emit<true, false><<<grid, kEmT, dyn, st>>>(q, s, rows, rows_cap);
+    if (pw) k_emit_write<true, true><<<grid, kEmT, dyn, st>>>(q, s, rows);
+    else k_emit_write<true, false><<<grid, kEmT, dyn, st>>>(q, s, rows);
   } else {
-    if (pw) k_emit<false, true><<<grid, kEmT, dyn, st>>>(q, s, rows, rows_cap);
-    else k_emit<false, false><<<grid, kEmT, dyn, st>>>(q, s, rows, rows_cap);
+    if (pw) k_emit_write<false, true><<<grid, kEmT, dyn, st>>>(q, s, rows);
+    else k_emit_write<false, false><<<grid, kEmT, dyn, st>>>(q, s, rows);
   }
   if (ev4) record_event(ev4[3], st);
-  if (launches) *launches += 5;
+  if (launches) *launches += 9;
   return cudaGetLastError();
 }
 

@@ -1,13 +1,17 @@
 // Partial groups -> sorted, unique window state.
 //
 // After the fused pass, a query's partial-group arrays hold the groups carried
-// over from the previous batch followed by this batch's per-tile groups, in no
+// over from the previous batch (sorted and unique: the previous batch's state
+// minus its closed panes) followed by this batch's per-tile groups, in no
 // particular order.  This file turns them into the window state: an LSD radix
-// sort of the 64-bit group keys (8-bit digits; digits that are equal in every
-// key are skipped, which the OR/AND masks gathered by the producers reveal),
-// then a reduce-by-key that combines equal (pane, key) groups, then the index
-// of distinct blocks.  All sizes are read on the device, so the whole sequence
-// launches without a host round trip.
+// sort of only the new groups' 64-bit keys (8-bit digits; digits that are
+// equal in every key are skipped, which the OR/AND masks gathered by the
+// producers reveal), a merge of the sorted new keys with the carried ones
+// (merge path; on equal keys the carried group comes first), then a
+// reduce-by-key that combines equal (pane, key) groups, then the index of
+// distinct blocks.  So a batch costs a sort of its own groups plus a linear
+// merge, however large the open state it carries.  All sizes are read on the
+// device, so the whole sequence launches without a host round trip.
 //
 // Chunked kernels use a fixed grid of kGrid CTAs, each owning one contiguous
 // chunk of the input; a per-chunk count, a single-CTA scan of the counts and a
@@ -26,14 +30,16 @@ struct SortSrc {
   const unsigned* vals;  // nullptr: identity
 };
 
-// Pass p reads the previous pass's output (or the partial keys for p == 0)
-// and writes buffer (p & 1) of the scratch pair.
+// Pass p reads the previous pass's output (or, for p == 0, the new partial
+// keys, after the sort_base carried ones) and writes buffer (p & 1) of the
+// scratch pair.  Values are indices into the partial arrays; nullptr means
+// the identity (index = sort_base + position).
 __device__ __forceinline__ SortSrc pass_src(const QueryDev& q, const Scratch& s, int p) {
-  if (p == 0) return {q.pkeys, nullptr};
+  if (p == 0) return {q.pkeys + q.ctl->sort_base, nullptr};
   return ((p - 1) & 1) ? SortSrc{s.keysB, s.valsB} : SortSrc{s.keysA, s.valsA};
 }
 __device__ __forceinline__ SortSrc final_src(const QueryDev& q, const Scratch& s, int np) {
-  if (np == 0) return {q.pkeys, nullptr};
+  if (np == 0) return {q.pkeys + q.ctl->sort_base, nullptr};
   return ((np - 1) & 1) ? SortSrc{s.keysB, s.valsB} : SortSrc{s.keysA, s.valsA};
 }
 
@@ -45,14 +51,38 @@ __device__ __forceinline__ void free_pair(const Scratch& s, int np, unsigned lon
   *v = final_b ? s.valsA : s.valsB;
 }
 
+// Input of the reduce: the merged keys (in the free pair) when groups were
+// carried, else the sorted new keys; `other` gets the pair it does not use.
+__device__ __forceinline__ SortSrc reduce_src(const QueryDev& q, const Scratch& s, int np,
+                                              unsigned long long** ok, unsigned** ov) {
+  unsigned long long* fk;
+  unsigned* fv;
+  free_pair(s, np, &fk, &fv);
+  if (q.ctl->sort_base == 0) {
+    *ok = fk;
+    *ov = fv;
+    return final_src(q, s, np);
+  }
+  const bool final_b = np > 0 && ((np - 1) & 1);  // the sort's own pair is free again
+  *ok = final_b ? s.keysB : s.keysA;
+  *ov = final_b ? s.valsB : s.valsA;
+  return SortSrc{fk, fv};
+}
+
+// Number of items sorted: the partials after the carried ones.
+__device__ __forceinline__ unsigned long long sort_count(const QCtl* c) {
+  return c->n_parts - c->sort_base;
+}
+
 __global__ void k_sort_plan(QCtl* c) {
   if (threadIdx.x != 0) return;
   const unsigned long long n = c->n_parts;
   c->parts_at_sort = n;
   c->n_long = 0;
+  c->sort_base = c->carried < n ? c->carried : n;
   const unsigned long long m = c->or_mask ^ c->and_mask;
   int np = 0;
-  if (n > 1)
+  if (n - c->sort_base > 1)
     for (int d = 0; d < 8; ++d)
       if ((m >> (8 * d)) & 0xffull) c->shifts[np++] = 8 * d;
   c->npasses = np;
@@ -67,7 +97,7 @@ __global__ void __launch_bounds__(256) k_sort_hist(const QueryDev q, const Scrat
   const int shift = c->shifts[p];
   const SortSrc src = pass_src(q, s, p);
   unsigned long long lo, hi;
-  chunk_range(c->n_parts, blockIdx.x, gridDim.x, &lo, &hi);
+  chunk_range(sort_count(c), blockIdx.x, gridDim.x, &lo, &hi);
   constexpr int kU = 8;  // keys loaded per thread before any is counted
   for (unsigned long long i0 = lo; i0 < hi; i0 += kU * blockDim.x) {
     unsigned d[kU];
@@ -154,7 +184,8 @@ __global__ void __launch_bounds__(256, 4) k_sort_scatter(const QueryDev q, const
   unsigned long long* dk = (p & 1) ? s.keysB : s.keysA;
   unsigned* dv = (p & 1) ? s.valsB : s.valsA;
   unsigned long long lo, hi;
-  chunk_range(c->n_parts, blockIdx.x, gridDim.x, &lo, &hi);
+  chunk_range(sort_count(c), blockIdx.x, gridDim.x, &lo, &hi);
+  const unsigned base = (unsigned)c->sort_base;
   {
     unsigned long long tot;
     const unsigned long long base =
@@ -184,7 +215,7 @@ __global__ void __launch_bounds__(256, 4) k_sort_scatter(const QueryDev q, const
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
       kk[r] = ikey[my + 32 * r];
-      vv[r] = src.vals ? ival[my + 32 * r] : (unsigned)(tb + my + 32 * r);
+      vv[r] = src.vals ? ival[my + 32 * r] : base + (unsigned)(tb + my + 32 * r);
     }
     if (tb + kScatterTile < hi) fetch(tb + kScatterTile);
     __syncthreads();
@@ -240,11 +271,101 @@ __global__ void __launch_bounds__(256, 4) k_sort_scatter(const QueryDev q, const
   }
 }
 
+// ---- merge of the sorted new keys with the carried ones --------------------
+
+// Number of carried keys among the first d keys of the merge of C[0, nc) and
+// N[0, nn) (merge path; on equal keys C comes first).
+__device__ __forceinline__ unsigned long long carry_split(const unsigned long long* C,
+                                                          unsigned long long nc,
+                                                          const unsigned long long* N,
+                                                          unsigned long long nn,
+                                                          unsigned long long d) {
+  unsigned long long lo = d > nn ? d - nn : 0ull, hi = d < nc ? d : nc;
+  while (lo < hi) {
+    const unsigned long long mid = (lo + hi) >> 1;
+    if (C[mid] <= N[d - 1 - mid]) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// The merged (key, partial index) sequence of the carried groups (pkeys[0,
+// sort_base), indices 0..) and the sorted new ones, written to the free pair.
+// Each CTA owns a chunk of the output: tiles of kMergeTile outputs whose
+// split points are found first (up to 256 at a time, in parallel), then each
+// tile's two input runs are staged in shared memory and every thread merges
+// kMergeItems consecutive outputs.
+constexpr int kMergeItems = 8;
+constexpr int kMergeTile = 256 * kMergeItems;
+
+__global__ void __launch_bounds__(256) k_merge_carry(const QueryDev q, const Scratch s) {
+  const QCtl* c = q.ctl;
+  const unsigned long long nc = c->sort_base;
+  if (nc == 0) return;
+  const unsigned long long n = c->n_parts, nn = n - nc;
+  const SortSrc N = final_src(q, s, c->npasses);
+  const unsigned long long* C = q.pkeys;
+  unsigned long long* mk;
+  unsigned* mv;
+  free_pair(s, c->npasses, &mk, &mv);
+  __shared__ unsigned long long sp[257];
+  __shared__ unsigned long long ck[kMergeTile], nk[kMergeTile];
+  __shared__ unsigned nv[kMergeTile];
+  const int tid = threadIdx.x;
+  unsigned long long lo, hi;
+  chunk_range(n, blockIdx.x, gridDim.x, &lo, &hi);
+  for (unsigned long long t0 = lo; t0 < hi; t0 += 256ull * kMergeTile) {
+    const unsigned long long span = hi - t0;
+    const unsigned nt = (unsigned)min(256ull, (span + kMergeTile - 1) / kMergeTile);
+    __syncthreads();  // the previous tiles no longer read sp
+    for (unsigned j = tid; j <= nt; j += 256) {
+      const unsigned long long d = min(t0 + (unsigned long long)j * kMergeTile, hi);
+      sp[j] = carry_split(C, nc, N.keys, nn, d);
+    }
+    __syncthreads();
+    for (unsigned j = 0; j < nt; ++j) {
+      const unsigned long long d0 = t0 + (unsigned long long)j * kMergeTile;
+      const unsigned long long d1 = min(d0 + kMergeTile, hi);
+      const unsigned long long a0 = sp[j], a1 = sp[j + 1];
+      const unsigned long long b0 = d0 - a0;
+      const unsigned la = (unsigned)(a1 - a0), lb = (unsigned)(d1 - d0) - la;
+      for (unsigned i = tid; i < la; i += 256) ck[i] = C[a0 + i];
+      for (unsigned i = tid; i < lb; i += 256) {
+        nk[i] = N.keys[b0 + i];
+        nv[i] = N.vals ? N.vals[b0 + i] : (unsigned)(nc + b0 + i);
+      }
+      __syncthreads();
+      const unsigned x0 = (unsigned)tid * kMergeItems, len = la + lb;
+      if (x0 < len) {
+        unsigned ia = x0 > lb ? x0 - lb : 0u, ib = x0 < la ? x0 : la;  // merge path in the tile
+        while (ia < ib) {
+          const unsigned mid = (ia + ib) >> 1;
+          if (ck[mid] <= nk[x0 - 1 - mid]) ia = mid + 1;
+          else ib = mid;
+        }
+        unsigned i = ia, k = x0 - ia;
+#pragma unroll
+        for (int e = 0; e < kMergeItems; ++e) {
+          const unsigned x = x0 + e;
+          if (x >= len) break;
+          const bool ta = k >= lb || (i < la && ck[i] <= nk[k]);
+          mk[d0 + x] = ta ? ck[i] : nk[k];
+          mv[d0 + x] = ta ? (unsigned)(a0 + i) : nv[k];
+          if (ta) ++i; else ++k;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
 // ---- reduce-by-key: sorted partials -> unique groups (window state) -------
 
 __global__ void __launch_bounds__(256) k_rbk_count(const QueryDev q, const Scratch s) {
   const QCtl* c = q.ctl;
-  const SortSrc src = final_src(q, s, c->npasses);
+  unsigned long long* ok;
+  unsigned* ov;
+  const SortSrc src = reduce_src(q, s, c->npasses, &ok, &ov);
   unsigned long long lo, hi;
   chunk_range(c->n_parts, blockIdx.x, gridDim.x, &lo, &hi);
   unsigned long long cnt = 0;
@@ -308,11 +429,10 @@ template <bool FLOAT>
 __global__ void __launch_bounds__(256, 4) k_rbk_write(const QueryDev q, const Scratch s) {
   QCtl* c = q.ctl;
   const unsigned long long n = c->n_parts;
-  const SortSrc src = final_src(q, s, c->npasses);
-  const unsigned long long* keys = src.keys;
   unsigned long long* lst;
   unsigned* lpos;
-  free_pair(s, c->npasses, &lst, &lpos);
+  const SortSrc src = reduce_src(q, s, c->npasses, &lst, &lpos);
+  const unsigned long long* keys = src.keys;
   unsigned long long lo, hi;
   chunk_range(n, blockIdx.x, gridDim.x, &lo, &hi);
   __shared__ unsigned long long sh_start, sh_end;
@@ -436,10 +556,9 @@ template <bool FLOAT>
 __global__ void __launch_bounds__(256) k_rbk_long(const QueryDev q, const Scratch s) {
   const QCtl* c = q.ctl;
   const unsigned long long nl = c->n_long;
-  const SortSrc src = final_src(q, s, c->npasses);
   unsigned long long* lst;
   unsigned* lpos;
-  free_pair(s, c->npasses, &lst, &lpos);
+  const SortSrc src = reduce_src(q, s, c->npasses, &lst, &lpos);
   __shared__ long long s_cnt[8];
   __shared__ unsigned long long s_sum[8];
   __shared__ unsigned s_mn[8], s_mx[8];
@@ -561,7 +680,15 @@ __device__ __forceinline__ void thread_share(unsigned long long n, unsigned long
   *b = min(hi, *a + per);
 }
 
+// Only emission reads the block index: when the batch closes no window (most
+// batches of a stream whose slide spans many batches) it is left empty.
+__device__ __forceinline__ bool closes_windows(const QCtl* c) { return c->w_hi >= c->cursor; }
+
 __global__ void __launch_bounds__(256) k_blk_count(const QueryDev q, const Scratch s) {
+  if (!closes_windows(q.ctl)) {
+    if (threadIdx.x == 0) s.chunk[blockIdx.x] = 0ull;
+    return;
+  }
   unsigned long long a, b, cnt = 0;
   thread_share(q.ctl->n_state, &a, &b);
   for_block_heads(q, a, b, [&](unsigned long long, unsigned) { ++cnt; });
@@ -573,6 +700,7 @@ __global__ void __launch_bounds__(256) k_blk_count(const QueryDev q, const Scrat
 
 __global__ void __launch_bounds__(256) k_blk_write(const QueryDev q, const Scratch s) {
   const QCtl* c = q.ctl;
+  if (!closes_windows(c)) return;
   const unsigned long long n = c->n_state;
   unsigned long long a, b, cnt = 0;
   thread_share(n, &a, &b);
@@ -606,6 +734,7 @@ cudaError_t launch_sort_reduce(const QueryDev& q, const Scratch& s, cudaStream_t
     k_sort_scatter<<<kGrid, 256, kScatterSmem, st>>>(q, s, p);
     nl += 3;
   }
+  k_merge_carry<<<kGrid, 256, 0, st>>>(q, s);
   k_rbk_count<<<kGrid, 256, 0, st>>>(q, s);
   k_scan_chunks<<<1, 1024, 0, st>>>(s.chunk, kGrid, &q.ctl->n_state);
   if (q.value_is_float) {
@@ -615,7 +744,7 @@ cudaError_t launch_sort_reduce(const QueryDev& q, const Scratch& s, cudaStream_t
     k_rbk_write<false><<<kGrid, 256, 0, st>>>(q, s);
     k_rbk_long<false><<<kGrid, 256, 0, st>>>(q, s);
   }
-  nl += 4;
+  nl += 5;
   if (launches) *launches += nl;
   return cudaGetLastError();
 }

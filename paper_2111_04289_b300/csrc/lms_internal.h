@@ -36,7 +36,6 @@ constexpr unsigned kErrPartsOverflow = 1u;   // partial-group buffer too small
 constexpr unsigned kErrItemOverflow = 2u;    // emission item list too small
 constexpr unsigned kErrRowsOverflow = 4u;    // result buffer too small
 constexpr unsigned kErrProbe = 16u;          // shared hash probe bound hit (never expected)
-constexpr unsigned kErrLookback = 32u;       // an item's bounded look-back wait ran out
 constexpr unsigned kErrOrderBy = 64u;        // ORDER BY: a window holds more than kOrderMax rows
 constexpr unsigned kErrNeedRetry = kErrItemOverflow | kErrRowsOverflow;
 
@@ -47,8 +46,6 @@ constexpr int kOrderMax = 16384;
 // start in one block).
 constexpr int kMaxItemWindows = 64;
 
-// Stream debug flags (lms_stream_config.debug_flags).
-constexpr unsigned kDebugHoldFirstItem = 1u;  // emission item 0 never publishes its row count
 
 // One (pane, key) group: a 32-byte record, so that a random gather of a group
 // touches one DRAM sector.
@@ -76,10 +73,13 @@ struct QCtl {
   unsigned long long row_base;   // rows held in the device result buffer
   unsigned long long carried;    // groups carried into the next batch
   unsigned long long trim_from;  // first state index that may be carried into the next batch
-  unsigned long long item_ticket;// next emission item (CTAs take items in order)
+  unsigned long long item_ticket;// next emission unit of the row count (CTAs take units by ticket)
+  unsigned long long unit_ticket;// next emission unit of the row writes
   unsigned long long rows_kept;  // rows HAVING kept of this batch's
   unsigned long long parts_at_sort; // partial groups the sort of this batch consumed
   unsigned long long n_long;     // long runs of equal keys left to the cooperative reduce
+  unsigned long long sort_base;  // carried groups at the front of the partials: only the rest
+                                 // is sorted, then merged with them
   unsigned int err;
   int npasses;
   int shifts[8];
@@ -116,8 +116,6 @@ struct QueryDev {
   int k;                       // size / slide
   int lb;                      // log2 of the block size B (smallest power of two >= k)
   int nw;                      // windows per emission item: min(B, kMaxItemWindows)
-  unsigned long long lookback_ns;  // bound of the emission's look-back wait
-  unsigned debug_flags;        // kDebug* bits (tests only)
   unsigned key_mask;           // GROUP BY: the bits of the key's selected fields
   int having_agg, having_op;   // HAVING agg OP having_value (agg 0: none)
   double having_value;
@@ -159,9 +157,10 @@ struct Scratch {
   unsigned long long blk_cap;
   unsigned long long* item_c;    // emission items: window chunk c (windows [c*nw, c*nw + nw))
   unsigned* item_j;              // index of the block that anchors the item
-  unsigned long long* item_stat; // look-back word per item: 0 = not ready,
-                                 // 1<<62 | rows (own count), 2<<62 | rows (inclusive prefix)
-  unsigned long long item_cap;
+  unsigned long long* item_stat; // per unit: its index in the item | the item's units << 32
+  unsigned long long* unit_off;  // kMaxItemWindows per unit: row counts, then output rows
+                                 // (a query uses nw of them per unit)
+  unsigned long long item_cap;   // units the unit arrays hold
 };
 
 struct ResultRowDev {  // device image of lms_result_row (48 bytes)

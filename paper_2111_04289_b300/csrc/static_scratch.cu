@@ -11,7 +11,7 @@
 // fixed array in device memory that the library declares at file scope.  The
 // caller passes the input columns and the output row buffer.
 //
-// The array (kStaticBytes, about 17 MiB) exists on every GPU that loads the
+// The array (kStaticBytes, about 31 MiB) exists on every GPU that loads the
 // library, for the life of the process.  Its device address is looked up with
 // cudaGetSymbolAddress once per device, with that device current, on the first
 // call made on that device.  Every call reads the batch's first event time
@@ -33,7 +33,7 @@ namespace lms {
 namespace {
 
 constexpr unsigned long long kStaticGroups = LMS_STATIC_MAX_ROWS;  // one group per row at most
-constexpr unsigned long long kStaticItems = 1ull << 17;  // emission items (runs of <= 64 windows)
+constexpr unsigned long long kStaticItems = 1ull << 15;  // emission units (item pieces)
 
 constexpr size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -41,7 +41,7 @@ struct Layout {
   size_t sctl, qctl;
   size_t parts, pkeys, state;
   size_t keysA, keysB, valsA, valsB, hist, chunk, blk_id, blk_begin;
-  size_t item_c, item_j, item_stat, total;
+  size_t item_c, item_j, item_stat, unit_off, total;
 };
 
 constexpr Layout make_layout() {
@@ -63,6 +63,7 @@ constexpr Layout make_layout() {
   L.item_c = o; o += al(8 * kStaticItems);
   L.item_j = o; o += al(4 * kStaticItems);
   L.item_stat = o; o += al(8 * kStaticItems);
+  L.unit_off = o; o += al(8 * kMaxItemWindows * kStaticItems);
   L.total = o;
   return L;
 }
@@ -169,6 +170,7 @@ extern "C" lms_status lms_aggregate_batch_static(const lms_query_spec* q, int32_
   s.item_c = reinterpret_cast<unsigned long long*>(base + kL.item_c);
   s.item_j = reinterpret_cast<unsigned*>(base + kL.item_j);
   s.item_stat = reinterpret_cast<unsigned long long*>(base + kL.item_stat);
+  s.unit_off = reinterpret_cast<unsigned long long*>(base + kL.unit_off);
   s.item_cap = kStaticItems;
 
   // ---- the query, with the batch's first row as event-time origin ----
@@ -182,8 +184,6 @@ extern "C" lms_status lms_aggregate_batch_static(const lms_query_spec* q, int32_
   d.size = size;
   d.k = (int)(size / slide);
   set_block_shape(&d);
-  d.lookback_ns = 4000000000ull;
-  d.debug_flags = 0u;
   d.key_mask = 0xffffffffu;
   d.agg_mask = q->agg_mask ? q->agg_mask : LMS_AGG_ALL;
   d.qid = 0;
@@ -232,7 +232,7 @@ extern "C" lms_status lms_aggregate_batch_static(const lms_query_spec* q, int32_
   if (cudaMemcpyAsync(&h, d.ctl, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return LMS_ECUDA;
-  if (h.err & (kErrPartsOverflow | kErrProbe | kErrLookback)) return LMS_EDEVICE;
+  if (h.err & (kErrPartsOverflow | kErrProbe)) return LMS_EDEVICE;
   if (h.err & kErrNeedRetry) return LMS_ENOMEM;  // item list or rows_cap too small
   *n_out = (size_t)h.rows_batch;
   return LMS_OK;

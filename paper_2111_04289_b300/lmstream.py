@@ -45,12 +45,11 @@ class StreamConfig(ctypes.Structure):
                 ("allowed_lateness_ms", ctypes.c_int64), ("max_batch_rows", ctypes.c_int64),
                 ("state_cap_bytes", ctypes.c_uint64), ("cuda_stream", ctypes.c_void_p),
                 ("origin_ts", ctypes.c_int64), ("k1_variant", ctypes.c_int32),
-                ("graph_mode", ctypes.c_int32), ("lookback_limit_us", ctypes.c_int32),
-                ("debug_flags", ctypes.c_uint32), ("key_fields", ctypes.c_uint32),
+                ("graph_mode", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("reserved1", ctypes.c_uint32), ("key_fields", ctypes.c_uint32),
                 ("reserved", ctypes.c_int32 * 3)]
 
 
-DEBUG_HOLD_FIRST_ITEM = 1
 
 
 class QuerySpec(ctypes.Structure):
@@ -442,7 +441,7 @@ class Stream:
                  allowed_lateness_ms: int = 0, max_batch_rows: int = 0, state_cap_bytes: int = 0,
                  cuda_stream: Optional[int] = None, origin_ts: Optional[int] = None,
                  enable_timing: bool = False, k1_variant: int = 0, graph_mode: int = 0,
-                 lookback_limit_us: int = 0, debug_flags: int = 0, key_fields=None):
+                 key_fields=None):
         self._lib = load()
         self.value_type = value_type
         self.is_float = value_type == "float32"
@@ -458,8 +457,6 @@ class Stream:
         cfg.origin_ts = ORIGIN_AUTO if origin_ts is None else int(origin_ts)
         cfg.k1_variant = int(k1_variant)
         cfg.graph_mode = int(graph_mode)
-        cfg.lookback_limit_us = int(lookback_limit_us)
-        cfg.debug_flags = int(debug_flags)
         # key_fields: bit widths of up to four packed key fields (field 0 lowest)
         cfg.key_fields = sum(int(w) << (8 * f) for f, w in enumerate(key_fields or ()))
         h = ctypes.c_void_p()

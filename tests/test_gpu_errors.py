@@ -74,18 +74,3 @@ def test_events_outside_the_event_time_span_are_dropped_and_counted():
     assert st["range_rows"] == 2
     orc, _ = run_oracle([b], q, False)
     assert_rows_match(eng[0], orc[0], False)
-
-
-def test_lookback_wait_runs_out_and_reports_edevice():
-    s = lm.Stream("int32", lookback_limit_us=2000, debug_flags=lm.DEBUG_HOLD_FIRST_ITEM)
-    s.register_query(1000)
-    b = synth.TinyIntStream(seed=9).next_batch(20_000)  # ~50 s of events: many windows close
-    assert _status(lambda: s.push(b.ts, b.key, b.value)) == lm.LMS_EDEVICE
-    # the error is latched on the stream ...
-    assert _status(lambda: s.push(b.ts, b.key, b.value)) == lm.LMS_EDEVICE
-    s.close()
-    # ... and the device is still usable
-    eng, _ = run_engine([b], [dict(size=1000)], False)
-    orc, _ = run_oracle([b], [dict(size=1000)], False)
-    assert_rows_match(eng[0], orc[0], False)
-    torch.cuda.synchronize()
