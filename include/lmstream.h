@@ -332,6 +332,20 @@ lms_status lms_stream_device_bytes(lms_stream *s, uint64_t *bytes);
  * stream has no cap; 0 when nothing fits. */
 lms_status lms_stream_admissible_rows(lms_stream *s, int32_t host_input, int64_t *n_out);
 
+/* Per-query split of the batch work (times need enable_timing; the fused
+ * pass is shared by all queries and counted in lms_stats.k1_ms only):
+ * sort + merge + reduce into the window state, emission row counts (unit list,
+ * counts, offsets) and emission row writes, in ms summed over the pushes; the
+ * rows the query emitted and the groups it carries into the next batch. */
+typedef struct lms_query_stats_t {
+  double sort_ms;
+  double emit_count_ms;
+  double emit_write_ms;
+  uint64_t rows_emitted;
+  uint64_t state_groups;
+} lms_query_stats_t;
+lms_status lms_query_stats(lms_stream *s, int32_t query_id, lms_query_stats_t *out);
+
 /* Drops query_id's unpolled rows (e.g. after consuming them on the device). */
 lms_status lms_results_discard(lms_stream *s, int32_t query_id);
 
@@ -683,6 +697,15 @@ lms_status lms_serve_gpu_create(const lms_stream_config *cfg, const lms_query_sp
 lms_status lms_serve_gpu_backend(lms_serve_gpu *g, lms_serve_backend *out);
 lms_stream *lms_serve_gpu_stream(lms_serve_gpu *g);
 int32_t lms_serve_gpu_device_input(const lms_serve_gpu *g); /* 1 if created with LMS_SERVE_DEVICE_INPUT */
+/* Brings the window state to steady state before a serving run: n_batches
+ * micro-batches of events_per_batch events of the load, with event times
+ * spread evenly over [t0_ms, t0_ms + span_ms), are pushed (as the backend's
+ * input mode pushes) and their rows discarded; nothing is measured.  A run
+ * whose arrivals start at t = 0 then finds the open panes of the last window
+ * already full, as a stream that has been running for span_ms would.
+ * events_per_batch <= the backend's max_batch_rows. */
+lms_status lms_serve_gpu_prefill(lms_serve_gpu *g, double t0_ms, double span_ms,
+                                 int32_t n_batches, int64_t events_per_batch);
 /* Writes the events the backend would generate for these chunks into host
  * arrays (for checks against the oracle). */
 lms_status lms_serve_gpu_generate(lms_serve_gpu *g, const lms_serve_chunk *chunks,

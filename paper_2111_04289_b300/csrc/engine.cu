@@ -73,6 +73,7 @@ struct QueryHost {
   unsigned long long n_state = 0;
   unsigned long long late_rows = 0, range_rows = 0;
   unsigned long long rows_emitted = 0;
+  double sort_ms = 0, emit_count_ms = 0, emit_write_ms = 0;  // with enable_timing
   bool hidden = false;  // a side of a join (its rows feed the join, not the caller)
 };
 
@@ -947,6 +948,7 @@ lms_status run_batch(lms_stream* s, const InSeg* seg, int nseg, long long n, int
       float x = 0;
       cudaEventElapsedTime(&x, s->qev[i][4], s->qev[i][5]);
       sort_ms += x;
+      s->qs[i].sort_ms += x;
     }
     cudaEventElapsedTime(&a, s->ev[0], s->ev[5]);
     cudaEventElapsedTime(&bms, s->ev[1], s->ev[2]);
@@ -961,6 +963,8 @@ lms_status run_batch(lms_stream* s, const InSeg* seg, int nseg, long long n, int
         float e1 = 0, e2 = 0;
         cudaEventElapsedTime(&e1, s->qev[i][0], s->qev[i][1]);
         cudaEventElapsedTime(&e2, s->qev[i][2], s->qev[i][3]);
+        s->qs[i].emit_count_ms += e1;
+        s->qs[i].emit_write_ms += e2;
         s->stats.e1_ms += e1;
         s->stats.e2_ms += e2;
       }
@@ -1304,6 +1308,20 @@ lms_status lms_stream_admissible_rows(lms_stream* s, int32_t host_input, int64_t
     if (c > carried + 1) best = std::max<long long>(best, (long long)(c - carried - 1));
   }
   *n_out = best;
+  return LMS_OK;
+}
+
+lms_status lms_query_stats(lms_stream* s, int32_t query_id, lms_query_stats_t* out) {
+  if (!s || !out) return LMS_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (query_id < 0 || query_id >= (int)s->qs.size() || s->qs[query_id].hidden)
+    return fail(s, LMS_EINVAL, "bad query id");
+  const QueryHost& q = s->qs[query_id];
+  out->sort_ms = q.sort_ms;
+  out->emit_count_ms = q.emit_count_ms;
+  out->emit_write_ms = q.emit_write_ms;
+  out->rows_emitted = q.rows_emitted;
+  out->state_groups = q.carried;
   return LMS_OK;
 }
 

@@ -374,6 +374,37 @@ int32_t lms_serve_gpu_device_input(const lms_serve_gpu* g) {
   return (g && g->device_input) ? 1 : 0;
 }
 
+lms_status lms_serve_gpu_prefill(lms_serve_gpu* g, double t0_ms, double span_ms,
+                                 int32_t n_batches, int64_t events_per_batch) {
+  if (!g || n_batches < 1 || events_per_batch < 1 || events_per_batch > g->max_rows ||
+      !(span_ms > 0))
+    return LMS_EINVAL;
+  if (cudaSetDevice(g->dev) != cudaSuccess) return LMS_ECUDA;
+  const double w = span_ms / n_batches;
+  for (int b = 0; b < n_batches; ++b) {
+    const long long first = (long long)b * events_per_batch;
+    g->h_chunks[0] = {t0_ms + b * w, w, events_per_batch, 0, first, 0};
+    if (cudaMemcpyAsync(g->d_chunks, g->h_chunks, sizeof(GenChunk), cudaMemcpyHostToDevice,
+                        g->gen_st) != cudaSuccess ||
+        launch_gen_ts(g->d_chunks, 1, events_per_batch, g->m_ts, g->sms, g->gen_st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(g->gen_st) != cudaSuccess)
+      return LMS_ECUDA;
+    const long long off = first % kPool;
+    lms_batch bt{};
+    bt.n_rows = events_per_batch;
+    bt.ts = reinterpret_cast<const int64_t*>(g->ts);
+    bt.key = g->key + off;
+    bt.value = g->val + off;
+    bt.memory = g->device_input ? LMS_MEM_DEVICE : LMS_MEM_HOST;
+    lms_status r = push_microbatch(g->s, &bt);
+    if (r != LMS_OK) return r;
+    for (int q = 0; q < g->nq; ++q)
+      if ((r = lms_results_discard(g->s, q)) != LMS_OK) return r;
+  }
+  return LMS_OK;
+}
+
 lms_status lms_serve_gpu_generate(lms_serve_gpu* g, const lms_serve_chunk* chunks,
                                   int32_t n_chunks, int64_t n_events, int64_t* ts,
                                   uint32_t* key, float* value) {

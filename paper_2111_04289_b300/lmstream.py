@@ -83,6 +83,12 @@ JOIN_ROW_DTYPE_FLOAT = np.dtype([("window_start", "<i8"), ("pairs", "<i8"),
                                  ("join_id", "<u4")])
 
 
+class QueryStatsC(ctypes.Structure):
+    _fields_ = [("sort_ms", ctypes.c_double), ("emit_count_ms", ctypes.c_double),
+                ("emit_write_ms", ctypes.c_double), ("rows_emitted", ctypes.c_uint64),
+                ("state_groups", ctypes.c_uint64)]
+
+
 class BatchC(ctypes.Structure):
     _fields_ = [("n_rows", ctypes.c_int64), ("ts", ctypes.c_void_p), ("key", ctypes.c_void_p),
                 ("value", ctypes.c_void_p), ("type", ctypes.c_void_p),
@@ -135,7 +141,8 @@ EXPORTED_SYMBOLS = ("stream_open", "query_register", "push_microbatch", "poll_re
                     "lms_variant_learned_observe", "lms_variant_learned_stats",
                     "lms_join_register", "lms_join_poll", "lms_shard_of", "lms_shard_split",
                     "lms_stream_set_batch_max_ts", "lms_stream_set_origin",
-                    "lms_stream_snapshot", "lms_stream_restore", "lms_stream_get_config")
+                    "lms_stream_snapshot", "lms_stream_restore", "lms_stream_get_config",
+                    "lms_serve_gpu_prefill", "lms_query_stats")
 ADMIT_PAPER, ADMIT_GUARDED = 0, 1
 QOPS = {"aggregation": 0, "filter": 1, "shuffle": 2, "project": 3, "join": 4, "expand": 5,
         "scan": 6, "sort": 7}
@@ -405,6 +412,10 @@ def load(build_if_missing: bool = True):
     lib.lms_serve_gpu_device_input.argtypes = [P]
     lib.lms_serve_gpu_stream.restype = P
     lib.lms_serve_gpu_stream.argtypes = [P]
+    lib.lms_serve_gpu_prefill.restype = I
+    lib.lms_serve_gpu_prefill.argtypes = [P, D, D, I, ctypes.c_int64]
+    lib.lms_query_stats.restype = I
+    lib.lms_query_stats.argtypes = [P, I, ctypes.POINTER(QueryStatsC)]
     lib.lms_serve_gpu_generate.restype = I
     lib.lms_serve_gpu_generate.argtypes = [P, P, I, ctypes.c_int64, P, P, P]
     lib.lms_serve_gpu_kept_rows.restype = I
@@ -679,6 +690,13 @@ class Stream:
         s = StatsC()
         self._check(self._lib.lms_stream_stats(self._h, ctypes.byref(s)), "lms_stream_stats")
         return {name: getattr(s, name) for name, _ in StatsC._fields_}
+
+    def query_stats(self, qid: int) -> dict:
+        """lms_query_stats: the query's share of the batch work."""
+        s = QueryStatsC()
+        self._check(self._lib.lms_query_stats(self._h, int(qid), ctypes.byref(s)),
+                    "lms_query_stats")
+        return {name: getattr(s, name) for name, _ in QueryStatsC._fields_}
 
     def close(self):
         if getattr(self, "_h", None):
@@ -1013,6 +1031,13 @@ class ServeGpu:
         out = StatsC()
         self._lib.lms_stream_stats(self._lib.lms_serve_gpu_stream(self._h), ctypes.byref(out))
         return {f[0]: getattr(out, f[0]) for f in StatsC._fields_}
+
+    def prefill(self, t0_ms: float, span_ms: float, n_batches: int, events_per_batch: int):
+        """lms_serve_gpu_prefill: window state to steady state before a run."""
+        st = self._lib.lms_serve_gpu_prefill(self._h, float(t0_ms), float(span_ms),
+                                             int(n_batches), int(events_per_batch))
+        if st != LMS_OK:
+            raise LmsError(st, "lms_serve_gpu_prefill")
 
     def admissible_rows(self) -> int:
         n = ctypes.c_int64()
