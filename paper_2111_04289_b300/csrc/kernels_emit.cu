@@ -993,7 +993,14 @@ __device__ void write_item_pw(const QueryDev& q, const Item& it, EmSmem& sm, con
   const unsigned long long wmask = nw >= 64 ? ~0ull : ((1ull << nw) - 1ull);
   const unsigned long long kmask = (1ull << K) - 1ull;
   const long long wstart0 = (it.wlo - kPaneBias) * (long long)q.slide + q.base;
-  for (int i = tid; i < nw; i += kEmT) sm.run[i] = 0u;
+  // every warp keeps the rows written so far of window lane (run0) and lane +
+  // 32 (run1), updated identically from the same counts, and the item's
+  // window bases; the key words start zeroed (each chunk zeroes what it used)
+  unsigned run0 = 0u, run1 = 0u;
+  const unsigned wb0 = (int)lane < nw ? (unsigned)sm.woff[lane] : 0u;
+  const unsigned wb1 = (int)lane + 32 < nw ? (unsigned)sm.woff[lane + 32] : 0u;
+  for (int k = tid; k < kEmC; k += kEmT) d.kw[k] = 0u;
+  unsigned par = 0u;  // which of the two count buffers this round uses
   for_merged_chunks(q, it, sm, d, true, [&](unsigned len, unsigned, unsigned long long,
                                             unsigned long long, bool) {
     // heads (a chunk starts with one) and each entry's key index
@@ -1013,9 +1020,7 @@ __device__ void write_item_pw(const QueryDev& q, const Item& it, EmSmem& sm, con
     for (int e = 0; e < kEmE; ++e)
       if (head[e]) d.hp[hpos++] = (unsigned short)(x0 + e);
     const unsigned nh = (unsigned)htot;
-    for (unsigned k = tid; k < nh; k += kEmT) d.kw[k] = 0u;
     if (tid == 0) d.hp[nh] = (unsigned short)len;
-    __syncthreads();
 #pragma unroll
     for (int e = 0; e < kEmE; ++e) {
       const unsigned x = x0 + e;
@@ -1047,33 +1052,36 @@ __device__ void write_item_pw(const QueryDev& q, const Item& it, EmSmem& sm, con
       const unsigned long long orm =
           ((unsigned long long)__reduce_or_sync(kFull, (unsigned)(mask >> 32)) << 32) |
           __reduce_or_sync(kFull, (unsigned)mask);
-      for (int i = lane; i < nw; i += 32) sm.wc[w][i] = 0u;
-      __syncwarp();
+      // this warp's rows per window (lane i holds windows i and i + 32), into
+      // this round's count buffer; the buffers alternate, so a warp already in
+      // the next round never overwrites counts a slower warp still reads
+      unsigned c0 = 0u, c1 = 0u;
       for (unsigned long long bits = orm; bits; bits &= bits - 1) {
         const int i = __ffsll((long long)bits) - 1;
         const unsigned bal = __ballot_sync(kFull, (mask >> i) & 1ull);
-        if (lane == 0) sm.wc[w][i] = (unsigned)__popc(bal);
-      }
-      __syncthreads();
-      // output offsets: warps inside each window, after the rows of the
-      // window's earlier rounds
-      if (tid < 32) {
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int i = tid + 32 * u;
-          if (i < nw) {
-            unsigned acc = (unsigned)sm.woff[i] + sm.run[i];
-#pragma unroll
-            for (int ww = 0; ww < kEmWarps; ++ww) {
-              const unsigned t = sm.wc[ww][i];
-              sm.wc[ww][i] = acc;
-              acc += t;
-            }
-            sm.run[i] = acc - (unsigned)sm.woff[i];
-          }
+        if ((int)lane == (i & 31)) {
+          if (i < 32) c0 = (unsigned)__popc(bal);
+          else c1 = (unsigned)__popc(bal);
         }
       }
+      unsigned (*cb)[kMaxItemWindows] = par ? sm.ball : sm.wc;
+      cb[w][lane] = c0;
+      cb[w][lane + 32] = c1;
       __syncthreads();
+      // every warp: its first output row per window (the item's base, the rows
+      // of earlier rounds, the rows of lower warps in this round)
+      unsigned off0 = wb0 + run0, off1 = wb1 + run1;
+#pragma unroll
+      for (int ww = 0; ww < kEmWarps; ++ww) {
+        const unsigned t0 = cb[ww][lane], t1 = cb[ww][lane + 32];
+        if (ww < w) {
+          off0 += t0;
+          off1 += t1;
+        }
+        run0 += t0;
+        run1 += t1;
+      }
+      par ^= 1u;
       // this warp's rows, window by window; consecutive windows of a key often
       // hold the same groups, so the row's aggregate parts are kept for the
       // last (first group, number of groups) and only recomputed on a change
@@ -1085,6 +1093,8 @@ __device__ void write_item_pw(const QueryDev& q, const Item& it, EmSmem& sm, con
         const int i = __ffsll((long long)bits) - 1;
         const bool in = (mask >> i) & 1ull;
         const unsigned bal = __ballot_sync(kFull, in);
+        // the warp's first row of window i (every lane takes part in the shuffle)
+        const unsigned wbase = __shfl_sync(kFull, i < 32 ? off0 : off1, i & 31);
         if (!in) continue;
         const int r = wrel0 + i;  // the window's first pane, relative to block b
         const unsigned x = hx + (unsigned)__popcll(word & ((1ull << r) - 1ull));
@@ -1113,10 +1123,11 @@ __device__ void write_item_pw(const QueryDev& q, const Item& it, EmSmem& sm, con
           cx = x;
           cn = nn;
         }
-        const unsigned pos = sm.wc[w][i] + (unsigned)__popc(bal & lt);
+        const unsigned pos = wbase + (unsigned)__popc(bal & lt);
         store_row(out + pos, wstart0 + (long long)i * (long long)q.slide, ccnt, p1, p2);
       }
     }
+    for (unsigned k = tid; k < nh; k += kEmT) d.kw[k] = 0u;  // for the next chunk
     __syncthreads();
   }, true);
 }
