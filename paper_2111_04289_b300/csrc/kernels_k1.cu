@@ -50,11 +50,12 @@ template <int ITEMS> struct K1Shape {
 // (at most 2048 events of at most 2^32 each: the low part stays below 2^43).
 constexpr int kCntShift = 43;
 
-// Phase A: the slot of group key g (inserted if new).  Returns the slot, or
-// kNoSlot if the probe bound is hit (cannot happen: a tile has <= H/2 groups).
+// Phase A: the slot of group key g (inserted if new; *created tells whether
+// this call inserted it).  Returns the slot, or kNoSlot if the probe bound is
+// hit (cannot happen: a tile has <= H/2 groups).
 template <int BITS>
-__device__ __forceinline__ unsigned insert_key(unsigned long long* hkey, unsigned short* list,
-                                               unsigned* nlist, unsigned long long g) {
+__device__ __forceinline__ unsigned insert_key(unsigned long long* hkey, unsigned long long g,
+                                               bool* created) {
   constexpr int H = 1 << BITS;
   unsigned slot = hash_slot(g, BITS);
   for (int probes = 0; probes < H; ++probes) {
@@ -63,8 +64,7 @@ __device__ __forceinline__ unsigned insert_key(unsigned long long* hkey, unsigne
     if (cur == kEmpty) {
       const unsigned long long prev = atomicCAS(&hkey[slot], kEmpty, g);
       if (prev == kEmpty) {
-        const unsigned li = atomicAdd(nlist, 1u);
-        list[li] = (unsigned short)slot;
+        *created = true;
         return slot;
       }
       if (prev == g) return slot;
@@ -72,6 +72,21 @@ __device__ __forceinline__ unsigned insert_key(unsigned long long* hkey, unsigne
     slot = (slot + 1) & (H - 1);
   }
   return kNoSlot;
+}
+
+// The tile's list of new groups: the lanes of a warp that inserted a key in
+// this step reserve their entries with one atomic (instead of one each: every
+// new group of a tile would otherwise meet on the same counter).  Called by
+// every lane of the warp.
+__device__ __forceinline__ void append_new(unsigned short* list, unsigned* nlist, bool created,
+                                           unsigned slot, unsigned lane) {
+  const unsigned cm = __ballot_sync(kFull, created);
+  if (!cm) return;
+  const int leader = __ffs(cm) - 1;
+  unsigned base = 0u;
+  if ((int)lane == leader) base = atomicAdd(nlist, (unsigned)__popc(cm));
+  base = __shfl_sync(kFull, base, leader);
+  if (created) list[base + __popc(cm & ((1u << lane) - 1u))] = (unsigned short)slot;
 }
 
 // Biased exponent used for alignment (denormals count as exponent 1).
@@ -310,8 +325,9 @@ __global__ void __launch_bounds__(kK1Threads, K1Shape<ITEMS>::kCtasPerSm)
             add = ((unsigned long long)__popc(peers) << kCntShift) + lo + ((unsigned long long)hi << 16);
           }
           unsigned sl = kNoSlot;
+          bool created = false;
           if (g != kEmpty && (int)lane == leader) {
-            sl = insert_key<kK1HashBits>(hkey, list, &s_nlist, g);
+            sl = insert_key<kK1HashBits>(hkey, g, &created);
             if (sl == kNoSlot) {
               atomicOr(&s_err[qi], kErrProbe);
             } else {
@@ -321,12 +337,15 @@ __global__ void __launch_bounds__(kK1Threads, K1Shape<ITEMS>::kCtasPerSm)
               else atomicAdd(&gsum[sl], add);
             }
           }
+          append_new(list, &s_nlist, created, sl, lane);
           sl = __shfl_sync(peers, sl, leader);
           slot[i] = g != kEmpty ? sl : kNoSlot;
-        } else if (g != kEmpty) {
-          const unsigned sl = insert_key<kK1HashBits>(hkey, list, &s_nlist, g);
+        } else {
+          bool created = false;
+          const unsigned sl = g != kEmpty ? insert_key<kK1HashBits>(hkey, g, &created) : kNoSlot;
+          append_new(list, &s_nlist, created, sl, lane);
           if (sl == kNoSlot) {
-            atomicOr(&s_err[qi], kErrProbe);
+            if (g != kEmpty) atomicOr(&s_err[qi], kErrProbe);
           } else {
             slot[i] = sl;
             atomicMin(&gmn[sl], enc);
