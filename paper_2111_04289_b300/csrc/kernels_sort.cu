@@ -79,13 +79,15 @@ __global__ void k_sort_plan(QCtl* c) {
   const unsigned long long n = c->n_parts;
   c->parts_at_sort = n;
   c->n_long = 0;
-  c->sort_base = c->carried < n ? c->carried : n;
   const unsigned long long m = c->or_mask ^ c->and_mask;
-  int np = 0;
-  if (n - c->sort_base > 1)
-    for (int d = 0; d < 8; ++d)
-      if ((m >> (8 * d)) & 0xffull) c->shifts[np++] = 8 * d;
-  c->npasses = np;
+  int nd = 0;  // digits that differ between keys
+  for (int d = 0; d < 8; ++d)
+    if ((m >> (8 * d)) & 0xffull) c->shifts[nd++] = 8 * d;
+  // Merging costs one pass over all the partials; sorting the carried groups
+  // along costs ~nd passes over them: when they are few, sort everything.
+  const unsigned long long carried = c->carried < n ? c->carried : n;
+  c->sort_base = carried * (unsigned long long)nd < n - carried ? 0ull : carried;
+  c->npasses = n - c->sort_base > 1 ? nd : 0;
 }
 
 __global__ void __launch_bounds__(256) k_sort_hist(const QueryDev q, const Scratch s, int p) {
