@@ -958,6 +958,22 @@ __device__ void write_item(const QueryDev& q, const Item& it, EmSmem& sm, const 
   });
 }
 
+// Position of set bit number n (from 0, lowest first) of m, by a halving
+// search on popcounts; some position below 32 if m has no more than n set bits.
+__device__ __forceinline__ unsigned nth_set_bit(unsigned m, unsigned n) {
+  unsigned pos = 0u;
+#pragma unroll
+  for (int w = 16; w >= 1; w >>= 1) {
+    const unsigned c = (unsigned)__popc(m & ((1u << w) - 1u));
+    if (n >= c) {
+      n -= c;
+      m >>= w;
+      pos += (unsigned)w;
+    }
+  }
+  return pos & 31u;
+}
+
 // The pane-word path of write_item, for items whose two blocks span 2B <= 32
 // panes (K <= 16).  Chunks are key-aligned, so every key of a chunk is whole
 // in shared memory.  Every merged entry ORs the bit of its pane (relative to
@@ -968,14 +984,14 @@ __device__ void write_item(const QueryDev& q, const Item& it, EmSmem& sm, const 
 // below r (the key's groups are in pane order), their number the set bits in
 // the range.  Per round of up to kEmT keys (one per thread): the warps'
 // ballots per window and one prefix over the warps give every row its output
-// position; then each warp writes its own keys' rows window by window (the
-// lanes whose key is in the window write consecutive rows), with no row
-// descriptors and no barrier between the warps' rows.
+// position; then each warp writes its own keys' rows, 32 at a time in output
+// order (one row per lane, so consecutive lanes write consecutive rows of a
+// window), with no row descriptors and no barrier between the warps' rows.
 template <bool FLOAT>
 __device__ void write_item_pw(const QueryDev& q, const Item& it, EmSmem& sm, const EmDyn& d,
                               ResultRowDev* out) {
   const int tid = threadIdx.x, w = tid >> 5;
-  const unsigned lane = lane_id(), lt = (1u << lane) - 1u;
+  const unsigned lane = lane_id();
   const int lb = q.lb, K = q.k;
   const int nw = (int)(it.whi - it.wlo + 1);
   if (K == 1) {  // tumbling: the unit's rows are its groups of the pane, in key order
@@ -988,17 +1004,18 @@ __device__ void write_item_pw(const QueryDev& q, const Item& it, EmSmem& sm, con
     __syncthreads();
     return;
   }
+  // an item holds the windows starting in one block, so nw <= B <= 16 here:
+  // lane i < 16 of every warp speaks for window i
   const unsigned long long blk = (unsigned long long)it.wlo >> lb;  // the item's block b
   const int wrel0 = (int)(it.wlo - (long long)(blk << lb));         // wlo relative to block b
-  const unsigned long long wmask = nw >= 64 ? ~0ull : ((1ull << nw) - 1ull);
-  const unsigned long long kmask = (1ull << K) - 1ull;
+  const unsigned wmask = (1u << nw) - 1u;
+  const unsigned kmask = (1u << K) - 1u;
   const long long wstart0 = (it.wlo - kPaneBias) * (long long)q.slide + q.base;
-  // every warp keeps the rows written so far of window lane (run0) and lane +
-  // 32 (run1), updated identically from the same counts, and the item's
-  // window bases; the key words start zeroed (each chunk zeroes what it used)
-  unsigned run0 = 0u, run1 = 0u;
-  const unsigned wb0 = (int)lane < nw ? (unsigned)sm.woff[lane] : 0u;
-  const unsigned wb1 = (int)lane + 32 < nw ? (unsigned)sm.woff[lane + 32] : 0u;
+  // every warp keeps the rows written so far of window lane (run), updated
+  // identically from the same counts, and the item's window bases; the key
+  // words start zeroed (each chunk zeroes what it used)
+  unsigned run = 0u;
+  const unsigned wb = (int)lane < nw ? (unsigned)sm.woff[lane] : 0u;
   for (int k = tid; k < kEmC; k += kEmT) d.kw[k] = 0u;
   unsigned par = 0u;  // which of the two count buffers this round uses
   for_merged_chunks(q, it, sm, d, true, [&](unsigned len, unsigned, unsigned long long,
@@ -1035,12 +1052,11 @@ __device__ void write_item_pw(const QueryDev& q, const Item& it, EmSmem& sm, con
     __syncthreads();
     for (unsigned r0 = 0; r0 < nh; r0 += kEmT) {
       const unsigned h = r0 + (unsigned)tid;
-      unsigned hx = 0u;
-      unsigned long long word = 0ull, mask = 0ull;
+      unsigned hx = 0u, word = 0u, mask = 0u, key = 0u;
       if (h < nh) {
         hx = d.hp[h];
         word = d.kw[h];
-        unsigned long long dl = word;  // dilation by K: bit r set iff a bit of [r, r + K) is
+        unsigned dl = word;  // dilation by K: bit r set iff a bit of [r, r + K) is
         int span = 1;
         while (2 * span <= K) {
           dl |= dl >> span;
@@ -1048,58 +1064,65 @@ __device__ void write_item_pw(const QueryDev& q, const Item& it, EmSmem& sm, con
         }
         if (span < K) dl |= dl >> (K - span);
         mask = (dl >> wrel0) & wmask;
+        key = gkey_key(d.gk[d.mo[hx]], lb);
       }
-      const unsigned long long orm =
-          ((unsigned long long)__reduce_or_sync(kFull, (unsigned)(mask >> 32)) << 32) |
-          __reduce_or_sync(kFull, (unsigned)mask);
-      // this warp's rows per window (lane i holds windows i and i + 32), into
-      // this round's count buffer; the buffers alternate, so a warp already in
-      // the next round never overwrites counts a slower warp still reads
-      unsigned c0 = 0u, c1 = 0u;
-      for (unsigned long long bits = orm; bits; bits &= bits - 1) {
-        const int i = __ffsll((long long)bits) - 1;
-        const unsigned bal = __ballot_sync(kFull, (mask >> i) & 1ull);
-        if ((int)lane == (i & 31)) {
-          if (i < 32) c0 = (unsigned)__popc(bal);
-          else c1 = (unsigned)__popc(bal);
-        }
+      // lane i: the ballot of this warp's keys that hold window i, and its rows
+      const unsigned orm = __reduce_or_sync(kFull, mask);
+      unsigned bal = 0u;
+      for (unsigned bits = orm; bits; bits &= bits - 1) {
+        const int i = __ffs((int)bits) - 1;
+        const unsigned b = __ballot_sync(kFull, (mask >> i) & 1u);
+        if ((int)lane == i) bal = b;
       }
+      const unsigned cw = (unsigned)__popc(bal);
+      // the warps' counts into this round's buffer; the buffers alternate, so a
+      // warp already in the next round never overwrites counts a slower warp
+      // still reads
       unsigned (*cb)[kMaxItemWindows] = par ? sm.ball : sm.wc;
-      cb[w][lane] = c0;
-      cb[w][lane + 32] = c1;
+      cb[w][lane] = cw;
       __syncthreads();
-      // every warp: its first output row per window (the item's base, the rows
-      // of earlier rounds, the rows of lower warps in this round)
-      unsigned off0 = wb0 + run0, off1 = wb1 + run1;
+      // this warp's first output row of window lane: the item's base, the rows
+      // of earlier rounds and the rows of lower warps in this round
+      unsigned off = wb + run;
 #pragma unroll
       for (int ww = 0; ww < kEmWarps; ++ww) {
-        const unsigned t0 = cb[ww][lane], t1 = cb[ww][lane + 32];
-        if (ww < w) {
-          off0 += t0;
-          off1 += t1;
-        }
-        run0 += t0;
-        run1 += t1;
+        const unsigned t = cb[ww][lane];
+        if (ww < w) off += t;
+        run += t;
       }
       par ^= 1u;
-      // this warp's rows, window by window; consecutive windows of a key often
-      // hold the same groups, so the row's aggregate parts are kept for the
-      // last (first group, number of groups) and only recomputed on a change
-      const unsigned key = gkey_key(d.gk[d.mo[hx]], lb);
-      unsigned cx = ~0u, cn = 0u;
-      long long ccnt = 0;
-      uint4 p1 = make_uint4(0u, 0u, 0u, 0u), p2 = p1;
-      for (unsigned long long bits = orm; bits; bits &= bits - 1) {
-        const int i = __ffsll((long long)bits) - 1;
-        const bool in = (mask >> i) & 1ull;
-        const unsigned bal = __ballot_sync(kFull, in);
-        // the warp's first row of window i (every lane takes part in the shuffle)
-        const unsigned wbase = __shfl_sync(kFull, i < 32 ? off0 : off1, i & 31);
-        if (!in) continue;
-        const int r = wrel0 + i;  // the window's first pane, relative to block b
-        const unsigned x = hx + (unsigned)__popcll(word & ((1ull << r) - 1ull));
-        const unsigned nn = (unsigned)__popcll(word & (kmask << r));
-        if (x != cx || nn != cn) {
+      // the warp's rows in output order (window by window, keys ascending)
+      // are numbered f = 0 .. total - 1; incl = rows of windows 0 .. lane
+      unsigned incl = cw;
+#pragma unroll
+      for (int o = 1; o < 16; o <<= 1) {
+        const unsigned v = __shfl_up_sync(kFull, incl, o);
+        if ((int)lane >= o) incl += v;
+      }
+      const unsigned total = __shfl_sync(kFull, incl, 15);
+      const unsigned excl = incl - cw;
+      // 32 rows at a time, row f on lane f mod 32: its window i is the number
+      // of windows all of whose rows come before f, its rank among the
+      // window's rows picks the key (the rank-th set bit of the window's
+      // ballot), whose lane holds the key's groups
+      for (unsigned f0 = 0; f0 < total; f0 += 32) {
+        const unsigned f = f0 + lane;
+        unsigned i = 0u;
+#pragma unroll
+        for (unsigned st = 8; st >= 1; st >>= 1)
+          if (__shfl_sync(kFull, incl, i + st - 1) <= f) i += st;
+        // (i <= 15: lanes past the last row read some window's values)
+        const unsigned rk = f - __shfl_sync(kFull, excl, i);
+        const unsigned bw = __shfl_sync(kFull, bal, i);
+        const unsigned ow = __shfl_sync(kFull, off, i);
+        const unsigned kl = nth_set_bit(bw, rk);
+        const unsigned hk = __shfl_sync(kFull, hx, kl);
+        const unsigned wk = __shfl_sync(kFull, word, kl);
+        const unsigned yk = __shfl_sync(kFull, key, kl);
+        if (f < total) {
+          const int r = wrel0 + (int)i;  // the window's first pane, relative to block b
+          const unsigned x = hk + (unsigned)__popc(wk & ((1u << r) - 1u));
+          const unsigned nn = (unsigned)__popc((unsigned)(((unsigned long long)wk >> r) & kmask));
           unsigned slot = d.mo[x];
           long long cnt = d.cnt[slot];
           unsigned long long isum = d.sum[slot];
@@ -1118,13 +1141,10 @@ __device__ void write_item_pw(const QueryDev& q, const Item& it, EmSmem& sm, con
           }
           const unsigned long long sb =
               FLOAT ? (unsigned long long)__double_as_longlong(fsum) : isum;
-          row_parts<FLOAT>(q, key, cnt, sb, mn, mx, &p1, &p2);
-          ccnt = cnt;
-          cx = x;
-          cn = nn;
+          uint4 p1, p2;
+          row_parts<FLOAT>(q, yk, cnt, sb, mn, mx, &p1, &p2);
+          store_row(out + (ow + rk), wstart0 + (long long)i * (long long)q.slide, cnt, p1, p2);
         }
-        const unsigned pos = wbase + (unsigned)__popc(bal & lt);
-        store_row(out + pos, wstart0 + (long long)i * (long long)q.slide, ccnt, p1, p2);
       }
     }
     for (unsigned k = tid; k < nh; k += kEmT) d.kw[k] = 0u;  // for the next chunk
