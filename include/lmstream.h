@@ -907,7 +907,7 @@ lms_status lms_server_destroy(lms_server *sv);
  * rows[0 .. rows_cap); *n_out receives their number.  The first row's ts is
  * the event-time origin.  Returns when the rows are written.
  *
- * Every intermediate buffer lives in one fixed array of about 31 MiB that the
+ * Every intermediate buffer lives in one fixed array of about 34 MiB that the
  * library declares in device memory: it is present on every GPU that loads the
  * library until the process exits, and this function calls no cudaMalloc,
  * cudaFree or other allocating routine.  The first call on a device looks the
@@ -923,7 +923,8 @@ lms_status lms_server_destroy(lms_server *sv);
  *
  * Errors: LMS_EINVAL for a bad argument or n_rows > LMS_STATIC_MAX_ROWS;
  * LMS_ENOMEM if the emission units (runs of up to 64 consecutive closed
- * windows, cut into pieces of about 32K state groups; at most 32768) or the
+ * windows, cut into pieces of about 32K state groups, or of about 1K when a
+ * window spans at most 16 panes; at most 32768) or the
  * rows do not fit (rows_cap >= n_rows * size/slide always suffices);
  * LMS_ECUDA for a CUDA failure; LMS_EDEVICE for an internal kernel flag. */
 lms_status lms_aggregate_batch_static(const lms_query_spec *q, int32_t value_type,

@@ -274,6 +274,7 @@ lms_status ensure_items(lms_stream* s, unsigned long long need) {
   if ((r = dgrow(s, &sc.item_stat, sc.item_cap, nc, 0)) != LMS_OK) return r;
   if ((r = dgrow(s, &sc.unit_off, sc.item_cap * kMaxItemWindows, nc * kMaxItemWindows, 0)) != LMS_OK)
     return r;
+  if ((r = dgrow(s, &sc.unit_bnd, sc.item_cap * kUnitBnd, nc * kUnitBnd, 0)) != LMS_OK) return r;
   sc.item_cap = nc;
   return LMS_OK;
 }
@@ -1261,7 +1262,7 @@ lms_status lms_stream_push_bytes(lms_stream* s, int64_t n_rows, int32_t host_inp
   }
   // emission buffers a first push allocates (later growth follows the rows
   // a batch emits and is not predicted here)
-  if (s->scr.item_cap == 0) total += 1024ull * (8 + 4 + 8 + 8 * kMaxItemWindows);
+  if (s->scr.item_cap == 0) total += 1024ull * (8 + 4 + 8 + 8 * kMaxItemWindows + 4 * kUnitBnd);
   for (const QueryHost& q : s->qs)
     if (q.rows_cap == 0) total += round_cap(4096 + 4096 / 4) * sizeof(lms_result_row);
   *bytes = total;

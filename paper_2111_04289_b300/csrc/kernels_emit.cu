@@ -144,13 +144,21 @@ __device__ __forceinline__ Item load_item(const QueryDev& q, const Scratch& s, c
 }
 
 // Merged entries per unit: an item's merged runs are cut into units of about
-// this many entries (at key boundaries), each taken by one CTA, so that a few
-// closed windows over a large state still spread over the whole GPU.
+// this many entries (at key boundaries), so that a few closed windows over a
+// large state still spread over the whole GPU.  A unit is one CTA's work on
+// the general path and one warp's on the pane-word path (2B <= 32).
 constexpr unsigned long long kUnitEntries = 32768;
+constexpr unsigned long long kUnitEntriesPW = (unsigned long long)kPwChunkEntries * kPwUnitChunks;
 
-__device__ __forceinline__ unsigned item_units(const Item& it) {
-  const unsigned long long L = it.na + it.nb;
-  return L == 0 ? 1u : (unsigned)((L + kUnitEntries - 1) / kUnitEntries);
+__device__ __forceinline__ bool pane_word_path(const QueryDev& q) { return (2 << q.lb) <= 32; }
+
+__device__ __forceinline__ unsigned long long unit_entries(const QueryDev& q) {
+  return pane_word_path(q) ? kUnitEntriesPW : kUnitEntries;
+}
+
+__device__ __forceinline__ unsigned item_units(const QueryDev& q, const Item& it) {
+  const unsigned long long L = it.na + it.nb, E = unit_entries(q);
+  return L == 0 ? 1u : (unsigned)((L + E - 1) / E);
 }
 
 // Merge order of the two runs: by key; on equal keys run A first (its panes
@@ -204,10 +212,10 @@ __device__ __forceinline__ Item load_unit(const QueryDev& q, const Scratch& s, c
   const unsigned long long st = s.item_stat[u];
   it.sub = (unsigned)st;
   it.nsub = (unsigned)(st >> 32);
-  const unsigned long long L = it.na + it.nb;
+  const unsigned long long L = it.na + it.nb, E = unit_entries(q);
   if (it.nsub > 1) {
-    const unsigned long long d0 = (unsigned long long)it.sub * kUnitEntries;
-    const unsigned long long d1 = it.sub + 1 < it.nsub ? d0 + kUnitEntries : L;
+    const unsigned long long d0 = (unsigned long long)it.sub * E;
+    const unsigned long long d1 = it.sub + 1 < it.nsub ? d0 + E : L;
     aligned_split(it, d0 < L ? d0 : L, q.lb, &it.a_lo, &it.b_lo);
     aligned_split(it, d1 < L ? d1 : L, q.lb, &it.a_hi, &it.b_hi);
   }
@@ -245,7 +253,7 @@ __device__ __forceinline__ unsigned long long block_units(const QueryDev& q, con
   long long a, b;
   block_items(q, s, c, j, &a, &b);
   unsigned long long n = 0;
-  for (long long cc = a; cc <= b; ++cc) n += item_units(load_item(q, s, c, cc, j));
+  for (long long cc = a; cc <= b; ++cc) n += item_units(q, load_item(q, s, c, cc, j));
   return n;
 }
 
@@ -291,7 +299,7 @@ __global__ void __launch_bounds__(256) k_item_write(const QueryDev q, const Scra
     unsigned long long tot;
     unsigned long long o = out + block_excl_scan(cnt, tmp, &tot);
     for (long long cc = a; cc <= b; ++cc) {
-      const unsigned nsub = item_units(load_item(q, s, c, cc, j));
+      const unsigned nsub = item_units(q, load_item(q, s, c, cc, j));
       for (unsigned t = 0; t < nsub; ++t, ++o) {
         s.item_c[o] = (unsigned long long)cc;
         s.item_j[o] = (unsigned)j;
@@ -299,6 +307,34 @@ __global__ void __launch_bounds__(256) k_item_write(const QueryDev q, const Scra
       }
     }
     out += tot;
+  }
+}
+
+// Pane-word path: the chunk boundaries of every unit, one thread per boundary,
+// so that the warps that count and write the units search nothing.  Boundary
+// t of unit (item, sub) is the key-aligned split at merged entry (sub *
+// kPwUnitChunks + t) * kPwChunkEntries, or the item's end.
+__global__ void __launch_bounds__(256) k_unit_bounds(const QueryDev q, const Scratch s) {
+  const QCtl* c = q.ctl;
+  const unsigned long long NI = c->n_items;
+  if (NI > s.item_cap) return;
+  const unsigned long long n = NI * (kPwUnitChunks + 1);
+  for (unsigned long long x = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+       x += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long u = x / (kPwUnitChunks + 1);
+    const unsigned t = (unsigned)(x - u * (kPwUnitChunks + 1));
+    const Item it = load_item(q, s, c, (long long)s.item_c[u], s.item_j[u]);
+    const unsigned long long sub = (unsigned)s.item_stat[u];
+    const unsigned long long d = (sub * kPwUnitChunks + t) * kPwChunkEntries;
+    unsigned long long a = it.na, b = it.nb;
+    if (d == 0) {
+      a = 0;
+      b = 0;
+    } else if (d < it.na + it.nb) {
+      aligned_split(it, d, q.lb, &a, &b);
+    }
+    s.unit_bnd[u * kUnitBnd + 2 * t] = (unsigned)a;
+    s.unit_bnd[u * kUnitBnd + 2 * t + 1] = (unsigned)b;
   }
 }
 
@@ -489,15 +525,13 @@ struct EmDyn {
   unsigned long long* mm;    // [kEmC] mn | mx << 32
   unsigned short* mo;        // [kEmC]
   unsigned short* hp;        // [kEmC + 1]
-  unsigned* kw;              // [kEmC] per key of the chunk: its panes (relative to the
-                             // item's block) as bits (pane-word path)
   unsigned* rln;             // [kEmRows] first group | number of groups << 16 (general path)
   unsigned short* rows;      // [kEmRows] (general path)
 };
-// Dynamic shared memory of the pane-word path (no row descriptors) and of the
-// general path.
-constexpr size_t kEmDynBytesPW = (size_t)kEmC * (4 * 8 + 2) + (kEmC + 1) * 2 + 6 + (size_t)kEmC * 4;
-constexpr size_t kEmDynBytes = kEmDynBytesPW + (size_t)kEmRows * (4 + 2);
+// Dynamic shared memory of the counting kernel (no row descriptors) and of the
+// writer.
+constexpr size_t kEmDynBytesCount = (size_t)kEmC * (4 * 8 + 2) + (kEmC + 1) * 2 + 6;
+constexpr size_t kEmDynBytes = kEmDynBytesCount + (size_t)kEmRows * (4 + 2);
 
 __device__ __forceinline__ EmDyn em_dyn() {
   extern __shared__ __align__(16) unsigned char em_smem[];
@@ -509,7 +543,6 @@ __device__ __forceinline__ EmDyn em_dyn() {
   d.mm = reinterpret_cast<unsigned long long*>(p); p += (size_t)kEmC * 8;
   d.mo = reinterpret_cast<unsigned short*>(p); p += (size_t)kEmC * 2;
   d.hp = reinterpret_cast<unsigned short*>(p); p += (size_t)(kEmC + 1) * 2 + 6;
-  d.kw = reinterpret_cast<unsigned*>(p); p += (size_t)kEmC * 4;
   d.rln = reinterpret_cast<unsigned*>(p); p += (size_t)kEmRows * 4;
   d.rows = reinterpret_cast<unsigned short*>(p);
   return d;
@@ -544,19 +577,16 @@ __device__ __forceinline__ unsigned long long pane_windows(long long p, int k, l
 // full == false) and merged into d.mo; then f(len, la, a0, b0, last) runs
 // with the chunk in shared memory (after a barrier) and must end with a
 // barrier.  sm.carry_g holds the previous chunk's last merged gkey (if
-// sm.carry_valid).  With key_aligned (only for 2B <= 32), chunks nominally
-// hold kEmC - 32 entries and every boundary is moved back to the first group
-// of the key there, so that no key straddles two chunks: a key has fewer than
-// 2B <= 32 groups before a boundary, so a chunk stays within kEmC entries.
+// sm.carry_valid).
 template <class F>
 __device__ void for_merged_chunks(const QueryDev& q, const Item& it, EmSmem& sm, const EmDyn& d,
-                                  bool full, F f, bool key_aligned = false) {
+                                  bool full, F f) {
   const int tid = threadIdx.x;
   const int lb = q.lb;
   // the unit's merged range [D0, D1) (it starts and ends at key boundaries)
   const unsigned long long D0 = it.a_lo + it.b_lo, D1 = it.a_hi + it.b_hi;
   const unsigned long long L = D1 - D0;
-  const unsigned long long C = key_aligned ? (unsigned long long)(kEmC - 32) : (unsigned long long)kEmC;
+  const unsigned long long C = (unsigned long long)kEmC;
   const unsigned long long nch = (L + C - 1) / C;
   if (tid == 0) sm.carry_valid = 0;
   for (unsigned long long k0 = 0; k0 < nch; k0 += kEmT) {
@@ -571,8 +601,6 @@ __device__ void for_merged_chunks(const QueryDev& q, const Item& it, EmSmem& sm,
       } else if (off == L) {
         a = it.a_hi;
         b = it.b_hi;
-      } else if (key_aligned) {
-        aligned_split(it, D0 + off, lb, &a, &b);
       } else {
         a = merge_split_g(it, D0 + off, lb);
         b = D0 + off - a;
@@ -958,6 +986,45 @@ __device__ void write_item(const QueryDev& q, const Item& it, EmSmem& sm, const 
   });
 }
 
+// ---- the pane-word path (2B <= 32): one warp per unit -------------------------
+//
+// An item of this path holds the windows starting in one block (nw = B <= 16,
+// so lane i < 16 of a warp can speak for window i) and its units are small
+// (kUnitEntriesPW merged entries).  One warp counts, and later writes, a unit
+// alone, with no CTA barrier and no wait on another warp: the warp walks its
+// unit in key-aligned chunks of at most kWC entries staged in its own slice of
+// shared memory.  Per chunk every merged entry ORs the bit of its pane
+// (relative to the item's block b) into its key's word; a key's windows are
+// then the word dilated by K (a window whose first pane is r, relative to
+// block b, holds the key iff a bit of [r, r + K) is set), and the groups of
+// its row in that window are the set bits of [r, r + K): the first is the
+// number of set bits below r (the key's groups are in pane order), their
+// number the set bits in the range.  Per round of 32 keys (one per lane), the
+// ballot of window i over the lanes counts the round's rows of the window;
+// the writer then numbers the round's rows in output order (window, then key)
+// and writes them 32 at a time, one per lane, so that consecutive lanes write
+// consecutive rows.
+
+constexpr int kWCn = kPwChunkEntries;  // nominal chunk
+constexpr int kWC = kWCn + 32;         // staged entries: a key adds fewer than 2B <= 32
+constexpr int kWE = kWC / 32;   // merged entries per lane
+constexpr int kPwWarps = 8;
+constexpr int kPwT = kPwWarps * 32;
+
+// One warp's staged chunk: records as columns, the merged order, the keys'
+// first merged positions and pane words, and the chunk starts of the unit.
+struct PwWarp {
+  unsigned long long gk[kWC];
+  long long cnt[kWC];
+  unsigned long long sum[kWC];
+  unsigned long long mm[kWC];   // mn | mx << 32
+  unsigned kw[kWC];             // per key of the chunk: its panes relative to block b, as bits
+  unsigned sa[kPwUnitChunks + 1];  // the unit's chunk boundaries: A and B entries of the
+  unsigned sb[kPwUnitChunks + 1];  // item before them
+  unsigned char mo[kWC];        // record slot of each merged position
+  unsigned char hp[kWC + 1];    // merged positions of the keys' first entries, then len
+};
+
 // Position of set bit number n (from 0, lowest first) of m, by a halving
 // search on popcounts; some position below 32 if m has no more than n set bits.
 __device__ __forceinline__ unsigned nth_set_bit(unsigned m, unsigned n) {
@@ -974,88 +1041,150 @@ __device__ __forceinline__ unsigned nth_set_bit(unsigned m, unsigned n) {
   return pos & 31u;
 }
 
-// The pane-word path of write_item, for items whose two blocks span 2B <= 32
-// panes (K <= 16).  Chunks are key-aligned, so every key of a chunk is whole
-// in shared memory.  Every merged entry ORs the bit of its pane (relative to
-// the item's block b) into its key's word; a key's windows are then the word
-// dilated by K (a window whose first pane is r, relative to block b, holds
-// the key iff a bit of [r, r + K) is set), and the groups of its row in that
-// window are the set bits of [r, r + K): the first is the number of set bits
-// below r (the key's groups are in pane order), their number the set bits in
-// the range.  Per round of up to kEmT keys (one per thread): the warps'
-// ballots per window and one prefix over the warps give every row its output
-// position; then each warp writes its own keys' rows, 32 at a time in output
-// order (one row per lane, so consecutive lanes write consecutive rows of a
-// window), with no row descriptors and no barrier between the warps' rows.
-template <bool FLOAT>
-__device__ void write_item_pw(const QueryDev& q, const Item& it, EmSmem& sm, const EmDyn& d,
-                              ResultRowDev* out) {
-  const int tid = threadIdx.x, w = tid >> 5;
+// One warp over unit `it`, whose nch chunks are bounded by W.sa / W.sb.  Lane
+// i < nw holds `off` for window i: on entry the output row of the unit's
+// first row in the window (WRITE) or 0 (count); on return that plus the
+// unit's rows in the window.  The key words start zeroed and are left zeroed.
+template <bool WRITE, bool FLOAT>
+__device__ void pw_unit(const QueryDev& q, const Item& it, unsigned nch, PwWarp& W,
+                        unsigned long long& off, ResultRowDev* out) {
   const unsigned lane = lane_id();
   const int lb = q.lb, K = q.k;
   const int nw = (int)(it.whi - it.wlo + 1);
   if (K == 1) {  // tumbling: the unit's rows are its groups of the pane, in key order
-    const long long wstart = (it.wlo - kPaneBias) * (long long)q.slide + q.base;
-    for (unsigned long long i = it.a_lo + tid; i < it.a_hi; i += kEmT) {
-      const Grp g = load_grp_v(it.A + i);
-      write_row<FLOAT>(q, out + sm.woff[0] + (i - it.a_lo), wstart, gkey_key(g.gkey, lb), g.cnt,
-                       g.sum, g.mn, g.mx);
+    if (WRITE) {
+      const unsigned long long o = __shfl_sync(kFull, off, 0);
+      const long long wstart = (it.wlo - kPaneBias) * (long long)q.slide + q.base;
+      for (unsigned long long i = it.a_lo + lane; i < it.a_hi; i += 32) {
+        const Grp g = load_grp_v(it.A + i);
+        write_row<FLOAT>(q, out + o + (i - it.a_lo), wstart, gkey_key(g.gkey, lb), g.cnt, g.sum,
+                         g.mn, g.mx);
+      }
     }
-    __syncthreads();
+    if (lane == 0) off += it.a_hi - it.a_lo;
     return;
   }
-  // an item holds the windows starting in one block, so nw <= B <= 16 here:
-  // lane i < 16 of every warp speaks for window i
   const unsigned long long blk = (unsigned long long)it.wlo >> lb;  // the item's block b
   const int wrel0 = (int)(it.wlo - (long long)(blk << lb));         // wlo relative to block b
   const unsigned wmask = (1u << nw) - 1u;
   const unsigned kmask = (1u << K) - 1u;
   const long long wstart0 = (it.wlo - kPaneBias) * (long long)q.slide + q.base;
-  // every warp keeps the rows written so far of window lane (run), updated
-  // identically from the same counts, and the item's window bases; the key
-  // words start zeroed (each chunk zeroes what it used)
-  unsigned run = 0u;
-  const unsigned wb = (int)lane < nw ? (unsigned)sm.woff[lane] : 0u;
-  for (int k = tid; k < kEmC; k += kEmT) d.kw[k] = 0u;
-  unsigned par = 0u;  // which of the two count buffers this round uses
-  for_merged_chunks(q, it, sm, d, true, [&](unsigned len, unsigned, unsigned long long,
-                                            unsigned long long, bool) {
-    // heads (a chunk starts with one) and each entry's key index
-    unsigned nh_t = 0;
-    bool head[kEmE];
-    const unsigned x0 = (unsigned)tid * kEmE;
+  // the count stages only gkeys, the next chunk's while this one is processed
+  unsigned long long pf[kWE];
+  if (!WRITE && nch > 0) {
+    const unsigned a0 = W.sa[0], b0 = W.sb[0], la = W.sa[1] - a0, len = la + W.sb[1] - b0;
 #pragma unroll
-    for (int e = 0; e < kEmE; ++e) {
-      const unsigned x = x0 + e;
-      head[e] = x < len && (x == 0 || gkey_key(d.gk[d.mo[x - 1]], lb) != gkey_key(d.gk[d.mo[x]], lb));
-      nh_t += head[e] ? 1u : 0u;
+    for (int e = 0; e < kWE; ++e) {
+      const unsigned r = lane + 32u * e;
+      pf[e] = r < len ? (r < la ? it.A[a0 + r].gkey : it.Bv[b0 + (r - la)].gkey) : 0ull;
     }
-    unsigned long long htot;
-    unsigned long long hpos = block_excl_scan((unsigned long long)nh_t, sm.tmp, &htot);
-    unsigned ki = (unsigned)hpos;  // key index + 1 of the current entry
+  }
+  for (unsigned kk = 0; kk < nch; ++kk) {
+    const unsigned a0 = W.sa[kk], b0 = W.sb[kk];
+    const unsigned la = W.sa[kk + 1] - a0;
+    const unsigned len = la + (W.sb[kk + 1] - b0);
+    if (WRITE) {
+      // the next chunk's records into L2 while this one is processed
+      if (kk + 1 < nch) {
+        const unsigned na = W.sa[kk + 2] - W.sa[kk + 1], nb = W.sb[kk + 2] - W.sb[kk + 1];
+        const char* pa = reinterpret_cast<const char*>(it.A + W.sa[kk + 1]);
+        const char* pb = reinterpret_cast<const char*>(it.Bv + W.sb[kk + 1]);
+        if (lane * 128u < na * (unsigned)sizeof(Grp))
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(pa + lane * 128u));
+        if (lane * 128u < nb * (unsigned)sizeof(Grp))
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(pb + lane * 128u));
+      }
+      // stage the chunk: two 16-byte halves per record
+      for (unsigned h = lane; h < 2 * len; h += 32) {
+        const unsigned r = h >> 1;
+        const Grp* src = r < la ? it.A + a0 + r : it.Bv + b0 + (r - la);
+        const uint4 v = reinterpret_cast<const uint4*>(src)[h & 1];
+        const unsigned long long lo = ((unsigned long long)v.y << 32) | v.x;
+        const unsigned long long hi = ((unsigned long long)v.w << 32) | v.z;
+        if (h & 1) {
+          W.sum[r] = lo;
+          W.mm[r] = hi;
+        } else {
+          W.gk[r] = lo;
+          W.cnt[r] = (long long)hi;
+        }
+      }
+    } else {
 #pragma unroll
-    for (int e = 0; e < kEmE; ++e)
-      if (head[e]) d.hp[hpos++] = (unsigned short)(x0 + e);
-    const unsigned nh = (unsigned)htot;
-    if (tid == 0) d.hp[nh] = (unsigned short)len;
+      for (int e = 0; e < kWE; ++e) {
+        const unsigned r = lane + 32u * e;
+        if (r < len) W.gk[r] = pf[e];
+      }
+      if (kk + 1 < nch) {
+        const unsigned c0 = W.sa[kk + 1], d0 = W.sb[kk + 1];
+        const unsigned ca = W.sa[kk + 2] - c0, cl = ca + W.sb[kk + 2] - d0;
 #pragma unroll
-    for (int e = 0; e < kEmE; ++e) {
-      const unsigned x = x0 + e;
-      if (x < len) {
-        ki += head[e] ? 1u : 0u;
-        const unsigned long long g = d.gk[d.mo[x]];
-        const unsigned rel =
-            (unsigned)(g & ((1ull << lb) - 1ull)) | ((unsigned)(gkey_block(g, lb) - blk) << lb);
-        atomicOr(&d.kw[ki - 1], 1u << rel);
+        for (int e = 0; e < kWE; ++e) {
+          const unsigned r = lane + 32u * e;
+          if (r < cl) pf[e] = r < ca ? it.A[c0 + r].gkey : it.Bv[d0 + (r - ca)].gkey;
+        }
       }
     }
-    __syncthreads();
-    for (unsigned r0 = 0; r0 < nh; r0 += kEmT) {
-      const unsigned h = r0 + (unsigned)tid;
+    __syncwarp();
+    // merge (by key, A first on equal keys): lane takes kWE merged positions
+    const unsigned x0 = lane * kWE;
+    if (x0 < len) {
+      const unsigned lbn = len - la;
+      unsigned i = merge_split_s(W.gk, la, lbn, x0, lb), j = x0 - i;
+#pragma unroll
+      for (int e = 0; e < kWE; ++e) {
+        if (x0 + e < len) {
+          const bool ta =
+              j >= lbn || (i < la && gkey_key(W.gk[i], lb) <= gkey_key(W.gk[la + j], lb));
+          W.mo[x0 + e] = (unsigned char)(ta ? i : la + j);
+          if (ta) ++i;
+          else ++j;
+        }
+      }
+    }
+    __syncwarp();
+    // heads and the keys' pane words
+    bool head[kWE];
+    unsigned nh_t = 0u;
+    unsigned long long g[kWE];
+#pragma unroll
+    for (int e = 0; e < kWE; ++e) {
+      const unsigned x = x0 + e;
+      g[e] = x < len ? W.gk[W.mo[x]] : 0ull;
+      head[e] = x < len && (x == 0 || gkey_key(W.gk[W.mo[x - 1]], lb) != gkey_key(g[e], lb));
+      nh_t += head[e] ? 1u : 0u;
+    }
+    unsigned hinc = nh_t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned v = __shfl_up_sync(kFull, hinc, o);
+      if ((int)lane >= o) hinc += v;
+    }
+    const unsigned nh = __shfl_sync(kFull, hinc, 31);
+    unsigned ki = hinc - nh_t;  // key index + 1 of the current entry
+    {
+      unsigned hpos = ki;
+#pragma unroll
+      for (int e = 0; e < kWE; ++e)
+        if (head[e]) W.hp[hpos++] = (unsigned char)(x0 + e);
+    }
+    if (lane == 0) W.hp[nh] = (unsigned char)len;
+#pragma unroll
+    for (int e = 0; e < kWE; ++e) {
+      if (x0 + e < len) {
+        ki += head[e] ? 1u : 0u;
+        const unsigned rel = (unsigned)(g[e] & ((1ull << lb) - 1ull)) |
+                             ((unsigned)(gkey_block(g[e], lb) - blk) << lb);
+        atomicOr(&W.kw[ki - 1], 1u << rel);
+      }
+    }
+    __syncwarp();
+    for (unsigned r0 = 0; r0 < nh; r0 += 32) {
+      const unsigned h = r0 + lane;
       unsigned hx = 0u, word = 0u, mask = 0u, key = 0u;
       if (h < nh) {
-        hx = d.hp[h];
-        word = d.kw[h];
+        hx = W.hp[h];
+        word = W.kw[h];
         unsigned dl = word;  // dilation by K: bit r set iff a bit of [r, r + K) is
         int span = 1;
         while (2 * span <= K) {
@@ -1064,9 +1193,9 @@ __device__ void write_item_pw(const QueryDev& q, const Item& it, EmSmem& sm, con
         }
         if (span < K) dl |= dl >> (K - span);
         mask = (dl >> wrel0) & wmask;
-        key = gkey_key(d.gk[d.mo[hx]], lb);
+        if (WRITE) key = gkey_key(W.gk[W.mo[hx]], lb);
       }
-      // lane i: the ballot of this warp's keys that hold window i, and its rows
+      // lane i: the ballot of the round's keys that hold window i, its rows
       const unsigned orm = __reduce_or_sync(kFull, mask);
       unsigned bal = 0u;
       for (unsigned bits = orm; bits; bits &= bits - 1) {
@@ -1075,90 +1204,76 @@ __device__ void write_item_pw(const QueryDev& q, const Item& it, EmSmem& sm, con
         if ((int)lane == i) bal = b;
       }
       const unsigned cw = (unsigned)__popc(bal);
-      // the warps' counts into this round's buffer; the buffers alternate, so a
-      // warp already in the next round never overwrites counts a slower warp
-      // still reads
-      unsigned (*cb)[kMaxItemWindows] = par ? sm.ball : sm.wc;
-      cb[w][lane] = cw;
-      __syncthreads();
-      // this warp's first output row of window lane: the item's base, the rows
-      // of earlier rounds and the rows of lower warps in this round
-      unsigned off = wb + run;
+      if (WRITE) {
+        // the round's rows in output order (window by window, keys
+        // ascending) are f = 0 .. total - 1; incl = rows of windows 0 .. lane
+        unsigned incl = cw;
 #pragma unroll
-      for (int ww = 0; ww < kEmWarps; ++ww) {
-        const unsigned t = cb[ww][lane];
-        if (ww < w) off += t;
-        run += t;
-      }
-      par ^= 1u;
-      // the warp's rows in output order (window by window, keys ascending)
-      // are numbered f = 0 .. total - 1; incl = rows of windows 0 .. lane
-      unsigned incl = cw;
+        for (int o = 1; o < 16; o <<= 1) {
+          const unsigned v = __shfl_up_sync(kFull, incl, o);
+          if ((int)lane >= o) incl += v;
+        }
+        const unsigned total = __shfl_sync(kFull, incl, 15);
+        const unsigned excl = incl - cw;
+        // 32 rows at a time, row f on lane f mod 32: its window i is the
+        // number of windows all of whose rows come before f, its rank in the
+        // window picks the key (the rank-th set bit of the window's ballot)
+        for (unsigned f0 = 0; f0 < total; f0 += 32) {
+          const unsigned f = f0 + lane;
+          unsigned i = 0u;  // at most 15
 #pragma unroll
-      for (int o = 1; o < 16; o <<= 1) {
-        const unsigned v = __shfl_up_sync(kFull, incl, o);
-        if ((int)lane >= o) incl += v;
-      }
-      const unsigned total = __shfl_sync(kFull, incl, 15);
-      const unsigned excl = incl - cw;
-      // 32 rows at a time, row f on lane f mod 32: its window i is the number
-      // of windows all of whose rows come before f, its rank among the
-      // window's rows picks the key (the rank-th set bit of the window's
-      // ballot), whose lane holds the key's groups
-      for (unsigned f0 = 0; f0 < total; f0 += 32) {
-        const unsigned f = f0 + lane;
-        unsigned i = 0u;
-#pragma unroll
-        for (unsigned st = 8; st >= 1; st >>= 1)
-          if (__shfl_sync(kFull, incl, i + st - 1) <= f) i += st;
-        // (i <= 15: lanes past the last row read some window's values)
-        const unsigned rk = f - __shfl_sync(kFull, excl, i);
-        const unsigned bw = __shfl_sync(kFull, bal, i);
-        const unsigned ow = __shfl_sync(kFull, off, i);
-        const unsigned kl = nth_set_bit(bw, rk);
-        const unsigned hk = __shfl_sync(kFull, hx, kl);
-        const unsigned wk = __shfl_sync(kFull, word, kl);
-        const unsigned yk = __shfl_sync(kFull, key, kl);
-        if (f < total) {
-          const int r = wrel0 + (int)i;  // the window's first pane, relative to block b
-          const unsigned x = hk + (unsigned)__popc(wk & ((1u << r) - 1u));
-          const unsigned nn = (unsigned)__popc((unsigned)(((unsigned long long)wk >> r) & kmask));
-          unsigned slot = d.mo[x];
-          long long cnt = d.cnt[slot];
-          unsigned long long isum = d.sum[slot];
-          double fsum = __longlong_as_double((long long)isum);
-          unsigned long long m = d.mm[slot];
-          unsigned mn = (unsigned)m, mx = (unsigned)(m >> 32);
-          for (unsigned e = 1; e < nn; ++e) {
-            slot = d.mo[x + e];
-            cnt += d.cnt[slot];
-            const unsigned long long sv = d.sum[slot];
-            if (FLOAT) fsum += __longlong_as_double((long long)sv);
-            else isum += sv;
-            m = d.mm[slot];
-            mn = min(mn, (unsigned)m);
-            mx = max(mx, (unsigned)(m >> 32));
+          for (unsigned st = 8; st >= 1; st >>= 1)
+            if (__shfl_sync(kFull, incl, i + st - 1) <= f) i += st;
+          const unsigned rk = f - __shfl_sync(kFull, excl, i);
+          const unsigned bw = __shfl_sync(kFull, bal, i);
+          const unsigned long long ow = __shfl_sync(kFull, off, i);
+          const unsigned kl = nth_set_bit(bw, rk);
+          const unsigned hk = __shfl_sync(kFull, hx, kl);
+          const unsigned wk = __shfl_sync(kFull, word, kl);
+          const unsigned yk = __shfl_sync(kFull, key, kl);
+          if (f < total) {
+            const int r = wrel0 + (int)i;  // the window's first pane, relative to block b
+            const unsigned x = hk + (unsigned)__popc(wk & ((1u << r) - 1u));
+            const unsigned nn = (unsigned)__popc((wk >> r) & kmask);
+            unsigned slot = W.mo[x];
+            long long cnt = W.cnt[slot];
+            unsigned long long isum = W.sum[slot];
+            double fsum = __longlong_as_double((long long)isum);
+            unsigned long long m = W.mm[slot];
+            unsigned mn = (unsigned)m, mx = (unsigned)(m >> 32);
+            for (unsigned e = 1; e < nn; ++e) {
+              slot = W.mo[x + e];
+              cnt += W.cnt[slot];
+              const unsigned long long sv = W.sum[slot];
+              if (FLOAT) fsum += __longlong_as_double((long long)sv);
+              else isum += sv;
+              m = W.mm[slot];
+              mn = min(mn, (unsigned)m);
+              mx = max(mx, (unsigned)(m >> 32));
+            }
+            const unsigned long long sb =
+                FLOAT ? (unsigned long long)__double_as_longlong(fsum) : isum;
+            write_row<FLOAT>(q, out + (ow + rk), wstart0 + (long long)i * (long long)q.slide,
+                             yk, cnt, sb, mn, mx);
           }
-          const unsigned long long sb =
-              FLOAT ? (unsigned long long)__double_as_longlong(fsum) : isum;
-          uint4 p1, p2;
-          row_parts<FLOAT>(q, yk, cnt, sb, mn, mx, &p1, &p2);
-          store_row(out + (ow + rk), wstart0 + (long long)i * (long long)q.slide, cnt, p1, p2);
         }
       }
+      off += cw;
     }
-    for (unsigned k = tid; k < nh; k += kEmT) d.kw[k] = 0u;  // for the next chunk
-    __syncthreads();
-  }, true);
+    for (unsigned k = lane; k < nh; k += 32) W.kw[k] = 0u;  // for the next chunk
+    __syncwarp();
+  }
 }
 
-// Emission, in two kernels over the units (CTAs take units by ticket, so the
+// Emission, in two kernels over the units (units are taken by ticket, so the
 // units of a large item spread over all SMs):
-//   k_emit_count: each unit's rows per window (count_item), stored at the
+//   k_emit_count / k_emit_count_pw: each unit's rows per window, stored at the
 //     unit's slots of s.unit_off;
 //   (k_uoff_*: the exclusive scan of s.unit_off, in output order)
-//   k_emit_write: each unit's rows, window i's from its scanned slot.
-// Neither kernel waits on another CTA.
+//   k_emit_write / k_emit_write_pw: each unit's rows, window i's from its
+//     scanned slot.
+// A unit is one CTA's on the general path, one warp's on the pane-word path;
+// no CTA or warp waits on another.
 __global__ void __launch_bounds__(kEmT, 4) k_emit_count(const QueryDev q, const Scratch s) {
   __shared__ EmSmem sm;
   const EmDyn d = em_dyn();
@@ -1181,8 +1296,8 @@ __global__ void __launch_bounds__(kEmT, 4) k_emit_count(const QueryDev q, const 
   }
 }
 
-template <bool FLOAT, bool PW>
-__global__ void __launch_bounds__(kEmT, PW ? 4 : 3)
+template <bool FLOAT>
+__global__ void __launch_bounds__(kEmT, 3)
     k_emit_write(const QueryDev q, const Scratch s, ResultRowDev* rows) {
   __shared__ EmSmem sm;
   const EmDyn d = em_dyn();
@@ -1201,9 +1316,54 @@ __global__ void __launch_bounds__(kEmT, PW ? 4 : 3)
     const unsigned long long* slot = s.unit_off + (u - it.sub) * (unsigned long long)q.nw + it.sub;
     for (int i = threadIdx.x; i < nw; i += kEmT) sm.woff[i] = slot[(unsigned long long)i * it.nsub];
     __syncthreads();
-    if (PW) write_item_pw<FLOAT>(q, it, sm, d, out);
-    else write_item<FLOAT>(q, it, sm, d, out);
+    write_item<FLOAT>(q, it, sm, d, out);
     __syncthreads();
+  }
+}
+
+// The pane-word path: each warp takes units by ticket and counts (WRITE =
+// false) or writes them alone.
+template <bool WRITE, bool FLOAT>
+__global__ void __launch_bounds__(kPwT, 4)
+    k_emit_pw(const QueryDev q, const Scratch s, ResultRowDev* rows) {
+  __shared__ PwWarp ws[kPwWarps];
+  PwWarp& W = ws[threadIdx.x >> 5];
+  const unsigned lane = lane_id();
+  QCtl* c = q.ctl;
+  if (c->err & kErrNeedRetry) return;
+  const unsigned long long NI = c->n_items;
+  ResultRowDev* out = WRITE ? rows + c->row_base : rows;
+  unsigned long long* ticket = WRITE ? &c->unit_ticket : &c->item_ticket;
+  for (unsigned k = lane; k < (unsigned)kWC; k += 32) W.kw[k] = 0u;
+  while (true) {
+    __syncwarp();  // the previous unit no longer reads W.sa / W.sb
+    unsigned long long u = 0ull;
+    if (lane == 0) u = atomicAdd(ticket, 1ull);
+    u = __shfl_sync(kFull, u, 0);
+    if (u >= NI) break;
+    Item it = load_item(q, s, c, (long long)s.item_c[u], s.item_j[u]);
+    const unsigned long long st = s.item_stat[u];
+    it.sub = (unsigned)st;
+    it.nsub = (unsigned)(st >> 32);
+    // the unit's chunks (nominal) and their boundaries from the table
+    const unsigned long long L = it.na + it.nb, d0 = (unsigned long long)it.sub * kUnitEntriesPW;
+    const unsigned long long dn = d0 + kUnitEntriesPW < L ? d0 + kUnitEntriesPW : L;
+    const unsigned nch = dn > d0 ? (unsigned)((dn - d0 + kWCn - 1) / kWCn) : 0u;
+    if (lane <= nch) {
+      W.sa[lane] = s.unit_bnd[u * kUnitBnd + 2 * lane];
+      W.sb[lane] = s.unit_bnd[u * kUnitBnd + 2 * lane + 1];
+    }
+    __syncwarp();
+    it.a_lo = W.sa[0];
+    it.b_lo = W.sb[0];
+    it.a_hi = W.sa[nch];
+    it.b_hi = W.sb[nch];
+    const int nw = (int)(it.whi - it.wlo + 1);
+    unsigned long long* slot = s.unit_off + (u - it.sub) * (unsigned long long)q.nw + it.sub;
+    unsigned long long off = 0ull;  // lane i < nw <= 16: window i
+    if (WRITE && (int)lane < nw) off = slot[(unsigned long long)lane * it.nsub];
+    pw_unit<WRITE, FLOAT>(q, it, nch, W, off, out);
+    if (!WRITE && (int)lane < q.nw) slot[(unsigned long long)lane * it.nsub] = (int)lane < nw ? off : 0ull;
   }
 }
 
@@ -1371,12 +1531,19 @@ cudaError_t launch_emit(const QueryDev& q, const Scratch& s, ResultRowDev* rows,
   k_item_scan<<<1, 1024, 0, st>>>(q, s);
   k_item_write<<<kGrid, 256, 0, st>>>(q, s);
   // devices whose smem limit is set, per kernel
-  static unsigned long long done[5] = {0, 0, 0, 0, 0};
-  cudaError_t e = set_smem_limit(reinterpret_cast<const void*>(k_emit_count), (int)kEmDynBytesPW,
-                                 &done[4]);
-  if (e != cudaSuccess) return e;
-  k_emit_count<<<4 * sms, kEmT, kEmDynBytesPW, st>>>(q, s);
+  static unsigned long long done[3] = {0, 0, 0};
+  const bool pw = (2 << q.lb) <= 32;
   const int g = kGrid;
+  if (pw) {
+    k_unit_bounds<<<kGrid, 256, 0, st>>>(q, s);
+    // four CTAs of eight warps per SM (64 registers, 39 KB of shared memory)
+    k_emit_pw<false, false><<<4 * sms, kPwT, 0, st>>>(q, s, rows);
+  } else {
+    cudaError_t e = set_smem_limit(reinterpret_cast<const void*>(k_emit_count),
+                                   (int)kEmDynBytesCount, &done[2]);
+    if (e != cudaSuccess) return e;
+    k_emit_count<<<4 * sms, kEmT, kEmDynBytesCount, st>>>(q, s);
+  }
   k_uoff_sum<<<g, 256, 0, st>>>(q, s);
   k_uoff_scan<<<1, 1024, 0, st>>>(q, s, rows_cap);
   k_uoff_write<<<g, 256, 0, st>>>(q, s);
@@ -1384,27 +1551,20 @@ cudaError_t launch_emit(const QueryDev& q, const Scratch& s, ResultRowDev* rows,
     record_event(ev4[1], st);
     record_event(ev4[2], st);
   }
-  const bool pw = (2 << q.lb) <= 32;
-  const void* fn = q.value_is_float
-                       ? (pw ? reinterpret_cast<const void*>(k_emit_write<true, true>)
-                             : reinterpret_cast<const void*>(k_emit_write<true, false>))
-                       : (pw ? reinterpret_cast<const void*>(k_emit_write<false, true>)
-                             : reinterpret_cast<const void*>(k_emit_write<false, false>));
-  const size_t dyn = pw ? kEmDynBytesPW : kEmDynBytes;
-  e = set_smem_limit(fn, (int)dyn, &done[(q.value_is_float ? 2 : 0) + (pw ? 1 : 0)]);
-  if (e != cudaSuccess) return e;
-  // resident CTAs per SM: four on the pane-word path (64 registers, 54 KB of
-  // shared memory), three on the general one (its row descriptors need more)
-  const int grid = (pw ? 4 : 3) * sms;
-  if (q.value_is_float) {
-    if (pw) k_emit_write<true, true><<<grid, kEmT, dyn, st>>>(q, s, rows);
-    else k_emit_write<true, false><<<grid, kEmT, dyn, st>>>(q, s, rows);
+  if (pw) {
+    if (q.value_is_float) k_emit_pw<true, true><<<4 * sms, kPwT, 0, st>>>(q, s, rows);
+    else k_emit_pw<true, false><<<4 * sms, kPwT, 0, st>>>(q, s, rows);
   } else {
-    if (pw) k_emit_write<false, true><<<grid, kEmT, dyn, st>>>(q, s, rows);
-    else k_emit_write<false, false><<<grid, kEmT, dyn, st>>>(q, s, rows);
+    const void* fn = q.value_is_float ? reinterpret_cast<const void*>(k_emit_write<true>)
+                                      : reinterpret_cast<const void*>(k_emit_write<false>);
+    cudaError_t e = set_smem_limit(fn, (int)kEmDynBytes, &done[q.value_is_float ? 1 : 0]);
+    if (e != cudaSuccess) return e;
+    // three CTAs per SM (the row descriptors of the general path need the room)
+    if (q.value_is_float) k_emit_write<true><<<3 * sms, kEmT, kEmDynBytes, st>>>(q, s, rows);
+    else k_emit_write<false><<<3 * sms, kEmT, kEmDynBytes, st>>>(q, s, rows);
   }
   if (ev4) record_event(ev4[3], st);
-  if (launches) *launches += 9;
+  if (launches) *launches += pw ? 10 : 9;
   return cudaGetLastError();
 }
 

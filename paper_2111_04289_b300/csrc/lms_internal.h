@@ -45,6 +45,12 @@ constexpr int kOrderMax = 16384;
 // Windows per emission item (an item is a run of consecutive window ids that
 // start in one block).
 constexpr int kMaxItemWindows = 64;
+// Pane-word emission (2B <= 32): a unit is kPwUnitChunks chunks of nominally
+// kPwChunkEntries merged entries; its chunk boundaries take 2 * (chunks + 1)
+// words of the unit boundary table.
+constexpr int kPwChunkEntries = 96;
+constexpr int kPwUnitChunks = 11;
+constexpr int kUnitBnd = 2 * (kPwUnitChunks + 1);
 
 
 // One (pane, key) group: a 32-byte record, so that a random gather of a group
@@ -160,6 +166,8 @@ struct Scratch {
   unsigned long long* item_stat; // per unit: its index in the item | the item's units << 32
   unsigned long long* unit_off;  // kMaxItemWindows per unit: row counts, then output rows
                                  // (a query uses nw of them per unit)
+  unsigned* unit_bnd;            // pane-word path, kUnitBnd per unit: its chunk boundaries,
+                                 // each as the (A, B) entries of the item before it
   unsigned long long item_cap;   // units the unit arrays hold
 };
 

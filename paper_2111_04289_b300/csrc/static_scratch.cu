@@ -11,7 +11,7 @@
 // fixed array in device memory that the library declares at file scope.  The
 // caller passes the input columns and the output row buffer.
 //
-// The array (kStaticBytes, about 31 MiB) exists on every GPU that loads the
+// The array (kStaticBytes, about 34 MiB) exists on every GPU that loads the
 // library, for the life of the process.  Its device address is looked up with
 // cudaGetSymbolAddress once per device, with that device current, on the first
 // call made on that device.  Every call reads the batch's first event time
@@ -41,7 +41,7 @@ struct Layout {
   size_t sctl, qctl;
   size_t parts, pkeys, state;
   size_t keysA, keysB, valsA, valsB, hist, chunk, blk_id, blk_begin;
-  size_t item_c, item_j, item_stat, unit_off, total;
+  size_t item_c, item_j, item_stat, unit_off, unit_bnd, total;
 };
 
 constexpr Layout make_layout() {
@@ -64,13 +64,14 @@ constexpr Layout make_layout() {
   L.item_j = o; o += al(4 * kStaticItems);
   L.item_stat = o; o += al(8 * kStaticItems);
   L.unit_off = o; o += al(8 * kMaxItemWindows * kStaticItems);
+  L.unit_bnd = o; o += al(4 * kUnitBnd * kStaticItems);
   L.total = o;
   return L;
 }
 
 constexpr Layout kL = make_layout();
 constexpr size_t kStaticBytes = kL.total;
-static_assert(kStaticBytes < (32ull << 20), "static scratch must stay modest");
+static_assert(kStaticBytes < (36ull << 20), "static scratch must stay modest");
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
 
@@ -171,6 +172,7 @@ extern "C" lms_status lms_aggregate_batch_static(const lms_query_spec* q, int32_
   s.item_j = reinterpret_cast<unsigned*>(base + kL.item_j);
   s.item_stat = reinterpret_cast<unsigned long long*>(base + kL.item_stat);
   s.unit_off = reinterpret_cast<unsigned long long*>(base + kL.unit_off);
+  s.unit_bnd = reinterpret_cast<unsigned*>(base + kL.unit_bnd);
   s.item_cap = kStaticItems;
 
   // ---- the query, with the batch's first row as event-time origin ----
