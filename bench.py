@@ -864,7 +864,7 @@ def run_ours(args):
     k1_bytes = EVENT_BYTES * n + GROUP_BYTES * d["partials"] / K
     k1 = roof("k1_fused", k1_bytes, d["k1_ms"] / max(1, d["k1_launches"]))
     e2_bytes = ROW_BYTES * d["rows_emitted"] / K + GROUP_BYTES * d["groups_built"] / K
-    e2 = roof("k_emit_write", e2_bytes, d["e2_ms"] / K)
+    e2 = roof("k_emit_pw", e2_bytes, d["e2_ms"] / K)  # the row writer of the pane-word path (K <= 16)
     share = {"k1_fused_ms": d["k1_ms"] / K, "sort_reduce_ms": d["sort_ms"] / K,
              "emit_ms": d["emit_ms"] / K, "emit_count_ms": d["e1_ms"] / K,
              "emit_write_ms": d["e2_ms"] / K}
