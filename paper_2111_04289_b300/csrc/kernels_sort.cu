@@ -337,7 +337,11 @@ __global__ void __launch_bounds__(256) k_merge_carry(const QueryDev q, const Scr
         nv[i] = N.vals ? N.vals[b0 + i] : (unsigned)(nc + b0 + i);
       }
       __syncthreads();
+      // each thread merges kMergeItems consecutive outputs into registers; the
+      // tile's outputs are then staged in ck / nv and written coalesced
       const unsigned x0 = (unsigned)tid * kMergeItems, len = la + lb;
+      unsigned long long ok_[kMergeItems];
+      unsigned ov_[kMergeItems];
       if (x0 < len) {
         unsigned ia = x0 > lb ? x0 - lb : 0u, ib = x0 < la ? x0 : la;  // merge path in the tile
         while (ia < ib) {
@@ -348,13 +352,24 @@ __global__ void __launch_bounds__(256) k_merge_carry(const QueryDev q, const Scr
         unsigned i = ia, k = x0 - ia;
 #pragma unroll
         for (int e = 0; e < kMergeItems; ++e) {
-          const unsigned x = x0 + e;
-          if (x >= len) break;
           const bool ta = k >= lb || (i < la && ck[i] <= nk[k]);
-          mk[d0 + x] = ta ? ck[i] : nk[k];
-          mv[d0 + x] = ta ? (unsigned)(a0 + i) : nv[k];
+          ok_[e] = ta ? ck[i < la ? i : 0] : nk[k < lb ? k : 0];
+          ov_[e] = ta ? (unsigned)(a0 + i) : nv[k < lb ? k : 0];
           if (ta) ++i; else ++k;
         }
+      }
+      __syncthreads();  // every thread is done reading ck / nk
+#pragma unroll
+      for (int e = 0; e < kMergeItems; ++e) {
+        if (x0 + e < len) {
+          ck[x0 + e] = ok_[e];
+          nv[x0 + e] = ov_[e];
+        }
+      }
+      __syncthreads();
+      for (unsigned x = tid; x < len; x += 256) {
+        mk[d0 + x] = ck[x];
+        mv[d0 + x] = nv[x];
       }
       __syncthreads();
     }
@@ -507,7 +522,7 @@ __global__ void __launch_bounds__(256, 4) k_rbk_write(const QueryDev q, const Sc
       nh += head[u] ? 1u : 0u;
       if (valid[u]) {
         const unsigned long long pi = src.vals ? src.vals[i] : i;
-        const Grp g = load_grp(q.parts + pi);
+        const Grp g = load_grp_v(q.parts + pi);
         v[u].f = head[u] ? 1u : 0u;
         v[u].cnt = g.cnt;
         v[u].sum = g.sum;
@@ -578,7 +593,7 @@ __global__ void __launch_bounds__(256) k_rbk_long(const QueryDev q, const Scratc
       for (int u = 0; u < kU; ++u) {
         const unsigned long long j = j0 + (unsigned long long)u * blockDim.x;
         const unsigned long long pi = j < b ? (src.vals ? src.vals[j] : j) : 0ull;
-        if (j < b) g[u] = load_grp(q.parts + pi);
+        if (j < b) g[u] = load_grp_v(q.parts + pi);
       }
 #pragma unroll
       for (int u = 0; u < kU; ++u) {
