@@ -395,18 +395,22 @@ def run_serving(args, lm, synth, local):
             fixed = {str(n): searcher(lm.POLICY_FIXED_SIZE, dev_in, min(a0, n / 3e5),
                                       fixed_rows=n, max_rows=n)
                      for n in args.fixed_sizes}
-            best = max(fixed, key=lambda k: fixed[k]["events_per_s"])
-            m["fixed_size_best"] = dict(fixed[best], fixed_rows=int(best))
-            m["fixed_size_sweep"] = {k: {"events_per_s": v["events_per_s"], "alpha": v["alpha"],
-                                         "p99_ms": v.get("p99_ms")} for k, v in fixed.items()}
+            if fixed:
+                best = max(fixed, key=lambda k: fixed[k]["events_per_s"])
+                m["fixed_size_best"] = dict(fixed[best], fixed_rows=int(best))
+                m["fixed_size_sweep"] = {k: {"events_per_s": v["events_per_s"],
+                                             "alpha": v["alpha"], "p99_ms": v.get("p99_ms")}
+                                         for k, v in fixed.items()}
+                lr, fb = m["learned"]["events_per_s"], m["fixed_size_best"]["events_per_s"]
+                m["learned_over_best_fixed_size"] = lr / fb if fb else None
             trig = {str(t): searcher(lm.POLICY_FIXED_TRIGGER, dev_in, a0 / 2, trigger_ms=t)
                     for t in args.fixed_triggers}
-            best = max(trig, key=lambda k: trig[k]["events_per_s"])
-            m["fixed_trigger_best"] = dict(trig[best], trigger_ms=float(best))
-            m["fixed_trigger_sweep"] = {k: {"events_per_s": v["events_per_s"], "alpha": v["alpha"],
-                                            "p99_ms": v.get("p99_ms")} for k, v in trig.items()}
-            lr, fb = m["learned"]["events_per_s"], m["fixed_size_best"]["events_per_s"]
-            m["learned_over_best_fixed_size"] = lr / fb if fb else None
+            if trig:
+                best = max(trig, key=lambda k: trig[k]["events_per_s"])
+                m["fixed_trigger_best"] = dict(trig[best], trigger_ms=float(best))
+                m["fixed_trigger_sweep"] = {k: {"events_per_s": v["events_per_s"],
+                                                "alpha": v["alpha"], "p99_ms": v.get("p99_ms")}
+                                            for k, v in trig.items()}
         m["training"] = {"samples": learned.samples(), "fit_steps": args.fit_steps,
                          "fit_loss": fit_loss, "fit_s": fit_s,
                          "online": "20 Adam steps every 50 batches"}
@@ -990,9 +994,9 @@ def main():
     ap.add_argument("--serve-iters", type=int, default=3)
     ap.add_argument("--explore-alpha", type=float, default=1.0)
     ap.add_argument("--fit-steps", type=int, default=5000)
-    ap.add_argument("--fixed-sizes", type=lambda x: [int(v) for v in x.split(",")],
+    ap.add_argument("--fixed-sizes", type=lambda x: [int(v) for v in x.split(",") if v],
                     default=[1 << k for k in (18, 20, 22, 24, 26)])
-    ap.add_argument("--fixed-triggers", type=lambda x: [float(v) for v in x.split(",")],
+    ap.add_argument("--fixed-triggers", type=lambda x: [float(v) for v in x.split(",") if v],
                     default=[5.0, 20.0, 80.0])
     ap.add_argument("--serve-modes", type=lambda x: x.split(","), default=["device", "host"],
                     help="input modes of the serving search: device, host")
