@@ -385,26 +385,31 @@ def run_serving(args, lm, synth, local):
         fit_loss = learned.fit(args.fit_steps, lr=1e-3)
         fit_s = time.perf_counter() - t0
         learned.set_online(refit_every=50, refit_steps=20)
-        m = {"learned": searcher(lm.POLICY_LEARNED, dev_in, start, learned)}
-        m["learned"]["judge"] = learned.stats()
-        # the other searches start at the learned policy's rate (fewer runs far
-        # from the boundary; the doubling / halving still finds it from there)
-        a0 = m["learned"].get("alpha") or start
-        m["analytic"] = searcher(lm.POLICY_ANALYTIC, dev_in, a0)
+        m = {}
+        a0 = start
+        if "learned" in args.serve_policies:
+            m["learned"] = searcher(lm.POLICY_LEARNED, dev_in, start, learned)
+            m["learned"]["judge"] = learned.stats()
+            # the other searches start at the learned policy's rate (fewer runs
+            # far from the boundary; the doubling / halving still finds it)
+            a0 = m["learned"].get("alpha") or start
+        if "analytic" in args.serve_policies:
+            m["analytic"] = searcher(lm.POLICY_ANALYTIC, dev_in, a0)
         if dev_in or args.serve_full:
             fixed = {str(n): searcher(lm.POLICY_FIXED_SIZE, dev_in, min(a0, n / 3e5),
                                       fixed_rows=n, max_rows=n)
-                     for n in args.fixed_sizes}
+                     for n in (args.fixed_sizes if "fixed" in args.serve_policies else [])}
             if fixed:
                 best = max(fixed, key=lambda k: fixed[k]["events_per_s"])
                 m["fixed_size_best"] = dict(fixed[best], fixed_rows=int(best))
                 m["fixed_size_sweep"] = {k: {"events_per_s": v["events_per_s"],
                                              "alpha": v["alpha"], "p99_ms": v.get("p99_ms")}
                                          for k, v in fixed.items()}
-                lr, fb = m["learned"]["events_per_s"], m["fixed_size_best"]["events_per_s"]
-                m["learned_over_best_fixed_size"] = lr / fb if fb else None
+                if "learned" in m:
+                    lr, fb = m["learned"]["events_per_s"], m["fixed_size_best"]["events_per_s"]
+                    m["learned_over_best_fixed_size"] = lr / fb if fb else None
             trig = {str(t): searcher(lm.POLICY_FIXED_TRIGGER, dev_in, a0 / 2, trigger_ms=t)
-                    for t in args.fixed_triggers}
+                    for t in (args.fixed_triggers if "trigger" in args.serve_policies else [])}
             if trig:
                 best = max(trig, key=lambda k: trig[k]["events_per_s"])
                 m["fixed_trigger_best"] = dict(trig[best], trigger_ms=float(best))
@@ -1000,6 +1005,9 @@ def main():
                     default=[5.0, 20.0, 80.0])
     ap.add_argument("--serve-modes", type=lambda x: x.split(","), default=["device", "host"],
                     help="input modes of the serving search: device, host")
+    ap.add_argument("--serve-policies", type=lambda x: x.split(","),
+                    default=["learned", "analytic", "fixed", "trigger"],
+                    help="policies of the serving search: learned, analytic, fixed, trigger")
     ap.add_argument("--ref-duration-ms", type=float, default=20_000.0)
     ap.add_argument("--profile-carry", action="store_true",
                     help="per-batch sort/merge cost against a growing open state, then exit")

@@ -93,8 +93,13 @@ __global__ void k_sort_plan(QCtl* c) {
 __global__ void __launch_bounds__(256) k_sort_hist(const QueryDev q, const Scratch s, int p) {
   const QCtl* c = q.ctl;
   if (p >= c->npasses) return;
-  __shared__ unsigned h[256];
-  h[threadIdx.x] = 0u;
+  // one histogram per warp, plain shared atomics (lanes with equal digits are
+  // serialised by the hardware; cheaper than grouping them first), summed at
+  // the end
+  __shared__ unsigned h[8][256];
+  const int w = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) h[j][threadIdx.x] = 0u;
   __syncthreads();
   const int shift = c->shifts[p];
   const SortSrc src = pass_src(q, s, p);
@@ -109,19 +114,16 @@ __global__ void __launch_bounds__(256) k_sort_hist(const QueryDev q, const Scrat
       d[u] = i < hi ? (unsigned)((src.keys[i] >> shift) & 0xffull) : 256u;
     }
 #pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      const unsigned peers = __match_any_sync(kFull, d[u]);
-      if (d[u] < 256u && (int)lane_id() == __ffs(peers) - 1)
-        atomicAdd(&h[d[u]], (unsigned)__popc(peers));
-    }
+    for (int u = 0; u < kU; ++u)
+      if (d[u] < 256u) atomicAdd(&h[w][d[u]], 1u);
   }
   __syncthreads();
-  s.hist[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
+  unsigned t = 0u;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) t += h[j][threadIdx.x];
+  s.hist[threadIdx.x * gridDim.x + blockIdx.x] = t;
 }
 
-// Per digit (one CTA each): exclusive scan over the chunks of hist[d][*] in
-// place (up to 4 chunks per thread), digit total -> hist[256 * kGrid + d].
-static_assert(kGrid <= 4 * 256, "k_sort_scan covers at most 1024 chunks");
 __global__ void __launch_bounds__(256) k_sort_scan(const QueryDev q, const Scratch s, int p) {
   if (p >= q.ctl->npasses) return;
   __shared__ unsigned long long tmp[33];
