@@ -327,7 +327,8 @@ def run_serving(args, lm, synth, local):
     mean = synth.ServingLoad().mean_rate()
     seeds = [synth.BASE_SEED + 40 + 7 * k for k in range(args.serve_seeds)]
 
-    def once(alpha, policy, device_input, seed, learned=None, max_rows=1 << 25, **kw):
+    def once(alpha, policy, device_input, seed, learned=None, max_rows=None, **kw):
+        max_rows = args.serve_max_rows if max_rows is None else max_rows
         ticks = synth.ServingLoad(rate_scale=alpha).ticks(seed, dur)
         g = lm.ServeGpu(SERVE_Q, seed=seed + 1, n_keys=1_000_000,
                         max_batch_rows=max(max_rows, PREFILL_EVENTS),
@@ -923,6 +924,11 @@ def run_ours(args):
                            "step": "one admitted micro-batch of the serving loop",
                            "p99_ms": lh.get("p99_ms"), "p50_ms": lh.get("p50_ms")}
         line["serving"] = serving
+        line["config"]["serving_runs"] = (
+            f"{args.serve_duration_ms / 1000:g} s of arrivals per run after a steady-state "
+            f"prefill, {args.serve_seeds} seed(s) (median), doubling then "
+            f"{args.serve_iters} bisection steps of alpha, batches of at most "
+            f"{args.serve_max_rows} events")
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args.cpu_log2, synth.BASE_SEED + 2)
     if rank == 0:
@@ -1005,6 +1011,8 @@ def main():
                     default=[5.0, 20.0, 80.0])
     ap.add_argument("--serve-modes", type=lambda x: x.split(","), default=["device", "host"],
                     help="input modes of the serving search: device, host")
+    ap.add_argument("--serve-max-rows", type=int, default=1 << 25,
+                    help="largest micro-batch the adaptive policies may admit")
     ap.add_argument("--serve-policies", type=lambda x: x.split(","),
                     default=["learned", "analytic", "fixed", "trigger"],
                     help="policies of the serving search: learned, analytic, fixed, trigger")
