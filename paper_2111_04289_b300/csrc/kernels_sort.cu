@@ -530,17 +530,23 @@ __global__ void __launch_bounds__(256, 4) k_rbk_write(const QueryDev q, const Sc
         v[u].sum = g.sum;
         v[u].mn = g.mn;
         v[u].mx = g.mx;
-        v[u].rank = 0;
       } else {
         v[u] = seg_identity();
       }
     }
-    // ranks of the heads
+    // output index of each element's run: the heads up to and including the
+    // element, minus one (a run has no head after its own)
     unsigned long long htot;
-    unsigned long long hpre = block_excl_scan((unsigned long long)nh, tmp, &htot);
+    const unsigned long long hpre = block_excl_scan((unsigned long long)nh, tmp, &htot);
+    int orank[kRbkItems];  // relative to out0 + heads_before (-1: a run headed in an earlier tile)
+    {
+      int hc = (int)hpre;
 #pragma unroll
-    for (int u = 0; u < kRbkItems; ++u)
-      if (head[u]) v[u].rank = out0 + heads_before + hpre++;
+      for (int u = 0; u < kRbkItems; ++u) {
+        if (head[u]) ++hc;
+        orank[u] = hc - 1;
+      }
+    }
     // thread-local inclusive segmented scan
 #pragma unroll
     for (int u = 1; u < kRbkItems; ++u) v[u] = seg_combine<FLOAT>(v[u - 1], v[u]);
@@ -562,7 +568,8 @@ __global__ void __launch_bounds__(256, 4) k_rbk_write(const QueryDev q, const Sc
     for (int u = 0; u < kRbkItems; ++u) {
       if (!last[u]) continue;
       const SegAgg r = seg_combine<FLOAT>(pre, v[u]);
-      store_grp(q.state + r.rank, k[u], r.cnt, r.sum, r.mn, r.mx);
+      store_grp(q.state + (long long)(out0 + heads_before) + orank[u], k[u], r.cnt, r.sum, r.mn,
+                r.mx);
     }
     heads_before += htot;
     __syncthreads();

@@ -160,12 +160,11 @@ __device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long
 
 // ---- segmented scans (reduce-by-key) -------------------------------------
 
-struct SegAgg {  // (run started here?, aggregate since the run's head, run's output index)
+struct SegAgg {  // (run started here?, aggregate since the run's head)
   unsigned f;
   long long cnt;
   unsigned long long sum;
   unsigned mn, mx;
-  unsigned long long rank;
 };
 
 template <bool FLOAT>
@@ -179,7 +178,6 @@ __device__ __forceinline__ SegAgg seg_combine(const SegAgg& x, const SegAgg& y) 
                 : x.sum + y.sum;
   r.mn = min(x.mn, y.mn);
   r.mx = max(x.mx, y.mx);
-  r.rank = x.rank;
   return r;
 }
 
@@ -190,7 +188,6 @@ __device__ __forceinline__ SegAgg seg_identity() {
   r.sum = 0ull;  // +0.0 for doubles
   r.mn = 0xffffffffu;
   r.mx = 0u;
-  r.rank = 0ull;
   return r;
 }
 
@@ -201,7 +198,6 @@ __device__ __forceinline__ SegAgg seg_shfl_up(const SegAgg& v, int d) {
   r.sum = __shfl_up_sync(kFull, v.sum, d);
   r.mn = __shfl_up_sync(kFull, v.mn, d);
   r.mx = __shfl_up_sync(kFull, v.mx, d);
-  r.rank = __shfl_up_sync(kFull, v.rank, d);
   return r;
 }
 
@@ -212,7 +208,6 @@ __device__ __forceinline__ SegAgg seg_shfl_idx(const SegAgg& v, int src) {
   r.sum = __shfl_sync(kFull, v.sum, src);
   r.mn = __shfl_sync(kFull, v.mn, src);
   r.mx = __shfl_sync(kFull, v.mx, src);
-  r.rank = __shfl_sync(kFull, v.rank, src);
   return r;
 }
 
