@@ -644,6 +644,15 @@ def run_small_configs(args, torch, lm, synth, dev, local):
     r = run_mix(keys, chooser=le)
     abl["learned_mlp"] = {k: v for k, v in r.items() if k != "per_query"}
     abl["learned_mlp"]["stats"] = le.stats()
+    abl["learned_mlp"]["refits"] = "50 Adam steps every 4 passes, inside the timed pushes"
+    # the same network refitted outside the timed region (the paper optimises
+    # its parameters in the background) and frozen while the mix is timed
+    le.fit(200)
+    le.set_online(refit_every=0, refit_steps=0)
+    r = run_mix(keys, chooser=le)
+    abl["learned_mlp_frozen"] = {k: v for k, v in r.items() if k != "per_query"}
+    abl["learned_mlp_frozen"]["stats"] = le.stats()
+    abl["learned_mlp_frozen"]["refits"] = "200 Adam steps before the timed pass, none during it"
     le.close()
     judge.close()
     net.close()
